@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module only draws random numbers and builds test problems; it holds none
+of the split/product/LU/refinement arithmetic of the method, so that the CUDA
+library and the CPU oracle can both be fed the same inputs without sharing any
+of the code under test.
+
+Workloads (all numpy ``default_rng(seed)``):
+
+* ``uniform_pm1``: FP32 entries uniform in [-1, 1], the narrow-range GEMM
+  case of Sec. IV-A (the paper draws with drand48 in [-1, 1]).
+* ``wide_range``: FP32 entries u * 2**e, u uniform in [-1, 1], e an integer
+  uniform in [emin, emax]; a controlled stand-in for the paper's wide
+  exponent-range GEMM case of Sec. IV-A.
+* ``svd_system``: A = U diag(sigma) V^T with U, V the Q factors of Householder
+  QR of Gaussian matrices and sigma geometric from 1 down to 1/kappa, rounded
+  to FP32 (the FP32 matrix *is* the problem), x_true Gaussian and
+  b = A32 x_true evaluated in FP64.  Used for the solves of Sec. III/IV-B at
+  prescribed condition numbers.
+* ``batched_systems`` / ``serving_stream``: many independent systems of that
+  kind with sizes, right-hand-side counts, conditioning and (for the stream)
+  Poisson arrival times drawn from stated distributions.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "uniform_pm1",
+    "wide_range",
+    "svd_system",
+    "SolveProblem",
+    "batched_systems",
+    "serving_stream",
+    "Request",
+    "special_values_f32",
+]
+
+
+def uniform_pm1(shape, seed: int) -> np.ndarray:
+    """FP32 array, entries uniform in [-1, 1] (seeded)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=shape).astype(np.float32)
+
+
+def wide_range(shape, seed: int, emin: int = -8, emax: int = 8) -> np.ndarray:
+    """FP32 array, entries u * 2**e with u ~ U[-1,1] (FP32) and e ~ U{emin..emax}.
+
+    The scaling by a power of two is exact, so every entry is exactly the
+    product of its two drawn factors.
+    """
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1.0, 1.0, size=shape).astype(np.float32)
+    e = rng.integers(emin, emax + 1, size=shape)
+    return np.ldexp(u, e).astype(np.float32)
+
+
+def special_values_f32() -> np.ndarray:
+    """A fixed set of FP32 edge cases (zeros, subnormals, extremes, Inf, NaN, ties)."""
+    bits = [
+        0x00000000, 0x80000000,  # +-0
+        0x00000001, 0x80000001,  # smallest subnormals
+        0x007FFFFF, 0x00400000, 0x00008000, 0x00018000,  # subnormals incl. ties
+        0x00800000, 0x00800001, 0x00808000, 0x00818000,  # smallest normals, ties
+        0x0C800000, 0x0C8FFFFF, 0x0CFFFFFF,  # around 2^-102 .. 2^-101
+        0x08800000, 0x088FFFFF,  # around 2^-110
+        0x3F800000, 0x3F808000, 0x3F818000, 0x3F80FFFF, 0x3F7FFFFF,  # around 1
+        0xBF808000, 0xBF818000, 0xBF7FFFFF,
+        0x7F7F0000, 0x7F7F7FFF, 0x7F7F8000, 0x7F7FFFFF,  # top of the range
+        0xFF7F8000, 0xFF7FFFFF,
+        0x7F800000, 0xFF800000,  # +-Inf
+        0x7FC00000, 0xFFC00001, 0x7F800001, 0x7FBFFFFF,  # NaNs (quiet, signalling)
+        0x00C0FFFF,  # the "bad number" shape of Sec. II-F (small exponent, low bits set)
+    ]
+    return np.array(bits, dtype=np.uint32).view(np.float32)
+
+
+def _haar_like_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Q factor (FP64) of a Householder QR of an n x n standard Gaussian matrix."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    # fix the sign convention so Q does not depend on LAPACK's choice of signs
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+@dataclass
+class SolveProblem:
+    """One dense system A32 x = b.  A32 is FP32 (the problem matrix itself)."""
+
+    A32: np.ndarray  # (n, n) float32, row-major
+    b: np.ndarray  # (n, nrhs) float64
+    x_true: np.ndarray  # (n, nrhs) float64
+    kappa_nominal: float
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return self.A32.shape[0]
+
+    @property
+    def nrhs(self) -> int:
+        return self.b.shape[1]
+
+
+def svd_system(n: int, kappa: float, seed: int, nrhs: int = 1) -> SolveProblem:
+    """A = U diag(sigma) V^T, sigma_i = kappa**(-i/(n-1)), rounded to FP32.
+
+    b = A32 @ x_true is evaluated in FP64 from the FP32 matrix, so x_true is the
+    exact solution of the FP32 problem up to the FP64 rounding of b.
+    """
+    rng = np.random.default_rng(seed)
+    U = _haar_like_orthogonal(n, rng)
+    V = _haar_like_orthogonal(n, rng)
+    if n > 1:
+        sigma = kappa ** (-np.arange(n, dtype=np.float64) / (n - 1))
+    else:
+        sigma = np.ones(1)
+    A64 = (U * sigma[None, :]) @ V.T
+    A32 = np.ascontiguousarray(A64.astype(np.float32))
+    x_true = rng.standard_normal((n, nrhs))
+    b = A32.astype(np.float64) @ x_true
+    return SolveProblem(A32=A32, b=b, x_true=x_true, kappa_nominal=float(kappa), seed=seed)
+
+
+def batched_systems(count: int, seed: int, n_lo: int = 32, n_hi: int = 512,
+                    log10k_lo: float = 2.0, log10k_hi: float = 8.0):
+    """Many independent systems: n ~ U{n_lo..n_hi}, log10(kappa) ~ U[lo, hi], nrhs = 1."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    lk = rng.uniform(log10k_lo, log10k_hi, size=count)
+    seeds = rng.integers(0, 2**31 - 1, size=count)
+    return [svd_system(int(n), float(10.0 ** k), int(s)) for n, k, s in zip(ns, lk, seeds)]
+
+
+def batched_sizes(count: int, seed: int, n_lo: int = 32, n_hi: int = 512):
+    """Only the size list of ``batched_systems`` (same draws), for cost estimates."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(n_lo, n_hi + 1, size=count)
+
+
+@dataclass
+class Request:
+    """One solve request of the serving stream."""
+
+    t_arrival: float  # seconds from stream start
+    n: int
+    nrhs: int
+    log10_kappa: float
+    seed: int
+
+
+def serving_stream(count: int, seed: int, rate: float = 5000.0, n_lo: int = 64,
+                   n_hi: int = 4096, nrhs_hi: int = 16, log10k_lo: float = 1.0,
+                   log10k_hi: float = 10.0):
+    """Poisson arrivals (exponential gaps of mean 1/rate) with mixed sizes.
+
+    n is log-uniform in [n_lo, n_hi] (rounded down to an integer), nrhs is
+    uniform in {1..nrhs_hi}, log10(kappa) is uniform in [lo, hi].
+    """
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    t = np.cumsum(gaps)
+    ns = np.floor(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi + 1), size=count))).astype(int)
+    ns = np.clip(ns, n_lo, n_hi)
+    nr = rng.integers(1, nrhs_hi + 1, size=count)
+    lk = rng.uniform(log10k_lo, log10k_hi, size=count)
+    seeds = rng.integers(0, 2**31 - 1, size=count)
+    return [Request(float(a), int(b), int(c), float(d), int(e))
+            for a, b, c, d, e in zip(t, ns, nr, lk, seeds)]

@@ -1,0 +1,537 @@
+/*
+ * CPU oracle for the BF16-split method of Henry, Tang & Heinecke,
+ * "Leveraging the bfloat16 Artificial Intelligence Datatype For
+ * Higher-Precision Computations" (ARITH 2019).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  It shares no code,
+ * header, table or constant with the CUDA library: it is a plain, slow,
+ * sequential statement of what the method computes, each function citing the
+ * passage it follows.  Build flags keep C float arithmetic IEEE binary32 with
+ * round-to-nearest, no contraction of a*b+c into an FMA unless fmaf() is
+ * written, and gradual underflow:  gcc -O2 -ffp-contract=off -fno-fast-math.
+ * OpenMP is used only to run independent outputs (rows, systems) on several
+ * host threads; it never changes the order of an accumulation.
+ *
+ * Readings of the paper taken here (the paper is silent or garbled):
+ *  R1 (B16) rounds to nearest, ties to even (Sec. II-A gives no mode; the bin
+ *     bound |a1| <= 2^-8 |a0| of Sec. II-G holds for this mode).
+ *  R3 a finite FP32 value whose RNE bfloat16 would overflow to infinity
+ *     (|x| >= 0x7F7F8000) gets hi = x truncated toward zero; the rest of the
+ *     split then proceeds as written, so the pieces still sum to x.
+ *  R4 Inf/NaN: hi carries the value (NaN made quiet, sign kept), mid = lo = +0.
+ *  R6 products and order: x1 = {00}; x3 = pair split, {00,01,10};
+ *     x6 = {00,01,10,02,11,20}; x9 = all nine; level sums and the
+ *     smallest-first combination exactly as written in Sec. II-D.
+ *  R9 refinement: r = b - A x (the paper's sign slip in Sec. III corrected),
+ *     residual, correction solve and update all in FP64 with the low-precision
+ *     factors (Sec. III: "do the solve in a higher precision like FP64").
+ *  R12 the "combined type" LU (Sec. IV-A) uses bf16xN only in the trailing
+ *     matrix update; panel and triangular block solve are plain FP32.
+ *  R13 GEMM result form C = alpha*Z + beta*C: t = fl32(alpha*Z), then
+ *     fmaf(beta, C, t); beta == 0 does not read C.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* bit views                                                            */
+/* ------------------------------------------------------------------ */
+static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static float f32_from_bits(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+/* (F32) of a bfloat16 bit pattern: exact widening (Sec. I: BF16 is the top
+ * 16 bits of an FP32 word). */
+static float bf16_to_f32(uint16_t h) { return f32_from_bits((uint32_t)h << 16); }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* O1  (B16): FP32 -> bfloat16, round to nearest, ties to even (R1).    */
+/* bfloat16 keeps sign, the full 8-bit exponent and the top 7 stored    */
+/* mantissa bits of FP32 (Sec. I).  The two bfloat16 neighbours of x    */
+/* that bracket it toward and away from zero are the truncation t and   */
+/* t + 1 ulp; the dropped 16 bits decide which one is nearer.           */
+/* ------------------------------------------------------------------ */
+uint16_t orc_bf16_rne(float x) {
+  uint32_t u = f32_bits(x);
+  if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu) != 0u)
+    return (uint16_t)((u >> 16) | 0x0040u); /* NaN: quiet, sign kept (R4) */
+  uint16_t toward_zero = (uint16_t)(u >> 16);
+  uint32_t dropped = u & 0xFFFFu;   /* distance to toward_zero, in 2^-16 ulp */
+  int away;
+  if (dropped > 0x8000u) away = 1;                 /* nearer the far neighbour */
+  else if (dropped < 0x8000u) away = 0;            /* nearer the truncation    */
+  else away = (toward_zero & 1u) ? 1 : 0;          /* tie: pick the even one   */
+  /* one ulp away from zero; a carry out of the mantissa moves to the next
+   * binade and past the largest finite value to infinity, as IEEE requires */
+  return (uint16_t)(toward_zero + (away ? 1u : 0u));
+}
+
+void orc_bf16_rne_array(int64_t n, const float* x, uint16_t* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_rne(x[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* O2  the decomposition of Sec. II-A:                                   */
+/*   b0 = (B16) a                                                        */
+/*   b1 = (B16)((F32)(a - (F32)b0))                                      */
+/*   b2 = (B16)((F32)(a - (F32)b0 - (F32)b1))   (left to right)          */
+/* npieces = 1, 2 or 3 writes b0 / b0,b1 / b0,b1,b2.  The pair split of  */
+/* Sec. I/II-G is the first two pieces of the triple split.             */
+/* ------------------------------------------------------------------ */
+static void split_one(float a, uint16_t* b0, uint16_t* b1, uint16_t* b2) {
+  uint32_t u = f32_bits(a);
+  if ((u & 0x7F800000u) == 0x7F800000u) {          /* Inf or NaN (R4) */
+    if ((u & 0x007FFFFFu) != 0u)
+      *b0 = (uint16_t)((u >> 16) | 0x0040u);       /* NaN, made quiet */
+    else
+      *b0 = (uint16_t)(u >> 16);                   /* +-Inf */
+    *b1 = 0; *b2 = 0;
+    return;
+  }
+  if ((u & 0x7FFFFFFFu) >= 0x7F7F8000u)            /* RNE would overflow (R3) */
+    *b0 = (uint16_t)(u >> 16);
+  else
+    *b0 = orc_bf16_rne(a);
+  float r1 = a - bf16_to_f32(*b0);                 /* (F32)(a - (F32)b0) */
+  *b1 = orc_bf16_rne(r1);
+  float r2 = (a - bf16_to_f32(*b0)) - bf16_to_f32(*b1);
+  *b2 = orc_bf16_rne(r2);
+}
+
+void orc_split(int64_t n, const float* x, int npieces, uint16_t* b0, uint16_t* b1,
+               uint16_t* b2) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    uint16_t p0, p1, p2;
+    split_one(x[i], &p0, &p1, &p2);
+    b0[i] = p0;
+    if (npieces >= 2) b1[i] = p1;
+    if (npieces >= 3) b2[i] = p2;
+  }
+}
+
+/* Split of every FP32 bit pattern in [start, start+count): used to compare
+ * against the device split over the whole 2^32 input space chunk by chunk. */
+void orc_split_bits_range(uint64_t start, int64_t count, int npieces, uint16_t* b0,
+                          uint16_t* b1, uint16_t* b2) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < count; ++i) {
+    uint16_t p0, p1, p2;
+    split_one(f32_from_bits((uint32_t)(start + (uint64_t)i)), &p0, &p1, &p2);
+    b0[i] = p0;
+    if (npieces >= 2) b1[i] = p1;
+    if (npieces >= 3) b2[i] = p2;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* O4  products of Sec. II-D in the paper's FP32-FMA model.              */
+/* For each used piece pair (i,j):                                      */
+/*   Z^(i,j) <- 0;  for l: Z^(i,j) <- FMA(x_l^(i), y_l^(j), Z^(i,j))     */
+/* then the level sums, in FP32:                                        */
+/*   Z0 = Z00;  Z1 = Z01 + Z10;  Z2 = Z02 + (Z11 + Z20);                 */
+/*   Z3 = Z12 + Z21;  Z4 = Z22                                           */
+/* and the combination, smallest first:                                  */
+/*   x1: Z0;  x3: Z0 + Z1;  x6 (= Z_2 of Sec. II-D): Z0 + (Z1 + Z2);     */
+/*   x9: Z0 + (Z1 + (Z2 + (Z3 + Z4)))                                    */
+/* sum64 != 0 is the "d" variant of Sec. IV-A: level sums and the final   */
+/* combination in FP64, one rounding to FP32 at the end.                 */
+/* mode 0 is the plain FP32 reference of Sec. II-C: Z <- FMA(x_l, y_l, Z) */
+/* Matrices are row-major: A is m x k (lda), B is k x n (ldb), C m x n.   */
+/* ------------------------------------------------------------------ */
+static int mode_pieces(int mode) {
+  switch (mode) {
+    case 1: return 1;
+    case 3: return 2;
+    case 6: return 3;
+    case 9: return 3;
+    default: return 0;
+  }
+}
+
+/* is product (i,j) used by the mode (R6) */
+static int mode_uses(int mode, int i, int j) {
+  switch (mode) {
+    case 1: return i == 0 && j == 0;
+    case 3: return i + j <= 1;
+    case 6: return i + j <= 2;
+    case 9: return 1;
+    default: return 0;
+  }
+}
+
+/* Shared body: when Cd != NULL the "d" combination is written to Cd in FP64
+ * without a final rounding (alpha, beta ignored); otherwise C (FP32) gets
+ * alpha*z + beta*C (R13). */
+static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                     float* C, int64_t ldc, double* Cd, int64_t ldcd) {
+  if (m < 0 || n < 0 || k < 0) return 1;
+  if (m == 0 || n == 0) return 0;
+  if (mode == 0) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        float Z = 0.0f;
+        for (int64_t l = 0; l < k; ++l) Z = fmaf(A[i * lda + l], B[l * ldb + j], Z);
+        if (Cd) { Cd[i * ldcd + j] = Z; continue; }
+        float t = alpha * Z;
+        C[i * ldc + j] = (beta == 0.0f) ? t : fmaf(beta, C[i * ldc + j], t);
+      }
+    return 0;
+  }
+  int np = mode_pieces(mode);
+  if (np == 0) return 1;
+  /* pieces, widened to FP32 (exact) */
+  float* Ap = (float*)malloc(sizeof(float) * 3 * (size_t)(m * k + 1));
+  float* Bp = (float*)malloc(sizeof(float) * 3 * (size_t)(k * n + 1));
+  if (!Ap || !Bp) { free(Ap); free(Bp); return 2; }
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t l = 0; l < k; ++l) {
+      uint16_t p[3];
+      split_one(A[i * lda + l], &p[0], &p[1], &p[2]);
+      for (int q = 0; q < 3; ++q)
+        Ap[(size_t)q * m * k + i * k + l] = (q < np) ? bf16_to_f32(p[q]) : 0.0f;
+    }
+  for (int64_t l = 0; l < k; ++l)
+    for (int64_t j = 0; j < n; ++j) {
+      uint16_t p[3];
+      split_one(B[l * ldb + j], &p[0], &p[1], &p[2]);
+      for (int q = 0; q < 3; ++q)
+        Bp[(size_t)q * k * n + l * n + j] = (q < np) ? bf16_to_f32(p[q]) : 0.0f;
+    }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      float Z[3][3] = {{0}};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          if (!mode_uses(mode, a, b)) continue;
+          const float* xa = Ap + (size_t)a * m * k + i * k;
+          const float* yb = Bp + (size_t)b * k * n + j;
+          float z = 0.0f;
+          for (int64_t l = 0; l < k; ++l) z = fmaf(xa[l], yb[l * n], z);
+          Z[a][b] = z;
+        }
+      if (!sum64) {
+        float Z0 = Z[0][0];
+        float Z1 = Z[0][1] + Z[1][0];
+        float Z2 = Z[0][2] + (Z[1][1] + Z[2][0]);
+        float Z3 = Z[1][2] + Z[2][1];
+        float Z4 = Z[2][2];
+        float zr;
+        switch (mode) {
+          case 1: zr = Z0; break;
+          case 3: zr = Z0 + Z1; break;
+          case 6: zr = Z0 + (Z1 + Z2); break;
+          default: zr = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
+        }
+        if (Cd) { Cd[i * ldcd + j] = zr; continue; }
+        float t = alpha * zr;
+        C[i * ldc + j] = (beta == 0.0f) ? t : fmaf(beta, C[i * ldc + j], t);
+      } else {
+        double Z0 = Z[0][0];
+        double Z1 = (double)Z[0][1] + (double)Z[1][0];
+        double Z2 = (double)Z[0][2] + ((double)Z[1][1] + (double)Z[2][0]);
+        double Z3 = (double)Z[1][2] + (double)Z[2][1];
+        double Z4 = Z[2][2];
+        double zd;
+        switch (mode) {
+          case 1: zd = Z0; break;
+          case 3: zd = Z0 + Z1; break;
+          case 6: zd = Z0 + (Z1 + Z2); break;
+          default: zd = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
+        }
+        if (Cd) { Cd[i * ldcd + j] = zd; continue; }
+        float t = alpha * (float)zd;
+        C[i * ldc + j] = (beta == 0.0f) ? t : fmaf(beta, C[i * ldc + j], t);
+      }
+    }
+  free(Ap);
+  free(Bp);
+  return 0;
+}
+
+int orc_gemm(int mode, int sum64, int64_t m, int64_t n, int64_t k, float alpha,
+             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+             float* C, int64_t ldc) {
+  return gemm_body(mode, sum64, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, NULL, 0);
+}
+
+/* The "d" variant of Sec. IV-A with the final answer kept in FP64:
+ * Cd = combination of the FP32 partial products, summed in FP64 when sum64. */
+int orc_gemm_f64out(int mode, int sum64, int64_t m, int64_t n, int64_t k, const float* A,
+                    int64_t lda, const float* B, int64_t ldb, double* Cd, int64_t ldcd) {
+  return gemm_body(mode, sum64, m, n, k, 1.0f, A, lda, B, ldb, 0.0f, NULL, 0, Cd, ldcd);
+}
+
+/* The nine partial inner products Z^(i,j) of Sec. II-D for one pair of
+ * vectors (x, y of length n), FP32 FMA accumulation, written to Z[3*i+j]. */
+void orc_dot_partials(int64_t n, const float* x, const float* y, float* Z) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      float z = 0.0f;
+      for (int64_t l = 0; l < n; ++l) {
+        uint16_t px[3], py[3];
+        split_one(x[l], &px[0], &px[1], &px[2]);
+        split_one(y[l], &py[0], &py[1], &py[2]);
+        z = fmaf(bf16_to_f32(px[a]), bf16_to_f32(py[b]), z);
+      }
+      Z[3 * a + b] = z;
+    }
+}
+
+/* inner product x^T y by the mode's products (Sec. II-B..II-D); mode 0 is
+ * the plain FP32 FMA loop of Sec. II-C. */
+float orc_dot(int mode, int sum64, int64_t n, const float* x, const float* y) {
+  float out = 0.0f;
+  orc_gemm(mode, sum64, 1, 1, n, 1.0f, x, n, y, 1, 0.0f, &out, 1);
+  return out;
+}
+
+/* ------------------------------------------------------------------ */
+/* O5  FP64 reference product and |A||B| for selected rows of C.         */
+/* C64[r, j] = sum_l A[i_r, l] B[l, j], Cabs = sum_l |A||B|, in FP64.     */
+/* ------------------------------------------------------------------ */
+void orc_dgemm_rows(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
+                    const float* A, int64_t lda, const float* B, int64_t ldb,
+                    double* C64, double* Cabs) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const float* a = A + rows[r] * lda;
+    double* c = C64 + r * n;
+    double* ca = Cabs + r * n;
+    for (int64_t j = 0; j < n; ++j) { c[j] = 0.0; ca[j] = 0.0; }
+    for (int64_t l = 0; l < k; ++l) {
+      double al = a[l];
+      const float* b = B + l * ldb;
+      for (int64_t j = 0; j < n; ++j) {
+        double bj = b[j];
+        c[j] += al * bj;
+        ca[j] += fabs(al * bj);
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* O6  LU with partial pivoting (the factorisation of LAPACK xGETRF).    */
+/* Row-major A (n x n, lda).  ipiv[j] = 0-based row swapped with row j.  */
+/* Pivot = first row index of the largest |a_ij| in the column.  The     */
+/* return value is LAPACK's info: 0, or the 1-based index of the first   */
+/* exactly zero pivot (the elimination still completes).                 */
+/* ------------------------------------------------------------------ */
+int orc_dgetrf(int64_t n, double* A, int64_t lda, int32_t* ipiv) {
+  int info = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = j;
+    double best = fabs(A[j * lda + j]);
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = fabs(A[i * lda + j]);
+      if (v > best) { best = v; p = i; }
+    }
+    ipiv[j] = (int32_t)p;
+    if (p != j)
+      for (int64_t c = 0; c < n; ++c) {
+        double t = A[j * lda + c]; A[j * lda + c] = A[p * lda + c]; A[p * lda + c] = t;
+      }
+    double piv = A[j * lda + j];
+    if (piv == 0.0) { if (info == 0) info = (int)(j + 1); continue; }
+    for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] /= piv;
+#pragma omp parallel for schedule(static) if (n - j > 256)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double l = A[i * lda + j];
+      if (l == 0.0) continue;
+      for (int64_t c = j + 1; c < n; ++c) A[i * lda + c] -= l * A[j * lda + c];
+    }
+  }
+  return info;
+}
+
+/* Solve with FP64 factors: x <- U^-1 L^-1 P b, nrhs columns, row-major b (ldb). */
+void orc_dgetrs(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const int32_t* ipiv,
+                double* b, int64_t ldb) {
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = ipiv[j];
+    if (p != j)
+      for (int64_t c = 0; c < nrhs; ++c) {
+        double t = b[j * ldb + c]; b[j * ldb + c] = b[p * ldb + c]; b[p * ldb + c] = t;
+      }
+  }
+  for (int64_t c = 0; c < nrhs; ++c) {
+    for (int64_t i = 0; i < n; ++i) {           /* L y = P b, L unit lower */
+      double s = b[i * ldb + c];
+      for (int64_t l = 0; l < i; ++l) s -= LU[i * lda + l] * b[l * ldb + c];
+      b[i * ldb + c] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {      /* U x = y */
+      double s = b[i * ldb + c];
+      for (int64_t l = i + 1; l < n; ++l) s -= LU[i * lda + l] * b[l * ldb + c];
+      b[i * ldb + c] = s / LU[i * lda + i];
+    }
+  }
+}
+
+/* LU of an FP32 matrix with the combined type of Sec. IV-A (R12): blocked
+ * right-looking with block width nb; the panel (unblocked, partial pivoting,
+ * division by the pivot, FMA rank-1 updates) and the unit-lower block solve
+ * U12 = L11^-1 A12 are FP32; the trailing update A22 <- A22 - L21 U12 is the
+ * mode's product (mode 0: the plain FP32 FMA product of Sec. II-C). */
+int orc_lu(int mode, int64_t n, int64_t nb, float* A, int64_t lda, int32_t* ipiv) {
+  if (nb <= 0) nb = 64;
+  int info = 0;
+  for (int64_t j0 = 0; j0 < n; j0 += nb) {
+    int64_t jb = (n - j0 < nb) ? n - j0 : nb;
+    /* panel A[j0:n, j0:j0+jb] */
+    for (int64_t j = j0; j < j0 + jb; ++j) {
+      int64_t p = j;
+      float best = fabsf(A[j * lda + j]);
+      for (int64_t i = j + 1; i < n; ++i) {
+        float v = fabsf(A[i * lda + j]);
+        if (v > best) { best = v; p = i; }
+      }
+      ipiv[j] = (int32_t)p;
+      if (p != j)   /* whole row: the same as swapping panel, left and right parts */
+        for (int64_t c = 0; c < n; ++c) {
+          float t = A[j * lda + c]; A[j * lda + c] = A[p * lda + c]; A[p * lda + c] = t;
+        }
+      float piv = A[j * lda + j];
+      if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
+      for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
+      for (int64_t i = j + 1; i < n; ++i) {
+        float l = A[i * lda + j];
+        for (int64_t c = j + 1; c < j0 + jb; ++c)
+          A[i * lda + c] = fmaf(-l, A[j * lda + c], A[i * lda + c]);
+      }
+    }
+    int64_t nr = n - j0 - jb;
+    if (nr <= 0) continue;
+    /* U12 = L11^-1 A12 (unit lower, forward substitution row by row) */
+    for (int64_t i = j0 + 1; i < j0 + jb; ++i)
+      for (int64_t l = j0; l < i; ++l) {
+        float lil = A[i * lda + l];
+        for (int64_t c = j0 + jb; c < n; ++c)
+          A[i * lda + c] = fmaf(-lil, A[l * lda + c], A[i * lda + c]);
+      }
+    /* A22 <- A22 - L21 U12 */
+    int rc = orc_gemm(mode, 0, nr, nr, jb, -1.0f, A + (j0 + jb) * lda + j0, lda,
+                      A + j0 * lda + j0 + jb, lda, 1.0f, A + (j0 + jb) * lda + j0 + jb, lda);
+    if (rc) return -rc;
+  }
+  return info;
+}
+
+/* ------------------------------------------------------------------ */
+/* O7  residual-form iterative refinement (Sec. III, reading R9).        */
+/* A32 (n x n, FP32, the problem matrix), b (n x nrhs, FP64), x (out).    */
+/* LU (FP32 factors from orc_lu) and ipiv are given.  For each column:   */
+/*   x <- LU^-1 b            (FP64 arithmetic with the FP32 factors)     */
+/*   repeat: r = b - A x (FP64); d = LU^-1 r (FP64); x += d (FP64)        */
+/*     stop, converged, when |d|_inf <= tol |x|_inf;                      */
+/*     stop when |d| >= stall * |d_prev| (no more progress: the limiting  */
+/*     accuracy is reached, or the factors are too inaccurate);           */
+/*     stop after max_iter corrections.                                   */
+/*   Finally r = b - A x; berr = |r|_inf / (|A|_inf |x|_inf + |b|_inf);    */
+/*   converged also when the last stop was a stall with berr <= tol_b.    */
+/* iters[c] = corrections applied after the first solve; conv[c] = 1/0.  */
+/* ------------------------------------------------------------------ */
+static void lu32_solve64(int64_t n, const float* LU, int64_t lda, const int32_t* ipiv,
+                         double* v) {
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = ipiv[j];
+    if (p != j) { double t = v[j]; v[j] = v[p]; v[p] = t; }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double s = v[i];
+    for (int64_t l = 0; l < i; ++l) s -= (double)LU[i * lda + l] * v[l];
+    v[i] = s;
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = v[i];
+    for (int64_t l = i + 1; l < n; ++l) s -= (double)LU[i * lda + l] * v[l];
+    v[i] = s / (double)LU[i * lda + i];
+  }
+}
+
+void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const float* LU,
+                  int64_t ldlu, const int32_t* ipiv, const double* b, int64_t ldb,
+                  double* x, int64_t ldx, int max_iter, double tol, double tol_b, double stall,
+                  int32_t* iters, int32_t* conv, double* berr_out) {
+  double anorm = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t l = 0; l < n; ++l) s += fabs((double)A32[i * lda + l]);
+    if (s > anorm) anorm = s;
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* xv = (double*)malloc(sizeof(double) * (size_t)n);
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double bnorm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      xv[i] = b[i * ldb + c];
+      if (fabs(b[i * ldb + c]) > bnorm) bnorm = fabs(b[i * ldb + c]);
+    }
+    lu32_solve64(n, LU, ldlu, ipiv, xv);
+    double dprev = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (fabs(xv[i]) > dprev) dprev = fabs(xv[i]);
+    int it = 0, ok = 0, stalled = 0;
+    while (it < max_iter) {
+      for (int64_t i = 0; i < n; ++i) {
+        double s = b[i * ldb + c];
+        for (int64_t l = 0; l < n; ++l) s -= (double)A32[i * lda + l] * xv[l];
+        r[i] = s;
+      }
+      lu32_solve64(n, LU, ldlu, ipiv, r);
+      double dn = 0.0, xn = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        xv[i] += r[i];
+        if (fabs(r[i]) > dn) dn = fabs(r[i]);
+        if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
+      }
+      ++it;
+      if (!(dn == dn) || !(xn == xn)) break;        /* NaN: diverged */
+      if (dn <= tol * xn) { ok = 1; break; }
+      if (dn >= stall * dprev) { stalled = 1; break; }
+      dprev = dn;
+    }
+    double rn = 0.0, xn = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double s = b[i * ldb + c];
+      for (int64_t l = 0; l < n; ++l) s -= (double)A32[i * lda + l] * xv[l];
+      if (fabs(s) > rn) rn = fabs(s);
+      if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
+    }
+    double den = anorm * xn + bnorm;
+    double berr = (den > 0.0) ? rn / den : 0.0;
+    if (!(berr == berr)) berr = INFINITY;
+    if (!ok && stalled && berr <= tol_b) ok = 1;
+    for (int64_t i = 0; i < n; ++i) x[i * ldx + c] = xv[i];
+    iters[c] = it;
+    conv[c] = ok;
+    if (berr_out) berr_out[c] = berr;
+    free(xv);
+    free(r);
+  }
+}

@@ -1,0 +1,148 @@
+/*
+ * bfx: FP32-accurate linear algebra assembled from bfloat16 pieces on the
+ * B300 (sm_103a) tensor cores, after Henry, Tang & Heinecke, "Leveraging the
+ * bfloat16 Artificial Intelligence Datatype For Higher-Precision
+ * Computations" (ARITH 2019).
+ *
+ * C ABI.  Every pointer argument named d_* is a device pointer on the current
+ * CUDA device; h_* pointers are host memory.  The caller owns every buffer:
+ * the library never frees caller memory and allocates none on the calls below
+ * (scratch space is a caller-provided workspace whose size a *_workspace_size
+ * query returns).  Matrices are row-major with a leading dimension (elements
+ * between the starts of consecutive rows).  bfloat16 values travel as their
+ * 16-bit patterns in uint16_t.
+ *
+ * Calls are asynchronous on the given stream (a cudaStream_t passed as
+ * bfx_stream; NULL is the legacy default stream).  The returned status only
+ * reports what is known at launch: invalid arguments (BFX_EINVAL), a shape or
+ * device the kernels do not support (BFX_EUNSUPPORTED), a workspace that is
+ * too small (BFX_ENOMEM) or a CUDA launch error (BFX_ECUDA).  Outcomes computed
+ * on the device (a zero pivot, non-convergence, a device-side wait that
+ * expired) are written to device memory the caller reads after synchronising.
+ *
+ * There is no CPU fallback: every entry point runs its work in the library's
+ * own sm_103a kernels.
+ */
+#ifndef BFX_H
+#define BFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define BFX_API __attribute__((visibility("default")))
+#else
+#define BFX_API
+#endif
+
+typedef void* bfx_stream; /* cudaStream_t */
+
+typedef enum bfx_status {
+  BFX_OK = 0,
+  BFX_EINVAL = 1,         /* invalid argument (negative size, null pointer, ld too small) */
+  BFX_ENOMEM = 2,         /* caller workspace too small */
+  BFX_ECUDA = 3,          /* CUDA runtime / launch error */
+  BFX_EUNSUPPORTED = 4,   /* valid but unsupported (alignment, device not sm_103) */
+  BFX_SINGULAR = 5,       /* an exactly zero pivot (reported on the device via info) */
+  BFX_NOT_CONVERGED = 6,  /* refinement stopped without converging (device-side result) */
+  BFX_TIMEOUT = 7         /* a bounded device-side wait expired (device error word) */
+} bfx_status;
+
+/* Which products assemble a result (Sec. II-D, II-G of the paper):
+ *   BFX_FP32 : no split; plain FP32 FMA accumulation (Sec. II-C), SIMT cores
+ *   BFX_X1   : hi*hi                                    (one bfloat16 piece)
+ *   BFX_X3   : + hi*mid + mid*hi                        (pair split, "bx2_3")
+ *   BFX_X6   : + hi*lo + mid*mid + lo*hi                (triple split, "bx3_6")
+ *   BFX_X9   : all nine products                       (triple split)
+ * The mode's value is the number of bfloat16 products per scalar product. */
+typedef enum bfx_mode { BFX_FP32 = 0, BFX_X1 = 1, BFX_X3 = 3, BFX_X6 = 6, BFX_X9 = 9 } bfx_mode;
+
+/* Library version (major*10000 + minor*100 + patch). */
+BFX_API int bfx_version(void);
+
+/* Static text for a status code; never NULL. */
+BFX_API const char* bfx_status_string(bfx_status s);
+
+/* Number of SMs of the current device, or -1 on error. */
+BFX_API int bfx_num_sms(void);
+
+/* Read and clear the device error word of the current device.  Kernels whose
+ * waits are bounded (tensor-core GEMM pipeline barriers) set it instead of
+ * hanging: 0 = no error, otherwise a code naming the wait that expired.
+ * Synchronises `stream`.  h_code: host int (output). */
+BFX_API bfx_status bfx_device_error(int* h_code, bfx_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Split (Sec. II-A).  For each FP32 element a of the rows x cols matrix d_x:
+ *   hi  = (B16) a
+ *   mid = (B16)((F32)(a - hi))
+ *   lo  = (B16)((F32)(a - hi - mid))
+ * with (B16) round-to-nearest-even.  For every finite |a| >= 2^-110 (and 0)
+ * the pieces sum exactly to a (Sec. II-F).  Edge readings: a finite value whose
+ * rounding would overflow to infinity gets hi = a truncated toward zero;
+ * Inf/NaN go to hi (NaN made quiet, sign kept) with mid = lo = +0.
+ * npieces: 1 (hi), 2 (hi, mid) or 3 (hi, mid, lo); unused piece pointers may
+ * be NULL.  Output planes share the leading dimension ldp (>= cols).
+ * Errors: BFX_EINVAL for rows/cols < 0, npieces outside 1..3, ld too small or
+ * a required pointer NULL. */
+BFX_API bfx_status bfx_split(int64_t rows, int64_t cols, const float* d_x, int64_t ldx, int npieces,
+                             uint16_t* d_hi, uint16_t* d_mid, uint16_t* d_lo, int64_t ldp,
+                             bfx_stream stream);
+
+/* Same split, written transposed: piece planes are cols x rows with leading
+ * dimension ldp (>= rows).  Lays a row-major right-hand operand out with its
+ * contraction index contiguous.  Errors as bfx_split. */
+BFX_API bfx_status bfx_split_transpose(int64_t rows, int64_t cols, const float* d_x, int64_t ldx,
+                                       int npieces, uint16_t* d_hi, uint16_t* d_mid,
+                                       uint16_t* d_lo, int64_t ldp, bfx_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * GEMM C = alpha * (A B) + beta * C from FP32 A (m x k, lda) and B (k x n, ldb)
+ * by the mode's bfloat16 products (Sec. II-D, II-G; Sec. IV-A: a GEMM that
+ * starts from FP32 data and converts it to one to three bfloat16 matrices
+ * behind the scenes).  The products run on the tcgen05 tensor cores with FP32
+ * accumulation in tensor memory; the hi*hi product is accumulated apart from
+ * the correction products, which are issued smallest bin first, and the two
+ * are added in FP32 in the epilogue.  Then t = alpha * Z and
+ * C = beta == 0 ? t : fma(beta, C, t) (C is not read when beta == 0).
+ * mode BFX_FP32 runs the plain FP32 SIMT GEMM instead (no workspace).
+ * Workspace: d_ws of ws_bytes >= bfx_gemm_workspace_size(mode, m, n, k), 256-
+ * byte aligned; it holds the pieces.  Errors: BFX_EINVAL (sizes, ld, pointers,
+ * mode), BFX_ENOMEM (workspace too small), BFX_EUNSUPPORTED (device not sm_103,
+ * or a dimension >= 2^31). */
+BFX_API size_t bfx_gemm_workspace_size(bfx_mode mode, int64_t m, int64_t n, int64_t k);
+BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
+                                   const float* d_A, int64_t lda, const float* d_B, int64_t ldb,
+                                   float beta, float* d_C, int64_t ldc, void* d_ws,
+                                   size_t ws_bytes, bfx_stream stream);
+
+/* GEMM from pieces already split.  d_Ap: npieces(mode) planes of m x k
+ * bfloat16 (row-major, leading dimension lda_p, plane p at d_Ap + p*a_plane),
+ * d_Btp: npieces planes of the TRANSPOSED right operand, n x k (leading
+ * dimension ldb_p, plane stride b_plane), e.g. from bfx_split /
+ * bfx_split_transpose.  npieces(mode) = 1, 2, 3, 3 for X1, X3, X6, X9.
+ * Requirements of the tensor-memory-access (TMA) descriptors: lda_p, ldb_p,
+ * a_plane and b_plane multiples of 8 elements, both base pointers 16-byte
+ * aligned; otherwise BFX_EUNSUPPORTED.  mode must be X1..X9 (BFX_EINVAL). */
+BFX_API bfx_status bfx_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
+                                     const uint16_t* d_Ap, int64_t lda_p, int64_t a_plane,
+                                     const uint16_t* d_Btp, int64_t ldb_p, int64_t b_plane,
+                                     float beta, float* d_C, int64_t ldc, bfx_stream stream);
+
+/* Plain FP32 SIMT GEMM (the Sec. II-C reference computation on CUDA cores;
+ * the same-GPU baseline).  Each C element is accumulated with one FMA per k
+ * in increasing k, then t = alpha*Z, C = beta == 0 ? t : fma(beta, C, t).
+ * Errors: BFX_EINVAL (sizes, ld, pointers). */
+BFX_API bfx_status bfx_sgemm_simt(int64_t m, int64_t n, int64_t k, float alpha, const float* d_A,
+                                  int64_t lda, const float* d_B, int64_t ldb, float beta,
+                                  float* d_C, int64_t ldc, bfx_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFX_H */

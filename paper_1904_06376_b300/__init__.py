@@ -1,0 +1,28 @@
+"""bfx: FP32-accurate GEMM, LU and iterative-refinement solves from bfloat16
+pieces on B300 tensor cores (Henry, Tang & Heinecke, ARITH 2019).
+
+This package is a thin binding over the C-ABI library ``libbfx.so`` (built
+in-tree from ``csrc/`` by ``build.py``; declarations in ``include/bfx.h``).
+Every computation runs in the library's sm_103a kernels; the Python layer only
+marshals torch tensors (device memory, streams) into pointers and sizes.
+There is no CPU fallback: without the built library every call raises.
+"""
+from ._bfx import (  # noqa: F401
+    BFX_FP32,
+    BFX_X1,
+    BFX_X3,
+    BFX_X6,
+    BFX_X9,
+    BfxError,
+    device_error,
+    gemm_bf16xN,
+    gemm_presplit,
+    gemm_workspace_size,
+    lib,
+    library_path,
+    num_sms,
+    sgemm_simt,
+    split,
+    split_transpose,
+    version,
+)

@@ -1,0 +1,187 @@
+"""ctypes binding of libbfx.so: argument marshalling only.
+
+Tensors are torch CUDA tensors; their data pointers, leading dimensions and
+the current torch stream are passed to the C entry points of ``include/bfx.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libbfx.so")
+
+BFX_FP32, BFX_X1, BFX_X3, BFX_X6, BFX_X9 = 0, 1, 3, 6, 9
+PIECES = {BFX_X1: 1, BFX_X3: 2, BFX_X6: 3, BFX_X9: 3}
+
+_STATUS = {
+    0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
+    4: "unsupported shape, alignment or device", 5: "exactly zero pivot",
+    6: "iterative refinement did not converge", 7: "a bounded device-side wait expired",
+}
+
+
+class BfxError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn}: {_STATUS.get(code, 'unknown')} (status {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbfx.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise ImportError(f"bfx CUDA library not built: {_LIBPATH} missing "
+                          "(run python -m paper_1904_06376_b300.build or __graft_entry__.build())")
+    L = ctypes.CDLL(_LIBPATH)
+    i64, i32, f32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "bfx_version": (i32, []),
+        "bfx_status_string": (ctypes.c_char_p, [i32]),
+        "bfx_num_sms": (i32, []),
+        "bfx_device_error": (i32, [vp, vp]),
+        "bfx_split": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
+        "bfx_split_transpose": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
+        "bfx_gemm_workspace_size": (sz, [i32, i64, i64, i64]),
+        "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
+        "bfx_gemm_presplit": (i32, [i32, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, vp]),
+        "bfx_sgemm_simt": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(fn: str, code: int) -> None:
+    if code != 0:
+        raise BfxError(fn, code)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit column stride (row-major)")
+    return t.stride(0)
+
+
+def version() -> int:
+    return lib().bfx_version()
+
+
+def num_sms() -> int:
+    return lib().bfx_num_sms()
+
+
+def device_error(stream=None) -> int:
+    """Read and clear the device error word (bounded-wait expiries)."""
+    code = ctypes.c_int(0)
+    _check("bfx_device_error", lib().bfx_device_error(ctypes.byref(code), _stream(stream)))
+    return code.value
+
+
+def split(x: torch.Tensor, npieces: int = 3, out=None, stream=None):
+    """hi, mid, lo bfloat16 pieces (as int16 bit patterns) of FP32 x (Sec. II-A)."""
+    assert x.dtype == torch.float32 and x.is_cuda
+    rows, cols = x.shape
+    if out is None:
+        out = [torch.empty((rows, cols), dtype=torch.int16, device=x.device) for _ in range(npieces)]
+    ldp = _ld(out[0]) if rows and cols else max(cols, 1)
+    ps = list(out) + [None] * (3 - len(out))
+    _check("bfx_split", lib().bfx_split(rows, cols, _ptr(x), _ld(x) if rows and cols else max(cols, 1),
+                                        npieces, _ptr(ps[0]), _ptr(ps[1]), _ptr(ps[2]), ldp,
+                                        _stream(stream)))
+    return out
+
+
+def split_transpose(x: torch.Tensor, npieces: int = 3, out=None, stream=None):
+    """Pieces of x written transposed (cols x rows)."""
+    assert x.dtype == torch.float32 and x.is_cuda
+    rows, cols = x.shape
+    if out is None:
+        out = [torch.empty((cols, rows), dtype=torch.int16, device=x.device) for _ in range(npieces)]
+    ldp = _ld(out[0]) if rows and cols else max(rows, 1)
+    ps = list(out) + [None] * (3 - len(out))
+    _check("bfx_split_transpose",
+           lib().bfx_split_transpose(rows, cols, _ptr(x), _ld(x) if rows and cols else max(cols, 1),
+                                     npieces, _ptr(ps[0]), _ptr(ps[1]), _ptr(ps[2]), ldp,
+                                     _stream(stream)))
+    return out
+
+
+def gemm_workspace_size(mode: int, m: int, n: int, k: int) -> int:
+    return int(lib().bfx_gemm_workspace_size(mode, m, n, k))
+
+
+def gemm_bf16xN(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None,
+                alpha: float = 1.0, beta: float = 0.0, workspace: torch.Tensor = None, stream=None):
+    """C = alpha * (A B by the mode's bfloat16 products) + beta * C."""
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        beta = 0.0
+    wsb = gemm_workspace_size(mode, m, n, k) if mode != BFX_FP32 else 0
+    if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    ws_ptr = _ptr(workspace) if wsb else None
+    ws_bytes = workspace.numel() * workspace.element_size() if wsb else 0
+    lda = A.stride(0) if m and k else max(k, 1)
+    ldb = B.stride(0) if k and n else max(n, 1)
+    ldc = C.stride(0) if m and n else max(n, 1)
+    _check("bfx_gemm_bf16xN", lib().bfx_gemm_bf16xN(mode, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
+                                                   beta, _ptr(C), ldc, ws_ptr, ws_bytes,
+                                                   _stream(stream)))
+    return C
+
+
+def gemm_presplit(mode: int, Ap: torch.Tensor, Btp: torch.Tensor, k: int, C: torch.Tensor,
+                  alpha: float = 1.0, beta: float = 0.0, stream=None):
+    """GEMM from piece planes: Ap (np, m, lda_p) and Btp (np, n, ldb_p) int16
+    bit patterns of bfloat16; the first k entries of each row are used."""
+    _, m, _ = Ap.shape
+    _, n, _ = Btp.shape
+    _check("bfx_gemm_presplit",
+           lib().bfx_gemm_presplit(mode, m, n, k, alpha, _ptr(Ap), Ap.stride(1), Ap.stride(0),
+                                   _ptr(Btp), Btp.stride(1), Btp.stride(0), beta, _ptr(C),
+                                   C.stride(0), _stream(stream)))
+    return C
+
+
+def sgemm_simt(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None, alpha: float = 1.0,
+               beta: float = 0.0, stream=None):
+    """Plain FP32 SIMT GEMM (Sec. II-C reference computation)."""
+    m, k = A.shape
+    _, n = B.shape
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        beta = 0.0
+    lda = A.stride(0) if m and k else max(k, 1)
+    ldb = B.stride(0) if k and n else max(n, 1)
+    ldc = C.stride(0) if m and n else max(n, 1)
+    _check("bfx_sgemm_simt", lib().bfx_sgemm_simt(m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                                                 _ptr(C), ldc, _stream(stream)))
+    return C

@@ -1,0 +1,422 @@
+// bf16xN GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// C = alpha * Z + beta * C with Z the sum of the mode's bfloat16 piece
+// products (Sec. II-D, II-G of the paper):
+//   x1: a0 b0;  x3: + a0 b1 + a1 b0;  x6: + a0 b2 + a1 b1 + a2 b0;  x9: all.
+// Each product of two bfloat16 values is exact in FP32 (Sec. I) and the
+// tensor core accumulates in FP32, the precision the paper's FMA model uses.
+//
+// Accumulation layout.  Two FP32 accumulators per output tile live in tensor
+// memory: D_main receives the hi*hi product (the 2^0 bin) and D_corr every
+// correction product.  Within each K-slice the corrections are issued from
+// the smallest bin to the largest (2^-32, 2^-24, 2^-16, 2^-8), as Sec. II-G
+// prescribes, and the epilogue forms Z = D_main + D_corr in FP32, the
+// "Z0 + (Z1 + Z2)" combination of Sec. II-D.  Keeping the small products out
+// of the large accumulator means their rounding errors are relative to the
+// correction's magnitude (~2^-8 |Z|), not to |Z|.
+//
+// Kernel structure (one CTA per SM, persistent over output tiles):
+//   warp 0    TMA producer: per K-slice one 3-D bulk-tensor load brings all
+//             pieces of the A tile and one all pieces of the B tile (the piece
+//             index is the third tensor dimension) into a 64/128-byte
+//             swizzled, K-major shared-memory stage; completion on `full`.
+//   warp 1    MMA issuer (one thread): tcgen05.mma kind::f16, M=128, N=BN,
+//             K=16, A and B from shared-memory descriptors, D in tensor memory;
+//             tcgen05.commit releases the stage (`empty`) and, after the last
+//             slice, hands the accumulator to the epilogue (`acc_full`).
+//   warps 2-5 epilogue: tcgen05.ld of both accumulators (each warp owns the
+//             32 tensor-memory lanes = tile rows its warp id selects), sum,
+//             alpha/beta, store; releases the accumulator (`acc_empty`) as
+//             soon as it has been read so the next tile's MMAs overlap the
+//             stores.
+// Every mbarrier wait is bounded; on expiry the kernel records an error code
+// in the device error word and all roles leave their loops, drain the
+// in-flight copies/MMAs (again with a bound) and free tensor memory.
+#include <cudaTypedefs.h>
+
+#include "bfx_internal.cuh"
+
+namespace bfx {
+namespace {
+
+constexpr int BM = 128;     // UMMA M (one CTA, cta_group::1)
+constexpr int GROUP_M = 16; // tile raster: groups of 16 row-blocks for L2 reuse
+
+struct Prod {
+  int a, b, acc;  // piece of A, piece of B, accumulator (0 = main, 1 = correction)
+};
+
+__host__ __device__ constexpr int mode_np(int mode) { return mode == 1 ? 1 : (mode == 3 ? 2 : 3); }
+
+// Issue order of the products: corrections smallest bin first, hi*hi last.
+__host__ __device__ constexpr Prod prod_of(int mode, int i) {
+  if (mode == 1) return Prod{0, 0, 0};
+  if (mode == 3) {
+    const Prod p[3] = {{1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+    return p[i];
+  }
+  if (mode == 6) {
+    const Prod p[6] = {{2, 0, 1}, {1, 1, 1}, {0, 2, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+    return p[i];
+  }
+  const Prod p[9] = {{2, 2, 1}, {2, 1, 1}, {1, 2, 1}, {2, 0, 1}, {1, 1, 1},
+                     {0, 2, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+  return p[i];
+}
+// Is product i the first one written into its accumulator?
+__host__ __device__ constexpr bool first_in_acc(int mode, int i) {
+  for (int j = 0; j < i; ++j)
+    if (prod_of(mode, j).acc == prod_of(mode, i).acc) return false;
+  return true;
+}
+
+struct TcArgs {
+  int M, N, K;
+  int tiles_m, tiles_n, num_tiles, k_tiles;
+  float alpha, beta;
+  float* C;
+  int64_t ldc;
+  int vec_c;  // C rows 16-byte aligned: float4 loads/stores
+  int* err;
+};
+
+__device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int& mb, int& nb) {
+  const int group = GROUP_M * a.tiles_n;
+  const int g = t / group;
+  const int first_m = g * GROUP_M;
+  const int gm = min(a.tiles_m - first_m, GROUP_M);
+  const int r = t - g * group;
+  mb = first_m + r % gm;
+  nb = r / gm;
+}
+
+template <int MODE, int BN, int BK, int STAGES>
+struct TcConfig {
+  static constexpr int NP = mode_np(MODE);
+  static constexpr int NPROD = MODE;
+  static constexpr int NACC = (MODE == 1) ? 1 : 2;
+  static constexpr int ACC_BUFS = (NACC * BN * 2 <= 512) ? 2 : 1;
+  static constexpr uint32_t TMEM_COLS = NACC * BN * ACC_BUFS;
+  static constexpr int SW = BK * 2;  // swizzle span = bytes of one K-slice row
+  static constexpr uint32_t A_TILE = BM * BK * 2;
+  static constexpr uint32_t B_TILE = BN * BK * 2;
+  static constexpr uint32_t STAGE_A = NP * A_TILE;
+  static constexpr uint32_t STAGE = NP * (A_TILE + B_TILE);
+  static constexpr uint32_t BAR_BYTES = 256;
+  static constexpr uint32_t SMEM = STAGES * STAGE + BAR_BYTES + 1024;  // + alignment slack
+  static_assert(SW == 64 || SW == 128, "BK must be 32 or 64 bfloat16");
+  static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
+                    TMEM_COLS == 512,
+                "tensor memory allocation must be a power of two");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+  static_assert(SMEM <= 232448, "shared memory");
+  static_assert((2 * STAGES + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
+};
+
+template <int MODE, int BN, int BK, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs args) {
+  using Cfg = TcConfig<MODE, BN, BK, STAGES>;
+  constexpr uint32_t IDESC = idesc_bf16_f32<BM, BN>();
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_addr(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + Cfg::ACC_BUFS;
+  uint64_t* drain = acc_empty + Cfg::ACC_BUFS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* err = args.err;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(drain, 1);
+    fence_barrier_init();
+    fence_proxy_async_smem();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+        int mb, nb;
+        tile_coords(t, args, mb, nb);
+        for (int kt = 0; kt < args.k_tiles; ++kt) {
+          if (!mbar_wait_bounded(&empty[s], ph ^ 1u, err, kErrWaitEmpty)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * Cfg::STAGE;
+          mbar_arrive_expect_tx(&full[s], Cfg::STAGE);
+          tma_load_3d(st, &tmA, &full[s], kt * BK, mb * BM, 0);
+          tma_load_3d(st + Cfg::STAGE_A, &tmB, &full[s], kt * BK, nb * BN, 0);
+          ++issued;
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // Every issued load must have landed before the CTA may exit: wait for
+      // the last phase issued on each stage (already complete in normal runs).
+      for (int q = 0; q < STAGES; ++q) {
+        if (issued <= q) break;
+        const int64_t last = q + ((issued - 1 - q) / STAGES) * STAGES;
+        mbar_wait_bounded(&full[q], static_cast<uint32_t>((last / STAGES) & 1), err,
+                          kErrWaitDrain);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      int s = 0, buf = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, err, kErrWaitAccEmpty)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + static_cast<uint32_t>(buf * Cfg::NACC * BN);
+        for (int kt = 0; kt < args.k_tiles; ++kt) {
+          if (!mbar_wait_bounded(&full[s], ph, err, kErrWaitFull)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_addr(smem + s * Cfg::STAGE);
+          const uint32_t sb = sa + Cfg::STAGE_A;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+            for (int p = 0; p < Cfg::NPROD; ++p) {
+              const Prod pr = prod_of(MODE, p);
+              const uint64_t ad = smem_desc_kmajor<Cfg::SW>(sa + pr.a * Cfg::A_TILE + kk * 32);
+              const uint64_t bd = smem_desc_kmajor<Cfg::SW>(sb + pr.b * Cfg::B_TILE + kk * 32);
+              const uint32_t accum = (kt > 0 || kk > 0 || !first_in_acc(MODE, p)) ? 1u : 0u;
+              umma_bf16_ss(d0 + static_cast<uint32_t>(pr.acc * BN), ad, bd, IDESC, accum);
+            }
+          }
+          umma_commit(&empty[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[buf]);
+        if (++buf == Cfg::ACC_BUFS) {
+          buf = 0;
+          aph ^= 1u;
+        }
+      }
+      // all MMAs issued by this thread complete before tensor memory is freed
+      umma_commit(drain);
+      mbar_wait_bounded(drain, 0u, err, kErrWaitDrain);
+    }
+  } else {
+    // -------------------------------------------------- epilogue (warps 2..5)
+    const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+    const int row_in_tile = q * 32 + lane;
+    int buf = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < args.num_tiles; t += gridDim.x) {
+      int mb, nb;
+      tile_coords(t, args, mb, nb);
+      bool ok = mbar_wait_bounded(&acc_full[buf], aph, err, kErrWaitAccFull);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const int row = mb * BM + row_in_tile;
+      const bool row_ok = row < args.M;
+      float* crow = args.C + static_cast<int64_t>(row_ok ? row : 0) * args.ldc;
+      const uint32_t tb = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                          static_cast<uint32_t>(buf * Cfg::NACC * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 16; ++c) {
+        __syncwarp();
+        float v[16];
+        tmem_ld16_wait(tb + c * 16, v);
+        if (Cfg::NACC == 2) {
+          float w[16];
+          tmem_ld16_wait(tb + BN + c * 16, w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = v[i] + w[i];  // Z = D_main + D_corr
+        }
+        if (c == BN / 16 - 1) {
+          tc_fence_before();
+          mbar_arrive(&acc_empty[buf]);
+        }
+        if (!row_ok) continue;
+        const int col0 = nb * BN + c * 16;
+        if (col0 >= args.N) continue;
+        float* dst = crow + col0;
+        if (args.vec_c && col0 + 16 <= args.N) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            float4 o;
+            float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (args.beta != 0.0f) old = *reinterpret_cast<const float4*>(dst + i);
+            o.x = args.alpha * v[i + 0];
+            o.y = args.alpha * v[i + 1];
+            o.z = args.alpha * v[i + 2];
+            o.w = args.alpha * v[i + 3];
+            if (args.beta != 0.0f) {
+              o.x = fmaf(args.beta, old.x, o.x);
+              o.y = fmaf(args.beta, old.y, o.y);
+              o.z = fmaf(args.beta, old.z, o.z);
+              o.w = fmaf(args.beta, old.w, o.w);
+            }
+            *reinterpret_cast<float4*>(dst + i) = o;
+          }
+        } else {
+          const int lim = min(16, args.N - col0);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < lim) {
+              const float tv = args.alpha * v[i];
+              dst[i] = (args.beta == 0.0f) ? tv : fmaf(args.beta, dst[i], tv);
+            }
+          }
+        }
+      }
+      if (++buf == Cfg::ACC_BUFS) {
+        buf = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D bfloat16 tensor {inner (K), rows, planes}, box {bk, box_rows, planes}.
+bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64_t rows,
+                    int planes, int64_t ld, int64_t plane, int bk, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(planes)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(plane) * 2};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows),
+                       static_cast<cuuint32_t>(planes)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = (bk * 2 == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, int BN, int BK, int STAGES>
+bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* Ap, int64_t lda_p,
+                  int64_t a_plane, const uint16_t* Btp, int64_t ldb_p, int64_t b_plane,
+                  float beta, float* C, int64_t ldc, cudaStream_t s) {
+  using Cfg = TcConfig<MODE, BN, BK, STAGES>;
+  // with a single piece only plane 0 is read; any legal plane stride will do
+  if (Cfg::NP == 1) {
+    a_plane = round_up(lda_p * m, 8);
+    b_plane = round_up(ldb_p * n, 8);
+  }
+  CUtensorMap ma, mb;
+  if (!make_piece_map(&ma, Ap, k, m, Cfg::NP, lda_p, a_plane, BK, BM)) return BFX_EUNSUPPORTED;
+  if (!make_piece_map(&mb, Btp, k, n, Cfg::NP, ldb_p, b_plane, BK, BN)) return BFX_EUNSUPPORTED;
+  TcArgs a;
+  a.M = static_cast<int>(m);
+  a.N = static_cast<int>(n);
+  a.K = static_cast<int>(k);
+  a.tiles_m = static_cast<int>(ceil_div(m, BM));
+  a.tiles_n = static_cast<int>(ceil_div(n, BN));
+  const int64_t tiles = static_cast<int64_t>(a.tiles_m) * a.tiles_n;
+  if (tiles > INT32_MAX) return BFX_EUNSUPPORTED;
+  a.num_tiles = static_cast<int>(tiles);
+  a.k_tiles = static_cast<int>(ceil_div(k, BK));
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.vec_c = (ldc % 4 == 0) && aligned(C, 16);
+  a.err = device_error_word();
+  if (!a.err) return BFX_ECUDA;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+      cudaSuccess)
+    return BFX_ECUDA;
+  const int sms = current_num_sms();
+  const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+  kern<<<grid, 192, Cfg::SMEM, s>>>(ma, mb, a);
+  return last_launch_status();
+}
+
+}  // namespace
+
+bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
+                                const uint16_t* Ap, int64_t lda_p, int64_t a_plane,
+                                const uint16_t* Btp, int64_t ldb_p, int64_t b_plane, float beta,
+                                float* C, int64_t ldc, cudaStream_t s) {
+  if (m == 0 || n == 0) return BFX_OK;
+  if (k == 0) return launch_scale(m, n, beta, C, ldc, s);
+  switch (mode) {
+    case BFX_X1:
+      return run_tc<1, 256, 64, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
+    case BFX_X3:
+      return run_tc<3, 256, 32, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
+    case BFX_X6:
+      return run_tc<6, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
+    case BFX_X9:
+      return run_tc<9, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
+    default:
+      return BFX_EINVAL;
+  }
+}
+
+}  // namespace bfx

@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the bf16xN split GEMM (Henry, Tang & Heinecke, Sec. IV-A / V).
+
+Workload (N = 1): FP32 A, B of 8192 x 8192 x 8192 with entries u * 2^e,
+u ~ U[-1, 1], e ~ U{-8..8} (seeded); one step = the whole GEMM path: split of
+A, transposed split of B, and the tcgen05 bf16x6 product with FP32 output.
+value = effective FP32 TFLOP/s = 2 m n k / step time, summed over ranks.
+Inputs (256 MiB each) and pieces (768 MiB) exceed the 126 MB L2, so no L2
+flush is needed between steps.
+
+Extra keys on the single JSON line: the other variants (bf16x3/x9, the
+16384 x 16384 x 256 tall-skinny shape, the FP32 SIMT baseline), the error on
+sampled rows against the FP64 oracle and the stated bound, the roofline of the
+dominant kernel, the CPU baseline (the oracle itself on a bounded row sample),
+clocks sampled during the timed region and the end-to-end number through the
+public API with host buffers.
+
+--impl reference times the CPU oracle (the only reference this paper has) on
+a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs its own independent GEMM of the same
+shape (weak scaling, no collective in the data path; a barrier brackets the
+timed region and the max time over ranks is used).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bf16xN GEMM eff. FP32 TFLOP/s at stated error; IR solves/s, p50/p99 latency"
+WORKLOAD = "split-BF16 GEMM at scale, 8192x8192x8192, u*2^e entries (e in [-8,8]), bf16x6"
+EPS = 2.0 ** -24
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["bfx", "reference"], default="bfx")
+    p.add_argument("--mode", type=int, default=6, choices=[1, 3, 6, 9])
+    p.add_argument("--m", type=int, default=8192)
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--k", type=int, default=8192)
+    p.add_argument("--quick", action="store_true",
+                   help="main measurement only (no variants, CPU baseline or e2e); for profiling")
+    p.add_argument("--cpu-rows", type=int, default=16, help="rows of the CPU-baseline sample")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d["bf16_tflops"], d["bf16_tflops_sustained"], "measured"
+    except Exception:
+        return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("gemm_tc.cu", "bfx_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1904_06376_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(mode, m, n, k):
+    """DRAM bytes per launch of the GEMM kernel from the committed ncu summary,
+    if it was taken on the current kernel source for this shape and mode."""
+    path = os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d["entries"][f"x{mode}_{m}x{n}x{k}"]
+        if e["kernel_hash"] != kernel_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The CPU oracle on the same workload: each step computes one 16 x 256
+    block of C (a bounded sample) with the oracle's FP32-FMA bf16xN model."""
+    if rank != 0:
+        return
+    import oracle
+    import bfx_inputs as bi
+
+    m, n, k, mode = args.m, args.n, args.k, args.mode
+    br, bc = 16, 256
+    A = bi.wide_range((m, k), 60)
+    B = bi.wide_range((k, n), 61)
+    oracle.lib()
+    rng = np.random.default_rng(5)
+
+    def one():
+        r0 = int(rng.integers(0, m - br + 1))
+        c0 = int(rng.integers(0, n - bc + 1))
+        oracle.gemm(mode, A[r0:r0 + br], np.ascontiguousarray(B[:, c0:c0 + bc]))
+
+    for _ in range(max(args.warmup, 0)):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    t = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = 2.0 * br * bc * k / t / 1e12
+    cores = min(br, oracle.num_threads())
+    sample = (f"one {br}x{bc} block of C per step from the {m}x{n}x{k} product, by the oracle's "
+              f"sequential FP32-FMA bf16x{mode} model")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": WORKLOAD.replace("bf16x6", f"bf16x{mode}"),
+                                        "m": m, "n": n, "k": k, "mode": f"x{mode}"},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- bfx arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import bfx_inputs as bi
+    import paper_1904_06376_b300 as bfx
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    m, n, k, mode = args.m, args.n, args.k, args.mode
+    npc = {1: 1, 3: 2, 6: 3, 9: 3}[mode]
+    Ah = torch.from_numpy(bi.wide_range((m, k), 60 + 2 * rank))
+    Bh = torch.from_numpy(bi.wide_range((k, n), 61 + 2 * rank))
+    A = Ah.to(dev)
+    B = Bh.to(dev)
+    C = torch.empty((m, n), dtype=torch.float32, device=dev)
+    kp = (k + 7) // 8 * 8
+    Ap = torch.empty((npc, m, kp), dtype=torch.int16, device=dev)
+    Bp = torch.empty((npc, n, kp), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        bfx.split(A, npc, out=[Ap[i][:, :k] for i in range(npc)])
+        bfx.split_transpose(B, npc, out=[Bp[i][:, :k] for i in range(npc)])
+        if ev is not None:
+            ev[1].record(stream)
+        bfx.gemm_presplit(mode, Ap, Bp, k, C)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    split_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    gemm_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    flops = 2.0 * m * n * k
+    value = world * flops / (ms * 1e-3) / 1e12
+    hbm, bf16_peak, bf16_sus, peak_src = peaks()
+    achieved = mode * flops / (gemm_ms * 1e-3) / 1e12
+    traffic = profiled_traffic(mode, m, n, k)
+    split_bytes = (m * k + k * n) * (4 + 2 * npc)
+    roof = {"kernel": f"gemm_tc_kernel<x{mode}>", "bound": "tensor", "achieved": achieved,
+            "peak": bf16_peak, "unit": "TFLOP/s", "frac": achieved / bf16_peak,
+            "peak_source": f"{peak_src} dense bf16 burst (MEASURED_PEAKS.json bf16_tflops)",
+            "algorithmic": f"{mode} bf16 products x 2mnk = {mode * flops:.4g} flop per launch",
+            "kernel_ms": gemm_ms, "traffic": traffic,
+            "split_pass": {"ms": split_ms, "bytes": split_bytes,
+                           "GB/s": split_bytes / (split_ms * 1e-3) / 1e9, "peak_GB/s": hbm,
+                           "frac": split_bytes / (split_ms * 1e-3) / 1e9 / hbm}}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x6->f32" if mode == 6 else f"bf16x{mode}->f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if mode == 6 else WORKLOAD.replace("bf16x6", f"bf16x{mode}"),
+                   "m": m, "n": n, "k": k, "mode": f"x{mode}", "global_batch": world,
+                   "l2": "inputs and pieces larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if args.quick or rank != 0:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---------------------------------------------------------- variants (rank 0)
+    def time_call(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    variants = {}
+    ws = torch.empty(bfx.gemm_workspace_size(9, m, n, k), dtype=torch.uint8, device=dev)
+    for md in (1, 3, 6, 9):
+        t = time_call(lambda: bfx.gemm_bf16xN(md, A, B, C, workspace=ws))
+        variants[f"x{md}_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
+    t = time_call(lambda: bfx.sgemm_simt(A, B, C), reps=2, warm=1)
+    variants[f"fp32_simt_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
+    ts = (16384, 16384, 256)
+    At = torch.from_numpy(bi.wide_range((ts[0], ts[2]), 70)).to(dev)
+    Bt = torch.from_numpy(bi.wide_range((ts[2], ts[1]), 71)).to(dev)
+    Ct = torch.empty((ts[0], ts[1]), device=dev)
+    wst = torch.empty(bfx.gemm_workspace_size(9, *ts), dtype=torch.uint8, device=dev)
+    fl_t = 2.0 * ts[0] * ts[1] * ts[2]
+    for md in (3, 6):
+        t = time_call(lambda: bfx.gemm_bf16xN(md, At, Bt, Ct, workspace=wst))
+        variants[f"x{md}_16384x16384x256"] = {"ms": t, "TFLOP/s": fl_t / (t * 1e-3) / 1e12}
+    t = time_call(lambda: bfx.sgemm_simt(At, Bt, Ct), reps=3, warm=1)
+    variants["fp32_simt_16384x16384x256"] = {"ms": t, "TFLOP/s": fl_t / (t * 1e-3) / 1e12}
+    del At, Bt, Ct, wst
+    line["variants"] = variants
+    line["speedup_vs_fp32_simt"] = variants[f"fp32_simt_{m}x{n}x{k}"]["ms"] / (gemm_ms + split_ms)
+
+    # ---------------------------------------------------------- end to end (host buffers)
+    Ahp = Ah.pin_memory()
+    Bhp = Bh.pin_memory()
+    Chp = torch.empty((m, n), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        A.copy_(Ahp, non_blocking=True)
+        B.copy_(Bhp, non_blocking=True)
+        bfx.gemm_bf16xN(mode, A, B, C, workspace=ws)
+        Chp.copy_(C, non_blocking=True)
+
+    te = time_call(e2e_step, reps=5, warm=1)
+    line["e2e"] = {"value": flops / (te * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": te,
+                   "h2d_bytes_per_step": 4 * (m * k + k * n), "d2h_bytes_per_step": 4 * m * n,
+                   "api": "paper_1904_06376_b300.gemm_bf16xN (C-ABI bfx_gemm_bf16xN) with pinned host buffers"}
+
+    # ---------------------------------------------------------- error + CPU baseline
+    import oracle
+
+    step()
+    torch.cuda.synchronize()
+    rows = np.sort(np.random.default_rng(7).choice(m, args.cpu_rows, replace=False)).astype(np.int64)
+    Cs = C[torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+    An, Bn = Ah.numpy(), Bh.numpy()
+    C64, Cabs = oracle.dgemm_rows(An, Bn, rows)
+    bound = 2 * max(k, 2) * EPS
+    ratio = float(np.max(np.abs(Cs - C64) / (bound * Cabs + 1e-38)))
+    relF = float(np.linalg.norm(Cs - C64) / np.linalg.norm(C64))
+    line["error"] = {"rows_checked": int(rows.size), "bound": "|C-C64| <= 2k 2^-24 (|A||B|) elementwise",
+                     "max_ratio_to_bound": ratio, "rel_frobenius_vs_fp64": relF,
+                     "within_bound": ratio <= 1.0}
+    t0c = time.perf_counter()
+    oracle.gemm(mode, An[rows], Bn)
+    tc = time.perf_counter() - t0c
+    cores = min(int(rows.size), oracle.num_threads())
+    line["cpu_baseline"] = {"value": 2.0 * rows.size * n * k / tc / 1e12, "unit": "TFLOP/s",
+                            "cores": cores, "kind": "oracle", "seconds": tc,
+                            "sample": f"{rows.size} rows of the {m}x{n}x{k} product, the oracle's "
+                                      f"sequential FP32-FMA bf16x{mode} model (split of B included)"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -133,6 +133,28 @@ BFX_API bfx_status bfx_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_
                                      const uint16_t* d_Btp, int64_t ldb_p, int64_t b_plane,
                                      float beta, float* d_C, int64_t ldc, bfx_stream stream);
 
+/* Workspace-free variant of bfx_gemm_bf16xN (same arguments minus the
+ * workspace, same result).  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, e.g. a plugin inside a host
+ * application that owns all device memory through its own pool and forbids
+ * libraries from calling cudaMalloc, or a latency-critical loop where an
+ * allocation is not acceptable.  The bfloat16 pieces go to a fixed 32 MiB
+ * device array inside the library (reserved on every device that loads it,
+ * held until the process exits); the call allocates nothing.  Limit: the
+ * pieces need 2 * npieces * (round_up(m*kp,128) + round_up(n*kp,128)) bytes,
+ * kp = k rounded up to 8, npieces = 1, 2, 3, 3 for X1, X3, X6, X9 (e.g. x6
+ * fits m = n = k = 1536); larger problems return BFX_ENOMEM.  mode must be
+ * X1..X9 (BFX_EINVAL otherwise).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads on the same device) race on it and must be serialised.  Other
+ * errors as bfx_gemm_bf16xN. */
+BFX_API bfx_status bfx_gemm_bf16xN_noalloc(bfx_mode mode, int64_t m, int64_t n, int64_t k,
+                                           float alpha, const float* d_A, int64_t lda,
+                                           const float* d_B, int64_t ldb, float beta, float* d_C,
+                                           int64_t ldc, bfx_stream stream);
+
 /* Plain FP32 SIMT GEMM (the Sec. II-C reference computation on CUDA cores;
  * the same-GPU baseline).  Each C element is accumulated with one FMA per k
  * in increasing k, then t = alpha*Z, C = beta == 0 ? t : fma(beta, C, t).

@@ -163,6 +163,77 @@ BFX_API bfx_status bfx_sgemm_simt(int64_t m, int64_t n, int64_t k, float alpha, 
                                   int64_t lda, const float* d_B, int64_t ldb, float beta,
                                   float* d_C, int64_t ldc, bfx_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Inner product x^T y of two FP32 vectors of length n (contiguous) by the
+ * mode's bfloat16 products (Sec. II-B..II-G): each element pair is split,
+ * every kept product is accumulated with FMA into the FP32 accumulator of its
+ * level i+j, levels are reduced in a fixed tree and combined smallest first.
+ * BFX_FP32 accumulates plain FMAs (Sec. II-C).  The FP32 result goes to
+ * device memory d_result.  Workspace: d_ws (16-byte aligned) of at least
+ * bfx_dot_workspace_size() bytes (per-block partial sums; depends on the
+ * current device's SM count).  Errors: BFX_EINVAL, BFX_ENOMEM. */
+BFX_API size_t bfx_dot_workspace_size(void);
+BFX_API bfx_status bfx_dot_bf16xN(bfx_mode mode, int64_t n, const float* d_x, const float* d_y,
+                                  float* d_result, void* d_ws, size_t ws_bytes, bfx_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * LU with partial pivoting (LAPACK xGETRF semantics) of the n x n FP32 matrix
+ * d_A (row-major, lda), in place: unit-lower L below the diagonal, U on and
+ * above it.  Blocked right-looking with block width nb (0 = 64, at most 128):
+ * the panel (warp-shuffle argmax pivot search, first row on ties), the row
+ * swaps and the unit-lower block solve are FP32; the trailing update
+ * A22 <- A22 - L21 U12 is the mode's bf16xN product on the tensor cores
+ * (Sec. IV-A, "SGETRF based on triplets"), or the FP32 SIMT GEMM for
+ * BFX_FP32.  d_ipiv[j] (int32, 0-based) is the row swapped with row j at
+ * step j.  d_info (device int32) receives 0 or the 1-based index of the first
+ * exactly zero pivot; the factorisation completes either way.  Workspace:
+ * bfx_lu_workspace_size(mode, n, nb) bytes, 256-byte aligned (0 for
+ * BFX_FP32).  Errors: BFX_EINVAL, BFX_ENOMEM, BFX_EUNSUPPORTED. */
+BFX_API size_t bfx_lu_workspace_size(bfx_mode mode, int64_t n, int nb);
+BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, int64_t lda,
+                                 int32_t* d_ipiv, int32_t* d_info, void* d_ws, size_t ws_bytes,
+                                 bfx_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Solve A x = b by residual-form iterative refinement (Sec. III): A32 is
+ * factored by bfx_lu_bf16xN (FP32 factors, bf16xN trailing updates); then
+ * r = b - A32 x in FP64, d = U^-1 L^-1 P r in FP64 arithmetic with the FP32
+ * factors, x += d in FP64.  A column converges when |d|_inf <= tol |x|_inf,
+ * or when its corrections stop shrinking (|d_i| >= stall |d_{i-1}|) with
+ * normwise backward error |r|_inf/(|A|_inf |x|_inf + |b|_inf) <= tol_b.
+ * With escalate != 0, columns that stop unconverged are refined further after
+ * refactoring with more products (x1 -> x3 -> x6).
+ * d_A: n x n FP32 (lda); d_b: n x nrhs FP64 (ldb); d_x: n x nrhs FP64 (ldx,
+ * output).  h_params may be NULL (max_iter 50, tol 2^-53, tol_b sqrt(n) 2^-53,
+ * stall 0.5, escalate 1, nb 64).  The call is synchronous: it returns after
+ * the refinement has finished and fills *h_result (host).  Returns BFX_OK
+ * when every column converged, BFX_NOT_CONVERGED otherwise (x holds the last
+ * iterate), BFX_SINGULAR on an exactly zero pivot (h_result->info > 0), and
+ * the usual argument / workspace errors.  Workspace:
+ * bfx_solve_ir_workspace_size(mode, n, nrhs, nb) bytes, 256-byte aligned. */
+typedef struct bfx_ir_params {
+  int max_iter;
+  double tol;
+  double tol_b;   /* < 0: sqrt(n) * 2^-53 */
+  double stall;
+  int escalate;
+  int nb;
+} bfx_ir_params;
+typedef struct bfx_ir_result {
+  int32_t info;             /* first zero pivot (1-based) or 0 */
+  int32_t mode_used;        /* mode of the final factorisation */
+  int32_t converged;        /* 1 if every column converged */
+  int32_t iters;            /* most corrections applied to any column */
+  int32_t refactorizations; /* escalations performed */
+  double berr;              /* largest normwise backward error over the columns */
+} bfx_ir_result;
+BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs, int nb);
+BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
+                                int64_t lda, const double* d_b, int64_t ldb, double* d_x,
+                                int64_t ldx, const bfx_ir_params* h_params,
+                                bfx_ir_result* h_result, void* d_ws, size_t ws_bytes,
+                                bfx_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,10 +15,13 @@ from ._bfx import (  # noqa: F401
     BFX_X9,
     BfxError,
     device_error,
+    dot_bf16xN,
     gemm_bf16xN,
     gemm_presplit,
     gemm_workspace_size,
     lib,
+    lu_bf16xN,
+    solve_ir,
     library_path,
     num_sms,
     sgemm_simt,

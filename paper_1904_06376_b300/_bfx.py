@@ -57,6 +57,12 @@ def lib() -> ctypes.CDLL:
         "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
         "bfx_gemm_presplit": (i32, [i32, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, vp]),
         "bfx_sgemm_simt": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
+        "bfx_dot_workspace_size": (sz, []),
+        "bfx_lu_workspace_size": (sz, [i32, i64, i32]),
+        "bfx_lu_bf16xN": (i32, [i32, i64, i32, vp, i64, vp, vp, vp, sz, vp]),
+        "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, i32]),
+        "bfx_solve_ir": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
+        "bfx_dot_bf16xN": (i32, [i32, i64, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -185,3 +191,75 @@ def sgemm_simt(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None, alpha: 
     _check("bfx_sgemm_simt", lib().bfx_sgemm_simt(m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
                                                  _ptr(C), ldc, _stream(stream)))
     return C
+
+
+def dot_bf16xN(mode: int, x: torch.Tensor, y: torch.Tensor, out: torch.Tensor = None,
+               workspace: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """x^T y by the mode's bfloat16 products; returns a 1-element device tensor."""
+    assert x.is_contiguous() and y.is_contiguous() and x.numel() == y.numel()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float32, device=x.device)
+    wsb = int(lib().bfx_dot_workspace_size())
+    if workspace is None or workspace.numel() * workspace.element_size() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=x.device)
+    _check("bfx_dot_bf16xN", lib().bfx_dot_bf16xN(mode, x.numel(), _ptr(x), _ptr(y), _ptr(out),
+                                                 _ptr(workspace), wsb, _stream(stream)))
+    return out
+
+
+class IrParams(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("tol_b", ctypes.c_double),
+                ("stall", ctypes.c_double), ("escalate", ctypes.c_int), ("nb", ctypes.c_int)]
+
+
+class IrResult(ctypes.Structure):
+    _fields_ = [("info", ctypes.c_int32), ("mode_used", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("refactorizations", ctypes.c_int32), ("berr", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lu_bf16xN(mode: int, A: torch.Tensor, nb: int = 64, ipiv: torch.Tensor = None,
+              info: torch.Tensor = None, workspace: torch.Tensor = None, stream=None):
+    """In-place LU with partial pivoting (bf16xN trailing update).  Returns (A, ipiv, info)."""
+    n = A.shape[0]
+    assert A.shape == (n, n) and A.dtype == torch.float32
+    if ipiv is None:
+        ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+    wsb = int(lib().bfx_lu_workspace_size(mode, n, nb))
+    if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    _check("bfx_lu_bf16xN", lib().bfx_lu_bf16xN(mode, n, nb, _ptr(A), A.stride(0) if n else 1,
+                                               _ptr(ipiv), _ptr(info), _ptr(workspace) if wsb else None,
+                                               wsb, _stream(stream)))
+    return A, ipiv, info
+
+
+def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None, max_iter: int = 50,
+             tol: float = 2.0 ** -53, tol_b: float = -1.0, stall: float = 0.5, escalate: bool = True,
+             nb: int = 64, workspace: torch.Tensor = None, stream=None, raise_on_status: bool = False):
+    """Solve A x = b (A FP32 n x n, b FP64 n x nrhs) by residual-form refinement.
+
+    Returns (x, result dict, status code).  Synchronous."""
+    n = A.shape[0]
+    if b.dim() == 1:
+        b = b[:, None]
+    nrhs = b.shape[1]
+    if x is None:
+        x = torch.empty((n, nrhs), dtype=torch.float64, device=A.device)
+    wsb = int(lib().bfx_solve_ir_workspace_size(mode, n, nrhs, nb))
+    if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    p = IrParams(max_iter, tol, tol_b, stall, int(bool(escalate)), nb)
+    r = IrResult()
+    code = lib().bfx_solve_ir(mode, n, nrhs, _ptr(A), A.stride(0) if n else 1, _ptr(b),
+                              b.stride(0) if n else 1, _ptr(x), x.stride(0) if n else 1,
+                              ctypes.byref(p), ctypes.byref(r), _ptr(workspace) if wsb else None, wsb,
+                              _stream(stream))
+    if code not in (0, 5, 6) or (raise_on_status and code != 0):
+        _check("bfx_solve_ir", code)
+    return x, r.as_dict(), code

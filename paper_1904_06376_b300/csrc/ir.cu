@@ -1,0 +1,468 @@
+// Residual-form iterative refinement (Sec. III of the paper).
+//
+//   factor   A32 = P L U with the bf16xN-update LU (lu.cu), FP32 factors;
+//   x0       = U^-1 L^-1 P b
+//   repeat   r = b - A32 x          (FP64, A32 widened exactly)
+//            d = U^-1 L^-1 P r      (FP64 arithmetic with the FP32 factors:
+//                                    "do the solve in a higher precision")
+//            x = x + d              (FP64)
+// The paper's r = A x - b with x + y is read as r = b - A x, x + d.  A column
+// stops converged when |d|_inf <= tol |x|_inf; it stops when the corrections no
+// longer shrink (|d_i| >= stall |d_{i-1}|) and then counts as converged if the
+// normwise backward error |r|_inf / (|A|_inf |x|_inf + |b|_inf) <= tol_b.
+// Escalation (an addition of this library): columns that stop without
+// converging are refined again after refactoring with more products
+// (x1 -> x3 -> x6), continuing from the current x.
+//
+// Everything runs in this library's kernels; the host only loops over
+// iterations and reads the per-column norms (a few doubles) to decide.
+// Triangular solves: row blocks of 64; for each block one launch in which
+// every CTA solves the 64 x 64 diagonal triangle (identically) and then
+// updates its own row block, so the FP64 work of each step is spread over
+// all SMs.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "bfx_internal.cuh"
+
+namespace bfx {
+
+bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, int32_t* ipiv,
+                     int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t lu_workspace_bytes(bfx_mode mode, int64_t n, int nb);
+
+namespace {
+
+constexpr int TB = 64;         // triangular-solve row block
+constexpr int MAXR = 16;       // right-hand sides handled per pass
+constexpr int SOLVE_THREADS = 256;
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns (NaN sorts above Inf)
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
+}
+
+// perm[i] = source row of row i of P*v, from sequential swaps ipiv.
+__global__ void ir_perm_kernel(const int32_t* __restrict__ ipiv, int n, int32_t* __restrict__ perm,
+                               bool use_smem) {
+  extern __shared__ int32_t sp[];
+  int32_t* p = use_smem ? sp : perm;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < n; ++j) {
+      const int q = ipiv[j];
+      if (q != j) {
+        const int32_t t = p[j];
+        p[j] = p[q];
+        p[q] = t;
+      }
+    }
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sp[i];
+}
+
+// out[c] = max_i |M[i, c]| for c < ncols (out must start at 0).
+__global__ void ir_colmax_kernel(const double* __restrict__ M, int64_t ld, int64_t n, int ncols,
+                                 double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * ncols;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / ncols;
+    const int c = static_cast<int>(e - i * ncols);
+    atomic_max_nonneg(&out[c], fabs(M[i * ld + c]));
+  }
+}
+
+// out[0] = |A|_inf = max_i sum_l |A[i, l]|, FP64 (out must start at 0).  Warp a row.
+__global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
+                                double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const float* a = A + row * lda;
+  double s = 0.0;
+  for (int l = lane; l < n; l += 32) s += fabs(static_cast<double>(a[l]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) atomic_max_nonneg(out, s);
+}
+
+// r = b - A x (FP64) for columns c0 .. c0+nc (nc <= MAXR); warp a row.
+// If rn != nullptr, rn[c] = max |r[:, c]| (must start at 0).
+__global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
+                                   const double* __restrict__ b, int64_t ldb,
+                                   const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
+                                   int64_t ldr, int c0, int nc, double* __restrict__ rn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const float* a = A + row * lda;
+  double acc[MAXR];
+#pragma unroll
+  for (int c = 0; c < MAXR; ++c) acc[c] = 0.0;
+  for (int l = lane; l < n; l += 32) {
+    const double al = static_cast<double>(a[l]);
+    const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
+#pragma unroll
+    for (int c = 0; c < MAXR; ++c)
+      if (c < nc) acc[c] = fma(al, xl[c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < MAXR; ++c) {
+    double v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    acc[c] = v;
+  }
+  if (lane < nc) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < MAXR; ++c)
+      if (c == lane) s = acc[c];
+    const double v = b[row * ldb + c0 + lane] - s;
+    r[row * ldr + c0 + lane] = v;
+    if (rn) atomic_max_nonneg(&rn[c0 + lane], fabs(v));
+  }
+}
+
+// d[i, c] = r[perm[i], c]
+__global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
+                                 const int32_t* __restrict__ perm, int64_t n, int nrhs,
+                                 double* __restrict__ d, int64_t ldd) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = static_cast<int>(e - i * nrhs);
+    d[i * ldd + c] = r[static_cast<int64_t>(perm[i]) * ldr + c];
+  }
+}
+
+// One block step of L y = v (unit lower) or U y = v (upper) for the diagonal
+// block [b0, b0+bs).  Every CTA reads the (already updated) diagonal rows of v
+// and solves the block triangle; CTA 0 writes the solved rows to `out`, CTA
+// k > 0 subtracts their contribution from row block k of the rows still to be
+// solved (below for L, above for U) in v.  The diagonal rows of v are only
+// read in this launch, so the CTAs do not race.
+template <bool LOWER>
+__global__ void __launch_bounds__(SOLVE_THREADS)
+    ir_trsv_step_kernel(const float* __restrict__ F, int64_t ldf, int n, int b0, int bs,
+                        double* __restrict__ v, double* __restrict__ out, int64_t ldv, int nrhs) {
+  __shared__ double Ft[TB][TB + 1];
+  __shared__ double y[TB][MAXR];
+  const int t = threadIdx.x;
+  for (int e = t; e < bs * bs; e += SOLVE_THREADS) {
+    const int i = e / bs, l = e - i * bs;
+    Ft[i][l] = static_cast<double>(F[static_cast<int64_t>(b0 + i) * ldf + b0 + l]);
+  }
+  for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
+    const int nc = min(MAXR, nrhs - c0);
+    for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+      const int i = e / nc, c = e - i * nc;
+      y[i][c] = v[static_cast<int64_t>(b0 + i) * ldv + c0 + c];
+    }
+    __syncthreads();
+    // triangle: column-oriented elimination inside the block
+    for (int jj = 0; jj < bs; ++jj) {
+      const int j = LOWER ? jj : bs - 1 - jj;
+      if (!LOWER) {
+        if (t < nc) y[j][t] = y[j][t] / Ft[j][j];
+        __syncthreads();
+      }
+      for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+        const int i = e / nc, c = e - i * nc;
+        if (LOWER ? (i > j) : (i < j)) y[i][c] = fma(-Ft[i][j], y[j][c], y[i][c]);
+      }
+      __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+      for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+        const int i = e / nc, c = e - i * nc;
+        out[static_cast<int64_t>(b0 + i) * ldv + c0 + c] = y[i][c];
+      }
+    } else {
+      // rows of this CTA's block: below (L) or above (U) the diagonal block
+      const int rs = LOWER ? b0 + bs + (blockIdx.x - 1) * TB : b0 - blockIdx.x * TB;
+      const int re = LOWER ? min(rs + TB, n) : rs + TB;
+      for (int e = t; e < (re - rs) * nc; e += SOLVE_THREADS) {
+        const int i = rs + e / nc, c = e % nc;
+        const float* fr = F + static_cast<int64_t>(i) * ldf + b0;
+        double s = v[static_cast<int64_t>(i) * ldv + c0 + c];
+        for (int l = 0; l < bs; ++l) s = fma(-static_cast<double>(fr[l]), y[l][c], s);
+        v[static_cast<int64_t>(i) * ldv + c0 + c] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// x += d on active columns; dn[c] = max|d|, xn[c] = max|x| (must start at 0).
+__global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
+                                 int64_t ldd, int64_t n, int nrhs, const int32_t* __restrict__ active,
+                                 double* __restrict__ dn, double* __restrict__ xn) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = static_cast<int>(e - i * nrhs);
+    if (!active[c]) continue;
+    const double dv = d[i * ldd + c];
+    const double xv = x[i * ldx + c] + dv;
+    x[i * ldx + c] = xv;
+    atomic_max_nonneg(&dn[c], fabs(dv));
+    atomic_max_nonneg(&xn[c], fabs(xv));
+  }
+}
+
+int grid_elems(int64_t work) {
+  const int sms = current_num_sms() > 0 ? current_num_sms() : 148;
+  const int64_t g = ceil_div(work, 256);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8LL * sms)));
+}
+
+struct IrWs {
+  float* LU;
+  int32_t* ipiv;
+  int32_t* perm;
+  int32_t* info;
+  int32_t* active;
+  double* r;
+  double* d;
+  double* norms;  // [0] anorm, then per column: bn, dn, xn, rn
+  void* luws;
+  size_t luws_bytes;
+  size_t total;
+};
+
+IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
+  IrWs w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return static_cast<char*>(base) + o;
+  };
+  w.LU = reinterpret_cast<float*>(take(sizeof(float) * n * n));
+  w.ipiv = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  w.perm = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  w.info = reinterpret_cast<int32_t*>(take(sizeof(int32_t)));
+  w.active = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * nrhs));
+  w.r = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
+  w.d = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
+  w.norms = reinterpret_cast<double*>(take(sizeof(double) * (1 + 4 * nrhs)));
+  size_t lub = 0;
+  for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X9})
+    if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
+  w.luws_bytes = lub;
+  w.luws = lub ? take(lub) : nullptr;
+  w.total = off;
+  return w;
+}
+
+// d <- U^-1 L^-1 P r (all columns).  r is consumed: the forward pass works in
+// place on d (gathered P r) and writes its solution to r; the backward pass
+// works in place on r and writes the correction to d.
+bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
+  const int N = static_cast<int>(n);
+  ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs);
+  const int nblk = static_cast<int>(ceil_div(n, TB));
+  for (int b = 0; b < nblk; ++b) {  // forward, unit lower
+    const int b0 = b * TB, bs = std::min(TB, N - b0);
+    const int below = static_cast<int>(ceil_div(N - b0 - bs, TB));
+    ir_trsv_step_kernel<true><<<1 + below, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.d, w.r,
+                                                                   nrhs, nrhs);
+  }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward, upper
+    const int b0 = b * TB, bs = std::min(TB, N - b0);
+    const int above = b0 / TB;
+    ir_trsv_step_kernel<false><<<1 + above, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.r, w.d,
+                                                                    nrhs, nrhs);
+  }
+  return last_launch_status();
+}
+
+bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int nrhs,
+                    const double* b, int64_t ldb, const double* x, int64_t ldx, double* rn,
+                    cudaStream_t s) {
+  const unsigned blocks = static_cast<unsigned>(ceil_div(n * 32, 256));
+  for (int c0 = 0; c0 < nrhs; c0 += MAXR)
+    ir_residual_kernel<<<blocks, 256, 0, s>>>(A, lda, static_cast<int>(n), b, ldb, x, ldx, w.r,
+                                              nrhs, c0, std::min(MAXR, nrhs - c0), rn);
+  return last_launch_status();
+}
+
+}  // namespace
+}  // namespace bfx
+
+using namespace bfx;
+
+extern "C" {
+
+BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
+  if (n <= 0 || nrhs <= 0) return 0;
+  if (nb <= 0) nb = 64;
+  return carve(nullptr, mode, n, nrhs, nb).total;
+}
+
+BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
+                                int64_t lda, const double* d_b, int64_t ldb, double* d_x,
+                                int64_t ldx, const bfx_ir_params* h_params,
+                                bfx_ir_result* h_result, void* d_ws, size_t ws_bytes,
+                                bfx_stream stream) {
+  if (mode != BFX_FP32 && mode_pieces(mode) == 0) return BFX_EINVAL;
+  if (n < 0 || nrhs < 0 || !h_result) return BFX_EINVAL;
+  bfx_ir_result res{};
+  res.mode_used = mode;
+  *h_result = res;
+  if (n == 0 || nrhs == 0) {
+    h_result->converged = 1;
+    return BFX_OK;
+  }
+  if (!d_A || !d_b || !d_x || lda < n || ldb < nrhs || ldx < nrhs) return BFX_EINVAL;
+  if (n >= (1 << 30) || nrhs > (1 << 20)) return BFX_EUNSUPPORTED;
+  bfx_ir_params p{50, 1.1102230246251565e-16, -1.0, 0.5, 1, 64};
+  if (h_params) p = *h_params;
+  if (p.nb <= 0) p.nb = 64;
+  if (p.nb > 128 || p.max_iter < 0) return BFX_EINVAL;
+  if (p.tol_b < 0) p.tol_b = 1.1102230246251565e-16 * std::sqrt(static_cast<double>(n));
+  if (mode != BFX_FP32 && !is_sm103()) return BFX_EUNSUPPORTED;
+  IrWs w = carve(d_ws, mode, n, nrhs, p.nb);
+  if (!d_ws || ws_bytes < w.total || !aligned(d_ws, 256)) return BFX_ENOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int R = static_cast<int>(nrhs);
+  const int N = static_cast<int>(n);
+  double* anorm = w.norms;
+  double* bn = w.norms + 1;
+  double* dn = bn + R;
+  double* xn = dn + R;
+  double* rn = xn + R;
+  std::vector<double> h(1 + 4 * static_cast<size_t>(R));
+  std::vector<int32_t> act(R, 1), conv(R, 0), iters(R, 0), stalled(R, 0);
+  std::vector<double> dprev(R, 0.0);
+
+  // |A|_inf and |b|_inf once
+  if (cudaMemsetAsync(w.norms, 0, sizeof(double) * (1 + 4 * R), s) != cudaSuccess) return BFX_ECUDA;
+  ir_anorm_kernel<<<static_cast<unsigned>(ceil_div(n * 32, 256)), 256, 0, s>>>(d_A, lda, N, anorm);
+  // b may have ldb > nrhs: column max over the first nrhs columns
+  ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_b, ldb, n, R, bn);
+
+  bfx_mode cur = mode;
+  bool first = true;
+  bfx_status st = BFX_OK;
+  for (;;) {
+    // ---- factor (again, after an escalation)
+    if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n, n,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return BFX_ECUDA;
+    st = lu_factor(cur, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s);
+    if (st != BFX_OK) return st;
+    int32_t info = 0;
+    if (cudaMemcpyAsync(&info, w.info, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return BFX_ECUDA;
+    h_result->info = info;
+    if (info != 0) return BFX_SINGULAR;
+    const bool sm = n <= 12288;  // permutation fits the default 48 KB of shared memory
+    ir_perm_kernel<<<1, 1024, sm ? sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+    if (cudaMemcpyAsync(w.active, act.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return BFX_ECUDA;
+    if (first) {
+      // x0 = LU^-1 b: r <- b, solve, x <- d
+      if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R, n,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return BFX_ECUDA;
+      if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
+      if (cudaMemcpy2DAsync(d_x, sizeof(double) * ldx, w.d, sizeof(double) * R, sizeof(double) * R, n,
+                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return BFX_ECUDA;
+      if (cudaMemsetAsync(xn, 0, sizeof(double) * R, s) != cudaSuccess) return BFX_ECUDA;
+      ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
+      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return BFX_ECUDA;
+      for (int c = 0; c < R; ++c) dprev[c] = h[1 + 2 * R + c];  // |x0|
+      first = false;
+    } else {
+      for (int c = 0; c < R; ++c) dprev[c] = INFINITY;  // fresh factors: no stall on step one
+    }
+    // ---- refinement loop
+    for (int it = 0; it < p.max_iter; ++it) {
+      bool any = false;
+      for (int c = 0; c < R; ++c) any = any || act[c];
+      if (!any) break;
+      if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s)) != BFX_OK) return st;
+      if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
+      if (cudaMemsetAsync(dn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
+      ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn);
+      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return BFX_ECUDA;
+      bool changed = false;
+      for (int c = 0; c < R; ++c) {
+        if (!act[c]) continue;
+        const double d_c = h[1 + R + c], x_c = h[1 + 2 * R + c];
+        ++iters[c];
+        if (!(d_c == d_c) || !(x_c == x_c)) {  // NaN: diverged
+          act[c] = 0;
+          changed = true;
+        } else if (d_c <= p.tol * x_c) {
+          act[c] = 0;
+          conv[c] = 1;
+          changed = true;
+        } else if (d_c >= p.stall * dprev[c]) {
+          act[c] = 0;
+          stalled[c] = 1;
+          changed = true;
+        } else {
+          dprev[c] = d_c;
+        }
+      }
+      if (changed &&
+          cudaMemcpyAsync(w.active, act.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, s) !=
+              cudaSuccess)
+        return BFX_ECUDA;
+    }
+    // ---- backward error of every column
+    if (cudaMemsetAsync(xn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
+    ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
+    if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, rn, s)) != BFX_OK) return st;
+    if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return BFX_ECUDA;
+    double berr_max = 0.0;
+    bool all = true;
+    for (int c = 0; c < R; ++c) {
+      const double den = h[0] * h[1 + 2 * R + c] + h[1 + c];
+      double be = den > 0 ? h[1 + 3 * R + c] / den : 0.0;
+      if (!(be == be)) be = INFINITY;
+      if (!conv[c] && stalled[c] && be <= p.tol_b) conv[c] = 1;
+      berr_max = std::max(berr_max, be);
+      all = all && conv[c];
+    }
+    h_result->berr = berr_max;
+    int itmax = 0;
+    for (int c = 0; c < R; ++c) itmax = std::max(itmax, iters[c]);
+    h_result->iters = itmax;
+    h_result->converged = all ? 1 : 0;
+    h_result->mode_used = cur;
+    if (all) return BFX_OK;
+    // ---- escalate: refactor with more products, refine the unconverged columns
+    bfx_mode next = cur;
+    if (cur == BFX_X1) next = BFX_X3;
+    else if (cur == BFX_X3) next = BFX_X6;
+    if (!p.escalate || next == cur) return BFX_NOT_CONVERGED;
+    cur = next;
+    h_result->refactorizations += 1;
+    for (int c = 0; c < R; ++c) {
+      act[c] = conv[c] ? 0 : 1;
+      stalled[c] = 0;
+    }
+  }
+}
+
+}  // extern "C"

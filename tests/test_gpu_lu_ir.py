@@ -1,0 +1,104 @@
+"""Device LU (bf16xN trailing update) and residual-form refinement against
+the oracle (Sec. III, IV-A, IV-B)."""
+import numpy as np
+import pytest
+import torch
+
+import bfx_inputs as bi
+
+pytestmark = pytest.mark.gpu
+
+
+def _apply_pivots(A, ipiv):
+    PA = np.array(A, dtype=np.float64, copy=True)
+    for j, p in enumerate(ipiv):
+        if p != j:
+            PA[[j, p]] = PA[[p, j]]
+    return PA
+
+
+def _lu_gpu(bfx, mode, A, nb):
+    Ad = torch.from_numpy(A.copy()).cuda()
+    _, ipiv, info = bfx.lu_bf16xN(mode, Ad, nb=nb)
+    return Ad.cpu().numpy(), ipiv.cpu().numpy()[: A.shape[0]], int(info.item())
+
+
+@pytest.mark.parametrize("n,nb", [(1, 64), (50, 16), (200, 64), (333, 32), (515, 128)])
+def test_lu_fp32_bit_exact(bfx, orc, n, nb):
+    """The FP32 path performs the oracle's FP32 LU operation for operation."""
+    A = bi.uniform_pm1((n, n), n)
+    LU, ipiv, info = _lu_gpu(bfx, 0, A, nb)
+    LUo, po, io = orc.lu(0, A, nb)
+    assert info == io == 0
+    assert np.array_equal(ipiv, po)
+    assert np.array_equal(LU, LUo)
+
+
+@pytest.mark.parametrize("mode", [3, 6, 9])
+@pytest.mark.parametrize("n,nb", [(200, 64), (333, 32), (700, 64)])
+def test_lu_bf16xn_vs_oracle(bfx, orc, mode, n, nb):
+    """Same pivots as the oracle's bf16xN LU (random matrices: well separated
+    pivots), factors within the tolerance, and the LU backward error bound."""
+    A = bi.uniform_pm1((n, n), 7 * n + mode)
+    LU, ipiv, info = _lu_gpu(bfx, mode, A, nb)
+    LUo, po, io = orc.lu(mode, A, nb)
+    assert info == io == 0
+    assert np.array_equal(ipiv, po)
+    u = 3 * 2.0 ** -16 if mode == 3 else 2.0 ** -24
+    L = np.tril(LU.astype(np.float64), -1) + np.eye(n)
+    U = np.triu(LU.astype(np.float64))
+    E = _apply_pivots(A, ipiv) - L @ U
+    assert np.all(np.abs(E) <= 2 * n * u * (np.abs(L) @ np.abs(U)))
+    scale = np.max(np.abs(LUo))
+    assert np.max(np.abs(LU - LUo)) <= 64 * n * u * scale
+
+
+def test_lu_singular_info(bfx, orc):
+    A = bi.uniform_pm1((100, 100), 9)
+    A[:, 37] = 0.0
+    for mode in (0, 3):
+        _, _, info = _lu_gpu(bfx, mode, A, 32)
+        assert info == 38
+
+
+@pytest.mark.parametrize("mode", [0, 3, 6])
+@pytest.mark.parametrize("kappa", [1e1, 1e4])
+def test_solve_ir_vs_oracle(bfx, orc, mode, kappa):
+    """n = 50 (Sec. IV-B) and a larger system: converged, solution within 10x
+    the FP64 LU error of x_true, and element by element close to the oracle's
+    refinement with the same factors' precision."""
+    for n, seed in ((50, 1), (300, 2)):
+        P = bi.svd_system(n, kappa, seed, nrhs=2)
+        A = torch.from_numpy(P.A32).cuda()
+        b = torch.from_numpy(P.b).cuda()
+        x, res, code = bfx.solve_ir(mode, A, b, nb=32, escalate=False)
+        assert code == 0 and res["converged"] == 1, res
+        x = x.cpu().numpy()
+        xd, _ = orc.dgesv(P.A32, P.b)
+        fe = np.max(np.abs(x - P.x_true)) / np.max(np.abs(P.x_true))
+        fe64 = np.max(np.abs(xd - P.x_true)) / np.max(np.abs(P.x_true))
+        assert fe <= 10 * fe64 + 1e-15, (fe, fe64)
+        xo, it_o, conv_o, _, _ = orc.lu_solve_ir(mode, P.A32, P.b, nb=32)
+        assert all(conv_o)
+        assert np.max(np.abs(x - xo)) <= 10 * kappa * 2.0 ** -53 * np.max(np.abs(xo)) * n
+
+
+def test_solve_ir_escalates_x3_at_high_condition(bfx, orc):
+    """cond 1e6 is beyond x3-factor refinement; escalation to x6 converges."""
+    P = bi.svd_system(256, 1e6, 3)
+    A = torch.from_numpy(P.A32).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    x, res, code = bfx.solve_ir(3, A, b, nb=32, escalate=True)
+    assert code == 0 and res["converged"] == 1
+    xd, _ = orc.dgesv(P.A32, P.b)
+    fe = np.max(np.abs(x.cpu().numpy() - P.x_true)) / np.max(np.abs(P.x_true))
+    fe64 = np.max(np.abs(xd - P.x_true)) / np.max(np.abs(P.x_true))
+    assert fe <= 10 * fe64
+
+
+def test_solve_ir_singular(bfx):
+    A = torch.eye(8, device="cuda")
+    A[3, 3] = 0.0
+    b = torch.ones((8, 1), dtype=torch.float64, device="cuda")
+    x, res, code = bfx.solve_ir(3, A, b)
+    assert code == 5 and res["info"] == 4

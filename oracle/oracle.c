@@ -393,50 +393,73 @@ void orc_dgetrs(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const in
   }
 }
 
-/* LU of an FP32 matrix with the combined type of Sec. IV-A (R12): blocked
- * right-looking with block width nb; the panel (unblocked, partial pivoting,
- * division by the pivot, FMA rank-1 updates) and the unit-lower block solve
- * U12 = L11^-1 A12 are FP32; the trailing update A22 <- A22 - L21 U12 is the
- * mode's product (mode 0: the plain FP32 FMA product of Sec. II-C). */
+/* LU of an FP32 matrix with the combined type of Sec. IV-A (R12), blocked
+ * like LAPACK's xGETRF (the routine the paper compares with): block columns
+ * of width nb; inside a block column, the panel is itself blocked in tiles of
+ * w columns (w = 8):
+ *   tile    unblocked LU of the tile columns, partial pivoting (first row of
+ *           the largest |a|), the whole row swapped, division by the pivot,
+ *           FMA rank-1 updates of the remaining tile columns;
+ *   rest of the block column: U rows of the tile by forward substitution with
+ *           the tile's unit lower triangle, then the rows below updated by
+ *           a <- fma(-l_rk, u_kc, a) for k over the tile columns in order;
+ * then U12 = L11^-1 A12 (unit lower, FP32 FMA, row by row) and the trailing
+ * update A22 <- A22 - L21 U12 as the mode's product (mode 0: the plain FP32
+ * FMA product of Sec. II-C) with alpha = -1, beta = 1. */
 int orc_lu(int mode, int64_t n, int64_t nb, float* A, int64_t lda, int32_t* ipiv) {
+  const int64_t w = 8;
   if (nb <= 0) nb = 64;
   int info = 0;
-  for (int64_t j0 = 0; j0 < n; j0 += nb) {
-    int64_t jb = (n - j0 < nb) ? n - j0 : nb;
-    /* panel A[j0:n, j0:j0+jb] */
-    for (int64_t j = j0; j < j0 + jb; ++j) {
-      int64_t p = j;
-      float best = fabsf(A[j * lda + j]);
-      for (int64_t i = j + 1; i < n; ++i) {
-        float v = fabsf(A[i * lda + j]);
-        if (v > best) { best = v; p = i; }
-      }
-      ipiv[j] = (int32_t)p;
-      if (p != j)   /* whole row: the same as swapping panel, left and right parts */
-        for (int64_t c = 0; c < n; ++c) {
-          float t = A[j * lda + c]; A[j * lda + c] = A[p * lda + c]; A[p * lda + c] = t;
+  for (int64_t J0 = 0; J0 < n; J0 += nb) {
+    int64_t JB = (n - J0 < nb) ? n - J0 : nb;
+    for (int64_t j0 = J0; j0 < J0 + JB; j0 += w) {
+      int64_t jw = (J0 + JB - j0 < w) ? J0 + JB - j0 : w;
+      for (int64_t j = j0; j < j0 + jw; ++j) {
+        int64_t p = j;
+        float best = fabsf(A[j * lda + j]);
+        for (int64_t i = j + 1; i < n; ++i) {
+          float v = fabsf(A[i * lda + j]);
+          if (v > best) { best = v; p = i; }
         }
-      float piv = A[j * lda + j];
-      if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
-      for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
-      for (int64_t i = j + 1; i < n; ++i) {
-        float l = A[i * lda + j];
-        for (int64_t c = j + 1; c < j0 + jb; ++c)
-          A[i * lda + c] = fmaf(-l, A[j * lda + c], A[i * lda + c]);
+        ipiv[j] = (int32_t)p;
+        if (p != j)   /* whole row: the same as swapping panel, left and right parts */
+          for (int64_t c = 0; c < n; ++c) {
+            float t = A[j * lda + c]; A[j * lda + c] = A[p * lda + c]; A[p * lda + c] = t;
+          }
+        float piv = A[j * lda + j];
+        if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
+        for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
+        for (int64_t i = j + 1; i < n; ++i) {
+          float l = A[i * lda + j];
+          for (int64_t c = j + 1; c < j0 + jw; ++c)
+            A[i * lda + c] = fmaf(-l, A[j * lda + c], A[i * lda + c]);
+        }
       }
+      /* rest of the block column: tile rows by forward substitution ... */
+      for (int64_t i = j0 + 1; i < j0 + jw; ++i)
+        for (int64_t l = j0; l < i; ++l)
+          for (int64_t c = j0 + jw; c < J0 + JB; ++c)
+            A[i * lda + c] = fmaf(-A[i * lda + l], A[l * lda + c], A[i * lda + c]);
+      /* ... and the rows below by the tile's rank-jw update */
+      for (int64_t r = j0 + jw; r < n; ++r)
+        for (int64_t c = j0 + jw; c < J0 + JB; ++c) {
+          float a = A[r * lda + c];
+          for (int64_t l = j0; l < j0 + jw; ++l) a = fmaf(-A[r * lda + l], A[l * lda + c], a);
+          A[r * lda + c] = a;
+        }
     }
-    int64_t nr = n - j0 - jb;
+    int64_t nr = n - J0 - JB;
     if (nr <= 0) continue;
     /* U12 = L11^-1 A12 (unit lower, forward substitution row by row) */
-    for (int64_t i = j0 + 1; i < j0 + jb; ++i)
-      for (int64_t l = j0; l < i; ++l) {
+    for (int64_t i = J0 + 1; i < J0 + JB; ++i)
+      for (int64_t l = J0; l < i; ++l) {
         float lil = A[i * lda + l];
-        for (int64_t c = j0 + jb; c < n; ++c)
+        for (int64_t c = J0 + JB; c < n; ++c)
           A[i * lda + c] = fmaf(-lil, A[l * lda + c], A[i * lda + c]);
       }
     /* A22 <- A22 - L21 U12 */
-    int rc = orc_gemm(mode, 0, nr, nr, jb, -1.0f, A + (j0 + jb) * lda + j0, lda,
-                      A + j0 * lda + j0 + jb, lda, 1.0f, A + (j0 + jb) * lda + j0 + jb, lda);
+    int rc = orc_gemm(mode, 0, nr, nr, JB, -1.0f, A + (J0 + JB) * lda + J0, lda,
+                      A + J0 * lda + J0 + JB, lda, 1.0f, A + (J0 + JB) * lda + J0 + JB, lda);
     if (rc) return -rc;
   }
   return info;

@@ -3,9 +3,13 @@
 // and six products"; Sec. III: the cubic work in low precision).
 //
 // For each block column j0 (width jb <= nb):
-//   panel   : unblocked FP32 LU of A[j0:n, j0:j0+jb] - pivot = first row of the
-//             largest |a| (warp-shuffle argmax), row swap inside the panel,
-//             division by the pivot, FMA rank-1 updates of the panel;
+//   panel   : FP32 LU of A[j0:n, j0:j0+jb], blocked like LAPACK's panel in
+//             tiles of 8 columns: each tile is factored by one CTA from
+//             shared memory (pivot = first row of the largest |a|, found by a
+//             warp-shuffle argmax; row swap across the block column; division
+//             by the pivot; FMA rank-1 updates inside the tile), its rows of
+//             the block columns to its right are forward-substituted, and the
+//             rows below get the tile's rank-8 update (FMA, in column order);
 //   laswp   : the panel's row swaps applied to the columns left and right of it;
 //   trsm    : U12 = L11^-1 A12 (unit lower, FP32 FMA, one thread a column);
 //   update  : A22 <- A22 - L21 U12 by the mode's bfloat16 products on the
@@ -14,6 +18,8 @@
 // Pivots: ipiv[j] (0-based) is the row swapped with row j at step j.  info is
 // LAPACK's: 0, or the 1-based index of the first exactly zero pivot (the
 // factorisation still completes).
+#include <algorithm>
+
 #include "bfx_internal.cuh"
 
 namespace bfx {
@@ -32,21 +38,43 @@ __device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
   return a;
 }
 
-// One CTA factors the panel A[j0:n, j0:j0+jb] in place.  Thread t owns rows
-// j0 + t, j0 + t + 1024, ...; rows above the current column are finished.
-__global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(float* __restrict__ A, int64_t lda,
-                                                               int n, int j0, int jb,
-                                                               int32_t* __restrict__ ipiv,
-                                                               int32_t* __restrict__ info) {
+constexpr int TILE_W = 8;                      // panel tile width
+constexpr size_t TILE_SMEM_MAX = 200 * 1024;   // tile rows kept in shared memory up to this
+
+// One CTA factors the tile A[j0:n, j0:j0+jw] (jw <= 8) of the block column
+// [J0, J0+JB), keeping the tile in shared memory when it fits:
+//   for each tile column j: pivot = first row of the largest |a| (warp-shuffle
+//   argmax), rows j and p swapped across the whole block column, division by
+//   the pivot, FMA rank-1 update of the remaining tile columns;
+// then the tile rows of the block columns right of the tile are solved with
+// the tile's unit lower triangle (forward substitution, FMA, l in order).
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_tile_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
+                   int32_t* __restrict__ ipiv, int32_t* __restrict__ info, int use_smem) {
+  extern __shared__ float tile[];  // (n - j0) x TILE_W when use_smem
   __shared__ ArgMax warp_best[PANEL_THREADS / 32];
   __shared__ int s_piv;
-  __shared__ float s_row[256];
+  __shared__ float s_row[TILE_W];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  for (int j = j0; j < j0 + jb; ++j) {
-    // ---- pivot search over rows j..n-1 of column j
+  const int rows = n - j0;
+  auto T = [&](int r, int c) -> float& {
+    return use_smem ? tile[static_cast<int64_t>(r - j0) * TILE_W + c]
+                    : A[static_cast<int64_t>(r) * lda + j0 + c];
+  };
+  if (use_smem) {
+    for (int e = t; e < rows * jw; e += PANEL_THREADS) {
+      const int r = j0 + e / jw, c = e % jw;
+      tile[static_cast<int64_t>(r - j0) * TILE_W + c] = A[static_cast<int64_t>(r) * lda + j0 + c];
+    }
+    __syncthreads();
+  }
+  const int nout = JB - jw;  // block-column columns outside the tile
+  for (int jj = 0; jj < jw; ++jj) {
+    const int j = j0 + jj;
+    // ---- pivot search over rows j..n-1
     ArgMax best{-1.0f, n};
     for (int r = j + t; r < n; r += PANEL_THREADS) {
-      float v = fabsf(A[static_cast<int64_t>(r) * lda + j]);
+      float v = fabsf(T(r, jj));
       if (v != v) v = -1.0f;  // NaN below the diagonal is never chosen
       best = better(best, ArgMax{v, r});
     }
@@ -65,7 +93,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(float* __restri
         best = better(best, other);
       }
       if (lane == 0) {
-        const float d = A[static_cast<int64_t>(j) * lda + j];
+        const float d = T(j, jj);
         // a NaN on the diagonal stays (nothing compares greater than it)
         s_piv = (d != d || best.i >= n) ? j : best.i;
         ipiv[j] = s_piv;
@@ -73,32 +101,69 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(float* __restri
     }
     __syncthreads();
     const int p = s_piv;
-    // ---- swap rows j and p inside the panel; keep the pivot row in shared memory
-    for (int c = t; c < jb; c += PANEL_THREADS) {
-      float* rj = A + static_cast<int64_t>(j) * lda + j0 + c;
-      float* rp = A + static_cast<int64_t>(p) * lda + j0 + c;
-      const float a = *rj, b = *rp;
+    // ---- swap rows j and p: tile part, then the rest of the block column
+    if (t < jw) {
+      const float a = T(j, t), b = T(p, t);
       if (p != j) {
-        *rj = b;
-        *rp = a;
+        T(j, t) = b;
+        T(p, t) = a;
       }
-      s_row[c] = (p != j) ? b : a;
+      s_row[t] = (p != j) ? b : a;
+    } else if (p != j && t - TILE_W < nout && t >= TILE_W) {
+      const int k = t - TILE_W;
+      const int c = (J0 + k < j0) ? J0 + k : J0 + k + jw;
+      float* rj = A + static_cast<int64_t>(j) * lda + c;
+      float* rp = A + static_cast<int64_t>(p) * lda + c;
+      const float a = *rj;
+      *rj = *rp;
+      *rp = a;
     }
     __syncthreads();
-    const float piv = s_row[j - j0];
+    const float piv = s_row[jj];
     if (piv == 0.0f) {
       if (t == 0 && *info == 0) *info = j + 1;
       __syncthreads();
       continue;
     }
-    // ---- scale the column and update the rest of the panel
+    // ---- scale the column, rank-1 update of the rest of the tile
     for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
-      float* row = A + static_cast<int64_t>(r) * lda + j0;
-      const float l = __fdiv_rn(row[j - j0], piv);
-      row[j - j0] = l;
-      for (int c = j - j0 + 1; c < jb; ++c) row[c] = fmaf(-l, s_row[c], row[c]);
+      const float l = __fdiv_rn(T(r, jj), piv);
+      T(r, jj) = l;
+      for (int c = jj + 1; c < jw; ++c) T(r, c) = fmaf(-l, s_row[c], T(r, c));
     }
     __syncthreads();
+  }
+  if (use_smem) {
+    for (int e = t; e < rows * jw; e += PANEL_THREADS) {
+      const int r = j0 + e / jw, c = e % jw;
+      A[static_cast<int64_t>(r) * lda + j0 + c] = tile[static_cast<int64_t>(r - j0) * TILE_W + c];
+    }
+  }
+  // ---- tile rows of the block columns right of the tile: forward substitution
+  for (int c = j0 + jw + t; c < J0 + JB; c += PANEL_THREADS) {
+    float* col = A + static_cast<int64_t>(j0) * lda + c;
+    for (int i = 1; i < jw; ++i) {
+      float acc = col[static_cast<int64_t>(i) * lda];
+      for (int l = 0; l < i; ++l) acc = fmaf(-T(j0 + i, l), col[static_cast<int64_t>(l) * lda], acc);
+      col[static_cast<int64_t>(i) * lda] = acc;
+    }
+  }
+}
+
+// Rows below the tile, block columns right of it: a <- fma(-l_rk, u_kc, a)
+// for the jw tile columns k in order.
+__global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
+                                      int j0, int jw) {
+  const int cs = j0 + jw, ncol = J0 + JB - cs;
+  const int64_t total = static_cast<int64_t>(n - cs) * ncol;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int r = cs + static_cast<int>(e / ncol);
+    const int c = cs + static_cast<int>(e % ncol);
+    const float* lr = A + static_cast<int64_t>(r) * lda + j0;
+    float a = A[static_cast<int64_t>(r) * lda + c];
+    for (int l = 0; l < jw; ++l) a = fmaf(-lr[l], A[static_cast<int64_t>(j0 + l) * lda + c], a);
+    A[static_cast<int64_t>(r) * lda + c] = a;
   }
 }
 
@@ -163,6 +228,9 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   const int np = mode_pieces(mode);
   LuWs w = lu_ws(np > 0 ? np : 1, n, nb);
   if (np > 0 && (!ws || ws_bytes < w.bytes || !aligned(ws, 256))) return BFX_ENOMEM;
+  if (cudaFuncSetAttribute(lu_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess)
+    return BFX_ECUDA;
   const size_t trsm_smem = static_cast<size_t>(nb) * nb * sizeof(float);
   if (trsm_smem > 48 * 1024 &&
       cudaFuncSetAttribute(lu_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -173,7 +241,19 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   const int N = static_cast<int>(n);
   for (int j0 = 0; j0 < N; j0 += nb) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
-    lu_panel_kernel<<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, ipiv, info);
+    for (int t0 = j0; t0 < j0 + jb; t0 += TILE_W) {
+      const int tw = std::min(TILE_W, j0 + jb - t0);
+      const size_t tsm = static_cast<size_t>(N - t0) * TILE_W * sizeof(float);
+      const int use_smem = tsm <= TILE_SMEM_MAX ? 1 : 0;
+      lu_tile_kernel<<<1, PANEL_THREADS, use_smem ? tsm : 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv,
+                                                                  info, use_smem);
+      const int ncol = j0 + jb - t0 - tw;
+      if (ncol > 0 && N - t0 - tw > 0) {
+        const int64_t work = static_cast<int64_t>(N - t0 - tw) * ncol;
+        const int g = static_cast<int>(std::min<int64_t>(ceil_div(work, 256), 8LL * 148));
+        lu_tile_update_kernel<<<g, 256, 0, s>>>(A, lda, N, j0, jb, t0, tw);
+      }
+    }
     if (N - jb > 0) {
       const int64_t cols = N - jb;
       lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(cols, 256)), 256, 0, s>>>(A, lda, N, j0, jb,

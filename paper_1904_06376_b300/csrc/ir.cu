@@ -16,10 +16,11 @@
 //
 // Everything runs in this library's kernels; the host only loops over
 // iterations and reads the per-column norms (a few doubles) to decide.
-// Triangular solves: row blocks of 64; for each block one launch in which
-// every CTA solves the 64 x 64 diagonal triangle (identically) and then
-// updates its own row block, so the FP64 work of each step is spread over
-// all SMs.
+// Triangular solves: row blocks of 64 whose diagonal blocks are inverted once
+// per factorisation (FP64); for each block one launch in which every CTA
+// applies the block's inverse (identically) and then updates its own row
+// block, so the FP64 work of each step is spread over all SMs and no step
+// waits on a 64-long chain of dependent FP64 operations.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -44,19 +45,24 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 }
 
 // perm[i] = source row of row i of P*v, from sequential swaps ipiv.
+// use_smem: both arrays (2 n ints) staged in shared memory.
 __global__ void ir_perm_kernel(const int32_t* __restrict__ ipiv, int n, int32_t* __restrict__ perm,
                                bool use_smem) {
   extern __shared__ int32_t sp[];
   int32_t* p = use_smem ? sp : perm;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+  const int32_t* q = use_smem ? sp + n : ipiv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    p[i] = i;
+    if (use_smem) sp[n + i] = ipiv[i];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) {
-      const int q = ipiv[j];
-      if (q != j) {
+      const int r = q[j];
+      if (r != j) {
         const int32_t t = p[j];
-        p[j] = p[q];
-        p[q] = t;
+        p[j] = p[r];
+        p[r] = t;
       }
     }
   }
@@ -140,58 +146,93 @@ __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
   }
 }
 
-// One block step of L y = v (unit lower) or U y = v (upper) for the diagonal
-// block [b0, b0+bs).  Every CTA reads the (already updated) diagonal rows of v
-// and solves the block triangle; CTA 0 writes the solved rows to `out`, CTA
-// k > 0 subtracts their contribution from row block k of the rows still to be
-// solved (below for L, above for U) in v.  The diagonal rows of v are only
-// read in this launch, so the CTAs do not race.
+// Inverses of the diagonal blocks of L (unit lower) and U (upper), FP64,
+// once per factorisation.  CTA b inverts block b: thread k solves
+// T x = e_k by column-oriented substitution in registers.
+template <bool LOWER>
+__global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __restrict__ F,
+                                                             int64_t ldf, int n,
+                                                             double* __restrict__ Dinv) {
+  __shared__ double T[TB][TB + 1];
+  const int b0 = blockIdx.x * TB, bs = min(TB, n - b0), k = threadIdx.x;
+  for (int e = k; e < TB * TB; e += TB) {
+    const int i = e / TB, l = e % TB;
+    T[i][l] = (i < bs && l < bs) ? static_cast<double>(F[static_cast<int64_t>(b0 + i) * ldf + b0 + l])
+                                 : (i == l ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  double x[TB];
+#pragma unroll
+  for (int i = 0; i < TB; ++i) x[i] = (i == k) ? 1.0 : 0.0;
+  if (LOWER) {
+#pragma unroll
+    for (int l = 0; l < TB - 1; ++l) {
+#pragma unroll
+      for (int i = l + 1; i < TB; ++i) x[i] = fma(-T[i][l], x[l], x[i]);
+    }
+  } else {
+#pragma unroll
+    for (int l = TB - 1; l >= 0; --l) {
+      x[l] = x[l] / T[l][l];
+#pragma unroll
+      for (int i = 0; i < l; ++i) x[i] = fma(-T[i][l], x[l], x[i]);
+    }
+  }
+  double* D = Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB;
+#pragma unroll
+  for (int i = 0; i < TB; ++i) D[i * TB + k] = x[i];  // column k of the inverse
+}
+
+// One block step of L y = v or U y = v for the diagonal block [b0, b0+bs),
+// with the block's precomputed inverse: y = Dinv v_b.  Every CTA forms y
+// (a 64 x 64 product, warp a row); CTA 0 writes it to `out`, CTA k > 0
+// subtracts F[rows, block] y from row block k of the rows still to be solved
+// (below for L, above for U) in v.  The diagonal rows of v are only read in
+// this launch, so the CTAs do not race.
 template <bool LOWER>
 __global__ void __launch_bounds__(SOLVE_THREADS)
     ir_trsv_step_kernel(const float* __restrict__ F, int64_t ldf, int n, int b0, int bs,
-                        double* __restrict__ v, double* __restrict__ out, int64_t ldv, int nrhs) {
-  __shared__ double Ft[TB][TB + 1];
+                        const double* __restrict__ Dinv, double* __restrict__ v,
+                        double* __restrict__ out, int64_t ldv, int nrhs) {
+  __shared__ double vb[TB][MAXR];
   __shared__ double y[TB][MAXR];
-  const int t = threadIdx.x;
-  for (int e = t; e < bs * bs; e += SOLVE_THREADS) {
-    const int i = e / bs, l = e - i * bs;
-    Ft[i][l] = static_cast<double>(F[static_cast<int64_t>(b0 + i) * ldf + b0 + l]);
-  }
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const double* D = Dinv + static_cast<int64_t>(b0 / TB) * TB * TB;
   for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
     const int nc = min(MAXR, nrhs - c0);
-    for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+    for (int e = t; e < TB * nc; e += SOLVE_THREADS) {
       const int i = e / nc, c = e - i * nc;
-      y[i][c] = v[static_cast<int64_t>(b0 + i) * ldv + c0 + c];
+      vb[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * ldv + c0 + c] : 0.0;
     }
     __syncthreads();
-    // triangle: column-oriented elimination inside the block
-    for (int jj = 0; jj < bs; ++jj) {
-      const int j = LOWER ? jj : bs - 1 - jj;
-      if (!LOWER) {
-        if (t < nc) y[j][t] = y[j][t] / Ft[j][j];
-        __syncthreads();
+    for (int i = wid; i < bs; i += SOLVE_THREADS / 32) {
+      const double d0 = D[i * TB + lane], d1 = D[i * TB + lane + 32];
+      for (int c = 0; c < nc; ++c) {
+        double s = fma(d0, vb[lane][c], d1 * vb[lane + 32][c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) y[i][c] = s;
       }
-      for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
-        const int i = e / nc, c = e - i * nc;
-        if (LOWER ? (i > j) : (i < j)) y[i][c] = fma(-Ft[i][j], y[j][c], y[i][c]);
-      }
-      __syncthreads();
     }
+    __syncthreads();
     if (blockIdx.x == 0) {
       for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
         const int i = e / nc, c = e - i * nc;
         out[static_cast<int64_t>(b0 + i) * ldv + c0 + c] = y[i][c];
       }
     } else {
-      // rows of this CTA's block: below (L) or above (U) the diagonal block
       const int rs = LOWER ? b0 + bs + (blockIdx.x - 1) * TB : b0 - blockIdx.x * TB;
       const int re = LOWER ? min(rs + TB, n) : rs + TB;
-      for (int e = t; e < (re - rs) * nc; e += SOLVE_THREADS) {
-        const int i = rs + e / nc, c = e % nc;
+      for (int i = rs + wid; i < re; i += SOLVE_THREADS / 32) {
         const float* fr = F + static_cast<int64_t>(i) * ldf + b0;
-        double s = v[static_cast<int64_t>(i) * ldv + c0 + c];
-        for (int l = 0; l < bs; ++l) s = fma(-static_cast<double>(fr[l]), y[l][c], s);
-        v[static_cast<int64_t>(i) * ldv + c0 + c] = s;
+        const double f0 = lane < bs ? static_cast<double>(fr[lane]) : 0.0;
+        const double f1 = lane + 32 < bs ? static_cast<double>(fr[lane + 32]) : 0.0;
+        for (int c = 0; c < nc; ++c) {
+          double s = fma(f0, lane < bs ? y[lane][c] : 0.0, f1 * (lane + 32 < bs ? y[lane + 32][c] : 0.0));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+          if (lane == 0) v[static_cast<int64_t>(i) * ldv + c0 + c] -= s;
+        }
       }
     }
     __syncthreads();
@@ -230,6 +271,8 @@ struct IrWs {
   double* r;
   double* d;
   double* norms;  // [0] anorm, then per column: bn, dn, xn, rn
+  double* Linv;   // inverses of the 64 x 64 diagonal blocks of L, then of U
+  double* Uinv;
   void* luws;
   size_t luws_bytes;
   size_t total;
@@ -251,6 +294,9 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
   w.r = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
   w.d = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
   w.norms = reinterpret_cast<double*>(take(sizeof(double) * (1 + 4 * nrhs)));
+  const int64_t nblk = (n + TB - 1) / TB;
+  w.Linv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
+  w.Uinv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   size_t lub = 0;
   for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X9})
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
@@ -270,14 +316,14 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
   for (int b = 0; b < nblk; ++b) {  // forward, unit lower
     const int b0 = b * TB, bs = std::min(TB, N - b0);
     const int below = static_cast<int>(ceil_div(N - b0 - bs, TB));
-    ir_trsv_step_kernel<true><<<1 + below, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.d, w.r,
-                                                                   nrhs, nrhs);
+    ir_trsv_step_kernel<true><<<1 + below, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.Linv, w.d,
+                                                                   w.r, nrhs, nrhs);
   }
   for (int b = nblk - 1; b >= 0; --b) {  // backward, upper
     const int b0 = b * TB, bs = std::min(TB, N - b0);
     const int above = b0 / TB;
-    ir_trsv_step_kernel<false><<<1 + above, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.r, w.d,
-                                                                    nrhs, nrhs);
+    ir_trsv_step_kernel<false><<<1 + above, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.Uinv, w.r,
+                                                                    w.d, nrhs, nrhs);
   }
   return last_launch_status();
 }
@@ -363,8 +409,11 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       return BFX_ECUDA;
     h_result->info = info;
     if (info != 0) return BFX_SINGULAR;
-    const bool sm = n <= 12288;  // permutation fits the default 48 KB of shared memory
-    ir_perm_kernel<<<1, 1024, sm ? sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+    const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
+    ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
+    ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
+    const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
+    ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
     if (cudaMemcpyAsync(w.active, act.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
       return BFX_ECUDA;

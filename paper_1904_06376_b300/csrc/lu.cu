@@ -48,9 +48,10 @@ constexpr size_t TILE_SMEM_MAX = 200 * 1024;   // tile rows kept in shared memor
 //   the pivot, FMA rank-1 update of the remaining tile columns;
 // then the tile rows of the block columns right of the tile are solved with
 // the tile's unit lower triangle (forward substitution, FMA, l in order).
+template <bool use_smem>
 __global__ void __launch_bounds__(PANEL_THREADS)
     lu_tile_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
-                   int32_t* __restrict__ ipiv, int32_t* __restrict__ info, int use_smem) {
+                   int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
   extern __shared__ float tile[];  // (n - j0) x TILE_W when use_smem
   __shared__ ArgMax warp_best[PANEL_THREADS / 32];
   __shared__ int s_piv;
@@ -62,9 +63,24 @@ __global__ void __launch_bounds__(PANEL_THREADS)
                     : A[static_cast<int64_t>(r) * lda + j0 + c];
   };
   if (use_smem) {
-    for (int e = t; e < rows * jw; e += PANEL_THREADS) {
-      const int r = j0 + e / jw, c = e % jw;
-      tile[static_cast<int64_t>(r - j0) * TILE_W + c] = A[static_cast<int64_t>(r) * lda + j0 + c];
+    // a row's tile values go through registers, all loads of a thread first
+    for (int r0 = j0 + t; r0 < n; r0 += 4 * PANEL_THREADS) {
+      float v[4][TILE_W];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + q * PANEL_THREADS;
+#pragma unroll
+        for (int c = 0; c < TILE_W; ++c)
+          v[q][c] = (r < n && c < jw) ? A[static_cast<int64_t>(r) * lda + j0 + c] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + q * PANEL_THREADS;
+        if (r < n) {
+#pragma unroll
+          for (int c = 0; c < TILE_W; ++c) tile[static_cast<int64_t>(r - j0) * TILE_W + c] = v[q][c];
+        }
+      }
     }
     __syncthreads();
   }
@@ -142,9 +158,16 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   // ---- tile rows of the block columns right of the tile: forward substitution
   for (int c = j0 + jw + t; c < J0 + JB; c += PANEL_THREADS) {
     float* col = A + static_cast<int64_t>(j0) * lda + c;
-    for (int i = 1; i < jw; ++i) {
-      float acc = col[static_cast<int64_t>(i) * lda];
-      for (int l = 0; l < i; ++l) acc = fmaf(-T(j0 + i, l), col[static_cast<int64_t>(l) * lda], acc);
+    float x[TILE_W];
+#pragma unroll
+    for (int i = 0; i < TILE_W; ++i) x[i] = i < jw ? col[static_cast<int64_t>(i) * lda] : 0.0f;
+#pragma unroll
+    for (int i = 1; i < TILE_W; ++i) {
+      if (i >= jw) break;
+      float acc = x[i];
+#pragma unroll
+      for (int l = 0; l < i; ++l) acc = fmaf(-T(j0 + i, l), x[l], acc);
+      x[i] = acc;
       col[static_cast<int64_t>(i) * lda] = acc;
     }
   }
@@ -168,39 +191,114 @@ __global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n,
 }
 
 // Apply the swaps ipiv[j0 .. j0+jb) to every column outside [j0, j0+jb).
-__global__ void lu_laswp_kernel(float* __restrict__ A, int64_t lda, int n, int j0, int jb,
-                                const int32_t* __restrict__ ipiv) {
-  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const int64_t ncols = n - jb;
-  if (idx >= ncols) return;
-  const int c = static_cast<int>(idx < j0 ? idx : idx + jb);
-  for (int j = j0; j < j0 + jb; ++j) {
-    const int p = ipiv[j];
-    if (p != j) {
-      float* a = A + static_cast<int64_t>(j) * lda + c;
-      float* b = A + static_cast<int64_t>(p) * lda + c;
-      const float tmp = *a;
-      *a = *b;
-      *b = tmp;
+// Warp 0 first turns the sequential swaps into their net effect on the at
+// most 2 jb rows they touch (slot k ends up holding the original row
+// cont[k]); then every thread moves the touched rows of its column with all
+// loads issued before the stores.
+constexpr int LASWP_COLS = 64;
+__global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict__ A, int64_t lda,
+                                                             int n, int j0, int jb,
+                                                             const int32_t* __restrict__ ipiv) {
+  extern __shared__ float vals[];  // (2 jb) x LASWP_COLS
+  __shared__ int rowid[256];
+  __shared__ int cont[256];
+  __shared__ int piv[128];
+  __shared__ int nslots;
+  const int t = threadIdx.x;
+  for (int j = t; j < jb; j += LASWP_COLS) piv[j] = ipiv[j0 + j];
+  __syncthreads();
+  if (t < 32) {
+    for (int k = t; k < jb; k += 32) {
+      rowid[k] = j0 + k;
+      cont[k] = j0 + k;
     }
+    int ns = jb;
+    __syncwarp();
+    for (int j = 0; j < jb; ++j) {
+      const int p = piv[j];
+      int sp;
+      if (p < j0 + jb) {
+        sp = p - j0;
+      } else {
+        sp = -1;
+        for (int base = jb; base < ns && sp < 0; base += 32) {
+          const int k = base + t;
+          const unsigned hit = __ballot_sync(0xFFFFFFFFu, k < ns && rowid[k] == p);
+          if (hit) sp = base + __ffs(hit) - 1;
+        }
+        if (sp < 0) {
+          sp = ns++;
+          if (t == 0) {
+            rowid[sp] = p;
+            cont[sp] = p;
+          }
+        }
+      }
+      __syncwarp();
+      if (t == 0 && sp != j) {
+        const int tmp = cont[j];
+        cont[j] = cont[sp];
+        cont[sp] = tmp;
+      }
+      __syncwarp();
+    }
+    if (t == 0) nslots = ns;
   }
+  __syncthreads();
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(LASWP_COLS) + t;
+  if (idx >= n - jb) return;
+  const int c = static_cast<int>(idx < j0 ? idx : idx + jb);
+  const int ns = nslots;
+  // batches of 16 loads in registers before their shared-memory stores, so
+  // the global loads are all in flight together
+  for (int k0 = 0; k0 < ns; k0 += 16) {
+    int src[16];
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) src[q] = (k0 + q < ns) ? cont[k0 + q] : -1;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = (src[q] >= 0) ? A[static_cast<int64_t>(src[q]) * lda + c] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (k0 + q < ns) vals[(k0 + q) * LASWP_COLS + t] = v[q];
+  }
+  for (int k = 0; k < ns; ++k)
+    A[static_cast<int64_t>(rowid[k]) * lda + c] = vals[k * LASWP_COLS + t];
 }
 
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
-// one thread a column of A12, accumulation order l = 0 .. i-1.
-__global__ void lu_trsm_kernel(float* __restrict__ A, int64_t lda, int n, int j0, int jb) {
-  extern __shared__ float L11[];  // jb x jb
-  for (int e = threadIdx.x; e < jb * jb; e += blockDim.x)
-    L11[e] = A[static_cast<int64_t>(j0 + e / jb) * lda + j0 + e % jb];
+// one thread a column of A12 held in registers (NB >= jb, unrolled).
+// Column-oriented: x_i receives -l_il x_l for l = 0, 1, ..., i-1 in order -
+// per element the same FMA sequence as row-by-row substitution - with the
+// updates for different i independent of each other.
+constexpr int TRSM_COLS = 64;
+template <int NB>
+__global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
+                                                           int n, int j0, int jb) {
+  extern __shared__ float L11[];  // NB x NB, the jb x jb triangle padded with zeros
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, l = e % NB;
+    L11[e] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
+  }
   __syncthreads();
-  const int64_t c = j0 + jb + blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t c = j0 + jb + blockIdx.x * static_cast<int64_t>(TRSM_COLS) + threadIdx.x;
   if (c >= n) return;
   float* col = A + static_cast<int64_t>(j0) * lda + c;
-  for (int i = 1; i < jb; ++i) {
-    float acc = col[static_cast<int64_t>(i) * lda];
-    for (int l = 0; l < i; ++l) acc = fmaf(-L11[i * jb + l], col[static_cast<int64_t>(l) * lda], acc);
-    col[static_cast<int64_t>(i) * lda] = acc;
+  float x[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = (i < jb) ? col[static_cast<int64_t>(i) * lda] : 0.0f;
+#pragma unroll
+  for (int l = 0; l < NB - 1; ++l) {
+    if (l < jb - 1) {
+      const float xl = x[l];
+#pragma unroll
+      for (int i = l + 1; i < NB; ++i)
+        if (i < jb) x[i] = fmaf(-L11[i * NB + l], xl, x[i]);
+    }
   }
+#pragma unroll
+  for (int i = 1; i < NB; ++i)
+    if (i < jb) col[static_cast<int64_t>(i) * lda] = x[i];
 }
 
 struct LuWs {
@@ -228,12 +326,16 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   const int np = mode_pieces(mode);
   LuWs w = lu_ws(np > 0 ? np : 1, n, nb);
   if (np > 0 && (!ws || ws_bytes < w.bytes || !aligned(ws, 256))) return BFX_ENOMEM;
-  if (cudaFuncSetAttribute(lu_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess)
+  if (cudaFuncSetAttribute(lu_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess ||
+      cudaFuncSetAttribute(lu_laswp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) != cudaSuccess)
     return BFX_ECUDA;
-  const size_t trsm_smem = static_cast<size_t>(nb) * nb * sizeof(float);
+  const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);  // register tile of the block solve
+  auto trsm = tnb == 32 ? lu_trsm_kernel<32> : (tnb == 64 ? lu_trsm_kernel<64> : lu_trsm_kernel<128>);
+  const size_t trsm_smem = static_cast<size_t>(tnb) * tnb * sizeof(float);
   if (trsm_smem > 48 * 1024 &&
-      cudaFuncSetAttribute(lu_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(trsm_smem)) != cudaSuccess)
     return BFX_ECUDA;
   uint16_t* Lp = static_cast<uint16_t*>(ws);
@@ -244,9 +346,10 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     for (int t0 = j0; t0 < j0 + jb; t0 += TILE_W) {
       const int tw = std::min(TILE_W, j0 + jb - t0);
       const size_t tsm = static_cast<size_t>(N - t0) * TILE_W * sizeof(float);
-      const int use_smem = tsm <= TILE_SMEM_MAX ? 1 : 0;
-      lu_tile_kernel<<<1, PANEL_THREADS, use_smem ? tsm : 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv,
-                                                                  info, use_smem);
+      if (tsm <= TILE_SMEM_MAX)
+        lu_tile_kernel<true><<<1, PANEL_THREADS, tsm, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
+      else
+        lu_tile_kernel<false><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
       const int ncol = j0 + jb - t0 - tw;
       if (ncol > 0 && N - t0 - tw > 0) {
         const int64_t work = static_cast<int64_t>(N - t0 - tw) * ncol;
@@ -256,13 +359,14 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     }
     if (N - jb > 0) {
       const int64_t cols = N - jb;
-      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(cols, 256)), 256, 0, s>>>(A, lda, N, j0, jb,
-                                                                              ipiv);
+      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(cols, LASWP_COLS)), LASWP_COLS,
+                        static_cast<size_t>(2 * jb) * LASWP_COLS * sizeof(float), s>>>(A, lda, N, j0,
+                                                                                     jb, ipiv);
     }
     const int nr = N - j0 - jb;
     if (nr <= 0) continue;
-    lu_trsm_kernel<<<static_cast<unsigned>(ceil_div(nr, 128)), 128, trsm_smem, s>>>(A, lda, N, j0,
-                                                                                jb);
+    trsm<<<static_cast<unsigned>(ceil_div(nr, TRSM_COLS)), TRSM_COLS, trsm_smem, s>>>(A, lda, N, j0,
+                                                                                     jb);
     float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
     float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb;
     float* A22 = A + static_cast<int64_t>(j0 + jb) * lda + j0 + jb;

@@ -96,41 +96,39 @@ __global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
   if (lane == 0) atomic_max_nonneg(out, s);
 }
 
-// r = b - A x (FP64) for columns c0 .. c0+nc (nc <= MAXR); warp a row.
+// r = b - A x (FP64) for columns c0 .. c0+NC; warp a row, lanes over the row
+// (coalesced), one FP64 shuffle reduction per column at the end.  NC is a
+// compile-time column count so no predicated-off FP64 work is issued (FP64
+// throughput is the bound of this kernel on B300).
 // If rn != nullptr, rn[c] = max |r[:, c]| (must start at 0).
+template <int NC>
 __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
                                    const double* __restrict__ b, int64_t ldb,
                                    const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
-                                   int64_t ldr, int c0, int nc, double* __restrict__ rn) {
+                                   int64_t ldr, int c0, double* __restrict__ rn) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   if (row >= n) return;
   const float* a = A + row * lda;
-  double acc[MAXR];
+  double acc[NC];
 #pragma unroll
-  for (int c = 0; c < MAXR; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
   for (int l = lane; l < n; l += 32) {
     const double al = static_cast<double>(a[l]);
     const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
 #pragma unroll
-    for (int c = 0; c < MAXR; ++c)
-      if (c < nc) acc[c] = fma(al, xl[c], acc[c]);
+    for (int c = 0; c < NC; ++c) acc[c] = fma(al, xl[c], acc[c]);
   }
 #pragma unroll
-  for (int c = 0; c < MAXR; ++c) {
+  for (int c = 0; c < NC; ++c) {
     double v = acc[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    acc[c] = v;
-  }
-  if (lane < nc) {
-    double s = 0.0;
-#pragma unroll
-    for (int c = 0; c < MAXR; ++c)
-      if (c == lane) s = acc[c];
-    const double v = b[row * ldb + c0 + lane] - s;
-    r[row * ldr + c0 + lane] = v;
-    if (rn) atomic_max_nonneg(&rn[c0 + lane], fabs(v));
+    if (lane == c) {
+      const double rv = b[row * ldb + c0 + c] - v;
+      r[row * ldr + c0 + c] = rv;
+      if (rn) atomic_max_nonneg(&rn[c0 + c], fabs(rv));
+    }
   }
 }
 
@@ -194,10 +192,18 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
     ir_trsv_step_kernel(const float* __restrict__ F, int64_t ldf, int n, int b0, int bs,
                         const double* __restrict__ Dinv, double* __restrict__ v,
                         double* __restrict__ out, int64_t ldv, int nrhs) {
-  __shared__ double vb[TB][MAXR];
-  __shared__ double y[TB][MAXR];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  __shared__ double vb[TB][MAXR + 1];
+  __shared__ double y[TB][MAXR + 1];
+  __shared__ float Fs[TB][TB + 1];  // this CTA's 64 x 64 block of F (off-diagonal CTAs)
+  const int t = threadIdx.x;
   const double* D = Dinv + static_cast<int64_t>(b0 / TB) * TB * TB;
+  const int rs = LOWER ? b0 + bs + (static_cast<int>(blockIdx.x) - 1) * TB
+                       : b0 - static_cast<int>(blockIdx.x) * TB;
+  const int nrow = blockIdx.x == 0 ? 0 : (LOWER ? min(rs + TB, n) : rs + TB) - rs;
+  for (int e = t; e < nrow * TB; e += SOLVE_THREADS) {
+    const int i = e / TB, l = e % TB;
+    Fs[i][l] = l < bs ? F[static_cast<int64_t>(rs + i) * ldf + b0 + l] : 0.0f;
+  }
   for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
     const int nc = min(MAXR, nrhs - c0);
     for (int e = t; e < TB * nc; e += SOLVE_THREADS) {
@@ -205,14 +211,19 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
       vb[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * ldv + c0 + c] : 0.0;
     }
     __syncthreads();
-    for (int i = wid; i < bs; i += SOLVE_THREADS / 32) {
-      const double d0 = D[i * TB + lane], d1 = D[i * TB + lane + 32];
-      for (int c = 0; c < nc; ++c) {
-        double s = fma(d0, vb[lane][c], d1 * vb[lane + 32][c]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) y[i][c] = s;
+    // y = Dinv vb: a thread per (row, column), four partial FMA chains
+    for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+      const int i = e / nc, c = e - i * nc;
+      const double* d = D + i * TB;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+      for (int l = 0; l < TB; l += 4) {
+        s0 = fma(d[l], vb[l][c], s0);
+        s1 = fma(d[l + 1], vb[l + 1][c], s1);
+        s2 = fma(d[l + 2], vb[l + 2][c], s2);
+        s3 = fma(d[l + 3], vb[l + 3][c], s3);
       }
+      y[i][c] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     if (blockIdx.x == 0) {
@@ -221,18 +232,17 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
         out[static_cast<int64_t>(b0 + i) * ldv + c0 + c] = y[i][c];
       }
     } else {
-      const int rs = LOWER ? b0 + bs + (blockIdx.x - 1) * TB : b0 - blockIdx.x * TB;
-      const int re = LOWER ? min(rs + TB, n) : rs + TB;
-      for (int i = rs + wid; i < re; i += SOLVE_THREADS / 32) {
-        const float* fr = F + static_cast<int64_t>(i) * ldf + b0;
-        const double f0 = lane < bs ? static_cast<double>(fr[lane]) : 0.0;
-        const double f1 = lane + 32 < bs ? static_cast<double>(fr[lane + 32]) : 0.0;
-        for (int c = 0; c < nc; ++c) {
-          double s = fma(f0, lane < bs ? y[lane][c] : 0.0, f1 * (lane + 32 < bs ? y[lane + 32][c] : 0.0));
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-          if (lane == 0) v[static_cast<int64_t>(i) * ldv + c0 + c] -= s;
+      for (int e = t; e < nrow * nc; e += SOLVE_THREADS) {
+        const int i = e / nc, c = e - i * nc;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+        for (int l = 0; l < TB; l += 4) {
+          s0 = fma(static_cast<double>(Fs[i][l]), y[l][c], s0);
+          s1 = fma(static_cast<double>(Fs[i][l + 1]), y[l + 1][c], s1);
+          s2 = fma(static_cast<double>(Fs[i][l + 2]), y[l + 2][c], s2);
+          s3 = fma(static_cast<double>(Fs[i][l + 3]), y[l + 3][c], s3);
         }
+        v[static_cast<int64_t>(rs + i) * ldv + c0 + c] -= (s0 + s1) + (s2 + s3);
       }
     }
     __syncthreads();
@@ -332,9 +342,16 @@ bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int n
                     const double* b, int64_t ldb, const double* x, int64_t ldx, double* rn,
                     cudaStream_t s) {
   const unsigned blocks = static_cast<unsigned>(ceil_div(n * 32, 256));
-  for (int c0 = 0; c0 < nrhs; c0 += MAXR)
-    ir_residual_kernel<<<blocks, 256, 0, s>>>(A, lda, static_cast<int>(n), b, ldb, x, ldx, w.r,
-                                              nrhs, c0, std::min(MAXR, nrhs - c0), rn);
+  const int N = static_cast<int>(n);
+  int c0 = 0;
+  for (; c0 + 8 <= nrhs; c0 += 8)
+    ir_residual_kernel<8><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+  for (; c0 + 4 <= nrhs; c0 += 4)
+    ir_residual_kernel<4><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+  for (; c0 + 2 <= nrhs; c0 += 2)
+    ir_residual_kernel<2><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+  for (; c0 < nrhs; ++c0)
+    ir_residual_kernel<1><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
   return last_launch_status();
 }
 

@@ -234,6 +234,44 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
                                 bfx_ir_result* h_result, void* d_ws, size_t ws_bytes,
                                 bfx_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent systems A_s x_s = b_s of uneven sizes
+ * (1 <= n_s <= 1024, the same nrhs <= 16 for all), each by the bf16xN-update
+ * LU and residual-form refinement of bfx_solve_ir, all systems together: every
+ * block-column step of every system's LU runs in one launch per kernel
+ * (panel tiles, row swaps and block solves one CTA per system; the trailing
+ * updates of all systems in one grouped tcgen05 GEMM), then the refinement
+ * runs with per-system stop decisions made on the device.  The whole sequence
+ * is captured once into a CUDA graph per set of buffers and replayed.
+ * Packed layout, systems in the caller's order: A at offset sum_{t<s} n_t^2
+ * (n_s x n_s row-major, FP32); b and x at offset sum_{t<s} n_t nrhs (n_s x
+ * nrhs row-major, FP64).
+ * bfx_batch_create plans the batch (host memory only); params may be NULL
+ * (as bfx_solve_ir; escalate is ignored: a batch keeps its mode).
+ * bfx_batch_solve enqueues the graph on `stream` and returns without
+ * waiting; d_status (device, one entry per system, caller order) is written
+ * at the end: converged, corrections applied, LAPACK info, backward error.
+ * The first call with a new set of buffers captures and instantiates the
+ * graph (do not call it while `stream` is being captured).
+ * Workspace: bfx_batch_workspace_size(plan) bytes, 256-byte aligned.
+ * Errors: BFX_EINVAL (sizes, mode FP32, pointers), BFX_ENOMEM,
+ * BFX_EUNSUPPORTED (device), BFX_ECUDA. */
+typedef struct bfx_batch_status {
+  int32_t converged;
+  int32_t iters;
+  int32_t info;
+  int32_t pad;
+  double berr;
+} bfx_batch_status;
+typedef struct bfx_batch_plan* bfx_batch;
+BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, const int32_t* h_n,
+                                    int nrhs, const bfx_ir_params* params);
+BFX_API size_t bfx_batch_workspace_size(bfx_batch plan);
+BFX_API bfx_status bfx_batch_solve(bfx_batch plan, const float* d_A, const double* d_b,
+                                   double* d_x, bfx_batch_status* d_status, void* d_ws,
+                                   size_t ws_bytes, bfx_stream stream);
+BFX_API void bfx_batch_destroy(bfx_batch plan);
+
 #ifdef __cplusplus
 }
 #endif

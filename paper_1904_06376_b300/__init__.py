@@ -13,6 +13,7 @@ from ._bfx import (  # noqa: F401
     BFX_X3,
     BFX_X6,
     BFX_X9,
+    Batch,
     BfxError,
     device_error,
     dot_bf16xN,

@@ -62,6 +62,10 @@ def lib() -> ctypes.CDLL:
         "bfx_lu_bf16xN": (i32, [i32, i64, i32, vp, i64, vp, vp, vp, sz, vp]),
         "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, i32]),
         "bfx_solve_ir": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
+        "bfx_batch_create": (i32, [vp, i32, i32, vp, i32, vp]),
+        "bfx_batch_workspace_size": (sz, [vp]),
+        "bfx_batch_solve": (i32, [vp, vp, vp, vp, vp, vp, sz, vp]),
+        "bfx_batch_destroy": (None, [vp]),
         "bfx_dot_bf16xN": (i32, [i32, i64, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
@@ -263,3 +267,69 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     if code not in (0, 5, 6) or (raise_on_status and code != 0):
         _check("bfx_solve_ir", code)
     return x, r.as_dict(), code
+
+
+class Batch:
+    """Batched solves of many uneven-size systems (bfx_batch_* of the C ABI).
+
+    ns: sizes of the systems (1..1024); matrices / right-hand sides are packed
+    back to back (see ``pack``).  ``solve`` enqueues one CUDA-graph launch and
+    returns the device status tensor (decode with ``decode_status``)."""
+
+    def __init__(self, mode: int, ns, nrhs: int = 1, max_iter: int = 20, tol: float = 2.0 ** -53,
+                 tol_b: float = -1.0, stall: float = 0.5):
+        import numpy as np
+
+        self.ns = np.asarray(ns, dtype=np.int32)
+        self.nrhs = nrhs
+        self.mode = mode
+        h = ctypes.c_void_p()
+        p = IrParams(max_iter, tol, tol_b, stall, 0, 64)
+        _check("bfx_batch_create", lib().bfx_batch_create(ctypes.byref(h), mode, int(self.ns.size),
+                                                         self.ns.ctypes.data, nrhs, ctypes.byref(p)))
+        self.handle = h
+        self.ws_bytes = int(lib().bfx_batch_workspace_size(h))
+        self.offA = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) ** 2)])
+        self.offV = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) * nrhs)])
+        self.workspace = None
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bfx_batch_destroy(self.handle)
+            self.handle = None
+
+    def pack(self, mats, rhs, device="cuda"):
+        """Pack lists of (n,n) FP32 matrices and (n,nrhs) FP64 right-hand sides."""
+        import numpy as np
+
+        A = np.concatenate([np.asarray(m, np.float32).ravel() for m in mats])
+        b = np.concatenate([np.asarray(v, np.float64).reshape(-1) for v in rhs])
+        return torch.from_numpy(A).to(device), torch.from_numpy(b).to(device)
+
+    def unpack(self, x):
+        import numpy as np
+
+        xa = x.cpu().numpy()
+        return [xa[self.offV[i]:self.offV[i + 1]].reshape(int(n), self.nrhs) for i, n in enumerate(self.ns)]
+
+    def solve(self, A, b, x=None, status=None, stream=None):
+        if x is None:
+            x = torch.empty(int(self.offV[-1]), dtype=torch.float64, device=A.device)
+        if status is None:
+            status = torch.zeros(3 * int(self.ns.size), dtype=torch.float64, device=A.device)
+        if self.workspace is None:
+            self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=A.device)
+        _check("bfx_batch_solve", lib().bfx_batch_solve(self.handle, _ptr(A), _ptr(b), _ptr(x),
+                                                       _ptr(status), _ptr(self.workspace), self.ws_bytes,
+                                                       _stream(stream)))
+        return x, status
+
+    @staticmethod
+    def decode_status(status):
+        """converged, iters, info (int arrays) and berr (float array) per system."""
+        import numpy as np
+
+        raw = status.cpu().numpy().view(np.uint8).reshape(-1, 24)
+        ints = raw[:, :16].copy().view(np.int32).reshape(-1, 4)
+        berr = raw[:, 16:].copy().view(np.float64).ravel()
+        return ints[:, 0], ints[:, 1], ints[:, 2], berr

@@ -49,6 +49,73 @@ bfx_status launch_scale(int64_t m, int64_t n, float beta, float* C, int64_t ldc,
 bfx_status launch_sgemm_simt(int64_t m, int64_t n, int64_t k, float alpha, const float* A,
                              int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                              int64_t ldc, cudaStream_t s);
+// Grouped tensor-core GEMM (many independent problems in one launch): the
+// pieces of problem p are planes plane0 .. plane0+np-1 of two packed buffers
+// (rows x kp bfloat16 each); tiles list the output tiles of all problems.
+struct GroupTile {
+  int prob, mb, nb, pad;
+};
+struct GroupProblem {
+  float* C;
+  int64_t ldc;
+  int M, N, k_tiles, plane0, vec_c, pad;
+};
+int gemm_bk(bfx_mode mode);  // K-slice width of the mode's kernel
+bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
+                               const GroupProblem* d_probs, const uint16_t* Apack,
+                               int64_t a_rows, const uint16_t* Bpack, int64_t b_rows,
+                               int64_t planes, int64_t kp, float alpha, float beta,
+                               cudaStream_t s);
+// Batched LU (lu.cu): one descriptor per system, systems sorted by n descending.
+struct BatchLu {
+  float* A;  // n x n, leading dimension n, factored in place
+  int n, pad;
+  int32_t* ipiv;
+  int32_t* info;
+};
+// One block column [J0, J0+nb) of the LU of every system with n > J0 (the
+// first S_active descriptors): tiles, row swaps, block solve, and the pieces
+// of L21 / U12^T written to the packs for a grouped trailing update (np
+// planes of slot_rows x kp per system); the grouped GEMM itself is launched
+// by the caller.  h_n_desc: the systems' n, descending, on the host.
+bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_desc, int S,
+                            int nb, int J0, uint16_t* packA, uint16_t* packB, int64_t slot_rows,
+                            int64_t kp, cudaStream_t s);
+// Batched refinement (ir.cu): one descriptor per system (same order as the
+// BatchLu array).  All buffers are n x nrhs (FP64) or n x n (FP32), leading
+// dimension n (resp. nrhs).
+struct BatchIrState {
+  int active, conv, stalled, iters;
+  double dprev, anorm, bnorm, berr;
+};
+struct BatchIr {
+  const float* A;   // the problem matrix (FP32)
+  const float* LU;  // its factors
+  const int32_t* ipiv;
+  const int32_t* info;
+  int32_t* perm;
+  const double* b;
+  double* x;
+  double* r;
+  double* d;
+  double* Linv;  // inverses of the 64 x 64 diagonal blocks of L, then U
+  double* Uinv;
+  BatchIrState* st;
+  bfx_batch_status* out;  // the caller's status slot of this system
+  int n, nrhs;
+};
+struct BatchIrParams {
+  double tol, tol_b, stall;
+};
+// The refinement of a batch, all on the device (launch sequence; no host
+// decisions): prepare (norms, state), factors' permutation and inverse
+// diagonal blocks, x0 = LU^-1 b, max_iter refinement steps (residual, solve,
+// update with per-system stop decisions), final backward errors.
+bfx_status ir_batched_prepare(const BatchIr* d_ir, int S, int nmax, cudaStream_t s);
+bfx_status ir_batched_post_lu(const BatchIr* d_ir, int S, int nmax, cudaStream_t s);
+bfx_status ir_batched_first_solve(const BatchIr* d_ir, int S, cudaStream_t s);
+bfx_status ir_batched_step(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s);
+bfx_status ir_batched_finish(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s);
 // tcgen05 GEMM on pieces (gemm_tc.cu)
 bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,
@@ -183,6 +250,33 @@ __device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, float (&v)[16]) {
                  "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])::"memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Split of one FP32 value into its bfloat16 pieces (Sec. II-A):
+// hi = (B16)a, mid = (B16)(a - hi), lo = (B16)(a - hi - mid), (B16) = RNE.
+// Readings for values the paper does not cover: Inf/NaN go to hi (NaN made
+// quiet, sign kept), mid = lo = +0; a finite value whose RNE would overflow
+// to infinity takes hi = a truncated toward zero.
+__device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_value(uint16_t h) {
+  return __uint_as_float(static_cast<uint32_t>(h) << 16);
+}
+__device__ __forceinline__ void split_elem(float a, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const uint32_t u = __float_as_uint(a);
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  if (mag >= 0x7F800000u) {
+    h = static_cast<uint16_t>((u >> 16) | (mag > 0x7F800000u ? 0x0040u : 0u));
+    m = 0;
+    l = 0;
+    return;
+  }
+  h = (mag >= 0x7F7F8000u) ? static_cast<uint16_t>(u >> 16) : bf16_bits_rn(a);
+  const float r1 = __fsub_rn(a, bf16_value(h));
+  m = bf16_bits_rn(r1);
+  const float r2 = __fsub_rn(r1, bf16_value(m));
+  l = bf16_bits_rn(r2);
 }
 
 // Shared-memory matrix descriptor for a K-major tile written by TMA with a

@@ -78,7 +78,21 @@ struct TcArgs {
   int64_t ldc;
   int vec_c;  // C rows 16-byte aligned: float4 loads/stores
   int* err;
+  // grouped mode: many independent problems in one launch
+  const GroupTile* tiles;   // num_tiles entries
+  const GroupProblem* probs;
 };
+
+// What one output tile needs, in both modes.
+struct TileInfo {
+  int mb, nb, k_tiles, c2, M, N;
+  float* C;
+  int64_t ldc;
+  int vec_c;
+};
+
+template <bool GROUPED>
+__device__ __forceinline__ TileInfo get_tile(int t, const TcArgs& a);
 
 __device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int& mb, int& nb) {
   const int group = GROUP_M * a.tiles_n;
@@ -88,6 +102,39 @@ __device__ __forceinline__ void tile_coords(int t, const TcArgs& a, int& mb, int
   const int r = t - g * group;
   mb = first_m + r % gm;
   nb = r / gm;
+}
+
+template <>
+__device__ __forceinline__ TileInfo get_tile<false>(int t, const TcArgs& a) {
+  TileInfo ti;
+  tile_coords(t, a, ti.mb, ti.nb);
+  ti.k_tiles = a.k_tiles;
+  ti.c2 = 0;
+  ti.M = a.M;
+  ti.N = a.N;
+  ti.C = a.C;
+  ti.ldc = a.ldc;
+  ti.vec_c = a.vec_c;
+  return ti;
+}
+
+// Grouped mode: tile t of the list belongs to problem tiles[t].prob; the
+// pieces of problem p are planes p*np .. p*np+np-1 of the packed buffers.
+template <>
+__device__ __forceinline__ TileInfo get_tile<true>(int t, const TcArgs& a) {
+  const GroupTile g = a.tiles[t];
+  const GroupProblem pr = a.probs[g.prob];
+  TileInfo ti;
+  ti.mb = g.mb;
+  ti.nb = g.nb;
+  ti.k_tiles = pr.k_tiles;
+  ti.c2 = pr.plane0;
+  ti.M = pr.M;
+  ti.N = pr.N;
+  ti.C = pr.C;
+  ti.ldc = pr.ldc;
+  ti.vec_c = pr.vec_c;
+  return ti;
 }
 
 template <int MODE, int BN, int BK, int STAGES>
@@ -113,7 +160,7 @@ struct TcConfig {
   static_assert((2 * STAGES + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
 };
 
-template <int MODE, int BN, int BK, int STAGES>
+template <int MODE, int BN, int BK, int STAGES, bool GROUPED>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs args) {
@@ -165,17 +212,16 @@ __global__ void __launch_bounds__(192, 1)
       int64_t issued = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
-        int mb, nb;
-        tile_coords(t, args, mb, nb);
-        for (int kt = 0; kt < args.k_tiles; ++kt) {
+        const TileInfo ti = get_tile<GROUPED>(t, args);
+        for (int kt = 0; kt < ti.k_tiles; ++kt) {
           if (!mbar_wait_bounded(&empty[s], ph ^ 1u, err, kErrWaitEmpty)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * Cfg::STAGE;
           mbar_arrive_expect_tx(&full[s], Cfg::STAGE);
-          tma_load_3d(st, &tmA, &full[s], kt * BK, mb * BM, 0);
-          tma_load_3d(st + Cfg::STAGE_A, &tmB, &full[s], kt * BK, nb * BN, 0);
+          tma_load_3d(st, &tmA, &full[s], kt * BK, ti.mb * BM, ti.c2);
+          tma_load_3d(st + Cfg::STAGE_A, &tmB, &full[s], kt * BK, ti.nb * BN, ti.c2);
           ++issued;
           if (++s == STAGES) {
             s = 0;
@@ -202,7 +248,8 @@ __global__ void __launch_bounds__(192, 1)
         if (!mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, err, kErrWaitAccEmpty)) break;
         tc_fence_after();
         const uint32_t d0 = tmem_base + static_cast<uint32_t>(buf * Cfg::NACC * BN);
-        for (int kt = 0; kt < args.k_tiles; ++kt) {
+        const int k_tiles = get_tile<GROUPED>(t, args).k_tiles;
+        for (int kt = 0; kt < k_tiles; ++kt) {
           if (!mbar_wait_bounded(&full[s], ph, err, kErrWaitFull)) {
             ok = false;
             break;
@@ -245,15 +292,15 @@ __global__ void __launch_bounds__(192, 1)
     int buf = 0;
     uint32_t aph = 0;
     for (int t = blockIdx.x; t < args.num_tiles; t += gridDim.x) {
-      int mb, nb;
-      tile_coords(t, args, mb, nb);
+      const TileInfo ti = get_tile<GROUPED>(t, args);
+      const int mb = ti.mb, nb = ti.nb;
       bool ok = mbar_wait_bounded(&acc_full[buf], aph, err, kErrWaitAccFull);
       ok = __all_sync(0xFFFFFFFFu, ok);
       if (!ok) break;
       tc_fence_after();
       const int row = mb * BM + row_in_tile;
-      const bool row_ok = row < args.M;
-      float* crow = args.C + static_cast<int64_t>(row_ok ? row : 0) * args.ldc;
+      const bool row_ok = row < ti.M;
+      float* crow = ti.C + static_cast<int64_t>(row_ok ? row : 0) * ti.ldc;
       const uint32_t tb = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                           static_cast<uint32_t>(buf * Cfg::NACC * BN);
 #pragma unroll 1
@@ -273,9 +320,9 @@ __global__ void __launch_bounds__(192, 1)
         }
         if (!row_ok) continue;
         const int col0 = nb * BN + c * 16;
-        if (col0 >= args.N) continue;
+        if (col0 >= ti.N) continue;
         float* dst = crow + col0;
-        if (args.vec_c && col0 + 16 <= args.N) {
+        if (ti.vec_c && col0 + 16 <= ti.N) {
 #pragma unroll
           for (int i = 0; i < 16; i += 4) {
             float4 o;
@@ -294,7 +341,7 @@ __global__ void __launch_bounds__(192, 1)
             *reinterpret_cast<float4*>(dst + i) = o;
           }
         } else {
-          const int lim = min(16, args.N - col0);
+          const int lim = min(16, ti.N - col0);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             if (i < lim) {
@@ -336,16 +383,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D bfloat16 tensor {inner (K), rows, planes}, box {bk, box_rows, planes}.
+// 3-D bfloat16 tensor {inner (K), rows, planes}, box {bk, box_rows, box_planes}
+// (box_planes = all planes by default).
 bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64_t rows,
-                    int planes, int64_t ld, int64_t plane, int bk, int box_rows) {
+                    int planes, int64_t ld, int64_t plane, int bk, int box_rows,
+                    int box_planes = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
                         static_cast<cuuint64_t>(planes)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(plane) * 2};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows),
-                       static_cast<cuuint32_t>(planes)};
+                       static_cast<cuuint32_t>(box_planes > 0 ? box_planes : planes)};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapSwizzle sw = (bk * 2 == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides,
@@ -382,8 +431,10 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
   a.ldc = ldc;
   a.vec_c = (ldc % 4 == 0) && aligned(C, 16);
   a.err = device_error_word();
+  a.tiles = nullptr;
+  a.probs = nullptr;
   if (!a.err) return BFX_ECUDA;
-  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES>;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
       cudaSuccess)
     return BFX_ECUDA;
@@ -393,7 +444,64 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
   return last_launch_status();
 }
 
+template <int MODE, int BN, int BK, int STAGES>
+bfx_status run_tc_grouped(int num_tiles, const GroupTile* d_tiles, const GroupProblem* d_probs,
+                          const uint16_t* Apack, int64_t a_rows, const uint16_t* Bpack,
+                          int64_t b_rows, int64_t planes, int64_t kp, float alpha, float beta,
+                          cudaStream_t s) {
+  using Cfg = TcConfig<MODE, BN, BK, STAGES>;
+  CUtensorMap ma, mb;
+  if (!make_piece_map(&ma, Apack, kp, a_rows, static_cast<int>(planes), kp, a_rows * kp, BK, BM,
+                      Cfg::NP))
+    return BFX_EUNSUPPORTED;
+  if (!make_piece_map(&mb, Bpack, kp, b_rows, static_cast<int>(planes), kp, b_rows * kp, BK, BN,
+                      Cfg::NP))
+    return BFX_EUNSUPPORTED;
+  TcArgs a{};
+  a.num_tiles = num_tiles;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.err = device_error_word();
+  a.tiles = d_tiles;
+  a.probs = d_probs;
+  if (!a.err) return BFX_ECUDA;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+      cudaSuccess)
+    return BFX_ECUDA;
+  const int sms = current_num_sms();
+  const int grid = num_tiles < sms ? num_tiles : sms;
+  kern<<<grid, 192, Cfg::SMEM, s>>>(ma, mb, a);
+  return last_launch_status();
+}
+
 }  // namespace
+
+int gemm_bk(bfx_mode mode) { return mode == BFX_X1 ? 64 : 32; }
+
+bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
+                               const GroupProblem* d_probs, const uint16_t* Apack,
+                               int64_t a_rows, const uint16_t* Bpack, int64_t b_rows,
+                               int64_t planes, int64_t kp, float alpha, float beta,
+                               cudaStream_t s) {
+  if (num_tiles <= 0) return BFX_OK;
+  switch (mode) {
+    case BFX_X1:
+      return run_tc_grouped<1, 256, 64, 4>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X3:
+      return run_tc_grouped<3, 256, 32, 4>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X6:
+      return run_tc_grouped<6, 256, 32, 3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X9:
+      return run_tc_grouped<9, 256, 32, 3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    default:
+      return BFX_EINVAL;
+  }
+}
 
 bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,

@@ -148,11 +148,10 @@ __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
 // once per factorisation.  CTA b inverts block b: thread k solves
 // T x = e_k by column-oriented substitution in registers.
 template <bool LOWER>
-__global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __restrict__ F,
-                                                             int64_t ldf, int n,
-                                                             double* __restrict__ Dinv) {
+__device__ __forceinline__ void diag_inverse_body(const float* __restrict__ F, int64_t ldf, int n,
+                                                  int blk, double* __restrict__ D) {
   __shared__ double T[TB][TB + 1];
-  const int b0 = blockIdx.x * TB, bs = min(TB, n - b0), k = threadIdx.x;
+  const int b0 = blk * TB, bs = min(TB, n - b0), k = threadIdx.x;
   for (int e = k; e < TB * TB; e += TB) {
     const int i = e / TB, l = e % TB;
     T[i][l] = (i < bs && l < bs) ? static_cast<double>(F[static_cast<int64_t>(b0 + i) * ldf + b0 + l])
@@ -176,9 +175,16 @@ __global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __rest
       for (int i = 0; i < l; ++i) x[i] = fma(-T[i][l], x[l], x[i]);
     }
   }
-  double* D = Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB;
 #pragma unroll
   for (int i = 0; i < TB; ++i) D[i * TB + k] = x[i];  // column k of the inverse
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __restrict__ F,
+                                                             int64_t ldf, int n,
+                                                             double* __restrict__ Dinv) {
+  diag_inverse_body<LOWER>(F, ldf, n, blockIdx.x,
+                           Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB);
 }
 
 // One block step of L y = v or U y = v for the diagonal block [b0, b0+bs),
@@ -263,6 +269,245 @@ __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const doub
     x[i * ldx + c] = xv;
     atomic_max_nonneg(&dn[c], fabs(dv));
     atomic_max_nonneg(&xn[c], fabs(xv));
+  }
+}
+
+// ------------------------------------------------------------- batched forms
+constexpr int BIR_THREADS = 256;
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  // max over the CTA of non-negative values (NaN propagates: compared as bits)
+  unsigned long long u = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, u, o);
+    u = w > u ? w : u;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __longlong_as_double(u);
+  __syncthreads();
+  unsigned long long m = 0;
+  for (int i = 0; i < BIR_THREADS / 32; ++i) {
+    const unsigned long long w = __double_as_longlong(red[i]);
+    m = w > m ? w : m;
+  }
+  return __longlong_as_double(m);
+}
+
+// |A|_inf, |b|_inf, state reset.
+__global__ void __launch_bounds__(BIR_THREADS) bir_prepare_kernel(const BatchIr* __restrict__ sys) {
+  __shared__ double red[BIR_THREADS / 32];
+  const BatchIr q = sys[blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double am = 0.0;
+  for (int i = wid; i < q.n; i += BIR_THREADS / 32) {
+    double sum = 0.0;
+    for (int l = lane; l < q.n; l += 32) sum += fabs(static_cast<double>(q.A[static_cast<int64_t>(i) * q.n + l]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    am = fmax(am, sum);
+  }
+  double bm = 0.0;
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) bm = fmax(bm, fabs(q.b[e]));
+  const double an = block_max(am, red);
+  const double bn = block_max(bm, red);
+  if (threadIdx.x == 0) {
+    BatchIrState st{};
+    st.active = 1;
+    st.anorm = an;
+    st.bnorm = bn;
+    st.dprev = INFINITY;
+    st.berr = INFINITY;
+    *q.st = st;
+  }
+}
+
+// After the factorisation: a zero pivot stops the system; permutation from the
+// pivots; inverses of the diagonal blocks (grid: blocks x systems).
+constexpr int BIR_MAXN = 1024;
+__global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restrict__ sys) {
+  __shared__ int32_t sp[2 * BIR_MAXN];
+  const BatchIr q = sys[blockIdx.y];
+  const int nblk = (q.n + TB - 1) / TB;
+  if (blockIdx.x == 0) {  // the permutation, staged in shared memory
+    for (int i = threadIdx.x; i < q.n; i += TB) {
+      sp[i] = i;
+      sp[BIR_MAXN + i] = q.ipiv[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (*q.info != 0) q.st->active = 0;
+      for (int j = 0; j < q.n; ++j) {
+        const int r = sp[BIR_MAXN + j];
+        if (r != j) {
+          const int32_t t = sp[j];
+          sp[j] = sp[r];
+          sp[r] = t;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < q.n; i += TB) q.perm[i] = sp[i];
+  }
+  if (static_cast<int>(blockIdx.x) >= 2 * nblk) return;
+  const bool lower = static_cast<int>(blockIdx.x) < nblk;
+  const int blk = lower ? blockIdx.x : blockIdx.x - nblk;
+  if (lower)
+    diag_inverse_body<true>(q.LU, q.n, q.n, blk, q.Linv + static_cast<int64_t>(blk) * TB * TB);
+  else
+    diag_inverse_body<false>(q.LU, q.n, q.n, blk, q.Uinv + static_cast<int64_t>(blk) * TB * TB);
+}
+
+// d <- U^-1 L^-1 P r for one system in one CTA: blocks in sequence, each
+// block's inverse applied (a thread per row and column), then the rows still
+// to solve updated.
+__device__ void bir_solve_body(const BatchIr& q) {
+  __shared__ double y[TB][MAXR + 1];
+  const int n = q.n, R = q.nrhs, t = threadIdx.x;
+  for (int e = t; e < n * R; e += BIR_THREADS) {
+    const int i = e / R, c = e % R;
+    q.d[e] = q.r[static_cast<int64_t>(q.perm[i]) * R + c];
+  }
+  __syncthreads();
+  const int nblk = (n + TB - 1) / TB;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lower = pass == 0;
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int blk = lower ? bb : nblk - 1 - bb;
+      const int b0 = blk * TB, bs = min(TB, n - b0);
+      const double* D = (lower ? q.Linv : q.Uinv) + static_cast<int64_t>(blk) * TB * TB;
+      for (int e = t; e < bs * R; e += BIR_THREADS) {
+        const int i = e / R, c = e % R;
+        double s0 = 0.0, s1 = 0.0;
+        for (int l = 0; l < bs; l += 2) {
+          s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+          if (l + 1 < bs) s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
+        }
+        y[i][c] = s0 + s1;
+      }
+      __syncthreads();
+      for (int e = t; e < bs * R; e += BIR_THREADS) {
+        const int i = e / R, c = e % R;
+        q.d[static_cast<int64_t>(b0 + i) * R + c] = y[i][c];
+      }
+      const int rs = lower ? b0 + bs : 0, re = lower ? n : b0;
+      for (int e = t; e < (re - rs) * R; e += BIR_THREADS) {
+        const int i = rs + e / R, c = e % R;
+        const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
+        double s0 = 0.0, s1 = 0.0;
+        for (int l = 0; l < bs; l += 2) {
+          s0 = fma(static_cast<double>(fr[l]), y[l][c], s0);
+          if (l + 1 < bs) s1 = fma(static_cast<double>(fr[l + 1]), y[l + 1][c], s1);
+        }
+        q.d[static_cast<int64_t>(i) * R + c] -= s0 + s1;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// x0 = LU^-1 b
+__global__ void __launch_bounds__(BIR_THREADS) bir_first_solve_kernel(const BatchIr* __restrict__ sys) {
+  __shared__ double red[BIR_THREADS / 32];
+  const BatchIr q = sys[blockIdx.x];
+  if (!q.st->active) return;
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) q.r[e] = q.b[e];
+  __syncthreads();
+  bir_solve_body(q);
+  double xm = 0.0;
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) {
+    q.x[e] = q.d[e];
+    xm = fmax(xm, fabs(q.d[e]));
+  }
+  const double xn = block_max(xm, red);
+  if (threadIdx.x == 0) q.st->dprev = xn;
+}
+
+// r = b - A x for one system (FP64; warp a row).  Returns max |r| when asked.
+__device__ double bir_residual_body(const BatchIr& q, double* red, bool want_max) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, n = q.n, R = q.nrhs;
+  double rm = 0.0;
+  for (int i = wid; i < n; i += BIR_THREADS / 32) {
+    const float* a = q.A + static_cast<int64_t>(i) * n;
+    for (int c = 0; c < R; ++c) {
+      double sum = 0.0;
+      for (int l = lane; l < n; l += 32) sum = fma(static_cast<double>(a[l]), q.x[static_cast<int64_t>(l) * R + c], sum);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+      const double v = q.b[static_cast<int64_t>(i) * R + c] - sum;
+      if (lane == 0) q.r[static_cast<int64_t>(i) * R + c] = v;
+      rm = fmax(rm, fabs(v));
+    }
+  }
+  return want_max ? block_max(rm, red) : 0.0;
+}
+
+// One refinement step of every active system: r = b - A x, d = LU^-1 P r,
+// x += d, and the stop decision (converged / stalled) on the device.
+__global__ void __launch_bounds__(BIR_THREADS) bir_step_kernel(const BatchIr* __restrict__ sys,
+                                                              BatchIrParams p) {
+  __shared__ double red[BIR_THREADS / 32];
+  const BatchIr q = sys[blockIdx.x];
+  if (!q.st->active) return;
+  bir_residual_body(q, red, false);
+  __syncthreads();
+  bir_solve_body(q);
+  double dm = 0.0, xm = 0.0;
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) {
+    const double xv = q.x[e] + q.d[e];
+    q.x[e] = xv;
+    dm = fmax(dm, fabs(q.d[e]));
+    xm = fmax(xm, fabs(xv));
+  }
+  const double dn = block_max(dm, red);
+  const double xn = block_max(xm, red);
+  if (threadIdx.x == 0) {
+    BatchIrState* st = q.st;
+    st->iters += 1;
+    if (!(dn == dn) || !(xn == xn)) {
+      st->active = 0;
+    } else if (dn <= p.tol * xn) {
+      st->active = 0;
+      st->conv = 1;
+    } else if (dn >= p.stall * st->dprev) {
+      st->active = 0;
+      st->stalled = 1;
+    } else {
+      st->dprev = dn;
+    }
+  }
+}
+
+// Backward error of every system; stalled systems within tol_b count as converged.
+__global__ void __launch_bounds__(BIR_THREADS) bir_finish_kernel(const BatchIr* __restrict__ sys,
+                                                                BatchIrParams p) {
+  __shared__ double red[BIR_THREADS / 32];
+  const BatchIr q = sys[blockIdx.x];
+  if (*q.info != 0) {
+    if (threadIdx.x == 0) {
+      q.out->converged = 0;
+      q.out->iters = 0;
+      q.out->info = *q.info;
+      q.out->berr = INFINITY;
+    }
+    return;
+  }
+  const double rn = bir_residual_body(q, red, true);
+  double xm = 0.0;
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) xm = fmax(xm, fabs(q.x[e]));
+  const double xn = block_max(xm, red);
+  if (threadIdx.x == 0) {
+    BatchIrState* st = q.st;
+    const double den = st->anorm * xn + st->bnorm;
+    double be = den > 0.0 ? rn / den : 0.0;
+    if (!(be == be)) be = INFINITY;
+    st->berr = be;
+    if (!st->conv && st->stalled && be <= p.tol_b) st->conv = 1;
+    st->active = 0;
+    q.out->converged = st->conv;
+    q.out->iters = st->iters;
+    q.out->info = 0;
+    q.out->berr = be;
   }
 }
 
@@ -356,6 +601,35 @@ bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int n
 }
 
 }  // namespace
+
+bfx_status ir_batched_prepare(const BatchIr* d_ir, int S, int nmax, cudaStream_t s) {
+  (void)nmax;
+  if (S <= 0) return BFX_OK;
+  bir_prepare_kernel<<<S, BIR_THREADS, 0, s>>>(d_ir);
+  return last_launch_status();
+}
+bfx_status ir_batched_post_lu(const BatchIr* d_ir, int S, int nmax, cudaStream_t s) {
+  if (S <= 0) return BFX_OK;
+  const unsigned nblk = static_cast<unsigned>(ceil_div(nmax, TB));
+  bir_post_lu_kernel<<<dim3(2 * nblk, S), TB, 0, s>>>(d_ir);
+  return last_launch_status();
+}
+bfx_status ir_batched_first_solve(const BatchIr* d_ir, int S, cudaStream_t s) {
+  if (S <= 0) return BFX_OK;
+  bir_first_solve_kernel<<<S, BIR_THREADS, 0, s>>>(d_ir);
+  return last_launch_status();
+}
+bfx_status ir_batched_step(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s) {
+  if (S <= 0) return BFX_OK;
+  bir_step_kernel<<<S, BIR_THREADS, 0, s>>>(d_ir, p);
+  return last_launch_status();
+}
+bfx_status ir_batched_finish(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s) {
+  if (S <= 0) return BFX_OK;
+  bir_finish_kernel<<<S, BIR_THREADS, 0, s>>>(d_ir, p);
+  return last_launch_status();
+}
+
 }  // namespace bfx
 
 using namespace bfx;

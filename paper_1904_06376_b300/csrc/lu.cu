@@ -49,9 +49,9 @@ constexpr size_t TILE_SMEM_MAX = 200 * 1024;   // tile rows kept in shared memor
 // then the tile rows of the block columns right of the tile are solved with
 // the tile's unit lower triangle (forward substitution, FMA, l in order).
 template <bool use_smem>
-__global__ void __launch_bounds__(PANEL_THREADS)
-    lu_tile_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
-                   int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+__device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, int n, int J0,
+                                          int JB, int j0, int jw, int32_t* __restrict__ ipiv,
+                                          int32_t* __restrict__ info) {
   extern __shared__ float tile[];  // (n - j0) x TILE_W when use_smem
   __shared__ ArgMax warp_best[PANEL_THREADS / 32];
   __shared__ int s_piv;
@@ -173,14 +173,22 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   }
 }
 
+template <bool use_smem>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_tile_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
+                   int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+  tile_body<use_smem>(A, lda, n, J0, JB, j0, jw, ipiv, info);
+}
+
 // Rows below the tile, block columns right of it: a <- fma(-l_rk, u_kc, a)
-// for the jw tile columns k in order.
-__global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
-                                      int j0, int jw) {
+// for the jw tile columns k in order.  Grid-stride with block `bid` of `nbk`.
+__device__ __forceinline__ void tile_update_body(float* __restrict__ A, int64_t lda, int n, int J0,
+                                                 int JB, int j0, int jw, int bid, int nbk) {
   const int cs = j0 + jw, ncol = J0 + JB - cs;
+  if (ncol <= 0) return;
   const int64_t total = static_cast<int64_t>(n - cs) * ncol;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  for (int64_t e = bid * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(nbk) * blockDim.x) {
     const int r = cs + static_cast<int>(e / ncol);
     const int c = cs + static_cast<int>(e % ncol);
     const float* lr = A + static_cast<int64_t>(r) * lda + j0;
@@ -190,15 +198,19 @@ __global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n,
   }
 }
 
+__global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
+                                      int j0, int jw) {
+  tile_update_body(A, lda, n, J0, JB, j0, jw, blockIdx.x, gridDim.x);
+}
+
 // Apply the swaps ipiv[j0 .. j0+jb) to every column outside [j0, j0+jb).
 // Warp 0 first turns the sequential swaps into their net effect on the at
 // most 2 jb rows they touch (slot k ends up holding the original row
 // cont[k]); then every thread moves the touched rows of its column with all
 // loads issued before the stores.
 constexpr int LASWP_COLS = 64;
-__global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict__ A, int64_t lda,
-                                                             int n, int j0, int jb,
-                                                             const int32_t* __restrict__ ipiv) {
+__device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int n, int j0,
+                                           int jb, const int32_t* __restrict__ ipiv, int cb) {
   extern __shared__ float vals[];  // (2 jb) x LASWP_COLS
   __shared__ int rowid[256];
   __shared__ int cont[256];
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict_
     if (t == 0) nslots = ns;
   }
   __syncthreads();
-  const int64_t idx = blockIdx.x * static_cast<int64_t>(LASWP_COLS) + t;
+  const int64_t idx = cb * static_cast<int64_t>(LASWP_COLS) + t;
   if (idx >= n - jb) return;
   const int c = static_cast<int>(idx < j0 ? idx : idx + jb);
   const int ns = nslots;
@@ -266,6 +278,12 @@ __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict_
     A[static_cast<int64_t>(rowid[k]) * lda + c] = vals[k * LASWP_COLS + t];
 }
 
+__global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict__ A, int64_t lda,
+                                                             int n, int j0, int jb,
+                                                             const int32_t* __restrict__ ipiv) {
+  laswp_body(A, lda, n, j0, jb, ipiv, blockIdx.x);
+}
+
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
 // one thread a column of A12 held in registers (NB >= jb, unrolled).
 // Column-oriented: x_i receives -l_il x_l for l = 0, 1, ..., i-1 in order -
@@ -273,15 +291,15 @@ __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict_
 // updates for different i independent of each other.
 constexpr int TRSM_COLS = 64;
 template <int NB>
-__global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
-                                                           int n, int j0, int jb) {
+__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int n, int j0,
+                                          int jb, int cb) {
   extern __shared__ float L11[];  // NB x NB, the jb x jb triangle padded with zeros
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, l = e % NB;
     L11[e] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
   }
   __syncthreads();
-  const int64_t c = j0 + jb + blockIdx.x * static_cast<int64_t>(TRSM_COLS) + threadIdx.x;
+  const int64_t c = j0 + jb + cb * static_cast<int64_t>(TRSM_COLS) + threadIdx.x;
   if (c >= n) return;
   float* col = A + static_cast<int64_t>(j0) * lda + c;
   float x[NB];
@@ -299,6 +317,90 @@ __global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(float* __restrict__ 
 #pragma unroll
   for (int i = 1; i < NB; ++i)
     if (i < jb) col[static_cast<int64_t>(i) * lda] = x[i];
+}
+
+template <int NB>
+__global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
+                                                           int n, int j0, int jb) {
+  trsm_body<NB>(A, lda, n, j0, jb, blockIdx.x);
+}
+
+// ------------------------------------------------------------- batched forms
+// blockIdx.y (or x for the tile kernel) selects a system; systems with no
+// work in the step return at once.
+template <bool use_smem>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_tile_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int j0) {
+  const BatchLu b = sys[blockIdx.x];
+  const int JB = min(nb, b.n - J0);
+  const int jw = min(TILE_W, J0 + JB - j0);
+  if (JB <= 0 || jw <= 0) return;
+  tile_body<use_smem>(b.A, b.n, b.n, J0, JB, j0, jw, b.ipiv, b.info);
+}
+
+__global__ void lu_tile_update_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0,
+                                              int j0) {
+  const BatchLu b = sys[blockIdx.y];
+  const int JB = min(nb, b.n - J0);
+  const int jw = min(TILE_W, J0 + JB - j0);
+  if (JB <= 0 || jw <= 0) return;
+  tile_update_body(b.A, b.n, b.n, J0, JB, j0, jw, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(LASWP_COLS)
+    lu_laswp_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
+  const BatchLu b = sys[blockIdx.y];
+  const int JB = min(nb, b.n - J0);
+  if (JB <= 0 || blockIdx.x * LASWP_COLS >= b.n - JB) return;
+  laswp_body(b.A, b.n, b.n, J0, JB, b.ipiv, blockIdx.x);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(TRSM_COLS)
+    lu_trsm_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
+  const BatchLu b = sys[blockIdx.y];
+  const int JB = min(nb, b.n - J0);
+  if (JB <= 0 || J0 + JB + static_cast<int>(blockIdx.x) * TRSM_COLS >= b.n) return;
+  trsm_body<NB>(b.A, b.n, b.n, J0, JB, blockIdx.x);
+}
+
+// Pieces of L21 (rows below the block, block columns) and of U12^T for the
+// grouped trailing update; columns past the block width are written as zero
+// so a K-slice never reads stale values.
+__global__ void lu_split_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int np,
+                                        uint16_t* __restrict__ packA, uint16_t* __restrict__ packB,
+                                        int64_t slot_rows, int64_t kp) {
+  const BatchLu b = sys[blockIdx.y];
+  const int JB = min(nb, b.n - J0);
+  const int M = b.n - J0 - JB;
+  if (JB <= 0 || M <= 0) return;
+  const int64_t plane = slot_rows * kp;
+  uint16_t* pa = packA + static_cast<int64_t>(blockIdx.y) * np * plane;
+  uint16_t* pb = packB + static_cast<int64_t>(blockIdx.y) * np * plane;
+  const int64_t total = static_cast<int64_t>(M) * kp;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    // L21: row r, column c  (c fastest: coalesced reads of a row)
+    {
+      const int r = static_cast<int>(e / kp), c = static_cast<int>(e % kp);
+      const float v = c < JB ? b.A[static_cast<int64_t>(J0 + JB + r) * b.n + J0 + c] : 0.0f;
+      uint16_t h, m, l;
+      split_elem(v, h, m, l);
+      pa[r * kp + c] = h;
+      if (np > 1) pa[plane + r * kp + c] = m;
+      if (np > 2) pa[2 * plane + r * kp + c] = l;
+    }
+    // U12^T: row c' (a column of U12), entry k  (c' fastest: coalesced reads)
+    {
+      const int k = static_cast<int>(e / M), cp = static_cast<int>(e % M);
+      const float v = k < JB ? b.A[static_cast<int64_t>(J0 + k) * b.n + J0 + JB + cp] : 0.0f;
+      uint16_t h, m, l;
+      split_elem(v, h, m, l);
+      pb[cp * kp + k] = h;
+      if (np > 1) pb[plane + cp * kp + k] = m;
+      if (np > 2) pb[2 * plane + cp * kp + k] = l;
+    }
+  }
 }
 
 struct LuWs {
@@ -385,6 +487,58 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     }
     if (st != BFX_OK) return st;
   }
+  return last_launch_status();
+}
+
+bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_desc, int S,
+                            int nb, int J0, uint16_t* packA, uint16_t* packB, int64_t slot_rows,
+                            int64_t kp, cudaStream_t s) {
+  int S_act = 0;
+  while (S_act < S && h_n_desc[S_act] > J0) ++S_act;
+  if (S_act == 0) return BFX_OK;
+  const int nmax = h_n_desc[0];
+  static bool attrs = false;
+  if (!attrs) {
+    if (cudaFuncSetAttribute(lu_tile_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess ||
+        cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) != cudaSuccess ||
+        cudaFuncSetAttribute(lu_trsm_batched_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             128 * 128 * static_cast<int>(sizeof(float))) != cudaSuccess)
+      return BFX_ECUDA;
+    attrs = true;
+  }
+  for (int j0 = J0; j0 < J0 + nb; j0 += TILE_W) {
+    int S_t = 0;
+    while (S_t < S_act && h_n_desc[S_t] > j0) ++S_t;
+    if (S_t == 0) break;
+    const size_t tsm = static_cast<size_t>(nmax - j0) * TILE_W * sizeof(float);
+    if (tsm <= TILE_SMEM_MAX)
+      lu_tile_batched_kernel<true><<<S_t, PANEL_THREADS, tsm, s>>>(d_sys, nb, J0, j0);
+    else
+      lu_tile_batched_kernel<false><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
+    const int64_t work = static_cast<int64_t>(nmax - j0) * nb;
+    const unsigned gx = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), 32)));
+    lu_tile_update_batched_kernel<<<dim3(gx, S_t), 256, 0, s>>>(d_sys, nb, J0, j0);
+  }
+  const unsigned cblk = static_cast<unsigned>(ceil_div(nmax, LASWP_COLS));
+  lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_COLS,
+                            static_cast<size_t>(2 * nb) * LASWP_COLS * sizeof(float), s>>>(d_sys, nb,
+                                                                                         J0);
+  const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
+  const size_t tsmem = static_cast<size_t>(tnb) * tnb * sizeof(float);
+  const unsigned tblk = static_cast<unsigned>(ceil_div(nmax, TRSM_COLS));
+  if (tnb == 32)
+    lu_trsm_batched_kernel<32><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+  else if (tnb == 64)
+    lu_trsm_batched_kernel<64><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+  else
+    lu_trsm_batched_kernel<128><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+  const int np = mode_pieces(mode);
+  const int64_t sw = static_cast<int64_t>(nmax) * kp;
+  const unsigned sblk = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(sw, 256), 64)));
+  lu_split_batched_kernel<<<dim3(sblk, S_act), 256, 0, s>>>(d_sys, nb, J0, np, packA, packB,
+                                                            slot_rows, kp);
   return last_launch_status();
 }
 

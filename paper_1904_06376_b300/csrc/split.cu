@@ -13,31 +13,7 @@
 namespace bfx {
 namespace {
 
-__device__ __forceinline__ uint16_t bf16_bits_rn(float x) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf16_value(uint16_t h) {
-  return __uint_as_float(static_cast<uint32_t>(h) << 16);
-}
-
-// One element.  Readings for values the paper does not cover: Inf/NaN go to
-// hi (NaN made quiet, sign kept), mid = lo = +0; a finite value whose RNE
-// would overflow to infinity takes hi = a truncated toward zero.
-__device__ __forceinline__ void split_elem(float a, uint16_t& h, uint16_t& m, uint16_t& l) {
-  const uint32_t u = __float_as_uint(a);
-  const uint32_t mag = u & 0x7FFFFFFFu;
-  if (mag >= 0x7F800000u) {
-    h = static_cast<uint16_t>((u >> 16) | (mag > 0x7F800000u ? 0x0040u : 0u));
-    m = 0;
-    l = 0;
-    return;
-  }
-  h = (mag >= 0x7F7F8000u) ? static_cast<uint16_t>(u >> 16) : bf16_bits_rn(a);
-  const float r1 = __fsub_rn(a, bf16_value(h));
-  m = bf16_bits_rn(r1);
-  const float r2 = __fsub_rn(r1, bf16_value(m));
-  l = bf16_bits_rn(r2);
-}
+// split_elem (the per-element decomposition) lives in bfx_internal.cuh.
 
 __device__ __forceinline__ uint4 pack8(const uint16_t* q) {
   uint4 o;

@@ -272,6 +272,53 @@ BFX_API bfx_status bfx_batch_solve(bfx_batch plan, const float* d_A, const doubl
                                    size_t ws_bytes, bfx_stream stream);
 BFX_API void bfx_batch_destroy(bfx_batch plan);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous admission of solve requests (A x = b, FP32 A, FP64 b,
+ * any n and nrhs) into a fixed device-memory budget.  A server allocates its
+ * pool (budget_bytes) once at creation and starts max_inflight worker threads,
+ * each with its own CUDA stream.  Requests wait in FIFO order and are admitted
+ * when a worker is free and the pool can hold the request's buffers (A, b, x
+ * and the bfx_solve_ir workspace); admitted requests run concurrently and
+ * their kernels overlap on the device.  Each request is solved exactly as
+ * bfx_solve_ir would solve it alone (same kernels, same order of operations),
+ * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb}.
+ * The caller's host buffers h_A (n x n), h_b (n x nrhs) must stay valid and
+ * h_x (n x nrhs, output) writable until the request completes.
+ * submit: BFX_ENOMEM if the request can never fit the budget; never blocks.
+ * wait: blocks until done (timeout_s < 0: no limit) and returns its result,
+ * releasing the ticket; BFX_TIMEOUT if still pending after timeout_s.
+ * destroy: running requests finish; queued ones are dropped. */
+typedef struct bfx_server_config {
+  size_t budget_bytes;
+  int max_inflight;
+  bfx_mode mode;
+  int nb;       /* LU block width (0 = 64) */
+  int escalate; /* refactor with more products when refinement stalls */
+} bfx_server_config;
+typedef struct bfx_request_result {
+  int32_t status;           /* bfx_status of the solve */
+  int32_t converged;
+  int32_t iters;
+  int32_t info;
+  int32_t mode_used;
+  int32_t refactorizations;
+  double berr;
+  double latency_s;         /* submission to completion */
+  double queue_s;           /* submission to admission */
+} bfx_request_result;
+typedef struct bfx_server_stats_t {
+  int32_t queued, running, peak_running, pad;
+  size_t pool_bytes, used_bytes, peak_used_bytes;
+} bfx_server_stats_t;
+typedef struct bfx_server_impl* bfx_server;
+BFX_API bfx_status bfx_server_create(bfx_server* out, const bfx_server_config* cfg);
+BFX_API bfx_status bfx_server_submit(bfx_server server, int64_t n, int64_t nrhs, const float* h_A,
+                                     const double* h_b, double* h_x, int64_t* ticket);
+BFX_API bfx_status bfx_server_wait(bfx_server server, int64_t ticket, bfx_request_result* out,
+                                   double timeout_s);
+BFX_API bfx_status bfx_server_stats(bfx_server server, bfx_server_stats_t* out);
+BFX_API void bfx_server_destroy(bfx_server server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ from ._bfx import (  # noqa: F401
     solve_ir,
     library_path,
     num_sms,
+    Server,
     sgemm_simt,
     split,
     split_transpose,

@@ -66,6 +66,11 @@ def lib() -> ctypes.CDLL:
         "bfx_batch_workspace_size": (sz, [vp]),
         "bfx_batch_solve": (i32, [vp, vp, vp, vp, vp, vp, sz, vp]),
         "bfx_batch_destroy": (None, [vp]),
+        "bfx_server_create": (i32, [vp, vp]),
+        "bfx_server_submit": (i32, [vp, i64, i64, vp, vp, vp, vp]),
+        "bfx_server_wait": (i32, [vp, i64, vp, ctypes.c_double]),
+        "bfx_server_stats": (i32, [vp, vp]),
+        "bfx_server_destroy": (None, [vp]),
         "bfx_dot_bf16xN": (i32, [i32, i64, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
@@ -333,3 +338,76 @@ class Batch:
         ints = raw[:, :16].copy().view(np.int32).reshape(-1, 4)
         berr = raw[:, 16:].copy().view(np.float64).ravel()
         return ints[:, 0], ints[:, 1], ints[:, 2], berr
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("mode", ctypes.c_int),
+                ("nb", ctypes.c_int), ("escalate", ctypes.c_int)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("converged", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("info", ctypes.c_int32), ("mode_used", ctypes.c_int32),
+                ("refactorizations", ctypes.c_int32), ("berr", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("peak_running", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("pool_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_used_bytes", ctypes.c_size_t)]
+
+
+class Server:
+    """Continuous-admission solve server (bfx_server_* of the C ABI).
+
+    submit() takes host numpy arrays (kept alive here until the request
+    completes) and returns a ticket; wait() returns (x, result dict)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 16, mode: int = BFX_X3, nb: int = 64,
+                 escalate: bool = True):
+        cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(mode), int(nb), int(bool(escalate)))
+        h = ctypes.c_void_p()
+        _check("bfx_server_create", lib().bfx_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self.handle = h
+        self._live = {}
+
+    def submit(self, A, b):
+        import numpy as np
+
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if b.ndim == 1:
+            b = b[:, None]
+        n, nrhs = b.shape
+        x = np.empty((n, nrhs), dtype=np.float64)
+        t = ctypes.c_int64()
+        _check("bfx_server_submit", lib().bfx_server_submit(self.handle, n, nrhs, A.ctypes.data, b.ctypes.data,
+                                                           x.ctypes.data, ctypes.byref(t)))
+        self._live[t.value] = (A, b, x)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        r = RequestResult()
+        code = lib().bfx_server_wait(self.handle, ticket, ctypes.byref(r), float(timeout_s))
+        if code == 7:
+            return None
+        _check("bfx_server_wait", code)
+        _, _, x = self._live.pop(ticket)
+        return x, r.as_dict()
+
+    def stats(self):
+        st = ServerStats()
+        _check("bfx_server_stats", lib().bfx_server_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "pad"}
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bfx_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

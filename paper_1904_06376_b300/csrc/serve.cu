@@ -1,0 +1,299 @@
+// Serving runtime: continuous admission of solve requests of mixed sizes.
+//
+// A server owns one device-memory pool of a fixed budget (allocated once at
+// creation) and a set of worker threads, each with its own CUDA stream.  A
+// submitted request waits in a FIFO queue; it is admitted as soon as a worker
+// is free AND the pool can hold its buffers (matrix, right-hand sides,
+// solution and the solve workspace).  Admitted requests run concurrently, so
+// kernels of different requests overlap on the device: the single-CTA panel
+// tiles of one factorisation run beside the grouped or tensor-core updates of
+// others.  Factors and refinement state stay in the request's device buffers
+// for the whole solve; only A, b (in) and x (out) cross the bus.  Latency is
+// measured from submission to completion.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "bfx_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit sub-allocator over one device allocation (256-byte granules).
+class Pool {
+ public:
+  bool init(size_t bytes) {
+    bytes_ = bytes / 256 * 256;
+    if (cudaMalloc(&base_, bytes_) != cudaSuccess) {
+      base_ = nullptr;
+      return false;
+    }
+    free_[0] = bytes_;
+    return true;
+  }
+  void release() {
+    if (base_) cudaFree(base_);
+    base_ = nullptr;
+  }
+  // offset or SIZE_MAX
+  size_t alloc(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        used_ += bytes;
+        return off;
+      }
+    }
+    return SIZE_MAX;
+  }
+  void free(size_t off, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {  // merge right
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {  // merge left
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  char* base() const { return static_cast<char*>(base_); }
+  size_t capacity() const { return bytes_; }
+  size_t used() const { return used_; }
+
+ private:
+  void* base_ = nullptr;
+  size_t bytes_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+struct Request {
+  int64_t ticket, n, nrhs;
+  const float* hA;
+  const double* hb;
+  double* hx;
+  Clock::time_point t_submit, t_start, t_done;
+  bfx_request_result res{};
+  bool done = false;
+  size_t bytes = 0, off = 0;
+};
+
+}  // namespace
+
+struct bfx_server_impl {
+  bfx_server_config cfg{};
+  int device = 0;
+  Pool pool;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::map<int64_t, Request*> all;
+  std::vector<std::thread> workers;
+  int64_t next_ticket = 1;
+  int running = 0;
+  bool stop = false;
+  size_t peak_used = 0;
+  int peak_running = 0;
+};
+
+namespace {
+
+size_t request_bytes(const bfx_server_config& cfg, int64_t n, int64_t nrhs) {
+  const size_t a = sizeof(float) * n * n;
+  const size_t v = sizeof(double) * n * nrhs;
+  const size_t ws = bfx_solve_ir_workspace_size(cfg.mode, n, nrhs, cfg.nb);
+  return (a + 255) / 256 * 256 + 2 * ((v + 255) / 256 * 256) + ws + 256;
+}
+
+void worker_main(bfx_server_impl* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (;;) {
+        if (S->stop) break;
+        if (!S->queue.empty()) {
+          Request* h = S->queue.front();
+          const size_t off = S->pool.alloc(h->bytes);
+          if (off != SIZE_MAX) {
+            h->off = off;
+            r = h;
+            S->queue.pop_front();
+            S->running += 1;
+            S->peak_running = std::max(S->peak_running, S->running);
+            S->peak_used = std::max(S->peak_used, S->pool.used());
+            break;
+          }
+        }
+        S->cv_work.wait(lk);
+      }
+    }
+    if (!r) break;
+    r->t_start = Clock::now();
+    char* base = S->pool.base() + r->off;
+    const int64_t n = r->n, R = r->nrhs;
+    float* dA = reinterpret_cast<float*>(base);
+    size_t o = (sizeof(float) * n * n + 255) / 256 * 256;
+    double* db = reinterpret_cast<double*>(base + o);
+    o += (sizeof(double) * n * R + 255) / 256 * 256;
+    double* dx = reinterpret_cast<double*>(base + o);
+    o += (sizeof(double) * n * R + 255) / 256 * 256;
+    void* ws = base + o;
+    const size_t wsb = r->bytes - o;
+    bfx_status status = BFX_OK;
+    if (cudaMemcpyAsync(dA, r->hA, sizeof(float) * n * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(db, r->hb, sizeof(double) * n * R, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      status = BFX_ECUDA;
+    bfx_ir_params p{50, 1.1102230246251565e-16, -1.0, 0.5, S->cfg.escalate, S->cfg.nb};
+    bfx_ir_result ir{};
+    if (status == BFX_OK)
+      status = bfx_solve_ir(S->cfg.mode, n, R, dA, n, db, R, dx, R, &p, &ir, ws, wsb, st);
+    if (status == BFX_OK || status == BFX_NOT_CONVERGED || status == BFX_SINGULAR) {
+      if (cudaMemcpyAsync(r->hx, dx, sizeof(double) * n * R, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        status = BFX_ECUDA;
+    } else {
+      cudaStreamSynchronize(st);
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      r->t_done = Clock::now();
+      r->res.status = status;
+      r->res.converged = ir.converged;
+      r->res.iters = ir.iters;
+      r->res.info = ir.info;
+      r->res.mode_used = ir.mode_used;
+      r->res.refactorizations = ir.refactorizations;
+      r->res.berr = ir.berr;
+      r->res.latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+      r->res.queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
+      r->done = true;
+      S->pool.free(r->off, r->bytes);
+      S->running -= 1;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+extern "C" {
+
+BFX_API bfx_status bfx_server_create(bfx_server* out, const bfx_server_config* cfg) {
+  if (!out || !cfg) return BFX_EINVAL;
+  *out = nullptr;
+  if (cfg->budget_bytes < (1u << 20) || cfg->max_inflight < 1 || cfg->max_inflight > 256)
+    return BFX_EINVAL;
+  if (cfg->mode != BFX_FP32 && bfx::mode_pieces(cfg->mode) == 0) return BFX_EINVAL;
+  auto* S = new bfx_server_impl();
+  S->cfg = *cfg;
+  if (S->cfg.nb <= 0) S->cfg.nb = 64;
+  if (cudaGetDevice(&S->device) != cudaSuccess || !S->pool.init(cfg->budget_bytes)) {
+    delete S;
+    return BFX_ENOMEM;
+  }
+  // one-time per-device lookups happen here, before any worker runs
+  if (!bfx::device_error_word() || bfx::current_num_sms() <= 0 || bfx::current_cc() <= 0) {
+    S->pool.release();
+    delete S;
+    return BFX_ECUDA;
+  }
+  for (int i = 0; i < cfg->max_inflight; ++i) S->workers.emplace_back(worker_main, S);
+  *out = S;
+  return BFX_OK;
+}
+
+BFX_API bfx_status bfx_server_submit(bfx_server S, int64_t n, int64_t nrhs, const float* h_A,
+                                     const double* h_b, double* h_x, int64_t* ticket) {
+  if (!S || !ticket || n < 1 || nrhs < 1 || nrhs > (1 << 20) || !h_A || !h_b || !h_x) return BFX_EINVAL;
+  if (n >= (1 << 30)) return BFX_EUNSUPPORTED;
+  auto* r = new Request();
+  r->n = n;
+  r->nrhs = nrhs;
+  r->hA = h_A;
+  r->hb = h_b;
+  r->hx = h_x;
+  r->bytes = request_bytes(S->cfg, n, nrhs);
+  if (r->bytes > S->pool.capacity()) {
+    delete r;
+    return BFX_ENOMEM;  // can never fit the budget
+  }
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    S->all[r->ticket] = r;
+    S->queue.push_back(r);
+  }
+  *ticket = r->ticket;
+  S->cv_work.notify_one();
+  return BFX_OK;
+}
+
+// Waits until the request is done (timeout_s < 0: no limit).  BFX_OK and the
+// result when done (the ticket is then released); BFX_TIMEOUT if still pending.
+BFX_API bfx_status bfx_server_wait(bfx_server S, int64_t ticket, bfx_request_result* out,
+                                   double timeout_s) {
+  if (!S || !out) return BFX_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return BFX_EINVAL;
+  Request* r = it->second;
+  auto pred = [&] { return r->done; };
+  if (timeout_s < 0)
+    S->cv_done.wait(lk, pred);
+  else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+    return BFX_TIMEOUT;
+  *out = r->res;
+  S->all.erase(it);
+  delete r;
+  return BFX_OK;
+}
+
+BFX_API bfx_status bfx_server_stats(bfx_server S, bfx_server_stats_t* out) {
+  if (!S || !out) return BFX_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  out->queued = static_cast<int32_t>(S->queue.size());
+  out->running = S->running;
+  out->peak_running = S->peak_running;
+  out->pool_bytes = S->pool.capacity();
+  out->used_bytes = S->pool.used();
+  out->peak_used_bytes = S->peak_used;
+  return BFX_OK;
+}
+
+BFX_API void bfx_server_destroy(bfx_server S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (auto& kv : S->all) delete kv.second;
+  S->pool.release();
+  delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""Serving runtime: continuous admission under a memory budget; every result
+is bit-for-bit the one the same request gets when solved alone."""
+import numpy as np
+import pytest
+import torch
+
+import bfx_inputs as bi
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(bfx, P, mode):
+    x, res, code = bfx.solve_ir(mode, torch.from_numpy(P.A32).cuda(), torch.from_numpy(P.b).cuda(),
+                                escalate=True, nb=64)
+    return x.cpu().numpy(), res, code
+
+
+def test_mixed_requests_same_as_alone(bfx):
+    rng = np.random.default_rng(5)
+    ns = [16, 300, 64, 1500, 77, 513, 128, 1024, 33, 700, 256, 90]
+    reqs = [bi.svd_system(n, 10 ** rng.uniform(1, 5), 100 + i, nrhs=int(rng.integers(1, 5)))
+            for i, n in enumerate(ns)]
+    srv = bfx.Server(budget_bytes=2 << 30, max_inflight=6, mode=3)
+    tickets = [srv.submit(P.A32, P.b) for P in reqs]
+    out = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_running"] >= 2  # requests did overlap
+    for P, (x, res) in zip(reqs, out):
+        assert res["status"] == 0 and res["converged"] == 1, res
+        xa, ra, code = _alone(bfx, P, 3)
+        assert code == 0
+        assert np.array_equal(x, xa)  # identical alone and in the mix
+        assert res["iters"] == ra["iters"]
+
+
+def test_budget_limits_admission(bfx):
+    n = 1024
+    reqs = [bi.svd_system(n, 100.0, 200 + i) for i in range(5)]
+    r256 = lambda v: (v + 255) // 256 * 256
+    per = r256(4 * n * n) + 2 * r256(8 * n) + int(bfx.lib().bfx_solve_ir_workspace_size(3, n, 1, 64)) + 256
+    srv = bfx.Server(budget_bytes=int(2.5 * per), max_inflight=8, mode=3)
+    tickets = [srv.submit(P.A32, P.b) for P in reqs]
+    res = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert all(r[1]["converged"] == 1 for r in res)
+    assert st["peak_used_bytes"] <= st["pool_bytes"]
+    assert st["peak_running"] <= 2  # only two fit the budget at once
+    assert max(r[1]["queue_s"] for r in res) > 0.0
+
+
+def test_oversized_request_rejected(bfx):
+    srv = bfx.Server(budget_bytes=8 << 20, max_inflight=2, mode=3)
+    with pytest.raises(bfx.BfxError) as e:
+        srv.submit(np.eye(2048, dtype=np.float32), np.ones(2048))
+    assert e.value.code == 2
+    srv.close()

@@ -187,8 +187,9 @@ BFX_API bfx_status bfx_dot_bf16xN(bfx_mode mode, int64_t n, const float* d_x, co
  * BFX_FP32.  d_ipiv[j] (int32, 0-based) is the row swapped with row j at
  * step j.  d_info (device int32) receives 0 or the 1-based index of the first
  * exactly zero pivot; the factorisation completes either way.  Workspace:
- * bfx_lu_workspace_size(mode, n, nb) bytes, 256-byte aligned (0 for
- * BFX_FP32).  Errors: BFX_EINVAL, BFX_ENOMEM, BFX_EUNSUPPORTED. */
+ * bfx_lu_workspace_size(mode, n, nb) bytes, 256-byte aligned (the row-swap
+ * bookkeeping of a block column, plus the bfloat16 pieces of the trailing
+ * update for X1..X9).  Errors: BFX_EINVAL, BFX_ENOMEM, BFX_EUNSUPPORTED. */
 BFX_API size_t bfx_lu_workspace_size(bfx_mode mode, int64_t n, int nb);
 BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, int64_t lda,
                                  int32_t* d_ipiv, int32_t* d_info, void* d_ws, size_t ws_bytes,

@@ -25,7 +25,7 @@
 namespace bfx {
 namespace {
 
-constexpr int PANEL_THREADS = 1024;
+constexpr int PANEL_THREADS = 512;
 
 struct ArgMax {
   float v;
@@ -204,25 +204,28 @@ __global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n,
 }
 
 // Apply the swaps ipiv[j0 .. j0+jb) to every column outside [j0, j0+jb).
-// Warp 0 first turns the sequential swaps into their net effect on the at
-// most 2 jb rows they touch (slot k ends up holding the original row
-// cont[k]); then every thread moves the touched rows of its column with all
+// The sequential swaps are first turned into their net effect on the at most
+// 2 jb rows they touch (slot k ends up holding the original row cont[k]) by
+// one warp; then every thread moves the touched rows of its column with all
 // loads issued before the stores.
 constexpr int LASWP_COLS = 64;
-__device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int n, int j0,
-                                           int jb, const int32_t* __restrict__ ipiv, int cb) {
-  extern __shared__ float vals[];  // (2 jb) x LASWP_COLS
-  __shared__ int rowid[256];
-  __shared__ int cont[256];
+struct SwapSet {
+  int rowid[256];
+  int cont[256];
+  int nslots;
+};
+
+// Warp 0 of the calling CTA fills *ss (shared or global memory).
+__device__ __forceinline__ void swapset_build(const int32_t* __restrict__ ipiv, int j0, int jb,
+                                              SwapSet* ss) {
   __shared__ int piv[128];
-  __shared__ int nslots;
   const int t = threadIdx.x;
-  for (int j = t; j < jb; j += LASWP_COLS) piv[j] = ipiv[j0 + j];
+  for (int j = t; j < jb; j += blockDim.x) piv[j] = ipiv[j0 + j];
   __syncthreads();
   if (t < 32) {
     for (int k = t; k < jb; k += 32) {
-      rowid[k] = j0 + k;
-      cont[k] = j0 + k;
+      ss->rowid[k] = j0 + k;
+      ss->cont[k] = j0 + k;
     }
     int ns = jb;
     __syncwarp();
@@ -235,39 +238,51 @@ __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, i
         sp = -1;
         for (int base = jb; base < ns && sp < 0; base += 32) {
           const int k = base + t;
-          const unsigned hit = __ballot_sync(0xFFFFFFFFu, k < ns && rowid[k] == p);
+          const unsigned hit = __ballot_sync(0xFFFFFFFFu, k < ns && ss->rowid[k] == p);
           if (hit) sp = base + __ffs(hit) - 1;
         }
         if (sp < 0) {
           sp = ns++;
           if (t == 0) {
-            rowid[sp] = p;
-            cont[sp] = p;
+            ss->rowid[sp] = p;
+            ss->cont[sp] = p;
           }
         }
       }
       __syncwarp();
       if (t == 0 && sp != j) {
-        const int tmp = cont[j];
-        cont[j] = cont[sp];
-        cont[sp] = tmp;
+        const int tmp = ss->cont[j];
+        ss->cont[j] = ss->cont[sp];
+        ss->cont[sp] = tmp;
       }
       __syncwarp();
     }
-    if (t == 0) nslots = ns;
+    if (t == 0) ss->nslots = ns;
   }
   __syncthreads();
+}
+
+__global__ void lu_swapset_kernel(const int32_t* __restrict__ ipiv, int j0, int jb,
+                                  SwapSet* __restrict__ out) {
+  swapset_build(ipiv, j0, jb, out);
+}
+
+// Move the touched rows of column block cb (ss: a finished swap set).
+__device__ __forceinline__ void laswp_apply(float* __restrict__ A, int64_t lda, int n, int j0,
+                                            int jb, const SwapSet* __restrict__ ss, int cb) {
+  extern __shared__ float vals[];  // (2 jb) x LASWP_COLS
+  const int t = threadIdx.x;
   const int64_t idx = cb * static_cast<int64_t>(LASWP_COLS) + t;
   if (idx >= n - jb) return;
   const int c = static_cast<int>(idx < j0 ? idx : idx + jb);
-  const int ns = nslots;
+  const int ns = ss->nslots;
   // batches of 16 loads in registers before their shared-memory stores, so
   // the global loads are all in flight together
   for (int k0 = 0; k0 < ns; k0 += 16) {
     int src[16];
     float v[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) src[q] = (k0 + q < ns) ? cont[k0 + q] : -1;
+    for (int q = 0; q < 16; ++q) src[q] = (k0 + q < ns) ? ss->cont[k0 + q] : -1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = (src[q] >= 0) ? A[static_cast<int64_t>(src[q]) * lda + c] : 0.0f;
 #pragma unroll
@@ -275,53 +290,72 @@ __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, i
       if (k0 + q < ns) vals[(k0 + q) * LASWP_COLS + t] = v[q];
   }
   for (int k = 0; k < ns; ++k)
-    A[static_cast<int64_t>(rowid[k]) * lda + c] = vals[k * LASWP_COLS + t];
+    A[static_cast<int64_t>(ss->rowid[k]) * lda + c] = vals[k * LASWP_COLS + t];
+}
+
+// batched systems: each CTA builds the (small) swap set itself
+__device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int n, int j0,
+                                           int jb, const int32_t* __restrict__ ipiv, int cb) {
+  __shared__ SwapSet ss;
+  swapset_build(ipiv, j0, jb, &ss);
+  laswp_apply(A, lda, n, j0, jb, &ss, cb);
 }
 
 __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict__ A, int64_t lda,
                                                              int n, int j0, int jb,
-                                                             const int32_t* __restrict__ ipiv) {
-  laswp_body(A, lda, n, j0, jb, ipiv, blockIdx.x);
+                                                             const SwapSet* __restrict__ ss) {
+  laswp_apply(A, lda, n, j0, jb, ss, blockIdx.x);
 }
 
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
-// one thread a column of A12 held in registers (NB >= jb, unrolled).
+// one warp a column of A12, lane k owning rows k, k+32, ... (registers).
 // Column-oriented: x_i receives -l_il x_l for l = 0, 1, ..., i-1 in order -
-// per element the same FMA sequence as row-by-row substitution - with the
-// updates for different i independent of each other.
-constexpr int TRSM_COLS = 64;
+// per element the same FMA sequence as row-by-row substitution - with x_l
+// broadcast from its owner lane.
+constexpr int TRSM_COLS = 8;  // columns (warps) a CTA
 template <int NB>
 __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int n, int j0,
                                           int jb, int cb) {
   extern __shared__ float L11[];  // NB x NB, the jb x jb triangle padded with zeros
+  constexpr int RPL = NB / 32;    // rows a lane
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, l = e % NB;
     L11[e] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
   }
   __syncthreads();
-  const int64_t c = j0 + jb + cb * static_cast<int64_t>(TRSM_COLS) + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t c = j0 + jb + cb * static_cast<int64_t>(TRSM_COLS) + w;
   if (c >= n) return;
   float* col = A + static_cast<int64_t>(j0) * lda + c;
-  float x[NB];
+  float x[RPL];
 #pragma unroll
-  for (int i = 0; i < NB; ++i) x[i] = (i < jb) ? col[static_cast<int64_t>(i) * lda] : 0.0f;
+  for (int q = 0; q < RPL; ++q) {
+    const int i = lane + 32 * q;
+    x[q] = i < jb ? col[static_cast<int64_t>(i) * lda] : 0.0f;
+  }
 #pragma unroll
-  for (int l = 0; l < NB - 1; ++l) {
-    if (l < jb - 1) {
-      const float xl = x[l];
+  for (int q0 = 0; q0 < RPL; ++q0) {
+    for (int ll = 0; ll < 32; ++ll) {
+      const int l = 32 * q0 + ll;
+      if (l >= jb - 1) break;
+      const float xl = __shfl_sync(0xFFFFFFFFu, x[q0], ll);
 #pragma unroll
-      for (int i = l + 1; i < NB; ++i)
-        if (i < jb) x[i] = fmaf(-L11[i * NB + l], xl, x[i]);
+      for (int q = q0; q < RPL; ++q) {
+        const int i = lane + 32 * q;
+        if (i > l && i < jb) x[q] = fmaf(-L11[i * NB + l], xl, x[q]);
+      }
     }
   }
 #pragma unroll
-  for (int i = 1; i < NB; ++i)
-    if (i < jb) col[static_cast<int64_t>(i) * lda] = x[i];
+  for (int q = 0; q < RPL; ++q) {
+    const int i = lane + 32 * q;
+    if (i >= 1 && i < jb) col[static_cast<int64_t>(i) * lda] = x[q];
+  }
 }
 
 template <int NB>
-__global__ void __launch_bounds__(TRSM_COLS) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
-                                                           int n, int j0, int jb) {
+__global__ void __launch_bounds__(TRSM_COLS * 32) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
+                                                                 int n, int j0, int jb) {
   trsm_body<NB>(A, lda, n, j0, jb, blockIdx.x);
 }
 
@@ -356,7 +390,7 @@ __global__ void __launch_bounds__(LASWP_COLS)
 }
 
 template <int NB>
-__global__ void __launch_bounds__(TRSM_COLS)
+__global__ void __launch_bounds__(TRSM_COLS * 32)
     lu_trsm_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
@@ -408,12 +442,16 @@ struct LuWs {
   size_t bytes;
 };
 
+constexpr size_t kSwapSetBytes = (sizeof(SwapSet) + 255) / 256 * 256;
+
+// Workspace: the swap set of the current block column, then np planes of the
+// L21 pieces and np planes of the U12^T pieces.
 LuWs lu_ws(int np, int64_t n, int nb) {
   LuWs w;
   w.kp = round_up(nb, 8);
   w.ap = round_up(n * w.kp, 128);
   w.bp = w.ap;
-  w.bytes = static_cast<size_t>(np) * static_cast<size_t>(w.ap + w.bp) * 2;
+  w.bytes = kSwapSetBytes + static_cast<size_t>(np) * static_cast<size_t>(w.ap + w.bp) * 2;
   return w;
 }
 
@@ -426,8 +464,9 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   if (cudaMemsetAsync(info, 0, sizeof(int32_t), s) != cudaSuccess) return BFX_ECUDA;
   if (n == 0) return BFX_OK;
   const int np = mode_pieces(mode);
-  LuWs w = lu_ws(np > 0 ? np : 1, n, nb);
-  if (np > 0 && (!ws || ws_bytes < w.bytes || !aligned(ws, 256))) return BFX_ENOMEM;
+  LuWs w = lu_ws(np, n, nb);
+  if (!ws || ws_bytes < w.bytes || !aligned(ws, 256)) return BFX_ENOMEM;
+  SwapSet* swapset = static_cast<SwapSet*>(ws);
   if (cudaFuncSetAttribute(lu_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess ||
       cudaFuncSetAttribute(lu_laswp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -440,8 +479,8 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
       cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(trsm_smem)) != cudaSuccess)
     return BFX_ECUDA;
-  uint16_t* Lp = static_cast<uint16_t*>(ws);
-  uint16_t* Up = Lp ? Lp + np * w.ap : nullptr;
+  uint16_t* Lp = reinterpret_cast<uint16_t*>(static_cast<char*>(ws) + kSwapSetBytes);
+  uint16_t* Up = Lp + np * w.ap;
   const int N = static_cast<int>(n);
   for (int j0 = 0; j0 < N; j0 += nb) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
@@ -461,14 +500,15 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     }
     if (N - jb > 0) {
       const int64_t cols = N - jb;
+      lu_swapset_kernel<<<1, 32, 0, s>>>(ipiv, j0, jb, swapset);
       lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(cols, LASWP_COLS)), LASWP_COLS,
                         static_cast<size_t>(2 * jb) * LASWP_COLS * sizeof(float), s>>>(A, lda, N, j0,
-                                                                                     jb, ipiv);
+                                                                                     jb, swapset);
     }
     const int nr = N - j0 - jb;
     if (nr <= 0) continue;
-    trsm<<<static_cast<unsigned>(ceil_div(nr, TRSM_COLS)), TRSM_COLS, trsm_smem, s>>>(A, lda, N, j0,
-                                                                                     jb);
+    trsm<<<static_cast<unsigned>(ceil_div(nr, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
+        A, lda, N, j0, jb);
     float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
     float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb;
     float* A22 = A + static_cast<int64_t>(j0 + jb) * lda + j0 + jb;
@@ -529,11 +569,11 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
   const size_t tsmem = static_cast<size_t>(tnb) * tnb * sizeof(float);
   const unsigned tblk = static_cast<unsigned>(ceil_div(nmax, TRSM_COLS));
   if (tnb == 32)
-    lu_trsm_batched_kernel<32><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+    lu_trsm_batched_kernel<32><<<dim3(tblk, S_act), TRSM_COLS * 32, tsmem, s>>>(d_sys, nb, J0);
   else if (tnb == 64)
-    lu_trsm_batched_kernel<64><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+    lu_trsm_batched_kernel<64><<<dim3(tblk, S_act), TRSM_COLS * 32, tsmem, s>>>(d_sys, nb, J0);
   else
-    lu_trsm_batched_kernel<128><<<dim3(tblk, S_act), TRSM_COLS, tsmem, s>>>(d_sys, nb, J0);
+    lu_trsm_batched_kernel<128><<<dim3(tblk, S_act), TRSM_COLS * 32, tsmem, s>>>(d_sys, nb, J0);
   const int np = mode_pieces(mode);
   const int64_t sw = static_cast<int64_t>(nmax) * kp;
   const unsigned sblk = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(sw, 256), 64)));
@@ -544,7 +584,7 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
 
 size_t lu_workspace_bytes(bfx_mode mode, int64_t n, int nb) {
   const int np = mode_pieces(mode);
-  if (np == 0 || n <= 0) return 0;
+  if (n <= 0) return 0;
   if (nb <= 0) nb = 64;
   return lu_ws(np, n, nb).bytes;
 }

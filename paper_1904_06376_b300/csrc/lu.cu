@@ -26,6 +26,7 @@ namespace bfx {
 namespace {
 
 constexpr int PANEL_THREADS = 512;
+static_assert(PANEL_THREADS % 32 == 0 && PANEL_THREADS <= 1024, "panel CTA size");
 
 struct ArgMax {
   float v;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
     if (lane == 0) warp_best[wid] = best;
     __syncthreads();
     if (wid == 0) {
-      best = warp_best[lane];
+      best = lane < PANEL_THREADS / 32 ? warp_best[lane] : ArgMax{-1.0f, n};
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, best.v, o), __shfl_xor_sync(0xFFFFFFFFu, best.i, o)};

@@ -57,6 +57,8 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
   __shared__ ArgMax warp_best[PANEL_THREADS / 32];
   __shared__ int s_piv;
   __shared__ float s_row[TILE_W];
+  __shared__ int s_pivs[TILE_W];
+  __shared__ int s_rows[2 * TILE_W], s_src[2 * TILE_W], s_ns;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int rows = n - j0;
   auto T = [&](int r, int c) -> float& {
@@ -126,15 +128,8 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
         T(p, t) = a;
       }
       s_row[t] = (p != j) ? b : a;
-    } else if (p != j && t - TILE_W < nout && t >= TILE_W) {
-      const int k = t - TILE_W;
-      const int c = (J0 + k < j0) ? J0 + k : J0 + k + jw;
-      float* rj = A + static_cast<int64_t>(j) * lda + c;
-      float* rp = A + static_cast<int64_t>(p) * lda + c;
-      const float a = *rj;
-      *rj = *rp;
-      *rp = a;
     }
+    if (t == 0) s_pivs[jj] = p;
     __syncthreads();
     const float piv = s_row[jj];
     if (piv == 0.0f) {
@@ -155,6 +150,48 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
       const int r = j0 + e / jw, c = e % jw;
       A[static_cast<int64_t>(r) * lda + j0 + c] = tile[static_cast<int64_t>(r - j0) * TILE_W + c];
     }
+  }
+  // ---- the tile's row swaps, applied once to the block-column columns outside
+  // the tile: net effect of the (at most 8) sequential swaps on the (at most
+  // 16) rows they touch, all loads of a column before its stores
+  if (t == 0) {
+    int ns = 0;
+    for (int jj = 0; jj < jw; ++jj) {
+      const int rr[2] = {j0 + jj, s_pivs[jj]};
+      for (int q = 0; q < 2; ++q) {
+        bool seen = false;
+        for (int k = 0; k < ns; ++k) seen = seen || s_rows[k] == rr[q];
+        if (!seen) {
+          s_rows[ns] = rr[q];
+          s_src[ns] = rr[q];
+          ++ns;
+        }
+      }
+      int a = 0, b = 0;
+      for (int k = 0; k < ns; ++k) {
+        if (s_rows[k] == j0 + jj) a = k;
+        if (s_rows[k] == s_pivs[jj]) b = k;
+      }
+      const int tmp = s_src[a];
+      s_src[a] = s_src[b];
+      s_src[b] = tmp;
+    }
+    s_ns = ns;
+  }
+  __syncthreads();
+  if (nout > 0) {
+    const int ns = s_ns;
+    for (int k = t; k < nout; k += PANEL_THREADS) {
+      const int c = (J0 + k < j0) ? J0 + k : J0 + k + jw;
+      float v[2 * TILE_W];
+#pragma unroll
+      for (int q = 0; q < 2 * TILE_W; ++q)
+        v[q] = q < ns ? A[static_cast<int64_t>(s_src[q]) * lda + c] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 2 * TILE_W; ++q)
+        if (q < ns) A[static_cast<int64_t>(s_rows[q]) * lda + c] = v[q];
+    }
+    __syncthreads();
   }
   // ---- tile rows of the block columns right of the tile: forward substitution
   for (int c = j0 + jw + t; c < J0 + JB; c += PANEL_THREADS) {
@@ -265,7 +302,13 @@ __device__ __forceinline__ void swapset_build(const int32_t* __restrict__ ipiv, 
 
 __global__ void lu_swapset_kernel(const int32_t* __restrict__ ipiv, int j0, int jb,
                                   SwapSet* __restrict__ out) {
-  swapset_build(ipiv, j0, jb, out);
+  __shared__ SwapSet ss;
+  swapset_build(ipiv, j0, jb, &ss);
+  for (int k = threadIdx.x; k < ss.nslots; k += blockDim.x) {
+    out->rowid[k] = ss.rowid[k];
+    out->cont[k] = ss.cont[k];
+  }
+  if (threadIdx.x == 0) out->nslots = ss.nslots;
 }
 
 // Move the touched rows of column block cb (ss: a finished swap set).

@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--quick", action="store_true",
                    help="main measurement only (no variants, CPU baseline or e2e); for profiling")
     p.add_argument("--cpu-rows", type=int, default=16, help="rows of the CPU-baseline sample")
+    p.add_argument("--no-solves", action="store_true",
+                   help="skip the solve workloads (single IR, batched, serving)")
+    p.add_argument("--serve-requests", type=int, default=200)
     return p.parse_args()
 
 
@@ -185,6 +188,123 @@ def run_reference(args, rank, world):
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- solve workloads
+def _fe(x, x_true):
+    return float(np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)))
+
+
+def bench_ir_single(bfx, oracle, bi, dev):
+    """Config 3: one n = 4096 system per condition number, bf16x3 trailing
+    updates with escalation, FP64 residual refinement; forward error against
+    x_true beside that of the FP64 oracle LU solve (timed on the host)."""
+    import torch
+
+    n, out = 4096, {"n": 4096, "mode": "x3 (escalate to x6)", "solves": []}
+    times = []
+    for kappa in (1e1, 1e4, 1e8, 1e12):
+        P = bi.svd_system(n, kappa, 11)
+        A = torch.from_numpy(P.A32).to(dev)
+        b = torch.from_numpy(P.b).to(dev)
+        bfx.solve_ir(3, A, b)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, res, code = bfx.solve_ir(3, A, b)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        t1 = time.perf_counter()
+        xd, _ = oracle.dgesv(P.A32, P.b)
+        tcpu = time.perf_counter() - t1
+        fe, fe64 = _fe(x.cpu().numpy(), P.x_true), _fe(xd, P.x_true)
+        out["solves"].append({"kappa": kappa, "ms": dt * 1e3, "status": code, "converged": res["converged"],
+                              "iters": res["iters"], "refactorizations": res["refactorizations"],
+                              "mode_used": res["mode_used"], "berr": res["berr"],
+                              "forward_error": fe, "forward_error_fp64_lu": fe64,
+                              "ratio_to_fp64": fe / fe64 if fe64 > 0 else None,
+                              "oracle_dgesv_s": tcpu})
+    out["solves_per_s"] = len(times) / sum(times)
+    out["cpu_baseline"] = {"value": len(times) / sum(s["oracle_dgesv_s"] for s in out["solves"]),
+                           "unit": "solves/s", "kind": "oracle", "cores": oracle.num_threads(),
+                           "sample": "the oracle's FP64 LU + solve of the same 4 systems"}
+    return out
+
+
+def bench_batched(bfx, oracle, bi, dev, count=2000):
+    """Config 4: 2000 systems, n ~ U{32..512}, log10 kappa ~ U[2,8], nrhs 1,
+    bf16x6, one CUDA-graph launch; solves/s, convergence and forward error."""
+    import torch
+
+    probs = bi.batched_systems(count, 0)
+    B = bfx.Batch(6, [p.n for p in probs], max_iter=12)
+    A, b = B.pack([p.A32 for p in probs], [p.b for p in probs])
+    x, st = B.solve(A, b)
+    torch.cuda.synchronize()
+    reps = 5
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        B.solve(A, b, x=x, status=st)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    conv, iters, info, berr = B.decode_status(st)
+    xs = B.unpack(x)
+    fe = np.array([_fe(xx, p.x_true) for xx, p in zip(xs, probs)])
+    lk = np.log10([p.kappa_nominal for p in probs])
+    by = {}
+    for lo in range(2, 8):
+        msk = (lk >= lo) & (lk < lo + 1)
+        by[f"1e{lo}-1e{lo + 1}"] = {"systems": int(msk.sum()), "converged": float(conv[msk].mean()),
+                                    "median_forward_error": float(np.median(fe[msk])),
+                                    "max_forward_error": float(fe[msk].max())}
+    sample = list(range(0, count, count // 16))[:16]
+    t0 = time.perf_counter()
+    for i in sample:
+        oracle.lu_solve_ir(6, probs[i].A32, probs[i].b, nb=64)
+    tcpu = time.perf_counter() - t0
+    flops = sum(2.0 / 3.0 * p.n ** 3 for p in probs)
+    return {"systems": count, "mode": "x6", "ms_per_batch": ms, "solves_per_s": count / (ms * 1e-3),
+            "lu_eff_tflops": flops / (ms * 1e-3) / 1e12, "converged": float(conv.mean()),
+            "mean_iters": float(iters.mean()), "by_condition": by,
+            "graph": "whole batch captured once, replayed per solve",
+            "cpu_baseline": {"value": len(sample) / tcpu, "unit": "solves/s", "kind": "oracle",
+                             "cores": 1, "sample": f"{len(sample)} of the systems by the oracle's "
+                                                   "bf16x6-update LU + FP64 refinement"}}
+
+
+def bench_serving(bfx, bi, count):
+    """Config 5: Poisson arrivals at 5000 req/s, n log-uniform [64, 4096],
+    nrhs U{1..16}, log10 kappa U[1,10], 60 GB pool, bf16x3 with escalation;
+    latency measured from submission to completion inside the server."""
+    reqs = bi.serving_stream(count, 3)
+    systems = [bi.fast_system(r.n, 10.0 ** r.log10_kappa, r.seed, nrhs=r.nrhs) for r in reqs]
+    srv = bfx.Server(budget_bytes=60 * 10 ** 9, max_inflight=32, mode=3, escalate=True)
+    t_start = time.perf_counter()
+    tickets = []
+    for r, P in zip(reqs, systems):
+        while time.perf_counter() - t_start < r.t_arrival:
+            pass
+        tickets.append(srv.submit(P.A32, P.b))
+    results = [srv.wait(t) for t in tickets]
+    t_end = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r[1]["latency_s"] for r in results])
+    conv = np.array([r[1]["converged"] for r in results])
+    fe = np.array([_fe(x, P.x_true) for (x, _), P in zip(results, systems)])
+    lk = np.array([r.log10_kappa for r in reqs])
+    return {"requests": count, "arrival_rate_per_s": 5000, "solves_per_s": count / (t_end - t_start),
+            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_queue_ms": float(np.mean([r[1]["queue_s"] for r in results]) * 1e3),
+            "converged": float(conv.mean()),
+            "converged_log10k_le_7": float(conv[lk <= 7].mean()),
+            "median_forward_error": float(np.median(fe)),
+            "peak_running": stats["peak_running"], "peak_pool_bytes": stats["peak_used_bytes"],
+            "budget_bytes": stats["pool_bytes"], "max_inflight": 32,
+            "generator": "O(n^2) Householder/permutation construction with exact kappa"}
 
 
 # ----------------------------------------------------------------- bfx arm
@@ -368,6 +488,12 @@ def main():
                             "cores": cores, "kind": "oracle", "seconds": tc,
                             "sample": f"{rows.size} rows of the {m}x{n}x{k} product, the oracle's "
                                       f"sequential FP32-FMA bf16x{mode} model (split of B included)"}
+    del A, B, C, Ap, Bp, ws, Ahp, Bhp, Chp
+    torch.cuda.empty_cache()
+    if not args.no_solves:
+        line["ir_single"] = bench_ir_single(bfx, oracle, bi, dev)
+        line["batched"] = bench_batched(bfx, oracle, bi, dev)
+        line["serving"] = bench_serving(bfx, bi, args.serve_requests)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -20,6 +20,11 @@ Workloads (all numpy ``default_rng(seed)``):
 * ``batched_systems`` / ``serving_stream``: many independent systems of that
   kind with sizes, right-hand-side counts, conditioning and (for the stream)
   Poisson arrival times drawn from stated distributions.
+* ``fast_system``: the same kind of system built in O(n^2): A = H1 H2 P1
+  diag(sigma) P2^T H4 H3 with Householder reflectors H = I - 2 v v^T / v^T v
+  of Gaussian v and random permutations P, so kappa(A) is exactly
+  sigma_max / sigma_min; used for the serving stream, whose thousands of
+  requests up to n = 4096 cannot each afford two QR factorisations.
 """
 from __future__ import annotations
 
@@ -37,6 +42,7 @@ __all__ = [
     "serving_stream",
     "Request",
     "special_values_f32",
+    "fast_system",
 ]
 
 
@@ -171,3 +177,28 @@ def serving_stream(count: int, seed: int, rate: float = 5000.0, n_lo: int = 64,
     seeds = rng.integers(0, 2**31 - 1, size=count)
     return [Request(float(a), int(b), int(c), float(d), int(e))
             for a, b, c, d, e in zip(t, ns, nr, lk, seeds)]
+
+
+def _apply_reflector_left(X: np.ndarray, v: np.ndarray) -> None:
+    X -= np.outer(v, (2.0 / (v @ v)) * (v @ X))
+
+
+def _apply_reflector_right(X: np.ndarray, v: np.ndarray) -> None:
+    X -= np.outer((2.0 / (v @ v)) * (X @ v), v)
+
+
+def fast_system(n: int, kappa: float, seed: int, nrhs: int = 1) -> SolveProblem:
+    """A = H1 H2 P1 diag(sigma) P2^T H4 H3 (see the module docstring), FP32."""
+    rng = np.random.default_rng(seed)
+    sigma = kappa ** (-np.arange(n, dtype=np.float64) / (n - 1)) if n > 1 else np.ones(1)
+    p1, p2 = rng.permutation(n), rng.permutation(n)
+    X = np.zeros((n, n))
+    X[p1, p2] = sigma
+    for _ in range(2):
+        _apply_reflector_left(X, rng.standard_normal(n))
+    for _ in range(2):
+        _apply_reflector_right(X, rng.standard_normal(n))
+    A32 = np.ascontiguousarray(X.astype(np.float32))
+    x_true = rng.standard_normal((n, nrhs))
+    b = A32.astype(np.float64) @ x_true
+    return SolveProblem(A32=A32, b=b, x_true=x_true, kappa_nominal=float(kappa), seed=seed)

@@ -389,6 +389,10 @@ bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64
                     int box_planes = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
+  // the driver-API encoder needs a current context on this thread; make the
+  // current device's primary context current (a no-op if it already is)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return false;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
                         static_cast<cuuint64_t>(planes)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(plane) * 2};

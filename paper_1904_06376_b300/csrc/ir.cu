@@ -217,9 +217,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
       vb[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * ldv + c0 + c] : 0.0;
     }
     __syncthreads();
-    // y = Dinv vb: a thread per (row, column), four partial FMA chains
-    for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
+    // y = Dinv vb: a thread per (row, column), four partial FMA chains.  Rows
+    // past a partial last block are set to zero: the update below reads all
+    // TB rows, and shared memory left by another kernel may hold NaN patterns.
+    for (int e = t; e < TB * nc; e += SOLVE_THREADS) {
       const int i = e / nc, c = e - i * nc;
+      if (i >= bs) {
+        y[i][c] = 0.0;
+        continue;
+      }
       const double* d = D + i * TB;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll 4

@@ -56,3 +56,26 @@ def test_oversized_request_rejected(bfx):
         srv.submit(np.eye(2048, dtype=np.float32), np.ones(2048))
     assert e.value.code == 2
     srv.close()
+
+
+def test_many_concurrent_requests_same_as_alone(bfx):
+    """32 workers on a Poisson stream of 40 mixed-size requests (most n not a
+    multiple of the 64-row solve block): each result equals solving alone.
+    Kernels of other requests share the SMs, so any read of shared memory a
+    kernel did not write shows up here as a changed or non-finite result."""
+    reqs = bi.serving_stream(40, 3)
+    systems = [bi.fast_system(r.n, 10.0 ** min(r.log10_kappa, 3), r.seed, nrhs=r.nrhs)
+               for r in reqs]
+    assert sum(P.n % 64 != 0 for P in systems) >= 30
+    srv = bfx.Server(budget_bytes=60 * 10**9, max_inflight=32, mode=3, escalate=False)
+    tickets = [srv.submit(P.A32, P.b) for P in systems]
+    out = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_running"] >= 8
+    for P, (x, res) in zip(systems, out):
+        assert np.isfinite(x).all()
+        xa, ra, code = bfx.solve_ir(3, torch.from_numpy(P.A32).cuda(), torch.from_numpy(P.b).cuda(),
+                                    escalate=False)
+        assert np.array_equal(x, xa.cpu().numpy())
+        assert res["iters"] == ra["iters"] and res["converged"] == ra["converged"]

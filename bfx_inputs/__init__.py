@@ -25,6 +25,10 @@ Workloads (all numpy ``default_rng(seed)``):
   of Gaussian v and random permutations P, so kappa(A) is exactly
   sigma_max / sigma_min; used for the serving stream, whose thousands of
   requests up to n = 4096 cannot each afford two QR factorisations.
+* ``diag_dominant_system``: row and column diagonally dominant unsymmetric
+  matrices (off-diagonal U[-1,1], each diagonal entry of random sign and
+  magnitude above both its row and its column sum of the other entries), the
+  GMRES case of Sec. IV-B.
 """
 from __future__ import annotations
 
@@ -43,6 +47,7 @@ __all__ = [
     "Request",
     "special_values_f32",
     "fast_system",
+    "diag_dominant_system",
 ]
 
 
@@ -202,3 +207,21 @@ def fast_system(n: int, kappa: float, seed: int, nrhs: int = 1) -> SolveProblem:
     x_true = rng.standard_normal((n, nrhs))
     b = A32.astype(np.float64) @ x_true
     return SolveProblem(A32=A32, b=b, x_true=x_true, kappa_nominal=float(kappa), seed=seed)
+
+
+def diag_dominant_system(n: int, seed: int, nrhs: int = 1, margin: float = 1.0) -> SolveProblem:
+    """Row and column diagonally dominant A (FP32), x_true Gaussian, b = A32 x_true (FP64).
+
+    Off-diagonal entries U[-1, 1]; |a_ii| = max(row sum, column sum of the
+    other |a_ij|) + margin * U[0, 1], with a random sign.
+    """
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1.0, 1.0, size=(n, n))
+    np.fill_diagonal(A, 0.0)
+    dom = np.maximum(np.abs(A).sum(axis=1), np.abs(A).sum(axis=0))
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    np.fill_diagonal(A, sign * (dom + margin * rng.random(n)))
+    A32 = np.ascontiguousarray(A.astype(np.float32))
+    x_true = rng.standard_normal((n, nrhs))
+    b = A32.astype(np.float64) @ x_true
+    return SolveProblem(A32=A32, b=b, x_true=x_true, kappa_nominal=float("nan"), seed=seed)

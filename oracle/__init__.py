@@ -61,6 +61,10 @@ def lib() -> ctypes.CDLL:
         L.orc_solve_ir.argtypes = [i64, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, i32, f64,
                                    f64, f64, vp, vp, vp]
         L.orc_num_threads.restype = i32
+        L.orc_gmres.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, f64, vp, vp]
+        L.orc_gmres.restype = i32
+        L.orc_solve_gmres_ir.argtypes = [i64, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, i32,
+                                         f64, f64, f64, i32, f64, vp, vp, vp, vp]
         L.orc_set_num_threads.argtypes = [i32]
         _lib = L
     return _lib
@@ -251,3 +255,44 @@ def lu_solve_ir(mode: int, A32, b, nb: int = 64, **kw):
     LU, ipiv, info = lu(mode, A32, nb)
     x, iters, conv, berr = solve_ir(A32, LU, ipiv, b, **kw)
     return x, iters, conv, berr, info
+
+
+def gmres(A32, LU, ipiv, rhs, m: int = 50, tau: float = 1e-10):
+    """Left-preconditioned GMRES on M^-1 A d = M^-1 rhs (M from the FP32
+    factors, FP64 arithmetic), zero first guess.  Returns d, the number of
+    Arnoldi steps k and the residual estimates |g_1| .. |g_k|."""
+    A32 = _f32(A32)
+    LU = _f32(LU)
+    n = A32.shape[0]
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64).reshape(n)
+    d = np.zeros(n)
+    hist = np.zeros(max(m, 1))
+    k = lib().orc_gmres(n, _p(A32), n, _p(LU), n, _p(np.ascontiguousarray(ipiv, np.int32)),
+                        _p(rhs), int(m), float(tau), _p(d), _p(hist))
+    return d, int(k), hist[:k].copy()
+
+
+def solve_gmres_ir(A32, LU, ipiv, b, max_iter: int = 50, tol: float = 2.0**-53, tol_b=None,
+                   stall: float = 0.5, m: int = 50, tau: float = 1e-10):
+    """Refinement whose corrections come from GMRES(m) preconditioned by the
+    FP32 factors (reading R18); stop rules as ``solve_ir``.  Returns x,
+    refinement steps, Arnoldi steps, converged flags and backward errors."""
+    A32 = _f32(A32)
+    LU = _f32(LU)
+    n = A32.shape[0]
+    b = np.array(b, dtype=np.float64, order="C", copy=True)
+    if b.ndim == 1:
+        b = b[:, None]
+    nrhs = b.shape[1]
+    if tol_b is None:
+        tol_b = 2.0 ** -53 * np.sqrt(n)
+    x = np.zeros((n, nrhs))
+    iters = np.zeros(nrhs, dtype=np.int32)
+    inner = np.zeros(nrhs, dtype=np.int32)
+    conv = np.zeros(nrhs, dtype=np.int32)
+    berr = np.zeros(nrhs)
+    lib().orc_solve_gmres_ir(n, nrhs, _p(A32), n, _p(LU), n,
+                             _p(np.ascontiguousarray(ipiv, np.int32)), _p(b), nrhs, _p(x), nrhs,
+                             int(max_iter), float(tol), float(tol_b), float(stall), int(m),
+                             float(tau), _p(iters), _p(inner), _p(conv), _p(berr))
+    return x, iters, inner, conv, berr

@@ -30,6 +30,9 @@
  *     matrix update; panel and triangular block solve are plain FP32.
  *  R13 GEMM result form C = alpha*Z + beta*C: t = fl32(alpha*Z), then
  *     fmaf(beta, C, t); beta == 0 does not read C.
+ *  R18 "GMRES with the LU as preconditioner" (Sec. III remark, Sec. IV-B):
+ *     left-preconditioned GMRES in FP64 solves each refinement step's
+ *     correction equation; restarts recompute r = b - A x in FP64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -556,5 +559,169 @@ void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const 
     if (berr_out) berr_out[c] = berr;
     free(xv);
     free(r);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* O8  GMRES with the low-precision LU as preconditioner (Sec. III, the   */
+/* GMRES remark, and the diagonally dominant table of Sec. IV-B).         */
+/* Reading R18: the correction equation A d = r of each refinement step   */
+/* is solved by left-preconditioned GMRES, M^-1 A d = M^-1 r with         */
+/* M = P^T L U (the FP32 factors applied in FP64), zero first guess.      */
+/* Arnoldi by modified Gram-Schmidt; the least-squares problem is         */
+/* reduced by Givens rotations (the textbook GMRES).  A refinement step   */
+/* with FP64 residual is a restart, so the whole is restarted GMRES(m)    */
+/* with the residual recomputed from x at every restart.                  */
+/* ------------------------------------------------------------------ */
+
+/* d = (M^-1 A)^-1 M^-1 rhs approximately; returns k, the Arnoldi steps    */
+/* taken.  Stops when the residual estimate |g_k| <= tau * beta, after m  */
+/* steps, or at breakdown (h_{k+1,k} = 0: the Krylov space is invariant   */
+/* and the solution in it exact).  hist[j] = |g_{j+1}| if hist != NULL.   */
+int orc_gmres(int64_t n, const float* A32, int64_t lda, const float* LU, int64_t ldlu,
+              const int32_t* ipiv, const double* rhs, int m, double tau, double* d,
+              double* hist) {
+  double* V = (double*)calloc((size_t)(m + 1) * (size_t)n, sizeof(double));
+  double* H = (double*)calloc((size_t)(m + 1) * (size_t)m, sizeof(double)); /* H[i*m+j] */
+  double* cs = (double*)calloc((size_t)m + 1, sizeof(double));
+  double* sn = (double*)calloc((size_t)m + 1, sizeof(double));
+  double* g = (double*)calloc((size_t)m + 1, sizeof(double));
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
+  /* r0 = M^-1 rhs, beta = |r0|_2, v0 = r0 / beta */
+  for (int64_t i = 0; i < n; ++i) w[i] = rhs[i];
+  lu32_solve64(n, LU, ldlu, ipiv, w);
+  double beta = 0.0;
+  for (int64_t i = 0; i < n; ++i) beta += w[i] * w[i];
+  beta = sqrt(beta);
+  int k = 0;
+  if (beta > 0.0 && beta == beta) {
+    for (int64_t i = 0; i < n; ++i) V[i] = w[i] / beta;
+    g[0] = beta;
+    for (int j = 0; j < m; ++j) {
+      /* w = M^-1 A v_j */
+      const double* vj = V + (size_t)j * (size_t)n;
+      for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t l = 0; l < n; ++l) s += (double)A32[i * lda + l] * vj[l];
+        w[i] = s;
+      }
+      lu32_solve64(n, LU, ldlu, ipiv, w);
+      /* modified Gram-Schmidt against v_0 .. v_j */
+      for (int i = 0; i <= j; ++i) {
+        const double* vi = V + (size_t)i * (size_t)n;
+        double h = 0.0;
+        for (int64_t l = 0; l < n; ++l) h += w[l] * vi[l];
+        H[i * m + j] = h;
+        for (int64_t l = 0; l < n; ++l) w[l] -= h * vi[l];
+      }
+      double hn = 0.0;
+      for (int64_t l = 0; l < n; ++l) hn += w[l] * w[l];
+      hn = sqrt(hn);
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0.0)
+        for (int64_t l = 0; l < n; ++l) V[(size_t)(j + 1) * (size_t)n + l] = w[l] / hn;
+      /* earlier rotations on column j, then the one that zeroes h_{j+1,j} */
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], b = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * b;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      {
+        const double a = H[j * m + j], b = H[(j + 1) * m + j];
+        const double rho = hypot(a, b);
+        cs[j] = (rho > 0.0) ? a / rho : 1.0;
+        sn[j] = (rho > 0.0) ? b / rho : 0.0;
+        H[j * m + j] = rho;
+        H[(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+      }
+      k = j + 1;
+      if (hist) hist[j] = fabs(g[j + 1]);
+      if (fabs(g[j + 1]) <= tau * beta || hn == 0.0 || !(hn == hn)) break;
+    }
+    /* y = R_k^-1 g_k (back substitution), d = V_k y */
+    double* y = (double*)calloc((size_t)k + 1, sizeof(double));
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+      y[i] = s / H[i * m + i];
+    }
+    for (int i = 0; i < k; ++i)
+      for (int64_t l = 0; l < n; ++l) d[l] += y[i] * V[(size_t)i * (size_t)n + l];
+    free(y);
+  }
+  free(V); free(H); free(cs); free(sn); free(g); free(w);
+  return k;
+}
+
+/* GMRES-IR: x0 = M^-1 b, then refinement steps r = b - A x (FP64),        */
+/* d = GMRES(m, tau) on M^-1 A d = M^-1 r, x += d, with the stop rules of  */
+/* O7 (tol on |d|/|x|, the stall ratio, max_iter, the backward-error test), */
+/* except that the first correction is not tested for a stall.              */
+/* iters[c] = refinement steps; inner[c] = Arnoldi steps summed over them. */
+void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const float* LU,
+                        int64_t ldlu, const int32_t* ipiv, const double* b, int64_t ldb,
+                        double* x, int64_t ldx, int max_iter, double tol, double tol_b,
+                        double stall, int m, double tau, int32_t* iters, int32_t* inner,
+                        int32_t* conv, double* berr_out) {
+  double anorm = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t l = 0; l < n; ++l) s += fabs((double)A32[i * lda + l]);
+    if (s > anorm) anorm = s;
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* xv = (double*)malloc(sizeof(double) * (size_t)n);
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double* d = (double*)malloc(sizeof(double) * (size_t)n);
+    double bnorm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      xv[i] = b[i * ldb + c];
+      if (fabs(b[i * ldb + c]) > bnorm) bnorm = fabs(b[i * ldb + c]);
+    }
+    lu32_solve64(n, LU, ldlu, ipiv, xv);
+    /* no stall test on the first correction: with poor factors x0 may be far */
+    /* off, and the first GMRES correction is then as large as x0 itself      */
+    double dprev = INFINITY;
+    int it = 0, ok = 0, stalled = 0, kin = 0;
+    while (it < max_iter) {
+      for (int64_t i = 0; i < n; ++i) {
+        double s = b[i * ldb + c];
+        for (int64_t l = 0; l < n; ++l) s -= (double)A32[i * lda + l] * xv[l];
+        r[i] = s;
+      }
+      kin += orc_gmres(n, A32, lda, LU, ldlu, ipiv, r, m, tau, d, NULL);
+      double dn = 0.0, xn = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        xv[i] += d[i];
+        if (fabs(d[i]) > dn) dn = fabs(d[i]);
+        if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
+      }
+      ++it;
+      if (!(dn == dn) || !(xn == xn)) break;
+      if (dn <= tol * xn) { ok = 1; break; }
+      if (dn >= stall * dprev) { stalled = 1; break; }
+      dprev = dn;
+    }
+    double rn = 0.0, xn = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double s = b[i * ldb + c];
+      for (int64_t l = 0; l < n; ++l) s -= (double)A32[i * lda + l] * xv[l];
+      if (fabs(s) > rn) rn = fabs(s);
+      if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
+    }
+    double den = anorm * xn + bnorm;
+    double berr = (den > 0.0) ? rn / den : 0.0;
+    if (!(berr == berr)) berr = INFINITY;
+    if (!ok && stalled && berr <= tol_b) ok = 1;
+    for (int64_t i = 0; i < n; ++i) x[i * ldx + c] = xv[i];
+    iters[c] = it;
+    inner[c] = kin;
+    conv[c] = ok;
+    if (berr_out) berr_out[c] = berr;
+    free(xv); free(r); free(d);
   }
 }

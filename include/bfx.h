@@ -204,14 +204,33 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
  * normwise backward error |r|_inf/(|A|_inf |x|_inf + |b|_inf) <= tol_b.
  * With escalate != 0, columns that stop unconverged are refined further after
  * refactoring with more products (x1 -> x3 -> x6).
+ * GMRES-IR (the GMRES remark of Sec. III, the GMRES table of Sec. IV-B): with
+ * gmres != 0 the correction of a refinement step is instead computed by
+ * left-preconditioned GMRES in FP64, M^-1 A d = M^-1 r with M = P^T L U from
+ * the FP32 factors, zero first guess, at most gmres_m Arnoldi steps, ending
+ * early when the preconditioned residual has fallen by gmres_tol.  gmres = 1:
+ * after plain refinement has stopped unconverged at the final mode (after any
+ * escalation), the unconverged columns continue from their current x by
+ * GMRES-IR; gmres = 2: GMRES-IR from the first correction.  The first GMRES
+ * correction is not tested for a stall.  The same stop rules apply otherwise.
  * d_A: n x n FP32 (lda); d_b: n x nrhs FP64 (ldb); d_x: n x nrhs FP64 (ldx,
  * output).  h_params may be NULL (max_iter 50, tol 2^-53, tol_b sqrt(n) 2^-53,
- * stall 0.5, escalate 1, nb 64).  The call is synchronous: it returns after
- * the refinement has finished and fills *h_result (host).  Returns BFX_OK
- * when every column converged, BFX_NOT_CONVERGED otherwise (x holds the last
- * iterate), BFX_SINGULAR on an exactly zero pivot (h_result->info > 0), and
- * the usual argument / workspace errors.  Workspace:
- * bfx_solve_ir_workspace_size(mode, n, nrhs, nb) bytes, 256-byte aligned. */
+ * stall 0.5, escalate 1, nb 64, gmres 1, gmres_m 0, gmres_tol 1e-10); a
+ * zero gmres_m means min(n, BFX_GMRES_MAX_M) (full GMRES up to that size:
+ * factors of FP32 precision leave about as many poorly approximated
+ * directions as A has singular values below ~2^-24 |A|, and a restart before
+ * they are all captured stagnates), a gmres_tol <= 0 means 1e-10; max_iter bounds the
+ * refinement steps of each phase (each factorisation, then GMRES-IR).
+ * The call is synchronous: it returns after the refinement has finished and
+ * fills *h_result (host).  Returns BFX_OK when every column converged,
+ * BFX_NOT_CONVERGED otherwise (x holds the last iterate), BFX_SINGULAR on an
+ * exactly zero pivot (h_result->info > 0), BFX_EINVAL for gmres outside 0..2
+ * or gmres_m outside 0..BFX_GMRES_MAX_M, and the usual argument / workspace
+ * errors.  Workspace: bfx_solve_ir_workspace_size(mode, n, nrhs, h_params)
+ * bytes (h_params NULL: the defaults), 256-byte aligned; with gmres != 0 it
+ * includes the Krylov basis, (gmres_m + 1) n nrhs doubles, and the
+ * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles. */
+#define BFX_GMRES_MAX_M 2048
 typedef struct bfx_ir_params {
   int max_iter;
   double tol;
@@ -219,6 +238,9 @@ typedef struct bfx_ir_params {
   double stall;
   int escalate;
   int nb;
+  int gmres;        /* 0 off, 1 after plain refinement stalls, 2 always */
+  int gmres_m;      /* Arnoldi steps per refinement step (0: min(n, BFX_GMRES_MAX_M)) */
+  double gmres_tol; /* relative residual reduction ending a GMRES cycle (<= 0: 1e-10) */
 } bfx_ir_params;
 typedef struct bfx_ir_result {
   int32_t info;             /* first zero pivot (1-based) or 0 */
@@ -227,8 +249,11 @@ typedef struct bfx_ir_result {
   int32_t iters;            /* most corrections applied to any column */
   int32_t refactorizations; /* escalations performed */
   double berr;              /* largest normwise backward error over the columns */
+  int32_t gmres_steps;      /* refinement steps whose correction came from GMRES */
+  int32_t arnoldi;          /* Arnoldi steps run, summed over those refinement steps */
 } bfx_ir_result;
-BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs, int nb);
+BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs,
+                                           const bfx_ir_params* h_params);
 BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
                                 int64_t lda, const double* d_b, int64_t ldb, double* d_x,
                                 int64_t ldx, const bfx_ir_params* h_params,
@@ -248,7 +273,8 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
  * (n_s x n_s row-major, FP32); b and x at offset sum_{t<s} n_t nrhs (n_s x
  * nrhs row-major, FP64).
  * bfx_batch_create plans the batch (host memory only); params may be NULL
- * (as bfx_solve_ir; escalate is ignored: a batch keeps its mode).
+ * (as bfx_solve_ir; escalate and gmres are ignored: a batch keeps its mode
+ * and refines by plain refinement).
  * bfx_batch_solve enqueues the graph on `stream` and returns without
  * waiting; d_status (device, one entry per system, caller order) is written
  * at the end: converged, corrections applied, LAPACK info, backward error.
@@ -282,7 +308,7 @@ BFX_API void bfx_batch_destroy(bfx_batch plan);
  * and the bfx_solve_ir workspace); admitted requests run concurrently and
  * their kernels overlap on the device.  Each request is solved exactly as
  * bfx_solve_ir would solve it alone (same kernels, same order of operations),
- * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb}.
+ * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb, gmres, 0, 1e-10}.
  * The caller's host buffers h_A (n x n), h_b (n x nrhs) must stay valid and
  * h_x (n x nrhs, output) writable until the request completes.
  * submit: BFX_ENOMEM if the request can never fit the budget; never blocks.
@@ -295,6 +321,7 @@ typedef struct bfx_server_config {
   bfx_mode mode;
   int nb;       /* LU block width (0 = 64) */
   int escalate; /* refactor with more products when refinement stalls */
+  int gmres;    /* bfx_ir_params.gmres of every request (0, 1 or 2) */
 } bfx_server_config;
 typedef struct bfx_request_result {
   int32_t status;           /* bfx_status of the solve */
@@ -306,6 +333,8 @@ typedef struct bfx_request_result {
   double berr;
   double latency_s;         /* submission to completion */
   double queue_s;           /* submission to admission */
+  int32_t gmres_steps;      /* as bfx_ir_result */
+  int32_t arnoldi;
 } bfx_request_result;
 typedef struct bfx_server_stats_t {
   int32_t queued, running, peak_running, pad;

@@ -15,6 +15,8 @@ from ._bfx import (  # noqa: F401
     BFX_X9,
     Batch,
     BfxError,
+    GMRES_MAX_M,
+    IrParams,
     device_error,
     dot_bf16xN,
     gemm_bf16xN,
@@ -23,6 +25,7 @@ from ._bfx import (  # noqa: F401
     lib,
     lu_bf16xN,
     solve_ir,
+    solve_ir_workspace_size,
     library_path,
     num_sms,
     Server,

@@ -60,7 +60,7 @@ def lib() -> ctypes.CDLL:
         "bfx_dot_workspace_size": (sz, []),
         "bfx_lu_workspace_size": (sz, [i32, i64, i32]),
         "bfx_lu_bf16xN": (i32, [i32, i64, i32, vp, i64, vp, vp, vp, sz, vp]),
-        "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, i32]),
+        "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, vp]),
         "bfx_solve_ir": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
         "bfx_batch_create": (i32, [vp, i32, i32, vp, i32, vp]),
         "bfx_batch_workspace_size": (sz, [vp]),
@@ -216,15 +216,20 @@ def dot_bf16xN(mode: int, x: torch.Tensor, y: torch.Tensor, out: torch.Tensor = 
     return out
 
 
+GMRES_MAX_M = 2048
+
+
 class IrParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("tol_b", ctypes.c_double),
-                ("stall", ctypes.c_double), ("escalate", ctypes.c_int), ("nb", ctypes.c_int)]
+                ("stall", ctypes.c_double), ("escalate", ctypes.c_int), ("nb", ctypes.c_int),
+                ("gmres", ctypes.c_int), ("gmres_m", ctypes.c_int), ("gmres_tol", ctypes.c_double)]
 
 
 class IrResult(ctypes.Structure):
     _fields_ = [("info", ctypes.c_int32), ("mode_used", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("iters", ctypes.c_int32),
-                ("refactorizations", ctypes.c_int32), ("berr", ctypes.c_double)]
+                ("refactorizations", ctypes.c_int32), ("berr", ctypes.c_double),
+                ("gmres_steps", ctypes.c_int32), ("arnoldi", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -248,11 +253,20 @@ def lu_bf16xN(mode: int, A: torch.Tensor, nb: int = 64, ipiv: torch.Tensor = Non
     return A, ipiv, info
 
 
+def solve_ir_workspace_size(mode: int, n: int, nrhs: int, params: "IrParams" = None) -> int:
+    return int(lib().bfx_solve_ir_workspace_size(mode, n, nrhs,
+                                                 ctypes.byref(params) if params is not None else None))
+
+
 def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None, max_iter: int = 50,
              tol: float = 2.0 ** -53, tol_b: float = -1.0, stall: float = 0.5, escalate: bool = True,
-             nb: int = 64, workspace: torch.Tensor = None, stream=None, raise_on_status: bool = False):
+             nb: int = 64, gmres: int = 1, gmres_m: int = 0, gmres_tol: float = 1e-10,
+             workspace: torch.Tensor = None, stream=None, raise_on_status: bool = False):
     """Solve A x = b (A FP32 n x n, b FP64 n x nrhs) by residual-form refinement.
 
+    gmres: 0 plain refinement only; 1 GMRES-IR once plain refinement stalls
+    (after any escalation); 2 GMRES-IR from the first correction.  gmres_m:
+    Arnoldi steps per refinement step (0: min(n, GMRES_MAX_M)).
     Returns (x, result dict, status code).  Synchronous."""
     n = A.shape[0]
     if b.dim() == 1:
@@ -260,10 +274,11 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     nrhs = b.shape[1]
     if x is None:
         x = torch.empty((n, nrhs), dtype=torch.float64, device=A.device)
-    wsb = int(lib().bfx_solve_ir_workspace_size(mode, n, nrhs, nb))
+    p = IrParams(max_iter, tol, tol_b, stall, int(bool(escalate)), nb, int(gmres), int(gmres_m),
+                 float(gmres_tol))
+    wsb = solve_ir_workspace_size(mode, n, nrhs, p)
     if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
         workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
-    p = IrParams(max_iter, tol, tol_b, stall, int(bool(escalate)), nb)
     r = IrResult()
     code = lib().bfx_solve_ir(mode, n, nrhs, _ptr(A), A.stride(0) if n else 1, _ptr(b),
                               b.stride(0) if n else 1, _ptr(x), x.stride(0) if n else 1,
@@ -289,7 +304,7 @@ class Batch:
         self.nrhs = nrhs
         self.mode = mode
         h = ctypes.c_void_p()
-        p = IrParams(max_iter, tol, tol_b, stall, 0, 64)
+        p = IrParams(max_iter, tol, tol_b, stall, 0, 64, 0, 0, 0.0)
         _check("bfx_batch_create", lib().bfx_batch_create(ctypes.byref(h), mode, int(self.ns.size),
                                                          self.ns.ctypes.data, nrhs, ctypes.byref(p)))
         self.handle = h
@@ -342,14 +357,15 @@ class Batch:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("mode", ctypes.c_int),
-                ("nb", ctypes.c_int), ("escalate", ctypes.c_int)]
+                ("nb", ctypes.c_int), ("escalate", ctypes.c_int), ("gmres", ctypes.c_int)]
 
 
 class RequestResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("converged", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("info", ctypes.c_int32), ("mode_used", ctypes.c_int32),
                 ("refactorizations", ctypes.c_int32), ("berr", ctypes.c_double),
-                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double)]
+                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("gmres_steps", ctypes.c_int32), ("arnoldi", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -368,8 +384,9 @@ class Server:
     completes) and returns a ticket; wait() returns (x, result dict)."""
 
     def __init__(self, budget_bytes: int, max_inflight: int = 16, mode: int = BFX_X3, nb: int = 64,
-                 escalate: bool = True):
-        cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(mode), int(nb), int(bool(escalate)))
+                 escalate: bool = True, gmres: int = 1):
+        cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(mode), int(nb), int(bool(escalate)),
+                           int(gmres))
         h = ctypes.c_void_p()
         _check("bfx_server_create", lib().bfx_server_create(ctypes.byref(h), ctypes.byref(cfg)))
         self.handle = h

@@ -96,7 +96,7 @@ __global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
   if (lane == 0) atomic_max_nonneg(out, s);
 }
 
-// r = b - A x (FP64) for columns c0 .. c0+NC; warp a row, lanes over the row
+// r = b - A x (FP64; r = A x when b is null) for columns c0 .. c0+NC; warp a row, lanes over the row
 // (coalesced), one FP64 shuffle reduction per column at the end.  NC is a
 // compile-time column count so no predicated-off FP64 work is issued (FP64
 // throughput is the bound of this kernel on B300).
@@ -125,7 +125,7 @@ __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     if (lane == c) {
-      const double rv = b[row * ldb + c0 + c] - v;
+      const double rv = b ? b[row * ldb + c0 + c] - v : v;  // no b: the product A x
       r[row * ldr + c0 + c] = rv;
       if (rn) atomic_max_nonneg(&rn[c0 + c], fabs(rv));
     }
@@ -275,6 +275,233 @@ __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const doub
     x[i * ldx + c] = xv;
     atomic_max_nonneg(&dn[c], fabs(dv));
     atomic_max_nonneg(&xn[c], fabs(xv));
+  }
+}
+
+// ------------------------------------------------------------- GMRES-IR
+// The correction equation of a refinement step, A d = r, solved by GMRES on
+// M^-1 A d = M^-1 r (M = P^T L U, the FP32 factors applied in FP64), zero
+// first guess, all right-hand sides together, each with its own Krylov basis
+// (GMRES remark of Sec. III; Sec. IV-B).  Vectors are n x R row-major like x,
+// so the basis V is (m+1) blocks of n x R.  Arnoldi orthogonalises by two
+// passes of classical Gram-Schmidt (each a dot-product launch and an update
+// launch, so the FP64 work is spread over the SMs instead of j dependent
+// launches); the Hessenberg column is reduced by Givens rotations as it is
+// formed, one thread per right-hand side.  Dot products are split into
+// chunks of rows; each chunk's partial sums go to `part` and every consumer
+// adds them in chunk order, so results do not depend on scheduling.
+constexpr int GM_THREADS = 256;
+constexpr int GM_ELEMS = 2048;  // vector elements one CTA covers in a dot product
+constexpr int GM_MAXCH = 64;    // most chunks a dot product is split into
+
+// part[(i * nchunk + ch) * R + c] = sum over the chunk's rows of V_i[r, c] w[r, c].
+// Threads own one column each and step through rows, so a warp reads
+// consecutive addresses; partial sums are combined in a fixed order.
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_dot_kernel(const double* __restrict__ V, int64_t vstride, const double* __restrict__ w,
+                  int n, int R, int rows_per_chunk, int nchunk, double* __restrict__ part) {
+  __shared__ double acc[GM_THREADS];
+  __shared__ double red[8 * MAXR];
+  const int i = blockIdx.x, ch = blockIdx.y, t = threadIdx.x;
+  const int tpc = GM_THREADS / R;  // rows a pass
+  const double* v = V + static_cast<int64_t>(i) * vstride;
+  const int r_begin = ch * rows_per_chunk, r_end = min(n, r_begin + rows_per_chunk);
+  double sum = 0.0;
+  if (t < tpc * R) {
+    const int c = t % R;
+    for (int r = r_begin + t / R; r < r_end; r += tpc) {
+      const int64_t e = static_cast<int64_t>(r) * R + c;
+      sum = fma(v[e], w[e], sum);
+    }
+  }
+  acc[t] = t < tpc * R ? sum : 0.0;
+  __syncthreads();
+  if (t < 8 * R) {  // acc[r0 * R + c]: eight strided partial sums per column
+    const int c = t % R, q = t / R;
+    double u = 0.0;
+    for (int r0 = q; r0 < tpc; r0 += 8) u += acc[r0 * R + c];
+    red[t] = u;
+  }
+  __syncthreads();
+  if (t < R) {
+    double u = 0.0;
+    for (int q = 0; q < 8; ++q) u += red[q * R + t];
+    part[(static_cast<int64_t>(i) * nchunk + ch) * R + t] = u;
+  }
+}
+
+// h_i[c] = sum of the chunk partials of <V_i, w> (chunk order), i < nv, into
+// hb[i * R + c]; on Arnoldi-active columns also written (accumulate = 0) or
+// added (accumulate = 1) into column j of H.
+__global__ void gm_reduce_h_kernel(const double* __restrict__ part, int nchunk, int nv, int R,
+                                   double* __restrict__ hb, double* __restrict__ H, int m, int j,
+                                   int accumulate, const int32_t* __restrict__ act) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nv * R) return;
+  const int i = e / R, c = e % R;
+  double u = 0.0;
+  for (int ch = 0; ch < nchunk; ++ch) u += part[(static_cast<int64_t>(i) * nchunk + ch) * R + c];
+  hb[e] = u;
+  if (act[c]) {
+    double* hp = H + (static_cast<int64_t>(c) * m + j) * (m + 1) + i;
+    *hp = accumulate ? *hp + u : u;
+  }
+}
+
+// One classical Gram-Schmidt update: w -= sum_i h_i V_i (i < nv, in order)
+// on Arnoldi-active columns.
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_orth_kernel(const double* __restrict__ V, int64_t vstride, int nv, double* __restrict__ w,
+                   int n, int R, const double* __restrict__ hb, const int32_t* __restrict__ act) {
+  __shared__ int32_t a[MAXR];
+  if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
+  __syncthreads();
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    if (!a[c]) continue;
+    double u = w[e];
+    for (int i = 0; i < nv; ++i) u = fma(-__ldg(hb + i * R + c), V[i * vstride + e], u);
+    w[e] = u;
+  }
+}
+
+// Start of a cycle: w = M^-1 r; beta = |w|_2 (from the partials of <w, w>),
+// V_0 = w / beta, g = beta e_1; a column takes part when it is refinement-
+// active and beta is positive and finite.
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_start_kernel(double* __restrict__ V, const double* __restrict__ w, int n, int R,
+                    const double* __restrict__ part, int nchunk, double* __restrict__ g,
+                    double* __restrict__ beta, int m, const int32_t* __restrict__ active,
+                    int32_t* __restrict__ act_out, int32_t* __restrict__ kdone) {
+  __shared__ double bs[MAXR];
+  __shared__ int32_t a[MAXR];
+  if (threadIdx.x < R) {
+    double u = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) u += part[static_cast<int64_t>(ch) * R + threadIdx.x];
+    const double b = sqrt(u);
+    bs[threadIdx.x] = b;
+    a[threadIdx.x] = active[threadIdx.x] && b > 0.0 && b <= 1.7976931348623157e308;
+  }
+  __syncthreads();
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    if (a[c]) V[e] = w[e] / bs[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x < R) {
+    const int c = threadIdx.x;
+    beta[c] = bs[c];
+    double* gc = g + static_cast<int64_t>(c) * (m + 1);
+    for (int i = 0; i <= m; ++i) gc[i] = 0.0;
+    gc[0] = bs[c];
+    kdone[c] = 0;
+    act_out[c] = a[c];
+  }
+}
+
+// End of Arnoldi step j: h_{j+1,j} = |w|_2 (partials of <w, w>),
+// V_{j+1} = w / h_{j+1,j}; CTA 0, thread c: the earlier rotations applied to
+// column j of H, the rotation that zeroes h_{j+1,j}, g updated; the column
+// stays Arnoldi-active unless |g_{j+1}| <= tau beta, the space became
+// invariant (h_{j+1,j} = 0), m steps are done, or a NaN appeared.
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_next_kernel(double* __restrict__ V, int64_t vstride, int j, const double* __restrict__ w,
+                   int n, int R, const double* __restrict__ part, int nchunk, double* __restrict__ H,
+                   double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                   const double* __restrict__ beta, int m, double tau,
+                   const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
+                   int32_t* __restrict__ kdone) {
+  __shared__ double hn[MAXR];
+  __shared__ int32_t a[MAXR];
+  if (threadIdx.x < R) {
+    double u = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) u += part[static_cast<int64_t>(ch) * R + threadIdx.x];
+    hn[threadIdx.x] = sqrt(u);
+    a[threadIdx.x] = act_in[threadIdx.x];
+  }
+  __syncthreads();
+  double* vn = V + static_cast<int64_t>(j + 1) * vstride;
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    if (a[c] && hn[c] > 0.0) vn[e] = w[e] / hn[c];
+  }
+  if (blockIdx.x == 0 && threadIdx.x < R) {
+    const int c = threadIdx.x;
+    int keep = a[c];
+    if (keep) {
+      double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
+      const double* csc = cs + static_cast<int64_t>(c) * m;
+      const double* snc = sn + static_cast<int64_t>(c) * m;
+      double* gc = g + static_cast<int64_t>(c) * (m + 1);
+      const double hj = hn[c];
+      // earlier rotations, the rotated lower entry carried in a register
+      double p = hcol[0];
+      for (int i = 0; i < j; ++i) {
+        const double q = hcol[i + 1];
+        hcol[i] = csc[i] * p + snc[i] * q;
+        p = -snc[i] * p + csc[i] * q;
+      }
+      const double rho = hypot(p, hj);
+      const double cj = rho > 0.0 ? p / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
+      cs[static_cast<int64_t>(c) * m + j] = cj;
+      sn[static_cast<int64_t>(c) * m + j] = sj;
+      hcol[j] = rho;
+      hcol[j + 1] = 0.0;
+      gc[j + 1] = -sj * gc[j];
+      gc[j] = cj * gc[j];
+      kdone[c] = j + 1;
+      const double res = fabs(gc[j + 1]);
+      if (res <= tau * beta[c] || !(hj > 0.0) || j + 1 >= m || !(res == res)) keep = 0;
+    }
+    act_out[c] = keep;
+  }
+}
+
+// y = R_k^-1 g_k for each refinement-active column (k = kdone[c]): CTA c,
+// one warp, back substitution with the lanes splitting each row's sum.
+__global__ void __launch_bounds__(32)
+    gm_solve_y_kernel(const double* __restrict__ H, const double* __restrict__ g,
+                      const int32_t* __restrict__ kdone, const int32_t* __restrict__ active, int m,
+                      double* __restrict__ y) {
+  extern __shared__ double ys[];  // m doubles
+  const int c = blockIdx.x, lane = threadIdx.x;
+  if (!active[c]) return;
+  const int k = kdone[c];
+  const double* Hc = H + static_cast<int64_t>(c) * m * (m + 1);  // H(i, l) at Hc[l (m+1) + i]
+  const double* gc = g + static_cast<int64_t>(c) * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double u = 0.0;
+    for (int l = i + 1 + lane; l < k; l += 32)
+      u = fma(Hc[static_cast<int64_t>(l) * (m + 1) + i], ys[l], u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, o);
+    if (lane == 0) ys[i] = (gc[i] - u) / Hc[static_cast<int64_t>(i) * (m + 1) + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < k; i += 32) y[static_cast<int64_t>(c) * m + i] = ys[i];
+}
+
+// d[:, c] = sum_{i < kdone[c]} y[c][i] V_i[:, c] on refinement-active columns, 0 elsewhere.
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_combine_kernel(const double* __restrict__ V, int64_t vstride, const double* __restrict__ y,
+                      const int32_t* __restrict__ kdone, const int32_t* __restrict__ active, int n,
+                      int R, int m, double* __restrict__ d) {
+  __shared__ int32_t ks[MAXR];
+  if (threadIdx.x < R) ks[threadIdx.x] = active[threadIdx.x] ? kdone[threadIdx.x] : 0;
+  __syncthreads();
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    const double* yc = y + static_cast<int64_t>(c) * m;
+    double u = 0.0;
+    for (int i = 0; i < ks[c]; ++i) u = fma(__ldg(yc + i), V[i * vstride + e], u);
+    d[e] = u;
   }
 }
 
@@ -536,10 +763,23 @@ struct IrWs {
   double* Uinv;
   void* luws;
   size_t luws_bytes;
+  // GMRES-IR (gm_m > 0 only)
+  int gm_m, gm_nchunk, gm_rows;
+  double* V;      // (m+1) blocks of n x R
+  double* H;      // R x m columns of m+1 (column j of column c's matrix contiguous)
+  double* cs;     // R x m
+  double* sn;     // R x m
+  double* g;      // R x (m+1)
+  double* y;      // R x m
+  double* beta;   // R
+  double* hb;     // (m+1) x R, one Gram-Schmidt pass's coefficients
+  double* part;   // (m+1) x nchunk x R
+  int32_t* flags; // 2 x R (Arnoldi-active, alternating between steps)
+  int32_t* kdone; // R
   size_t total;
 };
 
-IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
+IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m) {
   IrWs w{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -563,6 +803,29 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
   w.luws_bytes = lub;
   w.luws = lub ? take(lub) : nullptr;
+  w.gm_m = gm_m;
+  if (gm_m > 0) {
+    const int64_t R = nrhs, m = gm_m;
+    int64_t rows = std::max<int64_t>(1, GM_ELEMS / R);
+    int64_t nch = ceil_div(n, rows);
+    if (nch > GM_MAXCH) {
+      rows = ceil_div(n, GM_MAXCH);
+      nch = ceil_div(n, rows);
+    }
+    w.gm_rows = static_cast<int>(rows);
+    w.gm_nchunk = static_cast<int>(nch);
+    w.V = reinterpret_cast<double*>(take(sizeof(double) * (m + 1) * n * R));
+    w.H = reinterpret_cast<double*>(take(sizeof(double) * R * (m + 1) * m));
+    w.cs = reinterpret_cast<double*>(take(sizeof(double) * R * m));
+    w.sn = reinterpret_cast<double*>(take(sizeof(double) * R * m));
+    w.g = reinterpret_cast<double*>(take(sizeof(double) * R * (m + 1)));
+    w.y = reinterpret_cast<double*>(take(sizeof(double) * R * m));
+    w.beta = reinterpret_cast<double*>(take(sizeof(double) * R));
+    w.hb = reinterpret_cast<double*>(take(sizeof(double) * (m + 1) * R));
+    w.part = reinterpret_cast<double*>(take(sizeof(double) * (m + 1) * nch * R));
+    w.flags = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2 * R));
+    w.kdone = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * R));
+  }
   w.total = off;
   return w;
 }
@@ -606,6 +869,54 @@ bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int n
   return last_launch_status();
 }
 
+// One GMRES cycle for every refinement-active column.  On entry w.r holds
+// r = b - A x (consumed); on exit w.d holds the correction (0 in the other
+// columns).  *steps = Arnoldi steps run (the most over the columns).  The
+// host reads the R Arnoldi-active flags after each step to stop early.
+bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, int R, double tau,
+                       cudaStream_t s, int* steps) {
+  const int N = static_cast<int>(n), m = w.gm_m, nch = w.gm_nchunk;
+  const int64_t vstride = n * R;
+  const int grid = grid_elems(n * R);
+  bfx_status st;
+  *steps = 0;
+  if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;  // w.d = M^-1 r
+  gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
+  gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
+                                              w.flags, w.kdone);
+  std::vector<int32_t> fl(R);
+  int j = 0;
+  for (; j < m; ++j) {
+    int32_t* ain = w.flags + (j & 1) * R;
+    int32_t* aout = w.flags + ((j + 1) & 1) * R;
+    if (cudaMemcpyAsync(fl.data(), ain, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return BFX_ECUDA;
+    bool any = false;
+    for (int c = 0; c < R; ++c) any = any || fl[c];
+    if (!any) break;
+    const double* vj = w.V + static_cast<int64_t>(j) * vstride;
+    // w.d = M^-1 A v_j
+    if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s)) != BFX_OK) return st;
+    if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
+    for (int pass = 0; pass < 2; ++pass) {
+      gm_dot_kernel<<<dim3(j + 1, nch), GM_THREADS, 0, s>>>(w.V, vstride, w.d, N, R, w.gm_rows, nch,
+                                                            w.part);
+      gm_reduce_h_kernel<<<static_cast<unsigned>(ceil_div((j + 1) * R, 256)), 256, 0, s>>>(
+          w.part, nch, j + 1, R, w.hb, w.H, m, j, pass, ain);
+      gm_orth_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j + 1, w.d, N, R, w.hb, ain);
+    }
+    gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
+    gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, w.H, w.cs,
+                                               w.sn, w.g, w.beta, m, tau, ain, aout, w.kdone);
+  }
+  *steps = j;
+  gm_solve_y_kernel<<<R, 32, sizeof(double) * m, s>>>(w.H, w.g, w.kdone, w.active, m, w.y);
+  gm_combine_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, w.y, w.kdone, w.active, N, R, m, w.d);
+  return last_launch_status();
+}
+
 }  // namespace
 
 bfx_status ir_batched_prepare(const BatchIr* d_ir, int S, int nmax, cudaStream_t s) {
@@ -642,10 +953,44 @@ using namespace bfx;
 
 extern "C" {
 
-BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs, int nb) {
+namespace {
+
+bfx_ir_params ir_defaults() {
+  bfx_ir_params p{};
+  p.max_iter = 50;
+  p.tol = 1.1102230246251565e-16;
+  p.tol_b = -1.0;
+  p.stall = 0.5;
+  p.escalate = 1;
+  p.nb = 64;
+  p.gmres = 1;
+  p.gmres_m = 0;
+  p.gmres_tol = 1e-10;
+  return p;
+}
+
+// Fills the defaults of zero / negative fields; false if a field is out of range.
+bool ir_resolve(const bfx_ir_params* h, int64_t n, bfx_ir_params* out) {
+  bfx_ir_params p = h ? *h : ir_defaults();
+  if (p.nb <= 0) p.nb = 64;
+  if (p.gmres_m == 0) p.gmres_m = static_cast<int>(std::min<int64_t>(n, BFX_GMRES_MAX_M));
+  if (!(p.gmres_tol > 0.0)) p.gmres_tol = 1e-10;
+  if (p.tol_b < 0) p.tol_b = 1.1102230246251565e-16 * std::sqrt(static_cast<double>(n));
+  if (p.nb > 128 || p.max_iter < 0 || p.gmres < 0 || p.gmres > 2 || p.gmres_m < 0 ||
+      p.gmres_m > BFX_GMRES_MAX_M)
+    return false;
+  *out = p;
+  return true;
+}
+
+}  // namespace
+
+BFX_API size_t bfx_solve_ir_workspace_size(bfx_mode mode, int64_t n, int64_t nrhs,
+                                           const bfx_ir_params* h_params) {
   if (n <= 0 || nrhs <= 0) return 0;
-  if (nb <= 0) nb = 64;
-  return carve(nullptr, mode, n, nrhs, nb).total;
+  bfx_ir_params p;
+  if (!ir_resolve(h_params, n, &p)) return 0;
+  return carve(nullptr, mode, n, nrhs, p.nb, p.gmres ? p.gmres_m : 0).total;
 }
 
 BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
@@ -664,13 +1009,11 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
   }
   if (!d_A || !d_b || !d_x || lda < n || ldb < nrhs || ldx < nrhs) return BFX_EINVAL;
   if (n >= (1 << 30) || nrhs > (1 << 20)) return BFX_EUNSUPPORTED;
-  bfx_ir_params p{50, 1.1102230246251565e-16, -1.0, 0.5, 1, 64};
-  if (h_params) p = *h_params;
-  if (p.nb <= 0) p.nb = 64;
-  if (p.nb > 128 || p.max_iter < 0) return BFX_EINVAL;
-  if (p.tol_b < 0) p.tol_b = 1.1102230246251565e-16 * std::sqrt(static_cast<double>(n));
+  bfx_ir_params p;
+  if (!ir_resolve(h_params, n, &p)) return BFX_EINVAL;
+  if (p.gmres && nrhs > MAXR) return BFX_EUNSUPPORTED;  // one Krylov basis a column, <= 16
   if (mode != BFX_FP32 && !is_sm103()) return BFX_EUNSUPPORTED;
-  IrWs w = carve(d_ws, mode, n, nrhs, p.nb);
+  IrWs w = carve(d_ws, mode, n, nrhs, p.nb, p.gmres ? p.gmres_m : 0);
   if (!d_ws || ws_bytes < w.total || !aligned(d_ws, 256)) return BFX_ENOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int R = static_cast<int>(nrhs);
@@ -691,48 +1034,52 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
   ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_b, ldb, n, R, bn);
 
   bfx_mode cur = mode;
-  bool first = true;
+  bool first = true, refactor = true, use_gmres = p.gmres == 2;
   bfx_status st = BFX_OK;
   for (;;) {
-    // ---- factor (again, after an escalation)
-    if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n, n,
-                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return BFX_ECUDA;
-    st = lu_factor(cur, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s);
-    if (st != BFX_OK) return st;
-    int32_t info = 0;
-    if (cudaMemcpyAsync(&info, w.info, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return BFX_ECUDA;
-    h_result->info = info;
-    if (info != 0) return BFX_SINGULAR;
-    const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
-    ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
-    ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
-    const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
-    ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+    if (refactor) {
+      // ---- factor (again, after an escalation)
+      if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n,
+                            n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return BFX_ECUDA;
+      st = lu_factor(cur, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s);
+      if (st != BFX_OK) return st;
+      int32_t info = 0;
+      if (cudaMemcpyAsync(&info, w.info, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return BFX_ECUDA;
+      h_result->info = info;
+      if (info != 0) return BFX_SINGULAR;
+      const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
+      ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
+      ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
+      const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
+      ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+    }
     if (cudaMemcpyAsync(w.active, act.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
       return BFX_ECUDA;
     if (first) {
       // x0 = LU^-1 b: r <- b, solve, x <- d
-      if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R, n,
-                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R,
+                            n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return BFX_ECUDA;
       if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
-      if (cudaMemcpy2DAsync(d_x, sizeof(double) * ldx, w.d, sizeof(double) * R, sizeof(double) * R, n,
-                            cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      if (cudaMemcpy2DAsync(d_x, sizeof(double) * ldx, w.d, sizeof(double) * R, sizeof(double) * R,
+                            n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return BFX_ECUDA;
       if (cudaMemsetAsync(xn, 0, sizeof(double) * R, s) != cudaSuccess) return BFX_ECUDA;
       ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
-      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) !=
-              cudaSuccess ||
+      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess)
         return BFX_ECUDA;
-      for (int c = 0; c < R; ++c) dprev[c] = h[1 + 2 * R + c];  // |x0|
+      for (int c = 0; c < R; ++c) dprev[c] = use_gmres ? INFINITY : h[1 + 2 * R + c];  // |x0|
       first = false;
     } else {
-      for (int c = 0; c < R; ++c) dprev[c] = INFINITY;  // fresh factors: no stall on step one
+      // fresh factors, or the switch to GMRES: no stall test on the first correction
+      for (int c = 0; c < R; ++c) dprev[c] = INFINITY;
     }
     // ---- refinement loop
     for (int it = 0; it < p.max_iter; ++it) {
@@ -740,11 +1087,18 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       for (int c = 0; c < R; ++c) any = any || act[c];
       if (!any) break;
       if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s)) != BFX_OK) return st;
-      if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
+      if (use_gmres) {
+        int k = 0;
+        if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k)) != BFX_OK) return st;
+        h_result->gmres_steps += 1;
+        h_result->arnoldi += k;
+      } else if ((st = lu_solve64(w, n, R, s)) != BFX_OK) {
+        return st;
+      }
       if (cudaMemsetAsync(dn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
       ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn);
-      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s) !=
-              cudaSuccess ||
+      if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess)
         return BFX_ECUDA;
       bool changed = false;
@@ -797,13 +1151,20 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
     h_result->converged = all ? 1 : 0;
     h_result->mode_used = cur;
     if (all) return BFX_OK;
-    // ---- escalate: refactor with more products, refine the unconverged columns
+    // ---- next phase: refactor with more products, else GMRES-IR on these factors
     bfx_mode next = cur;
     if (cur == BFX_X1) next = BFX_X3;
     else if (cur == BFX_X3) next = BFX_X6;
-    if (!p.escalate || next == cur) return BFX_NOT_CONVERGED;
-    cur = next;
-    h_result->refactorizations += 1;
+    if (!use_gmres && p.escalate && next != cur) {
+      cur = next;
+      refactor = true;
+      h_result->refactorizations += 1;
+    } else if (!use_gmres && p.gmres) {
+      use_gmres = true;
+      refactor = false;
+    } else {
+      return BFX_NOT_CONVERGED;
+    }
     for (int c = 0; c < R; ++c) {
       act[c] = conv[c] ? 0 : 1;
       stalled[c] = 0;

@@ -113,10 +113,25 @@ struct bfx_server_impl {
 
 namespace {
 
+bfx_ir_params request_params(const bfx_server_config& cfg) {
+  bfx_ir_params p{};
+  p.max_iter = 50;
+  p.tol = 1.1102230246251565e-16;
+  p.tol_b = -1.0;
+  p.stall = 0.5;
+  p.escalate = cfg.escalate;
+  p.nb = cfg.nb;
+  p.gmres = cfg.gmres;
+  p.gmres_m = 0;
+  p.gmres_tol = 1e-10;
+  return p;
+}
+
 size_t request_bytes(const bfx_server_config& cfg, int64_t n, int64_t nrhs) {
   const size_t a = sizeof(float) * n * n;
   const size_t v = sizeof(double) * n * nrhs;
-  const size_t ws = bfx_solve_ir_workspace_size(cfg.mode, n, nrhs, cfg.nb);
+  const bfx_ir_params p = request_params(cfg);
+  const size_t ws = bfx_solve_ir_workspace_size(cfg.mode, n, nrhs, &p);
   return (a + 255) / 256 * 256 + 2 * ((v + 255) / 256 * 256) + ws + 256;
 }
 
@@ -162,7 +177,7 @@ void worker_main(bfx_server_impl* S) {
     if (cudaMemcpyAsync(dA, r->hA, sizeof(float) * n * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(db, r->hb, sizeof(double) * n * R, cudaMemcpyHostToDevice, st) != cudaSuccess)
       status = BFX_ECUDA;
-    bfx_ir_params p{50, 1.1102230246251565e-16, -1.0, 0.5, S->cfg.escalate, S->cfg.nb};
+    const bfx_ir_params p = request_params(S->cfg);
     bfx_ir_result ir{};
     if (status == BFX_OK)
       status = bfx_solve_ir(S->cfg.mode, n, R, dA, n, db, R, dx, R, &p, &ir, ws, wsb, st);
@@ -184,6 +199,8 @@ void worker_main(bfx_server_impl* S) {
       r->res.mode_used = ir.mode_used;
       r->res.refactorizations = ir.refactorizations;
       r->res.berr = ir.berr;
+      r->res.gmres_steps = ir.gmres_steps;
+      r->res.arnoldi = ir.arnoldi;
       r->res.latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
       r->res.queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
       r->done = true;
@@ -206,6 +223,7 @@ BFX_API bfx_status bfx_server_create(bfx_server* out, const bfx_server_config* c
   if (cfg->budget_bytes < (1u << 20) || cfg->max_inflight < 1 || cfg->max_inflight > 256)
     return BFX_EINVAL;
   if (cfg->mode != BFX_FP32 && bfx::mode_pieces(cfg->mode) == 0) return BFX_EINVAL;
+  if (cfg->gmres < 0 || cfg->gmres > 2) return BFX_EINVAL;
   auto* S = new bfx_server_impl();
   S->cfg = *cfg;
   if (S->cfg.nb <= 0) S->cfg.nb = 64;

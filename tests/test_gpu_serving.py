@@ -38,7 +38,8 @@ def test_budget_limits_admission(bfx):
     n = 1024
     reqs = [bi.svd_system(n, 100.0, 200 + i) for i in range(5)]
     r256 = lambda v: (v + 255) // 256 * 256
-    per = r256(4 * n * n) + 2 * r256(8 * n) + int(bfx.lib().bfx_solve_ir_workspace_size(3, n, 1, 64)) + 256
+    p = bfx.IrParams(50, 2.0**-53, -1.0, 0.5, 1, 64, 1, 0, 1e-10)
+    per = r256(4 * n * n) + 2 * r256(8 * n) + bfx.solve_ir_workspace_size(3, n, 1, p) + 256
     srv = bfx.Server(budget_bytes=int(2.5 * per), max_inflight=8, mode=3)
     tickets = [srv.submit(P.A32, P.b) for P in reqs]
     res = [srv.wait(t) for t in tickets]

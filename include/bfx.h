@@ -71,8 +71,10 @@ BFX_API const char* bfx_status_string(bfx_status s);
 BFX_API int bfx_num_sms(void);
 
 /* Read and clear the device error word of the current device.  Kernels whose
- * waits are bounded (tensor-core GEMM pipeline barriers) set it instead of
- * hanging: 0 = no error, otherwise a code naming the wait that expired.
+ * waits are bounded (tensor-core GEMM pipeline barriers, the refinement's
+ * triangular solves waiting on earlier row blocks) set it instead of
+ * hanging: 0 = no error, otherwise a code naming the wait that expired
+ * (1-5 GEMM pipeline, 6 triangular solve).
  * Synchronises `stream`.  h_code: host int (output). */
 BFX_API bfx_status bfx_device_error(int* h_code, bfx_stream stream);
 

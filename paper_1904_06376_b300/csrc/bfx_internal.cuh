@@ -21,6 +21,7 @@ enum DeviceError : int {
   kErrWaitAccFull = 3,   // epilogue waited too long for an accumulator
   kErrWaitAccEmpty = 4,  // MMA issuer waited too long for the epilogue
   kErrWaitDrain = 5,     // final drain of in-flight MMAs expired
+  kErrWaitBlock = 6,     // triangular solve waited too long for an earlier row block
 };
 
 int* device_error_word();  // nullptr on failure

@@ -37,7 +37,6 @@ namespace {
 
 constexpr int TB = 64;         // triangular-solve row block
 constexpr int MAXR = 16;       // right-hand sides handled per pass
-constexpr int SOLVE_THREADS = 256;
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   // non-negative doubles order like their bit patterns (NaN sorts above Inf)
@@ -187,79 +186,159 @@ __global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __rest
                            Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB);
 }
 
-// One block step of L y = v or U y = v for the diagonal block [b0, b0+bs),
-// with the block's precomputed inverse: y = Dinv v_b.  Every CTA forms y
-// (a 64 x 64 product, warp a row); CTA 0 writes it to `out`, CTA k > 0
-// subtracts F[rows, block] y from row block k of the rows still to be solved
-// (below for L, above for U) in v.  The diagonal rows of v are only read in
-// this launch, so the CTAs do not race.
-template <bool LOWER>
-__global__ void __launch_bounds__(SOLVE_THREADS)
-    ir_trsv_step_kernel(const float* __restrict__ F, int64_t ldf, int n, int b0, int bs,
-                        const double* __restrict__ Dinv, double* __restrict__ v,
-                        double* __restrict__ out, int64_t ldv, int nrhs) {
-  __shared__ double vb[TB][MAXR + 1];
-  __shared__ double y[TB][MAXR + 1];
-  __shared__ float Fs[TB][TB + 1];  // this CTA's 64 x 64 block of F (off-diagonal CTAs)
+// Triangular solve L y = v (unit lower, forward) or U y = v (upper, backward)
+// with the FP32 factors in FP64 arithmetic, in one launch without a grid-wide
+// barrier.  Row blocks of 64; right-hand sides in groups of up to 4 columns.
+// A CTA takes a (row block, column group) from an atomic ticket in solve
+// order, so every block it waits on belongs to a CTA that started earlier and
+// is running: the waits always end (and are bounded in time regardless).
+// CTA for block b, group g:
+//   acc = v_b;  for each earlier block k in solve order: wait until y_k is
+//   published, acc -= F[b, k] y_k;   y_b = Dinv_b acc (the block's inverse);
+//   store y_b, fence, publish.
+// The tile of F is fetched before the wait, so it overlaps the wait; the sums
+// run in a fixed order (deterministic).  sync: [0] ticket, [1 + k*G + g]
+// ready flags; all zero at launch.
+constexpr int TRSV_THREADS = 256;
+constexpr int TRSV_CG = 4;  // right-hand sides a CTA
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// out[i][c] (+)= sign * sum_l T[i][l] x[l][c], i < TB, c < cg; Q threads a
+// product (Q = 4, 2, 1 for cg = 1, 2, >2), their partial sums added by shuffle.
+template <typename T, int LDT>
+__device__ __forceinline__ void trsv_tile_product(const T* Tm, const double (*x)[TRSV_CG + 1],
+                                                  double (*out)[TRSV_CG + 1], int cg, bool sub) {
   const int t = threadIdx.x;
-  const double* D = Dinv + static_cast<int64_t>(b0 / TB) * TB * TB;
-  const int rs = LOWER ? b0 + bs + (static_cast<int>(blockIdx.x) - 1) * TB
-                       : b0 - static_cast<int>(blockIdx.x) * TB;
-  const int nrow = blockIdx.x == 0 ? 0 : (LOWER ? min(rs + TB, n) : rs + TB) - rs;
-  for (int e = t; e < nrow * TB; e += SOLVE_THREADS) {
-    const int i = e / TB, l = e % TB;
-    Fs[i][l] = l < bs ? F[static_cast<int64_t>(rs + i) * ldf + b0 + l] : 0.0f;
+  const int Q = cg == 1 ? 4 : (cg == 2 ? 2 : 1);
+  const int items = TB * cg * Q;  // <= 256
+  if (t >= items) return;
+  const int o = t / Q, q = t - o * Q;
+  const int i = o / cg, c = o - i * cg;
+  const int len = TB / Q, l0 = q * len;
+  const T* row = Tm + i * LDT + l0;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+  for (int l = 0; l < len; l += 2) {
+    s0 = fma(static_cast<double>(row[l]), x[l0 + l][c], s0);
+    s1 = fma(static_cast<double>(row[l + 1]), x[l0 + l + 1][c], s1);
   }
-  for (int c0 = 0; c0 < nrhs; c0 += MAXR) {
-    const int nc = min(MAXR, nrhs - c0);
-    for (int e = t; e < TB * nc; e += SOLVE_THREADS) {
-      const int i = e / nc, c = e - i * nc;
-      vb[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * ldv + c0 + c] : 0.0;
+  double sum = s0 + s1;
+  // items == 256 whenever Q > 1, so every lane of the warp takes part
+  if (Q >= 2) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+  if (Q >= 4) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 2);
+  if (q == 0) out[i][c] = sub ? out[i][c] - sum : sum;
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  // 4-byte asynchronous copy; an invalid element is zero-filled (source size 0)
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(smem)), "l"(gmem),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <bool LOWER>
+__global__ void __launch_bounds__(TRSV_THREADS)
+    ir_trsv_kernel(const float* __restrict__ F, int64_t ldf, int n,
+                   const double* __restrict__ Dinv, const double* __restrict__ v,
+                   double* __restrict__ y, int R, int* __restrict__ sync, int* __restrict__ err) {
+  extern __shared__ __align__(16) uint8_t trsv_smem[];
+  double* Ds = reinterpret_cast<double*>(trsv_smem);                       // [TB][TB + 1]
+  float* Fs = reinterpret_cast<float*>(Ds + TB * (TB + 1));                // 2 x [TB][TB + 1]
+  auto acc = reinterpret_cast<double (*)[TRSV_CG + 1]>(Fs + 2 * TB * (TB + 1));  // [TB][CG + 1]
+  auto xs = acc + TB;                                                       // [TB][CG + 1]
+  __shared__ int s_ticket, s_fail;
+  const int t = threadIdx.x;
+  const int nblk = (n + TB - 1) / TB;
+  const int G = (R + TRSV_CG - 1) / TRSV_CG;
+  if (t == 0) {
+    s_ticket = atomicAdd(sync, 1);
+    s_fail = 0;
+  }
+  __syncthreads();
+  const int step = s_ticket / G, grp = s_ticket - step * G;
+  const int b = LOWER ? step : nblk - 1 - step;
+  const int b0 = b * TB, bs = min(TB, n - b0);
+  const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
+  int* ready = sync + 1;
+  // F[b, k] -> Fs buffer (s & 1), asynchronously; rows >= bs / columns >= ks zero
+  auto prefetch = [&](int s) {
+    const int k = LOWER ? s : nblk - 1 - s;
+    const int k0 = k * TB, ks = min(TB, n - k0);
+    float* dst = Fs + (s & 1) * TB * (TB + 1);
+    for (int e = t; e < TB * TB; e += TRSV_THREADS) {
+      const int i = e / TB, l = e % TB;
+      const bool ok = i < bs && l < ks;
+      cp_async4(dst + i * (TB + 1) + l, ok ? F + static_cast<int64_t>(b0 + i) * ldf + k0 + l : F, ok);
     }
-    __syncthreads();
-    // y = Dinv vb: a thread per (row, column), four partial FMA chains.  Rows
-    // past a partial last block are set to zero: the update below reads all
-    // TB rows, and shared memory left by another kernel may hold NaN patterns.
-    for (int e = t; e < TB * nc; e += SOLVE_THREADS) {
-      const int i = e / nc, c = e - i * nc;
-      if (i >= bs) {
-        y[i][c] = 0.0;
-        continue;
-      }
-      const double* d = D + i * TB;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll 4
-      for (int l = 0; l < TB; l += 4) {
-        s0 = fma(d[l], vb[l][c], s0);
-        s1 = fma(d[l + 1], vb[l + 1][c], s1);
-        s2 = fma(d[l + 2], vb[l + 2][c], s2);
-        s3 = fma(d[l + 3], vb[l + 3][c], s3);
-      }
-      y[i][c] = (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
-      for (int e = t; e < bs * nc; e += SOLVE_THREADS) {
-        const int i = e / nc, c = e - i * nc;
-        out[static_cast<int64_t>(b0 + i) * ldv + c0 + c] = y[i][c];
-      }
-    } else {
-      for (int e = t; e < nrow * nc; e += SOLVE_THREADS) {
-        const int i = e / nc, c = e - i * nc;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll 4
-        for (int l = 0; l < TB; l += 4) {
-          s0 = fma(static_cast<double>(Fs[i][l]), y[l][c], s0);
-          s1 = fma(static_cast<double>(Fs[i][l + 1]), y[l + 1][c], s1);
-          s2 = fma(static_cast<double>(Fs[i][l + 2]), y[l + 2][c], s2);
-          s3 = fma(static_cast<double>(Fs[i][l + 3]), y[l + 3][c], s3);
+  };
+  if (step > 0) prefetch(0);
+  cp_async_commit();
+  // the block's inverse (independent of the other blocks), and acc = v_b
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  for (int e = t; e < TB * TB; e += TRSV_THREADS) Ds[(e / TB) * (TB + 1) + e % TB] = D[e];
+  for (int e = t; e < TB * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    acc[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
+  }
+  for (int s = 0; s < step; ++s) {
+    if (s + 1 < step) prefetch(s + 1);
+    cp_async_commit();
+    const int k = LOWER ? s : nblk - 1 - s;
+    const int k0 = k * TB, ks = min(TB, n - k0);
+    if (t < 32) {  // warp 0: wait until y_k is published, then fetch it
+      if (t == 0 && !s_fail) {
+        const int* f = ready + k * G + grp;
+        if (ld_acquire_gpu(f) == 0) {
+          const uint64_t t0 = global_ns();
+          while (ld_acquire_gpu(f) == 0) {
+            if (global_ns() - t0 > 4000000000ull) {
+              atomicExch(err, kErrWaitBlock);
+              s_fail = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
         }
-        v[static_cast<int64_t>(rs + i) * ldv + c0 + c] -= (s0 + s1) + (s2 + s3);
+      }
+      __syncwarp();
+      for (int e = t; e < TB * cg; e += 32) {
+        const int i = e / cg, c = e - i * cg;
+        xs[i][c] = i < ks ? __ldcg(y + static_cast<int64_t>(k0 + i) * R + c0 + c) : 0.0;
       }
     }
+    cp_async_wait1();  // this thread's copies of tile s have landed
     __syncthreads();
+    trsv_tile_product<float, TB + 1>(Fs + (s & 1) * TB * (TB + 1), xs, acc, cg, true);
+    __syncthreads();
+  }
+  // y_b = Dinv_b acc (rows past a partial block come out 0: acc and the
+  // inverse's padding are zero / identity there)
+  __syncthreads();
+  trsv_tile_product<double, TB + 1>(Ds, acc, xs, cg, false);
+  __syncthreads();
+  for (int e = t; e < bs * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    y[static_cast<int64_t>(b0 + i) * R + c0 + c] = xs[i][c];
+  }
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    st_release_gpu(ready + b * G + grp, 1);
   }
 }
+
+constexpr size_t kTrsvSmem = sizeof(double) * TB * (TB + 1) + 2 * sizeof(float) * TB * (TB + 1) +
+                             2 * sizeof(double) * TB * (TRSV_CG + 1);
 
 // x += d on active columns; dn[c] = max|d|, xn[c] = max|x| (must start at 0).
 __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
@@ -761,6 +840,7 @@ struct IrWs {
   double* norms;  // [0] anorm, then per column: bn, dn, xn, rn
   double* Linv;   // inverses of the 64 x 64 diagonal blocks of L, then of U
   double* Uinv;
+  int32_t* tsync; // triangular-solve tickets and ready flags, both triangles
   void* luws;
   size_t luws_bytes;
   // GMRES-IR (gm_m > 0 only)
@@ -798,6 +878,8 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   const int64_t nblk = (n + TB - 1) / TB;
   w.Linv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.Uinv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
+  w.tsync = reinterpret_cast<int32_t*>(
+      take(sizeof(int32_t) * 2 * (1 + nblk * ceil_div(nrhs, TRSV_CG))));
   size_t lub = 0;
   for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X9})
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
@@ -830,25 +912,30 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   return w;
 }
 
-// d <- U^-1 L^-1 P r (all columns).  r is consumed: the forward pass works in
-// place on d (gathered P r) and writes its solution to r; the backward pass
-// works in place on r and writes the correction to d.
+// d <- U^-1 L^-1 P r (all columns).  r is consumed: d = P r (gathered), the
+// forward solve writes r, the backward solve writes d.
 bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
+  static const bool attr_ok = [] {
+    return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kTrsvSmem)) == cudaSuccess &&
+           cudaFuncSetAttribute(ir_trsv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kTrsvSmem)) == cudaSuccess;
+  }();
+  if (!attr_ok) return BFX_ECUDA;
+  int* err = device_error_word();
+  if (!err) return BFX_ECUDA;
   const int N = static_cast<int>(n);
-  ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs);
   const int nblk = static_cast<int>(ceil_div(n, TB));
-  for (int b = 0; b < nblk; ++b) {  // forward, unit lower
-    const int b0 = b * TB, bs = std::min(TB, N - b0);
-    const int below = static_cast<int>(ceil_div(N - b0 - bs, TB));
-    ir_trsv_step_kernel<true><<<1 + below, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.Linv, w.d,
-                                                                   w.r, nrhs, nrhs);
-  }
-  for (int b = nblk - 1; b >= 0; --b) {  // backward, upper
-    const int b0 = b * TB, bs = std::min(TB, N - b0);
-    const int above = b0 / TB;
-    ir_trsv_step_kernel<false><<<1 + above, SOLVE_THREADS, 0, s>>>(w.LU, n, N, b0, bs, w.Uinv, w.r,
-                                                                    w.d, nrhs, nrhs);
-  }
+  const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
+  const unsigned grid = static_cast<unsigned>(nblk * G);
+  if (cudaMemsetAsync(w.tsync, 0, sizeof(int32_t) * 2 * (1 + static_cast<size_t>(nblk) * G), s) !=
+      cudaSuccess)
+    return BFX_ECUDA;
+  ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs);
+  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.d, w.r, nrhs,
+                                                             w.tsync, err);
+  ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(
+      w.LU, n, N, w.Uinv, w.r, w.d, nrhs, w.tsync + 1 + static_cast<size_t>(nblk) * G, err);
   return last_launch_status();
 }
 

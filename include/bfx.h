@@ -122,6 +122,19 @@ BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t 
                                    float beta, float* d_C, int64_t ldc, void* d_ws,
                                    size_t ws_bytes, bfx_stream stream);
 
+/* The same GEMM with the split fused into the kernel (Sec. V: the conversion
+ * "can be hidden"): the FP32 tiles of A and B are loaded by TMA and split in
+ * registers into the bfloat16 pieces the tensor cores read, so no workspace is
+ * needed and no pieces go through global memory.  Same result as
+ * bfx_gemm_bf16xN bit for bit (same pieces, same products in the same order).
+ * Requirements of the TMA descriptors: lda and ldb multiples of 4, d_A and
+ * d_B 16-byte aligned; otherwise BFX_EUNSUPPORTED.  mode must be X1..X9
+ * (BFX_EINVAL).  Other errors as bfx_gemm_bf16xN. */
+BFX_API bfx_status bfx_gemm_bf16xN_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k,
+                                         float alpha, const float* d_A, int64_t lda,
+                                         const float* d_B, int64_t ldb, float beta, float* d_C,
+                                         int64_t ldc, bfx_stream stream);
+
 /* GEMM from pieces already split.  d_Ap: npieces(mode) planes of m x k
  * bfloat16 (row-major, leading dimension lda_p, plane p at d_Ap + p*a_plane),
  * d_Btp: npieces planes of the TRANSPOSED right operand, n x k (leading

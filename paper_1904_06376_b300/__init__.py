@@ -20,6 +20,7 @@ from ._bfx import (  # noqa: F401
     device_error,
     dot_bf16xN,
     gemm_bf16xN,
+    gemm_bf16xN_fused,
     gemm_presplit,
     gemm_workspace_size,
     lib,

@@ -55,6 +55,7 @@ def lib() -> ctypes.CDLL:
         "bfx_split_transpose": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
         "bfx_gemm_workspace_size": (sz, [i32, i64, i64, i64]),
         "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
+        "bfx_gemm_bf16xN_fused": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
         "bfx_gemm_presplit": (i32, [i32, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, vp]),
         "bfx_sgemm_simt": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
         "bfx_dot_workspace_size": (sz, []),
@@ -170,6 +171,26 @@ def gemm_bf16xN(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = N
     _check("bfx_gemm_bf16xN", lib().bfx_gemm_bf16xN(mode, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
                                                    beta, _ptr(C), ldc, ws_ptr, ws_bytes,
                                                    _stream(stream)))
+    return C
+
+
+def gemm_bf16xN_fused(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None,
+                      alpha: float = 1.0, beta: float = 0.0, stream=None):
+    """As ``gemm_bf16xN`` with the split fused into the tensor-core kernel (no
+    workspace).  Row strides of A and B must be multiples of 4 elements."""
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        beta = 0.0
+    lda = A.stride(0) if m and k else max(k, 1)
+    ldb = B.stride(0) if k and n else max(n, 1)
+    ldc = C.stride(0) if m and n else max(n, 1)
+    _check("bfx_gemm_bf16xN_fused",
+           lib().bfx_gemm_bf16xN_fused(mode, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C),
+                                       ldc, _stream(stream)))
     return C
 
 

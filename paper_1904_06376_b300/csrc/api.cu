@@ -237,4 +237,20 @@ BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t 
   return launch_gemm_presplit(mode, m, n, k, alpha, Ap, kp, ap, Bp, kp, bp, beta, d_C, ldc, s);
 }
 
+BFX_API bfx_status bfx_gemm_bf16xN_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k,
+                                         float alpha, const float* d_A, int64_t lda,
+                                         const float* d_B, int64_t ldb, float beta, float* d_C,
+                                         int64_t ldc, bfx_stream stream) {
+  if (mode_pieces(mode) == 0) return BFX_EINVAL;
+  bfx_status st = check_gemm_args(m, n, k, d_A, lda, d_B, ldb, d_C, ldc);
+  if (st != BFX_OK) return st;
+  if (m == 0 || n == 0) return BFX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (k == 0) return launch_scale(m, n, beta, d_C, ldc, s);
+  if (ldb < n) return BFX_EINVAL;
+  if (m >= INT32_MAX || n >= INT32_MAX || k >= INT32_MAX) return BFX_EUNSUPPORTED;
+  if (!is_sm103()) return BFX_EUNSUPPORTED;
+  return launch_gemm_fused(mode, m, n, k, alpha, d_A, lda, d_B, ldb, beta, d_C, ldc, s);
+}
+
 }  // extern "C"

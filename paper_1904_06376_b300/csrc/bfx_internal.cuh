@@ -62,6 +62,11 @@ struct GroupProblem {
   int M, N, k_tiles, plane0, vec_c, pad;
 };
 int gemm_bk(bfx_mode mode);  // K-slice width of the mode's kernel
+// Fused split + product: FP32 A (m x k, lda) and B (k x n, ldb) read by TMA
+// and split in the kernel (lda, ldb multiples of 4, A, B 16-byte aligned).
+bfx_status launch_gemm_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
+                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                             float* C, int64_t ldc, cudaStream_t s);
 bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
                                const GroupProblem* d_probs, const uint16_t* Apack,
                                int64_t a_rows, const uint16_t* Bpack, int64_t b_rows,
@@ -191,6 +196,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, uint64_
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
       "l"(tmap), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_t* bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(smem_addr(bar)), "r"(c0), "r"(c1)
       : "memory");
 }
 

@@ -29,6 +29,14 @@
 //             alpha/beta, store; releases the accumulator (`acc_empty`) as
 //             soon as it has been read so the next tile's MMAs overlap the
 //             stores.
+// Fused variant (FUSED = true): warp 0 loads FP32 tiles of A (128 x 16) and
+// B (16 x BN) by TMA into a ring of FP32 stages; sixteen converter warps split
+// each element in registers into its bfloat16 pieces (the same per-element
+// split as the separate pass, Sec. II-A) and store them, already in the
+// swizzled K-major layout the MMA descriptors expect, into the piece stages;
+// the MMA and epilogue roles are unchanged.  No piece buffer in global memory
+// is needed, and the results equal those of the separate split + GEMM bit for
+// bit (same pieces, same MMA sequence).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code
 // in the device error word and all roles leave their loops, drain the
 // in-flight copies/MMAs (again with a bound) and free tensor memory.
@@ -137,7 +145,7 @@ __device__ __forceinline__ TileInfo get_tile<true>(int t, const TcArgs& a) {
   return ti;
 }
 
-template <int MODE, int BN, int BK, int STAGES>
+template <int MODE, int BN, int BK, int STAGES, bool FUSED = false>
 struct TcConfig {
   static constexpr int NP = mode_np(MODE);
   static constexpr int NPROD = MODE;
@@ -149,41 +157,168 @@ struct TcConfig {
   static constexpr uint32_t B_TILE = BN * BK * 2;
   static constexpr uint32_t STAGE_A = NP * A_TILE;
   static constexpr uint32_t STAGE = NP * (A_TILE + B_TILE);
+  // fused: FP32 stages of 16 K-columns (A 128 x 16 with 64-byte swizzle, B 16 x BN plain)
+  static constexpr int KF = 16;
+  static constexpr uint32_t A32_TILE = BM * KF * 4;
+  static constexpr uint32_t STAGE32 = FUSED ? (BM + BN) * KF * 4 : 1;
+  // as many FP32 stages as the rest of shared memory holds (up to 8): they
+  // carry the loads in flight that hide the memory latency
+  static constexpr int S32_FIT = static_cast<int>((232448u - 1280u - STAGES * STAGE) / STAGE32);
+  static constexpr int S32 = FUSED ? (S32_FIT < 8 ? S32_FIT : 8) : 0;
+  static constexpr int CONV_WARPS = FUSED ? 16 : 0;
+  static constexpr int THREADS = 192 + 32 * CONV_WARPS;
   static constexpr uint32_t BAR_BYTES = 256;
-  static constexpr uint32_t SMEM = STAGES * STAGE + BAR_BYTES + 1024;  // + alignment slack
+  static constexpr uint32_t SMEM = STAGES * STAGE + S32 * STAGE32 + BAR_BYTES + 1024;  // + alignment
   static_assert(SW == 64 || SW == 128, "BK must be 32 or 64 bfloat16");
+  static_assert(!FUSED || (BK == 32 && BN == 256), "fused: BK 32 (two FP32 stages a K-slice), BN 256");
   static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
                     TMEM_COLS == 512,
                 "tensor memory allocation must be a power of two");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
   static_assert(SMEM <= 232448, "shared memory");
-  static_assert((2 * STAGES + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
+  static_assert((2 * STAGES + 2 * S32 + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
 };
 
-template <int MODE, int BN, int BK, int STAGES, bool GROUPED>
-__global__ void __launch_bounds__(192, 1)
+// Converter warps of the fused kernel: split one FP32 stage (16 K-columns)
+// into half of a piece stage (K-chunks 2h, 2h+1 of the 32-wide slice).
+// Chunk c of row r of a 64-byte-swizzled K-major tile sits at r*64 + 16*(c ^ ((r>>1)&3)).
+//
+// Fast path: pairs of values through cvt.rn.bf16x2 (two RNE conversions in one
+// instruction), remainders by exact FP32 subtraction: bit for bit the split
+// of split_elem for every finite value whose RNE bfloat16 does not overflow.
+// A warp in which any hi piece comes out with an all-ones exponent (Inf/NaN
+// input, or the overflow case of the split's reading R3) redoes its values
+// with split_elem.
+
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo_elem, float hi_elem) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+  return r;
+}
+
+// w[p] = (piece p of e1) << 16 | (piece p of e0); returns nonzero if a hi half
+// has an all-ones exponent (then the pair needs split_elem).
+template <int NP>
+__device__ __forceinline__ uint32_t split_pair(float e0, float e1, uint32_t (&w)[3]) {
+  const uint32_t h = cvt_bf16x2(e0, e1);
+  w[0] = h;
+  if (NP >= 2) {
+    const float r0 = __fsub_rn(e0, __uint_as_float(h << 16));
+    const float r1 = __fsub_rn(e1, __uint_as_float(h & 0xFFFF0000u));
+    const uint32_t m = cvt_bf16x2(r0, r1);
+    w[1] = m;
+    if (NP >= 3) {
+      const float s0 = __fsub_rn(r0, __uint_as_float(m << 16));
+      const float s1 = __fsub_rn(r1, __uint_as_float(m & 0xFFFF0000u));
+      w[2] = cvt_bf16x2(s0, s1);
+    }
+  }
+  return __vcmpeq2(h & 0x7F807F80u, 0x7F807F80u);
+}
+
+// Pieces of 8 consecutive values as one 16-byte word per piece.
+template <int NP>
+__device__ __forceinline__ void split8(const float (&e)[8], uint4 (&o)[3]) {
+  uint32_t w[4][3];
+  uint32_t bad = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) bad |= split_pair<NP>(e[2 * j], e[2 * j + 1], w[j]);
+  if (__any_sync(0xFFFFFFFFu, bad != 0)) {
+    uint16_t q[3][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) split_elem(e[i], q[0][i], q[1][i], q[2][i]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        w[j][p] = q[p][2 * j] | (static_cast<uint32_t>(q[p][2 * j + 1]) << 16);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) o[p] = make_uint4(w[0][p], w[1][p], w[2][p], w[3][p]);
+}
+
+// Pieces of 4 consecutive values as one 8-byte word per piece.
+template <int NP>
+__device__ __forceinline__ void split4(const float4 x, uint2 (&o)[3]) {
+  uint32_t w[2][3];
+  uint32_t bad = split_pair<NP>(x.x, x.y, w[0]) | split_pair<NP>(x.z, x.w, w[1]);
+  if (__any_sync(0xFFFFFFFFu, bad != 0)) {
+    const float e[4] = {x.x, x.y, x.z, x.w};
+    uint16_t q[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_elem(e[i], q[0][i], q[1][i], q[2][i]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        w[j][p] = q[p][2 * j] | (static_cast<uint32_t>(q[p][2 * j + 1]) << 16);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) o[p] = make_uint2(w[0][p], w[1][p]);
+}
+
+// 16 converter warps, thread ct (0..511).  A: row ct/4, FP32 chunk ct%4 (4
+// K-values) -> half of a 16-byte piece chunk.  B: column ct%256, K-values
+// 8*(ct/256) .. +7 of the stage -> one 16-byte piece chunk of row n of B^T
+// (a warp reads 32 consecutive columns: no bank conflicts).
+template <int NP, int BN>
+__device__ __forceinline__ void convert_half(const uint8_t* st32, uint8_t* pst, int h, int ct) {
+  constexpr uint32_t A_TILE = BM * 32 * 2, B_TILE = BN * 32 * 2, A32_TILE = BM * 16 * 4;
+  {  // A: FP32 rows of 16 values (64 bytes, 64-byte swizzle as written by TMA)
+    const int m = ct >> 2, j = ct & 3, sw = (m >> 1) & 3;
+    const float4 x = *reinterpret_cast<const float4*>(st32 + m * 64 + 16 * (j ^ sw));
+    uint2 o[3];
+    split4<NP>(x, o);
+    const int off = m * 64 + 16 * ((2 * h + (j >> 1)) ^ sw) + 8 * (j & 1);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) *reinterpret_cast<uint2*>(pst + p * A_TILE + off) = o[p];
+  }
+  {  // B: FP32 rows k of BN values (plain); column n becomes row n of B^T
+    const int n = ct & (BN - 1), c = ct / BN, sw = (n >> 1) & 3;
+    const float* b32 = reinterpret_cast<const float*>(st32 + A32_TILE);
+    float e[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e[k] = b32[(8 * c + k) * BN + n];
+    uint4 o[3];
+    split8<NP>(e, o);
+    uint8_t* bt = pst + NP * A_TILE + n * 64 + 16 * ((2 * h + c) ^ sw);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) *reinterpret_cast<uint4*>(bt + p * B_TILE) = o[p];
+  }
+}
+
+template <int MODE, int BN, int BK, int STAGES, bool GROUPED, bool FUSED = false>
+__global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED>::THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs args) {
-  using Cfg = TcConfig<MODE, BN, BK, STAGES>;
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED>;
   constexpr uint32_t IDESC = idesc_bf16_f32<BM, BN>();
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_addr(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE);
+  uint8_t* smem32 = smem + STAGES * Cfg::STAGE;  // fused: FP32 stages
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem32 + Cfg::S32 * Cfg::STAGE32);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;
   uint64_t* acc_empty = acc_full + Cfg::ACC_BUFS;
   uint64_t* drain = acc_empty + Cfg::ACC_BUFS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* full32 = drain + 1;  // fused only
+  uint64_t* empty32 = full32 + Cfg::S32;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty32 + Cfg::S32);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = args.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      // fused: the piece stage is filled by the converter warps
+      mbar_init(&full[s], FUSED ? Cfg::CONV_WARPS : 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < Cfg::S32; ++s) {
+      mbar_init(&full32[s], 1);
+      mbar_init(&empty32[s], Cfg::CONV_WARPS);
     }
     for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -207,23 +342,35 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------ TMA producer
+      constexpr int NS = FUSED ? Cfg::S32 : STAGES;
+      uint64_t* fbar = FUSED ? full32 : full;
+      uint64_t* ebar = FUSED ? empty32 : empty;
       int s = 0;
       uint32_t ph = 0;
       int64_t issued = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
         const TileInfo ti = get_tile<GROUPED>(t, args);
-        for (int kt = 0; kt < ti.k_tiles; ++kt) {
-          if (!mbar_wait_bounded(&empty[s], ph ^ 1u, err, kErrWaitEmpty)) {
+        const int loads = FUSED ? 2 * ti.k_tiles : ti.k_tiles;
+        for (int kt = 0; kt < loads; ++kt) {
+          if (!mbar_wait_bounded(&ebar[s], ph ^ 1u, err, kErrWaitEmpty)) {
             ok = false;
             break;
           }
-          uint8_t* st = smem + s * Cfg::STAGE;
-          mbar_arrive_expect_tx(&full[s], Cfg::STAGE);
-          tma_load_3d(st, &tmA, &full[s], kt * BK, ti.mb * BM, ti.c2);
-          tma_load_3d(st + Cfg::STAGE_A, &tmB, &full[s], kt * BK, ti.nb * BN, ti.c2);
+          if constexpr (FUSED) {
+            // FP32 K-columns kt*16 .. kt*16+15 of the A row block and the B column block
+            uint8_t* st = smem32 + s * Cfg::STAGE32;
+            mbar_arrive_expect_tx(&fbar[s], Cfg::STAGE32);
+            tma_load_2d(st, &tmA, &fbar[s], kt * Cfg::KF, ti.mb * BM);
+            tma_load_2d(st + Cfg::A32_TILE, &tmB, &fbar[s], ti.nb * BN, kt * Cfg::KF);
+          } else {
+            uint8_t* st = smem + s * Cfg::STAGE;
+            mbar_arrive_expect_tx(&fbar[s], Cfg::STAGE);
+            tma_load_3d(st, &tmA, &fbar[s], kt * BK, ti.mb * BM, ti.c2);
+            tma_load_3d(st + Cfg::STAGE_A, &tmB, &fbar[s], kt * BK, ti.nb * BN, ti.c2);
+          }
           ++issued;
-          if (++s == STAGES) {
+          if (++s == NS) {
             s = 0;
             ph ^= 1u;
           }
@@ -231,11 +378,46 @@ __global__ void __launch_bounds__(192, 1)
       }
       // Every issued load must have landed before the CTA may exit: wait for
       // the last phase issued on each stage (already complete in normal runs).
-      for (int q = 0; q < STAGES; ++q) {
+      for (int q = 0; q < NS; ++q) {
         if (issued <= q) break;
-        const int64_t last = q + ((issued - 1 - q) / STAGES) * STAGES;
-        mbar_wait_bounded(&full[q], static_cast<uint32_t>((last / STAGES) & 1), err,
-                          kErrWaitDrain);
+        const int64_t last = q + ((issued - 1 - q) / NS) * NS;
+        mbar_wait_bounded(&fbar[q], static_cast<uint32_t>((last / NS) & 1), err, kErrWaitDrain);
+      }
+    }
+  } else if (FUSED && warp >= 6) {
+    // -------------------------------------------------- converters (fused)
+    const int ct = threadIdx.x - 192;  // 0..511
+    int s32 = 0, sp = 0;
+    uint32_t ph32 = 0, php = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+      const int k_tiles = get_tile<GROUPED>(t, args).k_tiles;
+      for (int kt = 0; kt < k_tiles && ok; ++kt) {
+        // the piece stage must have been consumed by the MMAs issued from it
+        ok = mbar_wait_bounded(&empty[sp], php ^ 1u, err, kErrWaitEmpty);
+        ok = __all_sync(0xFFFFFFFFu, ok);
+        if (!ok) break;
+        uint8_t* pst = smem + sp * Cfg::STAGE;
+        for (int h = 0; h < 2; ++h) {
+          ok = mbar_wait_bounded(&full32[s32], ph32, err, kErrWaitFull);
+          ok = __all_sync(0xFFFFFFFFu, ok);
+          if (!ok) break;
+          convert_half<Cfg::NP, BN>(smem32 + s32 * Cfg::STAGE32, pst, h, ct);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty32[s32]);  // FP32 stage free for the next load
+          if (++s32 == Cfg::S32) {
+            s32 = 0;
+            ph32 ^= 1u;
+          }
+        }
+        if (!ok) break;
+        fence_proxy_async_smem();  // piece writes visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[sp]);
+        if (++sp == STAGES) {
+          sp = 0;
+          php ^= 1u;
+        }
       }
     }
   } else if (warp == 1) {
@@ -447,6 +629,60 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
   return last_launch_status();
 }
 
+// 2-D FP32 tensor {inner, rows} with row stride ld elements, box {box_inner, box_rows}.
+bool make_f32_map(CUtensorMap* map, const float* base, int64_t inner, int64_t rows, int64_t ld,
+                  int box_inner, int box_rows, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, int STAGES>
+bfx_status run_tc_fused(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                        cudaStream_t s) {
+  constexpr int BN = 256, BK = 32;
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, true>;
+  CUtensorMap ma, mb;
+  if (!make_f32_map(&ma, A, k, m, lda, Cfg::KF, BM, CU_TENSOR_MAP_SWIZZLE_64B))
+    return BFX_EUNSUPPORTED;
+  if (!make_f32_map(&mb, B, n, k, ldb, BN, Cfg::KF, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return BFX_EUNSUPPORTED;
+  TcArgs a{};
+  a.M = static_cast<int>(m);
+  a.N = static_cast<int>(n);
+  a.K = static_cast<int>(k);
+  a.tiles_m = static_cast<int>(ceil_div(m, BM));
+  a.tiles_n = static_cast<int>(ceil_div(n, BN));
+  const int64_t tiles = static_cast<int64_t>(a.tiles_m) * a.tiles_n;
+  if (tiles > INT32_MAX) return BFX_EUNSUPPORTED;
+  a.num_tiles = static_cast<int>(tiles);
+  a.k_tiles = static_cast<int>(ceil_div(k, BK));
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.vec_c = (ldc % 4 == 0) && aligned(C, 16);
+  a.err = device_error_word();
+  if (!a.err) return BFX_ECUDA;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false, true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
+      cudaSuccess)
+    return BFX_ECUDA;
+  const int sms = current_num_sms();
+  const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+  kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(ma, mb, a);
+  return last_launch_status();
+}
+
 template <int MODE, int BN, int BK, int STAGES>
 bfx_status run_tc_grouped(int num_tiles, const GroupTile* d_tiles, const GroupProblem* d_probs,
                           const uint16_t* Apack, int64_t a_rows, const uint16_t* Bpack,
@@ -501,6 +737,27 @@ bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_
     case BFX_X9:
       return run_tc_grouped<9, 256, 32, 3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
                                            b_rows, planes, kp, alpha, beta, s);
+    default:
+      return BFX_EINVAL;
+  }
+}
+
+bfx_status launch_gemm_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
+                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                             float* C, int64_t ldc, cudaStream_t s) {
+  if (m == 0 || n == 0) return BFX_OK;
+  if (k == 0) return launch_scale(m, n, beta, C, ldc, s);
+  // TMA: 16-byte aligned bases and row strides
+  if (lda % 4 != 0 || ldb % 4 != 0 || !aligned(A, 16) || !aligned(B, 16)) return BFX_EUNSUPPORTED;
+  switch (mode) {
+    case BFX_X1:
+      return run_tc_fused<1, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    case BFX_X3:
+      return run_tc_fused<3, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    case BFX_X6:
+      return run_tc_fused<6, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    case BFX_X9:
+      return run_tc_fused<9, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
     default:
       return BFX_EINVAL;
   }

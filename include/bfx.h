@@ -308,6 +308,49 @@ typedef struct bfx_batch_status {
 typedef struct bfx_batch_plan* bfx_batch;
 BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, const int32_t* h_n,
                                     int nrhs, const bfx_ir_params* params);
+/* Tile shapes of a batch: nb = block-column width of the LU (32, 64 or 128;
+ * also the K of every grouped trailing update), gemm_bn = N width of the
+ * grouped tensor-core tiles (64, 128 or 256); 0 = default (64, 256).
+ * bfx_batch_create is bfx_batch_create_config with config NULL.  The shape
+ * changes the blocking (so the rounding) of the factorisation, not the
+ * method.  BFX_EINVAL for other values. */
+typedef struct bfx_batch_config {
+  int nb;
+  int gemm_bn;
+} bfx_batch_config;
+BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int count,
+                                           const int32_t* h_n, int nrhs,
+                                           const bfx_ir_params* params,
+                                           const bfx_batch_config* config);
+BFX_API bfx_status bfx_batch_get_config(bfx_batch plan, bfx_batch_config* out);
+/* Autotuner: solves the caller's batch (packed d_A, d_b as for
+ * bfx_batch_solve) under each of the 9 shapes nb x gemm_bn, each as the
+ * captured graph the batch replays: one untimed solve, then `reps` timed with
+ * CUDA events on `stream` (median).  Workspaces are allocated with cudaMalloc
+ * and freed per shape; a shape whose workspace does not fit is skipped
+ * (BFX_ENOMEM in its table entry).  d_x and d_status are overwritten.
+ * Returns the fastest shape in *h_best (and its median ms in *h_best_ms if
+ * not NULL); if h_table_len is not NULL, up to *h_table_len entries (one per
+ * shape: shape, median ms or -1, status) go to h_table and *h_table_len is
+ * set to the number of shapes tried.  The result is also remembered for the
+ * process under a coarse signature of the batch (mode, nrhs, max_iter,
+ * count to two digits, the size histogram in bins of 128 to 1/20), which
+ * bfx_batch_tuned_config looks up (BFX_EINVAL if absent).  Synchronous.
+ * Errors: BFX_EINVAL (arguments, or the batch itself), BFX_ENOMEM (no shape
+ * fits), BFX_ECUDA. */
+typedef struct bfx_tune_entry {
+  bfx_batch_config config;
+  float ms;
+  int32_t status;
+} bfx_tune_entry;
+BFX_API bfx_status bfx_batch_autotune(bfx_mode mode, int count, const int32_t* h_n, int nrhs,
+                                      const bfx_ir_params* params, const float* d_A,
+                                      const double* d_b, double* d_x,
+                                      bfx_batch_status* d_status, int reps, bfx_stream stream,
+                                      bfx_batch_config* h_best, float* h_best_ms,
+                                      bfx_tune_entry* h_table, int* h_table_len);
+BFX_API bfx_status bfx_batch_tuned_config(bfx_mode mode, int count, const int32_t* h_n, int nrhs,
+                                          const bfx_ir_params* params, bfx_batch_config* out);
 BFX_API size_t bfx_batch_workspace_size(bfx_batch plan);
 BFX_API bfx_status bfx_batch_solve(bfx_batch plan, const float* d_A, const double* d_b,
                                    double* d_x, bfx_batch_status* d_status, void* d_ws,

@@ -14,6 +14,8 @@ from ._bfx import (  # noqa: F401
     BFX_X6,
     BFX_X9,
     Batch,
+    BatchConfig,
+    batch_autotune,
     BfxError,
     GMRES_MAX_M,
     IrParams,

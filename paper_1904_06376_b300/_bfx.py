@@ -67,6 +67,10 @@ def lib() -> ctypes.CDLL:
         "bfx_batch_workspace_size": (sz, [vp]),
         "bfx_batch_solve": (i32, [vp, vp, vp, vp, vp, vp, sz, vp]),
         "bfx_batch_destroy": (None, [vp]),
+        "bfx_batch_create_config": (i32, [vp, i32, i32, vp, i32, vp, vp]),
+        "bfx_batch_get_config": (i32, [vp, vp]),
+        "bfx_batch_autotune": (i32, [i32, i32, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]),
+        "bfx_batch_tuned_config": (i32, [i32, i32, vp, i32, vp, vp]),
         "bfx_server_create": (i32, [vp, vp]),
         "bfx_server_submit": (i32, [vp, i64, i64, vp, vp, vp, vp]),
         "bfx_server_wait": (i32, [vp, i64, vp, ctypes.c_double]),
@@ -310,25 +314,78 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     return x, r.as_dict(), code
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("gemm_bn", ctypes.c_int)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("config", BatchConfig), ("ms", ctypes.c_float), ("status", ctypes.c_int32)]
+
+
+def _batch_params(max_iter, tol, tol_b, stall):
+    return IrParams(max_iter, tol, tol_b, stall, 0, 64, 0, 0, 0.0)
+
+
+def batch_autotune(mode: int, ns, A, b, nrhs: int = 1, x=None, status=None, reps: int = 3,
+                   max_iter: int = 20, tol: float = 2.0 ** -53, tol_b: float = -1.0,
+                   stall: float = 0.5, stream=None):
+    """Time the batch (packed A, b on the device) under every tile shape and
+    return ((nb, gemm_bn) of the fastest, its median ms, [(nb, gemm_bn, ms,
+    status), ...])."""
+    import numpy as np
+
+    ns = np.asarray(ns, dtype=np.int32)
+    if x is None:
+        x = torch.empty(int((ns.astype(np.int64) * nrhs).sum()), dtype=torch.float64, device=A.device)
+    if status is None:
+        status = torch.zeros(3 * int(ns.size), dtype=torch.float64, device=A.device)
+    p = _batch_params(max_iter, tol, tol_b, stall)
+    best = BatchConfig()
+    best_ms = ctypes.c_float()
+    table = (TuneEntry * 9)()
+    tlen = ctypes.c_int(9)
+    _check("bfx_batch_autotune",
+           lib().bfx_batch_autotune(mode, int(ns.size), ns.ctypes.data, nrhs, ctypes.byref(p), _ptr(A),
+                                    _ptr(b), _ptr(x), _ptr(status), int(reps), _stream(stream),
+                                    ctypes.byref(best), ctypes.byref(best_ms), table, ctypes.byref(tlen)))
+    rows = [(e.config.nb, e.config.gemm_bn, float(e.ms), int(e.status)) for e in table[: tlen.value]]
+    return (best.nb, best.gemm_bn), float(best_ms.value), rows
+
+
 class Batch:
     """Batched solves of many uneven-size systems (bfx_batch_* of the C ABI).
 
     ns: sizes of the systems (1..1024); matrices / right-hand sides are packed
     back to back (see ``pack``).  ``solve`` enqueues one CUDA-graph launch and
-    returns the device status tensor (decode with ``decode_status``)."""
+    returns the device status tensor (decode with ``decode_status``).
+    config: None (default shape), (nb, gemm_bn), or "tuned" (the shape the
+    autotuner recorded for batches like this one; default if none)."""
 
     def __init__(self, mode: int, ns, nrhs: int = 1, max_iter: int = 20, tol: float = 2.0 ** -53,
-                 tol_b: float = -1.0, stall: float = 0.5):
+                 tol_b: float = -1.0, stall: float = 0.5, config=None):
         import numpy as np
 
         self.ns = np.asarray(ns, dtype=np.int32)
         self.nrhs = nrhs
         self.mode = mode
         h = ctypes.c_void_p()
-        p = IrParams(max_iter, tol, tol_b, stall, 0, 64, 0, 0, 0.0)
-        _check("bfx_batch_create", lib().bfx_batch_create(ctypes.byref(h), mode, int(self.ns.size),
-                                                         self.ns.ctypes.data, nrhs, ctypes.byref(p)))
+        p = _batch_params(max_iter, tol, tol_b, stall)
+        cfg = None
+        if config == "tuned":
+            c = BatchConfig()
+            if lib().bfx_batch_tuned_config(mode, int(self.ns.size), self.ns.ctypes.data, nrhs,
+                                            ctypes.byref(p), ctypes.byref(c)) == 0:
+                cfg = c
+        elif config is not None:
+            cfg = BatchConfig(int(config[0]), int(config[1]))
+        _check("bfx_batch_create_config",
+               lib().bfx_batch_create_config(ctypes.byref(h), mode, int(self.ns.size), self.ns.ctypes.data,
+                                             nrhs, ctypes.byref(p),
+                                             ctypes.byref(cfg) if cfg is not None else None))
         self.handle = h
+        got = BatchConfig()
+        _check("bfx_batch_get_config", lib().bfx_batch_get_config(h, ctypes.byref(got)))
+        self.config = (got.nb, got.gemm_bn)
         self.ws_bytes = int(lib().bfx_batch_workspace_size(h))
         self.offA = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) ** 2)])
         self.offV = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) * nrhs)])

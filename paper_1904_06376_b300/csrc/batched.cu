@@ -15,7 +15,8 @@
 namespace bfx {
 namespace {
 
-constexpr int kBatchNb = 64;      // block-column width of the batched LU
+constexpr int kBatchNb = 64;      // default block-column width of the batched LU
+constexpr int kBatchBn = 256;     // default tile width of the grouped trailing updates
 constexpr int kBatchMaxN = 1024;  // largest system of a batch
 constexpr int kSolveTB = 64;      // diagonal-block size of the refinement solves
 
@@ -32,7 +33,7 @@ using namespace bfx;
 
 struct bfx_batch_plan {
   bfx_mode mode;
-  int S, nrhs, nb, max_iter, np, nmax;
+  int S, nrhs, nb, bn, max_iter, np, nmax;
   BatchIrParams p;
   std::vector<int> n;       // caller order
   std::vector<int> sorted;  // sorted[k] = caller index, n descending
@@ -77,7 +78,7 @@ bfx_status enqueue(bfx_batch_plan* P, cudaStream_t s) {
                           packB, P->slot_rows, P->kp, s);
     if (st != BFX_OK) return st;
     if (P->step_ntiles[k] > 0) {
-      st = launch_gemm_grouped(P->mode, P->step_ntiles[k], tiles + P->step_tile_off[k],
+      st = launch_gemm_grouped(P->mode, P->bn, P->step_ntiles[k], tiles + P->step_tile_off[k],
                                probs + P->step_prob_off[k], packA, P->slot_rows, packB,
                                P->slot_rows, static_cast<int64_t>(P->S) * P->np, P->kp, -1.0f,
                                1.0f, s);
@@ -149,7 +150,7 @@ bfx_status write_tables(bfx_batch_plan* P, cudaStream_t s) {
       const int pi = static_cast<int>(pr.size()) - p0;
       pr.push_back(g);
       for (int mb = 0; mb < ceil_div(M, 128); ++mb)
-        for (int nbk = 0; nbk < ceil_div(M, 256); ++nbk) tl.push_back(GroupTile{pi, mb, nbk, 0});
+        for (int nbk = 0; nbk < ceil_div(M, P->bn); ++nbk) tl.push_back(GroupTile{pi, mb, nbk, 0});
     }
   }
   if (static_cast<int64_t>(tl.size()) != P->ntiles_all || static_cast<int64_t>(pr.size()) != P->nprobs_all)
@@ -172,21 +173,36 @@ bfx_status write_tables(bfx_batch_plan* P, cudaStream_t s) {
 
 extern "C" {
 
-BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, const int32_t* h_n,
-                                    int nrhs, const bfx_ir_params* params) {
+BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int count,
+                                           const int32_t* h_n, int nrhs,
+                                           const bfx_ir_params* params,
+                                           const bfx_batch_config* config) {
   if (!out) return BFX_EINVAL;
   *out = nullptr;
   if (mode_pieces(mode) == 0 || count <= 0 || !h_n || nrhs < 1 || nrhs > 16) return BFX_EINVAL;
   for (int s = 0; s < count; ++s)
     if (h_n[s] < 1 || h_n[s] > kBatchMaxN) return BFX_EINVAL;
-  bfx_ir_params ip{50, 1.1102230246251565e-16, -1.0, 0.5, 0, kBatchNb};
+  bfx_ir_params ip{};
+  ip.max_iter = 50;
+  ip.tol = 1.1102230246251565e-16;
+  ip.tol_b = -1.0;
+  ip.stall = 0.5;
   if (params) ip = *params;
   if (ip.max_iter < 0 || ip.max_iter > 200) return BFX_EINVAL;
+  bfx_batch_config cfg{kBatchNb, kBatchBn};
+  if (config) {
+    cfg.nb = config->nb ? config->nb : kBatchNb;
+    cfg.gemm_bn = config->gemm_bn ? config->gemm_bn : kBatchBn;
+  }
+  if ((cfg.nb != 32 && cfg.nb != 64 && cfg.nb != 128) ||
+      (cfg.gemm_bn != 64 && cfg.gemm_bn != 128 && cfg.gemm_bn != 256))
+    return BFX_EINVAL;
   auto* P = new bfx_batch_plan();
   P->mode = mode;
   P->S = count;
   P->nrhs = nrhs;
-  P->nb = kBatchNb;
+  P->nb = cfg.nb;
+  P->bn = cfg.gemm_bn;
   P->max_iter = ip.max_iter;
   P->np = mode_pieces(mode);
   P->n.assign(h_n, h_n + count);
@@ -222,7 +238,7 @@ BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, co
       const int M = n - J0 - std::min(P->nb, n - J0);
       if (M <= 0) continue;
       ++npb;
-      nt += static_cast<int>(ceil_div(M, 128) * ceil_div(M, 256));
+      nt += static_cast<int>(ceil_div(M, 128) * ceil_div(M, P->bn));
     }
     P->step_J0.push_back(J0);
     P->step_ntiles.push_back(nt);
@@ -251,6 +267,18 @@ BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, co
   P->o_probs = take(off, sizeof(GroupProblem) * std::max<int64_t>(1, P->nprobs_all));
   P->total = off;
   *out = P;
+  return BFX_OK;
+}
+
+BFX_API bfx_status bfx_batch_create(bfx_batch* out, bfx_mode mode, int count, const int32_t* h_n,
+                                    int nrhs, const bfx_ir_params* params) {
+  return bfx_batch_create_config(out, mode, count, h_n, nrhs, params, nullptr);
+}
+
+BFX_API bfx_status bfx_batch_get_config(bfx_batch plan, bfx_batch_config* out) {
+  if (!plan || !out) return BFX_EINVAL;
+  out->nb = plan->nb;
+  out->gemm_bn = plan->bn;
   return BFX_OK;
 }
 

@@ -67,7 +67,7 @@ int gemm_bk(bfx_mode mode);  // K-slice width of the mode's kernel
 bfx_status launch_gemm_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                              const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
                              float* C, int64_t ldc, cudaStream_t s);
-bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
+bfx_status launch_gemm_grouped(bfx_mode mode, int bn, int num_tiles, const GroupTile* d_tiles,
                                const GroupProblem* d_probs, const uint16_t* Apack,
                                int64_t a_rows, const uint16_t* Bpack, int64_t b_rows,
                                int64_t planes, int64_t kp, float alpha, float beta,

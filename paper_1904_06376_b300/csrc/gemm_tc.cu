@@ -718,25 +718,48 @@ bfx_status run_tc_grouped(int num_tiles, const GroupTile* d_tiles, const GroupPr
 
 int gemm_bk(bfx_mode mode) { return mode == BFX_X1 ? 64 : 32; }
 
-bfx_status launch_gemm_grouped(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
+// Grouped launches for one UMMA N (tile width of the grouped problems).
+template <int BN>
+bfx_status grouped_bn(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
+                      const GroupProblem* d_probs, const uint16_t* Apack, int64_t a_rows,
+                      const uint16_t* Bpack, int64_t b_rows, int64_t planes, int64_t kp,
+                      float alpha, float beta, cudaStream_t s) {
+  // stages: as many as fit (at most 6); a narrower tile holds more in flight
+  constexpr int S1 = BN == 256 ? 4 : 6, S3 = BN == 256 ? 4 : 6, S6 = BN == 256 ? 3 : (BN == 128 ? 4 : 5);
+  switch (mode) {
+    case BFX_X1:
+      return run_tc_grouped<1, BN, 64, S1>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X3:
+      return run_tc_grouped<3, BN, 32, S3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X6:
+      return run_tc_grouped<6, BN, 32, S6>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    case BFX_X9:
+      return run_tc_grouped<9, BN, 32, S6>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
+    default:
+      return BFX_EINVAL;
+  }
+}
+
+bfx_status launch_gemm_grouped(bfx_mode mode, int bn, int num_tiles, const GroupTile* d_tiles,
                                const GroupProblem* d_probs, const uint16_t* Apack,
                                int64_t a_rows, const uint16_t* Bpack, int64_t b_rows,
                                int64_t planes, int64_t kp, float alpha, float beta,
                                cudaStream_t s) {
   if (num_tiles <= 0) return BFX_OK;
-  switch (mode) {
-    case BFX_X1:
-      return run_tc_grouped<1, 256, 64, 4>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
-                                           b_rows, planes, kp, alpha, beta, s);
-    case BFX_X3:
-      return run_tc_grouped<3, 256, 32, 4>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
-                                           b_rows, planes, kp, alpha, beta, s);
-    case BFX_X6:
-      return run_tc_grouped<6, 256, 32, 3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
-                                           b_rows, planes, kp, alpha, beta, s);
-    case BFX_X9:
-      return run_tc_grouped<9, 256, 32, 3>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
-                                           b_rows, planes, kp, alpha, beta, s);
+  switch (bn) {
+    case 64:
+      return grouped_bn<64>(mode, num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack, b_rows,
+                            planes, kp, alpha, beta, s);
+    case 128:
+      return grouped_bn<128>(mode, num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack, b_rows,
+                             planes, kp, alpha, beta, s);
+    case 256:
+      return grouped_bn<256>(mode, num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack, b_rows,
+                             planes, kp, alpha, beta, s);
     default:
       return BFX_EINVAL;
   }

@@ -581,17 +581,19 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
   while (S_act < S && h_n_desc[S_act] > J0) ++S_act;
   if (S_act == 0) return BFX_OK;
   const int nmax = h_n_desc[0];
-  static bool attrs = false;
-  if (!attrs) {
-    if (cudaFuncSetAttribute(lu_tile_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess ||
-        cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) != cudaSuccess ||
-        cudaFuncSetAttribute(lu_trsm_batched_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             128 * 128 * static_cast<int>(sizeof(float))) != cudaSuccess)
-      return BFX_ECUDA;
-    attrs = true;
-  }
+  // once per process (thread-safe initialisation)
+  static const bool attrs = [] {
+    return cudaFuncSetAttribute(lu_tile_batched_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(TILE_SMEM_MAX)) == cudaSuccess &&
+           cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(lu_trsm_batched_kernel<128>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                128 * 128 * static_cast<int>(sizeof(float))) == cudaSuccess;
+  }();
+  if (!attrs) return BFX_ECUDA;
   for (int j0 = J0; j0 < J0 + nb; j0 += TILE_W) {
     int S_t = 0;
     while (S_t < S_act && h_n_desc[S_t] > j0) ++S_t;

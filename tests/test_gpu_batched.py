@@ -64,3 +64,52 @@ def test_batched_graph_replay_and_rebind(bfx):
     B.solve(A, b, x=x3, status=st2)  # replay of the same graph
     torch.cuda.synchronize()
     assert torch.equal(x1, x2) and torch.equal(x1, x3)
+
+
+@pytest.mark.parametrize("nb,bn", [(32, 64), (32, 256), (64, 128), (128, 64), (128, 256)])
+def test_batched_every_tile_shape(bfx, orc, nb, bn):
+    """Each shape the autotuner may pick solves the batch to FP64-LU accuracy;
+    nb = 32 / 128 also exercise the narrow and wide block columns."""
+    ns = [1, 31, 64, 96, 130, 200, 257, 400, 17]
+    kap = [1e1, 1e2, 1e3, 1e2, 1e4, 1e1, 1e3, 1e2, 1e5]
+    probs = _make(ns, kap, 300)
+    B = bfx.Batch(3, ns, config=(nb, bn))
+    assert B.config == (nb, bn)
+    A, b = B.pack([p.A32 for p in probs], [p.b for p in probs])
+    x, status = B.solve(A, b)
+    torch.cuda.synchronize()
+    conv, iters, info, berr = B.decode_status(status)
+    assert conv.all() and (info == 0).all()
+    for p, xb in zip(probs, B.unpack(x)):
+        xd, _ = orc.dgesv(p.A32, p.b)
+        fe = np.max(np.abs(xb - p.x_true)) / np.max(np.abs(p.x_true))
+        fe64 = np.max(np.abs(xd - p.x_true)) / np.max(np.abs(p.x_true))
+        assert fe <= 10 * fe64 + 1e-15, (p.n, fe, fe64)
+
+
+def test_autotune_picks_the_fastest_and_records_it(bfx):
+    rng = np.random.default_rng(4)
+    ns = rng.integers(32, 257, size=60)
+    probs = [bi.fast_system(int(n), 100.0, 400 + i) for i, n in enumerate(ns)]
+    B0 = bfx.Batch(3, ns)
+    A, b = B0.pack([p.A32 for p in probs], [p.b for p in probs])
+    best, best_ms, table = bfx.batch_autotune(3, ns, A, b, reps=2)
+    assert len(table) == 9
+    ok = [r for r in table if r[3] == 0]
+    assert len(ok) == 9 and all(r[2] > 0 for r in ok)
+    assert best_ms == min(r[2] for r in ok)
+    assert best in [(r[0], r[1]) for r in ok if r[2] == best_ms]
+    # a batch of the same make-up takes the recorded shape
+    Bt = bfx.Batch(3, ns, config="tuned")
+    assert Bt.config == best
+    x, status = Bt.solve(A, b)
+    torch.cuda.synchronize()
+    conv, iters, info, berr = Bt.decode_status(status)
+    assert conv.all()
+
+
+def test_batch_config_rejected(bfx):
+    with pytest.raises(bfx.BfxError):
+        bfx.Batch(3, [10, 20], config=(48, 256))
+    with pytest.raises(bfx.BfxError):
+        bfx.Batch(3, [10, 20], config=(64, 96))

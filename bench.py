@@ -197,11 +197,12 @@ def _fe(x, x_true):
 
 def bench_ir_single(bfx, oracle, bi, dev):
     """Config 3: one n = 4096 system per condition number, bf16x3 trailing
-    updates with escalation, FP64 residual refinement; forward error against
-    x_true beside that of the FP64 oracle LU solve (timed on the host)."""
+    updates with escalation to x6, then GMRES-IR if plain refinement stalls;
+    FP64 residual; forward error against x_true beside that of the FP64
+    oracle LU solve (timed on the host)."""
     import torch
 
-    n, out = 4096, {"n": 4096, "mode": "x3 (escalate to x6)", "solves": []}
+    n, out = 4096, {"n": 4096, "mode": "x3 (escalate to x6, then GMRES-IR)", "solves": []}
     times = []
     for kappa in (1e1, 1e4, 1e8, 1e12):
         P = bi.svd_system(n, kappa, 11)
@@ -220,6 +221,7 @@ def bench_ir_single(bfx, oracle, bi, dev):
         fe, fe64 = _fe(x.cpu().numpy(), P.x_true), _fe(xd, P.x_true)
         out["solves"].append({"kappa": kappa, "ms": dt * 1e3, "status": code, "converged": res["converged"],
                               "iters": res["iters"], "refactorizations": res["refactorizations"],
+                              "gmres_steps": res["gmres_steps"], "arnoldi_steps": res["arnoldi"],
                               "mode_used": res["mode_used"], "berr": res["berr"],
                               "forward_error": fe, "forward_error_fp64_lu": fe64,
                               "ratio_to_fp64": fe / fe64 if fe64 > 0 else None,
@@ -237,8 +239,13 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
     import torch
 
     probs = bi.batched_systems(count, 0)
-    B = bfx.Batch(6, [p.n for p in probs], max_iter=12)
-    A, b = B.pack([p.A32 for p in probs], [p.b for p in probs])
+    ns = [p.n for p in probs]
+    B0 = bfx.Batch(6, ns, max_iter=12)
+    A, b = B0.pack([p.A32 for p in probs], [p.b for p in probs])
+    del B0
+    # the project's autotuner picks the tile shapes for this batch
+    best, best_ms, table = bfx.batch_autotune(6, ns, A, b, reps=2, max_iter=12)
+    B = bfx.Batch(6, ns, max_iter=12, config=best)
     x, st = B.solve(A, b)
     torch.cuda.synchronize()
     reps = 5
@@ -269,6 +276,8 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
             "lu_eff_tflops": flops / (ms * 1e-3) / 1e12, "converged": float(conv.mean()),
             "mean_iters": float(iters.mean()), "by_condition": by,
             "graph": "whole batch captured once, replayed per solve",
+            "tile_shape": {"nb": best[0], "gemm_bn": best[1]},
+            "autotune": [{"nb": r[0], "gemm_bn": r[1], "ms": r[2], "status": r[3]} for r in table],
             "cpu_baseline": {"value": len(sample) / tcpu, "unit": "solves/s", "kind": "oracle",
                              "cores": 1, "sample": f"{len(sample)} of the systems by the oracle's "
                                                    "bf16x6-update LU + FP64 refinement"}}
@@ -432,6 +441,12 @@ def main():
     for md in (1, 3, 6, 9):
         t = time_call(lambda: bfx.gemm_bf16xN(md, A, B, C, workspace=ws))
         variants[f"x{md}_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
+    for md in (3, 6):  # split fused into the tensor-core kernel (no piece workspace)
+        t = time_call(lambda: bfx.gemm_bf16xN_fused(md, A, B, C))
+        variants[f"x{md}_fused_split_{m}x{n}x{k}"] = {
+            "ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12,
+            "bf16_TFLOP/s": md * flops / (t * 1e-3) / 1e12,
+            "vs_separate_split": variants[f"x{md}_{m}x{n}x{k}"]["ms"] / t}
     t = time_call(lambda: bfx.sgemm_simt(A, B, C), reps=2, warm=1)
     variants[f"fp32_simt_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
     ts = (16384, 16384, 256)
@@ -443,6 +458,8 @@ def main():
     for md in (3, 6):
         t = time_call(lambda: bfx.gemm_bf16xN(md, At, Bt, Ct, workspace=wst))
         variants[f"x{md}_16384x16384x256"] = {"ms": t, "TFLOP/s": fl_t / (t * 1e-3) / 1e12}
+        t = time_call(lambda: bfx.gemm_bf16xN_fused(md, At, Bt, Ct))
+        variants[f"x{md}_fused_split_16384x16384x256"] = {"ms": t, "TFLOP/s": fl_t / (t * 1e-3) / 1e12}
     t = time_call(lambda: bfx.sgemm_simt(At, Bt, Ct), reps=3, warm=1)
     variants["fp32_simt_16384x16384x256"] = {"ms": t, "TFLOP/s": fl_t / (t * 1e-3) / 1e12}
     del At, Bt, Ct, wst

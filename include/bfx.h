@@ -245,7 +245,7 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
  * bytes (h_params NULL: the defaults), 256-byte aligned; with gmres != 0 it
  * includes the Krylov basis, (gmres_m + 1) n nrhs doubles, and the
  * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles. */
-#define BFX_GMRES_MAX_M 2048
+#define BFX_GMRES_MAX_M 4096
 typedef struct bfx_ir_params {
   int max_iter;
   double tol;
@@ -366,7 +366,9 @@ BFX_API void bfx_batch_destroy(bfx_batch plan);
  * and the bfx_solve_ir workspace); admitted requests run concurrently and
  * their kernels overlap on the device.  Each request is solved exactly as
  * bfx_solve_ir would solve it alone (same kernels, same order of operations),
- * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb, gmres, 0, 1e-10}.
+ * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb, gmres,
+ * min(n, 1024), 1e-10} (the Krylov length capped so that one large request's
+ * reservation does not crowd the pool).
  * The caller's host buffers h_A (n x n), h_b (n x nrhs) must stay valid and
  * h_x (n x nrhs, output) writable until the request completes.
  * submit: BFX_ENOMEM if the request can never fit the budget; never blocks.

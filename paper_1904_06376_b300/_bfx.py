@@ -241,7 +241,7 @@ def dot_bf16xN(mode: int, x: torch.Tensor, y: torch.Tensor, out: torch.Tensor = 
     return out
 
 
-GMRES_MAX_M = 2048
+GMRES_MAX_M = 4096
 
 
 class IrParams(ctypes.Structure):

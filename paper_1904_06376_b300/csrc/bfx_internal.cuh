@@ -141,6 +141,23 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// FP32 -> FP64, exact, on the integer pipe for zeros and normal values (the
+// exponent rebiased by 1023 - 127 = 896, the significand shifted into place);
+// subnormals, Inf and NaN take the hardware conversion.  On B300 the
+// hardware conversion shares the FP64 pipe, whose throughput bounds the
+// FP64 refinement kernels that widen every FP32 matrix element they read.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu, mant = u & 0x7FFFFFu;
+  const uint64_t sign = static_cast<uint64_t>(u & 0x80000000u) << 32;
+  if ((e == 0u && mant != 0u) || e == 0xFFu) return static_cast<double>(f);
+  const uint64_t d = e == 0u ? sign
+                             : (sign | (static_cast<uint64_t>(e + 896u) << 52) |
+                                (static_cast<uint64_t>(mant) << 29));
+  return __longlong_as_double(static_cast<long long>(d));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // ---- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)

@@ -89,7 +89,7 @@ __global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
   if (row >= n) return;
   const float* a = A + row * lda;
   double s = 0.0;
-  for (int l = lane; l < n; l += 32) s += fabs(static_cast<double>(a[l]));
+  for (int l = lane; l < n; l += 32) s += fabs(widen(a[l]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
   if (lane == 0) atomic_max_nonneg(out, s);
@@ -113,7 +113,7 @@ __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = 0.0;
   for (int l = lane; l < n; l += 32) {
-    const double al = static_cast<double>(a[l]);
+    const double al = widen(a[l]);
     const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = fma(al, xl[c], acc[c]);
@@ -186,6 +186,41 @@ __global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __rest
                            Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB);
 }
 
+// G_b = Dinv_b F[b, p] for every row block b with a predecessor p in solve
+// order (p = b - 1 forward, b + 1 backward), FP64, once per factorisation:
+// the triangular solve then needs only one 64 x 64 product between the
+// arrival of y_p and the publication of y_b (y_b = z_b - G_b y_p, z_b the
+// inverse applied to everything else).  CTA b, a thread per 16 outputs.
+template <bool LOWER>
+__global__ void __launch_bounds__(256)
+    ir_chain_kernel(const float* __restrict__ F, int64_t ldf, int n,
+                    const double* __restrict__ Dinv, double* __restrict__ G) {
+  __shared__ double Ds[TB][TB];  // rows read by broadcast, Fs rows by consecutive lanes:
+  __shared__ float Fs[TB][TB];   // no padding needed (48 KB in all)
+  const int nblk = (n + TB - 1) / TB;
+  const int b = LOWER ? blockIdx.x + 1 : blockIdx.x;  // blocks with a predecessor
+  const int p = LOWER ? b - 1 : b + 1;
+  if (p < 0 || p >= nblk) return;
+  const int b0 = b * TB, bs = min(TB, n - b0), p0 = p * TB, ps = min(TB, n - p0);
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, l = e % TB;
+    Ds[i][l] = D[e];
+    Fs[i][l] = (i < bs && l < ps) ? F[static_cast<int64_t>(b0 + i) * ldf + p0 + l] : 0.0f;
+  }
+  __syncthreads();
+  double* g = G + static_cast<int64_t>(b) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, j = e % TB;
+    double s0 = 0.0, s1 = 0.0;
+    for (int l = 0; l < TB; l += 2) {
+      s0 = fma(Ds[i][l], static_cast<double>(Fs[l][j]), s0);
+      s1 = fma(Ds[i][l + 1], static_cast<double>(Fs[l + 1][j]), s1);
+    }
+    g[e] = s0 + s1;
+  }
+}
+
 // Triangular solve L y = v (unit lower, forward) or U y = v (upper, backward)
 // with the FP32 factors in FP64 arithmetic, in one launch without a grid-wide
 // barrier.  Row blocks of 64; right-hand sides in groups of up to 4 columns.
@@ -227,8 +262,8 @@ __device__ __forceinline__ void trsv_tile_product(const T* Tm, const double (*x)
   double s0 = 0.0, s1 = 0.0;
 #pragma unroll 4
   for (int l = 0; l < len; l += 2) {
-    s0 = fma(static_cast<double>(row[l]), x[l0 + l][c], s0);
-    s1 = fma(static_cast<double>(row[l + 1]), x[l0 + l + 1][c], s1);
+    s0 = fma(widen(row[l]), x[l0 + l][c], s0);
+    s1 = fma(widen(row[l + 1]), x[l0 + l + 1][c], s1);
   }
   double sum = s0 + s1;
   // items == 256 whenever Q > 1, so every lane of the warp takes part
@@ -249,13 +284,16 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 template <bool LOWER>
 __global__ void __launch_bounds__(TRSV_THREADS)
     ir_trsv_kernel(const float* __restrict__ F, int64_t ldf, int n,
-                   const double* __restrict__ Dinv, const double* __restrict__ v,
-                   double* __restrict__ y, int R, int* __restrict__ sync, int* __restrict__ err) {
+                   const double* __restrict__ Dinv, const double* __restrict__ Gm,
+                   const double* __restrict__ v, double* __restrict__ y, int R,
+                   int* __restrict__ sync, int* __restrict__ err) {
   extern __shared__ __align__(16) uint8_t trsv_smem[];
   double* Ds = reinterpret_cast<double*>(trsv_smem);                       // [TB][TB + 1]
-  float* Fs = reinterpret_cast<float*>(Ds + TB * (TB + 1));                // 2 x [TB][TB + 1]
+  double* Gs = Ds + TB * (TB + 1);                                          // [TB][TB + 1]
+  float* Fs = reinterpret_cast<float*>(Gs + TB * (TB + 1));                // 2 x [TB][TB + 1]
   auto acc = reinterpret_cast<double (*)[TRSV_CG + 1]>(Fs + 2 * TB * (TB + 1));  // [TB][CG + 1]
   auto xs = acc + TB;                                                       // [TB][CG + 1]
+  auto zs = xs + TB;                                                        // [TB][CG + 1]
   __shared__ int s_ticket, s_fail;
   const int t = threadIdx.x;
   const int nblk = (n + TB - 1) / TB;
@@ -281,21 +319,25 @@ __global__ void __launch_bounds__(TRSV_THREADS)
       cp_async4(dst + i * (TB + 1) + l, ok ? F + static_cast<int64_t>(b0 + i) * ldf + k0 + l : F, ok);
     }
   };
-  if (step > 0) prefetch(0);
+  // tiles of all predecessors but the last (that one goes through G_b)
+  const int ntile = step > 0 ? step - 1 : 0;
+  if (ntile > 0) prefetch(0);
   cp_async_commit();
-  // the block's inverse (independent of the other blocks), and acc = v_b
+  // the block's inverse and chain matrix (independent of the other blocks), acc = v_b
   const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
-  for (int e = t; e < TB * TB; e += TRSV_THREADS) Ds[(e / TB) * (TB + 1) + e % TB] = D[e];
+  const double* Gb = Gm + static_cast<int64_t>(b) * TB * TB;
+  for (int e = t; e < TB * TB; e += TRSV_THREADS) {
+    Ds[(e / TB) * (TB + 1) + e % TB] = D[e];
+    if (step > 0) Gs[(e / TB) * (TB + 1) + e % TB] = Gb[e];
+  }
   for (int e = t; e < TB * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
     acc[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
   }
-  for (int s = 0; s < step; ++s) {
-    if (s + 1 < step) prefetch(s + 1);
-    cp_async_commit();
-    const int k = LOWER ? s : nblk - 1 - s;
+  // warp 0: wait until y_k is published, then fetch it into xs
+  auto fetch = [&](int k) {
     const int k0 = k * TB, ks = min(TB, n - k0);
-    if (t < 32) {  // warp 0: wait until y_k is published, then fetch it
+    if (t < 32) {
       if (t == 0 && !s_fail) {
         const int* f = ready + k * G + grp;
         if (ld_acquire_gpu(f) == 0) {
@@ -316,16 +358,32 @@ __global__ void __launch_bounds__(TRSV_THREADS)
         xs[i][c] = i < ks ? __ldcg(y + static_cast<int64_t>(k0 + i) * R + c0 + c) : 0.0;
       }
     }
+  };
+  for (int s = 0; s < ntile; ++s) {
+    if (s + 1 < ntile) prefetch(s + 1);
+    cp_async_commit();
+    fetch(LOWER ? s : nblk - 1 - s);
     cp_async_wait1();  // this thread's copies of tile s have landed
     __syncthreads();
     trsv_tile_product<float, TB + 1>(Fs + (s & 1) * TB * (TB + 1), xs, acc, cg, true);
     __syncthreads();
   }
-  // y_b = Dinv_b acc (rows past a partial block come out 0: acc and the
+  // z_b = Dinv_b acc (rows past a partial block come out 0: acc and the
   // inverse's padding are zero / identity there)
   __syncthreads();
-  trsv_tile_product<double, TB + 1>(Ds, acc, xs, cg, false);
+  trsv_tile_product<double, TB + 1>(Ds, acc, step > 0 ? zs : xs, cg, false);
   __syncthreads();
+  if (step > 0) {  // y_b = z_b - G_b y_p, p the last predecessor
+    fetch(LOWER ? b - 1 : b + 1);
+    __syncthreads();
+    trsv_tile_product<double, TB + 1>(Gs, xs, zs, cg, true);
+    __syncthreads();
+    for (int e = t; e < TB * cg; e += TRSV_THREADS) {
+      const int i = e / cg, c = e - i * cg;
+      xs[i][c] = zs[i][c];
+    }
+    __syncthreads();
+  }
   for (int e = t; e < bs * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
     y[static_cast<int64_t>(b0 + i) * R + c0 + c] = xs[i][c];
@@ -337,8 +395,8 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   }
 }
 
-constexpr size_t kTrsvSmem = sizeof(double) * TB * (TB + 1) + 2 * sizeof(float) * TB * (TB + 1) +
-                             2 * sizeof(double) * TB * (TRSV_CG + 1);
+constexpr size_t kTrsvSmem = 2 * sizeof(double) * TB * (TB + 1) + 2 * sizeof(float) * TB * (TB + 1) +
+                             3 * sizeof(double) * TB * (TRSV_CG + 1);
 
 // x += d on active columns; dn[c] = max|d|, xn[c] = max|x| (must start at 0).
 __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
@@ -614,7 +672,7 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_prepare_kernel(const BatchIr*
   double am = 0.0;
   for (int i = wid; i < q.n; i += BIR_THREADS / 32) {
     double sum = 0.0;
-    for (int l = lane; l < q.n; l += 32) sum += fabs(static_cast<double>(q.A[static_cast<int64_t>(i) * q.n + l]));
+    for (int l = lane; l < q.n; l += 32) sum += fabs(widen(q.A[static_cast<int64_t>(i) * q.n + l]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
     am = fmax(am, sum);
@@ -708,8 +766,8 @@ __device__ void bir_solve_body(const BatchIr& q) {
         const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
         double s0 = 0.0, s1 = 0.0;
         for (int l = 0; l < bs; l += 2) {
-          s0 = fma(static_cast<double>(fr[l]), y[l][c], s0);
-          if (l + 1 < bs) s1 = fma(static_cast<double>(fr[l + 1]), y[l + 1][c], s1);
+          s0 = fma(widen(fr[l]), y[l][c], s0);
+          if (l + 1 < bs) s1 = fma(widen(fr[l + 1]), y[l + 1][c], s1);
         }
         q.d[static_cast<int64_t>(i) * R + c] -= s0 + s1;
       }
@@ -743,7 +801,7 @@ __device__ double bir_residual_body(const BatchIr& q, double* red, bool want_max
     const float* a = q.A + static_cast<int64_t>(i) * n;
     for (int c = 0; c < R; ++c) {
       double sum = 0.0;
-      for (int l = lane; l < n; l += 32) sum = fma(static_cast<double>(a[l]), q.x[static_cast<int64_t>(l) * R + c], sum);
+      for (int l = lane; l < n; l += 32) sum = fma(widen(a[l]), q.x[static_cast<int64_t>(l) * R + c], sum);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
       const double v = q.b[static_cast<int64_t>(i) * R + c] - sum;
@@ -840,6 +898,8 @@ struct IrWs {
   double* norms;  // [0] anorm, then per column: bn, dn, xn, rn
   double* Linv;   // inverses of the 64 x 64 diagonal blocks of L, then of U
   double* Uinv;
+  double* Lg;     // chain matrices G_b = Linv_b L[b, b-1] and Uinv_b U[b, b+1]
+  double* Ug;
   int32_t* tsync; // triangular-solve tickets and ready flags, both triangles
   void* luws;
   size_t luws_bytes;
@@ -878,6 +938,8 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   const int64_t nblk = (n + TB - 1) / TB;
   w.Linv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.Uinv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
+  w.Lg = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
+  w.Ug = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.tsync = reinterpret_cast<int32_t*>(
       take(sizeof(int32_t) * 2 * (1 + nblk * ceil_div(nrhs, TRSV_CG))));
   size_t lub = 0;
@@ -932,10 +994,10 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
       cudaSuccess)
     return BFX_ECUDA;
   ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs);
-  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.d, w.r, nrhs,
-                                                             w.tsync, err);
+  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.r,
+                                                             nrhs, w.tsync, err);
   ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(
-      w.LU, n, N, w.Uinv, w.r, w.d, nrhs, w.tsync + 1 + static_cast<size_t>(nblk) * G, err);
+      w.LU, n, N, w.Uinv, w.Ug, w.r, w.d, nrhs, w.tsync + 1 + static_cast<size_t>(nblk) * G, err);
   return last_launch_status();
 }
 
@@ -1141,6 +1203,10 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
       ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
       ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
+      if (nblk > 1) {
+        ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
+        ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
+      }
       const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
       ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
     }

@@ -113,7 +113,10 @@ struct bfx_server_impl {
 
 namespace {
 
-bfx_ir_params request_params(const bfx_server_config& cfg) {
+// Every request is solved with these parameters; the Krylov length is capped
+// at 1024 so that a large request's reservation (the basis and Hessenberg
+// matrices grow with gmres_m x n x nrhs) does not crowd the pool.
+bfx_ir_params request_params(const bfx_server_config& cfg, int64_t n, int64_t nrhs) {
   bfx_ir_params p{};
   p.max_iter = 50;
   p.tol = 1.1102230246251565e-16;
@@ -121,8 +124,8 @@ bfx_ir_params request_params(const bfx_server_config& cfg) {
   p.stall = 0.5;
   p.escalate = cfg.escalate;
   p.nb = cfg.nb;
-  p.gmres = cfg.gmres;
-  p.gmres_m = 0;
+  p.gmres = nrhs <= 16 ? cfg.gmres : 0;  // one Krylov basis per right-hand side, at most 16
+  p.gmres_m = static_cast<int>(std::min<int64_t>(n, 1024));
   p.gmres_tol = 1e-10;
   return p;
 }
@@ -130,7 +133,7 @@ bfx_ir_params request_params(const bfx_server_config& cfg) {
 size_t request_bytes(const bfx_server_config& cfg, int64_t n, int64_t nrhs) {
   const size_t a = sizeof(float) * n * n;
   const size_t v = sizeof(double) * n * nrhs;
-  const bfx_ir_params p = request_params(cfg);
+  const bfx_ir_params p = request_params(cfg, n, nrhs);
   const size_t ws = bfx_solve_ir_workspace_size(cfg.mode, n, nrhs, &p);
   return (a + 255) / 256 * 256 + 2 * ((v + 255) / 256 * 256) + ws + 256;
 }
@@ -177,7 +180,7 @@ void worker_main(bfx_server_impl* S) {
     if (cudaMemcpyAsync(dA, r->hA, sizeof(float) * n * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(db, r->hb, sizeof(double) * n * R, cudaMemcpyHostToDevice, st) != cudaSuccess)
       status = BFX_ECUDA;
-    const bfx_ir_params p = request_params(S->cfg);
+    const bfx_ir_params p = request_params(S->cfg, n, R);
     bfx_ir_result ir{};
     if (status == BFX_OK)
       status = bfx_solve_ir(S->cfg.mode, n, R, dA, n, db, R, dx, R, &p, &ir, ws, wsb, st);

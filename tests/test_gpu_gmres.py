@@ -109,7 +109,7 @@ def test_gmres_diag_dominant_table(bfx, orc):
 def test_gmres_argument_checks(bfx):
     A = torch.eye(4, device="cuda")
     b = torch.ones((4, 1), dtype=torch.float64, device="cuda")
-    for kw in ({"gmres": 3}, {"gmres_m": 2049}, {"gmres": -1}):
+    for kw in ({"gmres": 3}, {"gmres_m": 4097}, {"gmres": -1}):
         with pytest.raises(bfx.BfxError) as e:
             bfx.solve_ir(3, A, b, **kw)
         assert e.value.code == 1

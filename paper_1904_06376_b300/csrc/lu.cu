@@ -211,11 +211,215 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
   }
 }
 
+// The same tile factorisation with the tile in registers, for tiles of at
+// most PANEL_THREADS * RPT rows: thread t holds rows j0 + t + q*PANEL_THREADS
+// (q < RPT), all 8 columns.  Per column two barriers: one after every warp
+// has posted its best candidate together with that row's values (so the
+// pivot row is known as soon as the argmax is), one after warp 0 has chosen;
+// the shared rows alternate between two buffers by column parity, so a
+// thread still updating with column jj's pivot row never sees column jj+1's.
+// Every element sees the same operations as in tile_body (same pivot rule,
+// __fdiv_rn, fmaf order).
+template <int RPT>
+__device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t lda, int n, int J0,
+                                               int JB, int j0, int jw,
+                                               int32_t* __restrict__ ipiv,
+                                               int32_t* __restrict__ info) {
+  constexpr int NW = PANEL_THREADS / 32;
+  __shared__ ArgMax wbest[2][NW];
+  __shared__ float wrow[2][NW][TILE_W];   // each warp's candidate row
+  __shared__ float rowj[2][TILE_W];       // row j before the swap
+  __shared__ float rowp[2][TILE_W];       // the pivot row (row j after the swap)
+  __shared__ int s_piv[2];
+  __shared__ int s_pivs[TILE_W];
+  __shared__ int s_rows[2 * TILE_W], s_src[2 * TILE_W], s_ns;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  float v[RPT][TILE_W];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = j0 + t + q * PANEL_THREADS;
+#pragma unroll
+    for (int c = 0; c < TILE_W; ++c)
+      v[q][c] = (r < n && c < jw) ? A[static_cast<int64_t>(r) * lda + j0 + c] : 0.0f;
+  }
+#pragma unroll
+  for (int jj = 0; jj < TILE_W; ++jj) {  // unrolled: register indices stay static
+    if (jj >= jw) break;
+    const int j = j0 + jj, bf = jj & 1;
+    // ---- pivot search over rows j..n-1; row j's owner posts row j
+    ArgMax best{-1.0f, n};
+    int bq = -1;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = j0 + t + q * PANEL_THREADS;
+      if (r == j) {
+#pragma unroll
+        for (int c = 0; c < TILE_W; ++c) rowj[bf][c] = v[q][c];
+      }
+      if (r >= j && r < n) {
+        float a = fabsf(v[q][jj]);
+        if (a != a) a = -1.0f;  // NaN below the diagonal is never chosen
+        const ArgMax cand{a, r};
+        const ArgMax nb = better(best, cand);
+        if (nb.i != best.i) bq = q;
+        best = nb;
+      }
+    }
+    const int own = best.i;  // this thread's candidate row
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, best.v, o), __shfl_xor_sync(0xFFFFFFFFu, best.i, o)};
+      best = better(best, other);
+    }
+    if (lane == 0) wbest[bf][wid] = best;
+    if (bq >= 0 && own == best.i) {  // the lane holding the warp's winner posts its row
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (q == bq) {
+#pragma unroll
+          for (int c = 0; c < TILE_W; ++c) wrow[bf][wid][c] = v[q][c];
+        }
+    }
+    __syncthreads();
+    if (wid == 0) {
+      ArgMax b = lane < NW ? wbest[bf][lane] : ArgMax{-1.0f, n};
+      int w = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, b.v, o), __shfl_xor_sync(0xFFFFFFFFu, b.i, o)};
+        const int ow = __shfl_xor_sync(0xFFFFFFFFu, w, o);
+        const ArgMax nb = better(b, other);
+        if (nb.i != b.i) w = ow;
+        b = nb;
+      }
+      // lane 0: the winning warp is w (b.i < n), else no candidate
+      const float d = rowj[bf][jj];
+      const bool keep = (d != d || b.i >= n);  // a NaN on the diagonal stays
+      const int p = keep ? j : b.i;
+      if (lane < TILE_W) rowp[bf][lane] = keep ? rowj[bf][lane] : wrow[bf][w][lane];
+      if (lane == 0) {
+        s_piv[bf] = p;
+        s_pivs[jj] = p;
+        ipiv[j] = p;
+      }
+    }
+    __syncthreads();
+    const int p = s_piv[bf];
+    // ---- swap rows j and p (tile part)
+    if (p != j) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = j0 + t + q * PANEL_THREADS;
+        if (r == j) {
+#pragma unroll
+          for (int c = 0; c < TILE_W; ++c) v[q][c] = rowp[bf][c];
+        } else if (r == p) {
+#pragma unroll
+          for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
+        }
+      }
+    }
+    const float piv = rowp[bf][jj];
+    if (piv == 0.0f) {
+      if (t == 0 && *info == 0) *info = j + 1;
+      continue;
+    }
+    // ---- scale the column, rank-1 update of the rest of the tile
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = j0 + t + q * PANEL_THREADS;
+      if (r > j && r < n) {
+        const float l = __fdiv_rn(v[q][jj], piv);
+        v[q][jj] = l;
+#pragma unroll
+        for (int c = 0; c < TILE_W; ++c)
+          if (c > jj && c < jw) v[q][c] = fmaf(-l, rowp[bf][c], v[q][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = j0 + t + q * PANEL_THREADS;
+    if (r < n) {
+#pragma unroll
+      for (int c = 0; c < TILE_W; ++c)
+        if (c < jw) A[static_cast<int64_t>(r) * lda + j0 + c] = v[q][c];
+    }
+  }
+  // ---- the tile's row swaps on the block-column columns outside the tile
+  // (net effect of the sequential swaps, as in tile_body)
+  __syncthreads();
+  if (t == 0) {
+    int ns = 0;
+    for (int jj = 0; jj < jw; ++jj) {
+      const int rr[2] = {j0 + jj, s_pivs[jj]};
+      for (int q = 0; q < 2; ++q) {
+        bool seen = false;
+        for (int k = 0; k < ns; ++k) seen = seen || s_rows[k] == rr[q];
+        if (!seen) {
+          s_rows[ns] = rr[q];
+          s_src[ns] = rr[q];
+          ++ns;
+        }
+      }
+      int a = 0, b = 0;
+      for (int k = 0; k < ns; ++k) {
+        if (s_rows[k] == j0 + jj) a = k;
+        if (s_rows[k] == s_pivs[jj]) b = k;
+      }
+      const int tmp = s_src[a];
+      s_src[a] = s_src[b];
+      s_src[b] = tmp;
+    }
+    s_ns = ns;
+  }
+  __syncthreads();
+  const int nout = JB - jw;
+  if (nout > 0) {
+    const int ns = s_ns;
+    for (int k = t; k < nout; k += PANEL_THREADS) {
+      const int c = (J0 + k < j0) ? J0 + k : J0 + k + jw;
+      float w[2 * TILE_W];
+#pragma unroll
+      for (int q = 0; q < 2 * TILE_W; ++q)
+        w[q] = q < ns ? A[static_cast<int64_t>(s_src[q]) * lda + c] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 2 * TILE_W; ++q)
+        if (q < ns) A[static_cast<int64_t>(s_rows[q]) * lda + c] = w[q];
+    }
+    __syncthreads();
+  }
+  // ---- tile rows of the block columns right of the tile: forward substitution
+  for (int c = j0 + jw + t; c < J0 + JB; c += PANEL_THREADS) {
+    float* col = A + static_cast<int64_t>(j0) * lda + c;
+    float x[TILE_W];
+#pragma unroll
+    for (int i = 0; i < TILE_W; ++i) x[i] = i < jw ? col[static_cast<int64_t>(i) * lda] : 0.0f;
+#pragma unroll
+    for (int i = 1; i < TILE_W; ++i) {
+      if (i >= jw) break;
+      float acc = x[i];
+#pragma unroll
+      for (int l = 0; l < i; ++l)
+        acc = fmaf(-A[static_cast<int64_t>(j0 + i) * lda + j0 + l], x[l], acc);
+      x[i] = acc;
+      col[static_cast<int64_t>(i) * lda] = acc;
+    }
+  }
+}
+
 template <bool use_smem>
 __global__ void __launch_bounds__(PANEL_THREADS)
     lu_tile_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
                    int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
   tile_body<use_smem>(A, lda, n, J0, JB, j0, jw, ipiv, info);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_tile_regs_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB, int j0, int jw,
+                        int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+  tile_body_regs<RPT>(A, lda, n, J0, JB, j0, jw, ipiv, info);
 }
 
 // Rows below the tile, block columns right of it: a <- fma(-l_rk, u_kc, a)
@@ -416,6 +620,16 @@ __global__ void __launch_bounds__(PANEL_THREADS)
   tile_body<use_smem>(b.A, b.n, b.n, J0, JB, j0, jw, b.ipiv, b.info);
 }
 
+template <int RPT>
+__global__ void __launch_bounds__(PANEL_THREADS)
+    lu_tile_regs_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int j0) {
+  const BatchLu b = sys[blockIdx.x];
+  const int JB = min(nb, b.n - J0);
+  const int jw = min(TILE_W, J0 + JB - j0);
+  if (JB <= 0 || jw <= 0) return;
+  tile_body_regs<RPT>(b.A, b.n, b.n, J0, JB, j0, jw, b.ipiv, b.info);
+}
+
 __global__ void lu_tile_update_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0,
                                               int j0) {
   const BatchLu b = sys[blockIdx.y];
@@ -530,8 +744,17 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     const int jb = (N - j0 < nb) ? N - j0 : nb;
     for (int t0 = j0; t0 < j0 + jb; t0 += TILE_W) {
       const int tw = std::min(TILE_W, j0 + jb - t0);
-      const size_t tsm = static_cast<size_t>(N - t0) * TILE_W * sizeof(float);
-      if (tsm <= TILE_SMEM_MAX)
+      const int rows = N - t0;
+      const size_t tsm = static_cast<size_t>(rows) * TILE_W * sizeof(float);
+      if (rows <= PANEL_THREADS)
+        lu_tile_regs_kernel<1><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
+      else if (rows <= 2 * PANEL_THREADS)
+        lu_tile_regs_kernel<2><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
+      else if (rows <= 4 * PANEL_THREADS)
+        lu_tile_regs_kernel<4><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
+      else if (rows <= 8 * PANEL_THREADS)
+        lu_tile_regs_kernel<8><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
+      else if (tsm <= TILE_SMEM_MAX)
         lu_tile_kernel<true><<<1, PANEL_THREADS, tsm, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
       else
         lu_tile_kernel<false><<<1, PANEL_THREADS, 0, s>>>(A, lda, N, j0, jb, t0, tw, ipiv, info);
@@ -598,8 +821,13 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
     int S_t = 0;
     while (S_t < S_act && h_n_desc[S_t] > j0) ++S_t;
     if (S_t == 0) break;
-    const size_t tsm = static_cast<size_t>(nmax - j0) * TILE_W * sizeof(float);
-    if (tsm <= TILE_SMEM_MAX)
+    const int rows = nmax - j0;
+    const size_t tsm = static_cast<size_t>(rows) * TILE_W * sizeof(float);
+    if (rows <= PANEL_THREADS)
+      lu_tile_regs_batched_kernel<1><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
+    else if (rows <= 2 * PANEL_THREADS)
+      lu_tile_regs_batched_kernel<2><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
+    else if (tsm <= TILE_SMEM_MAX)
       lu_tile_batched_kernel<true><<<S_t, PANEL_THREADS, tsm, s>>>(d_sys, nb, J0, j0);
     else
       lu_tile_batched_kernel<false><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);

@@ -23,7 +23,7 @@ def _lu_gpu(bfx, mode, A, nb):
     return Ad.cpu().numpy(), ipiv.cpu().numpy()[: A.shape[0]], int(info.item())
 
 
-@pytest.mark.parametrize("n,nb", [(1, 64), (50, 16), (200, 64), (333, 32), (515, 128)])
+@pytest.mark.parametrize("n,nb", [(1, 64), (50, 16), (200, 64), (333, 32), (515, 128), (2100, 64)])
 def test_lu_fp32_bit_exact(bfx, orc, n, nb):
     """The FP32 path performs the oracle's FP32 LU operation for operation."""
     A = bi.uniform_pm1((n, n), n)

@@ -288,8 +288,11 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
  * (n_s x n_s row-major, FP32); b and x at offset sum_{t<s} n_t nrhs (n_s x
  * nrhs row-major, FP64).
  * bfx_batch_create plans the batch (host memory only); params may be NULL
- * (as bfx_solve_ir; escalate and gmres are ignored: a batch keeps its mode
- * and refines by plain refinement).
+ * (as bfx_solve_ir; escalate is ignored: a batch keeps its mode).  With
+ * gmres != 0 (the default) systems whose plain refinement stops unconverged
+ * continue by GMRES-IR, each in one CTA of a persistent grid that takes them
+ * from a queue: restarted GMRES(min(n, 256)), at most 20 refinement steps,
+ * inner tolerance 1e-10 (d_status.gmres_steps counts its steps).
  * bfx_batch_solve enqueues the graph on `stream` and returns without
  * waiting; d_status (device, one entry per system, caller order) is written
  * at the end: converged, corrections applied, LAPACK info, backward error.
@@ -300,9 +303,9 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
  * BFX_EUNSUPPORTED (device), BFX_ECUDA. */
 typedef struct bfx_batch_status {
   int32_t converged;
-  int32_t iters;
+  int32_t iters;       /* refinement steps, plain and GMRES-IR */
   int32_t info;
-  int32_t pad;
+  int32_t gmres_steps; /* of which GMRES-IR refinement steps */
   double berr;
 } bfx_batch_status;
 typedef struct bfx_batch_plan* bfx_batch;

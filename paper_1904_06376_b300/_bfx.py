@@ -322,13 +322,13 @@ class TuneEntry(ctypes.Structure):
     _fields_ = [("config", BatchConfig), ("ms", ctypes.c_float), ("status", ctypes.c_int32)]
 
 
-def _batch_params(max_iter, tol, tol_b, stall):
-    return IrParams(max_iter, tol, tol_b, stall, 0, 64, 0, 0, 0.0)
+def _batch_params(max_iter, tol, tol_b, stall, gmres=1):
+    return IrParams(max_iter, tol, tol_b, stall, 0, 64, int(gmres), 0, 0.0)
 
 
 def batch_autotune(mode: int, ns, A, b, nrhs: int = 1, x=None, status=None, reps: int = 3,
                    max_iter: int = 20, tol: float = 2.0 ** -53, tol_b: float = -1.0,
-                   stall: float = 0.5, stream=None):
+                   stall: float = 0.5, gmres: int = 1, stream=None):
     """Time the batch (packed A, b on the device) under every tile shape and
     return ((nb, gemm_bn) of the fastest, its median ms, [(nb, gemm_bn, ms,
     status), ...])."""
@@ -339,7 +339,7 @@ def batch_autotune(mode: int, ns, A, b, nrhs: int = 1, x=None, status=None, reps
         x = torch.empty(int((ns.astype(np.int64) * nrhs).sum()), dtype=torch.float64, device=A.device)
     if status is None:
         status = torch.zeros(3 * int(ns.size), dtype=torch.float64, device=A.device)
-    p = _batch_params(max_iter, tol, tol_b, stall)
+    p = _batch_params(max_iter, tol, tol_b, stall, gmres)
     best = BatchConfig()
     best_ms = ctypes.c_float()
     table = (TuneEntry * 9)()
@@ -362,14 +362,14 @@ class Batch:
     autotuner recorded for batches like this one; default if none)."""
 
     def __init__(self, mode: int, ns, nrhs: int = 1, max_iter: int = 20, tol: float = 2.0 ** -53,
-                 tol_b: float = -1.0, stall: float = 0.5, config=None):
+                 tol_b: float = -1.0, stall: float = 0.5, config=None, gmres: int = 1):
         import numpy as np
 
         self.ns = np.asarray(ns, dtype=np.int32)
         self.nrhs = nrhs
         self.mode = mode
         h = ctypes.c_void_p()
-        p = _batch_params(max_iter, tol, tol_b, stall)
+        p = _batch_params(max_iter, tol, tol_b, stall, gmres)
         cfg = None
         if config == "tuned":
             c = BatchConfig()
@@ -431,6 +431,14 @@ class Batch:
         ints = raw[:, :16].copy().view(np.int32).reshape(-1, 4)
         berr = raw[:, 16:].copy().view(np.float64).ravel()
         return ints[:, 0], ints[:, 1], ints[:, 2], berr
+
+    @staticmethod
+    def gmres_steps(status):
+        """GMRES-IR refinement steps per system (0 if plain refinement converged)."""
+        import numpy as np
+
+        raw = status.cpu().numpy().view(np.uint8).reshape(-1, 24)
+        return raw[:, :16].copy().view(np.int32).reshape(-1, 4)[:, 3]
 
 
 class ServerConfig(ctypes.Structure):

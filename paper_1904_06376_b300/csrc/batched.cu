@@ -19,6 +19,10 @@ constexpr int kBatchNb = 64;      // default block-column width of the batched L
 constexpr int kBatchBn = 256;     // default tile width of the grouped trailing updates
 constexpr int kBatchMaxN = 1024;  // largest system of a batch
 constexpr int kSolveTB = 64;      // diagonal-block size of the refinement solves
+constexpr int kGmresM = 256;      // Krylov length of the batched GMRES-IR (capped at n)
+constexpr int kGmresOuter = 20;   // its refinement steps at most
+constexpr double kGmresTau = 1e-10;
+constexpr size_t kGmresSlotBudget = size_t(1) << 30;  // Krylov memory of all slots, at most
 
 size_t take(size_t& off, size_t bytes) {
   const size_t o = off;
@@ -34,6 +38,8 @@ using namespace bfx;
 struct bfx_batch_plan {
   bfx_mode mode;
   int S, nrhs, nb, bn, max_iter, np, nmax;
+  int gmres, gm_slots;
+  int64_t gm_slot_doubles;
   BatchIrParams p;
   std::vector<int> n;       // caller order
   std::vector<int> sorted;  // sorted[k] = caller index, n descending
@@ -43,7 +49,7 @@ struct bfx_batch_plan {
   int64_t kp = 0, slot_rows = 0;
   // workspace layout (byte offsets)
   size_t o_LU, o_ipiv, o_info, o_perm, o_r, o_d, o_Linv, o_Uinv, o_state, o_packA, o_packB;
-  size_t o_lu_tab, o_ir_tab, o_tiles, o_probs, total;
+  size_t o_lu_tab, o_ir_tab, o_tiles, o_probs, o_gm_queue, o_gm_slots, total;
   std::vector<int> step_J0, step_ntiles, step_nprobs;
   std::vector<size_t> step_tile_off, step_prob_off;  // element offsets into the tables
   int64_t ntiles_all = 0, nprobs_all = 0;
@@ -89,7 +95,11 @@ bfx_status enqueue(bfx_batch_plan* P, cudaStream_t s) {
   if ((st = ir_batched_first_solve(ir_tab, P->S, s)) != BFX_OK) return st;
   for (int it = 0; it < P->max_iter; ++it)
     if ((st = ir_batched_step(ir_tab, P->S, P->p, s)) != BFX_OK) return st;
-  return ir_batched_finish(ir_tab, P->S, P->p, s);
+  if ((st = ir_batched_finish(ir_tab, P->S, P->p, s)) != BFX_OK) return st;
+  if (!P->gmres) return BFX_OK;
+  return ir_batched_gmres(ir_tab, P->S, reinterpret_cast<int*>(ws + P->o_gm_queue),
+                          reinterpret_cast<double*>(ws + P->o_gm_slots), P->gm_slot_doubles,
+                          P->gm_slots, kGmresM, P->p, kGmresOuter, kGmresTau, s);
 }
 
 // Fill the device tables for the bound buffers (host staging, one copy each).
@@ -187,7 +197,9 @@ BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int co
   ip.tol = 1.1102230246251565e-16;
   ip.tol_b = -1.0;
   ip.stall = 0.5;
+  ip.gmres = 1;
   if (params) ip = *params;
+  if (ip.gmres < 0 || ip.gmres > 2) return BFX_EINVAL;
   if (ip.max_iter < 0 || ip.max_iter > 200) return BFX_EINVAL;
   bfx_batch_config cfg{kBatchNb, kBatchBn};
   if (config) {
@@ -203,6 +215,7 @@ BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int co
   P->nrhs = nrhs;
   P->nb = cfg.nb;
   P->bn = cfg.gemm_bn;
+  P->gmres = ip.gmres != 0;  // 1 and 2 both: GMRES-IR after plain refinement
   P->max_iter = ip.max_iter;
   P->np = mode_pieces(mode);
   P->n.assign(h_n, h_n + count);
@@ -265,6 +278,16 @@ BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int co
   P->o_ir_tab = take(off, sizeof(BatchIr) * count);
   P->o_tiles = take(off, sizeof(GroupTile) * std::max<int64_t>(1, P->ntiles_all));
   P->o_probs = take(off, sizeof(GroupProblem) * std::max<int64_t>(1, P->nprobs_all));
+  if (P->gmres) {
+    P->gm_slot_doubles = batched_gmres_slot_doubles(kGmresM, P->nmax, nrhs);
+    const int64_t per = P->gm_slot_doubles * static_cast<int64_t>(sizeof(double));
+    const int sms = current_num_sms() > 0 ? current_num_sms() : 148;
+    int64_t slots = std::min<int64_t>(count, sms);
+    slots = std::min<int64_t>(slots, std::max<int64_t>(1, static_cast<int64_t>(kGmresSlotBudget) / per));
+    P->gm_slots = static_cast<int>(slots);
+    P->o_gm_queue = take(off, sizeof(int));
+    P->o_gm_slots = take(off, static_cast<size_t>(per) * slots);
+  }
   P->total = off;
   *out = P;
   return BFX_OK;

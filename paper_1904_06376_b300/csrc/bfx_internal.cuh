@@ -122,6 +122,12 @@ bfx_status ir_batched_post_lu(const BatchIr* d_ir, int S, int nmax, cudaStream_t
 bfx_status ir_batched_first_solve(const BatchIr* d_ir, int S, cudaStream_t s);
 bfx_status ir_batched_step(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s);
 bfx_status ir_batched_finish(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s);
+// GMRES-IR for the systems still unconverged after ir_batched_finish
+// (persistent grid of nslots CTAs, one Krylov slot of slot_doubles each).
+bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_slots,
+                            int64_t slot_doubles, int nslots, int m, BatchIrParams p,
+                            int max_outer, double tau, cudaStream_t s);
+int64_t batched_gmres_slot_doubles(int m, int nmax, int R);
 // tcgen05 GEMM on pieces (gemm_tc.cu)
 bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,

@@ -793,23 +793,31 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_first_solve_kernel(const Batc
   if (threadIdx.x == 0) q.st->dprev = xn;
 }
 
-// r = b - A x for one system (FP64; warp a row).  Returns max |r| when asked.
-__device__ double bir_residual_body(const BatchIr& q, double* red, bool want_max) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, n = q.n, R = q.nrhs;
+// out = b - A x (b null: out = A x) for one system, n x R columns (FP64;
+// warp a row).  Returns max |out| when asked.
+__device__ double bir_matvec(const float* __restrict__ A, int n, int R, const double* x,
+                             const double* __restrict__ b, double* out, double* red,
+                             bool want_max) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double rm = 0.0;
   for (int i = wid; i < n; i += BIR_THREADS / 32) {
-    const float* a = q.A + static_cast<int64_t>(i) * n;
+    const float* a = A + static_cast<int64_t>(i) * n;
     for (int c = 0; c < R; ++c) {
       double sum = 0.0;
-      for (int l = lane; l < n; l += 32) sum = fma(widen(a[l]), q.x[static_cast<int64_t>(l) * R + c], sum);
+      for (int l = lane; l < n; l += 32) sum = fma(widen(a[l]), x[static_cast<int64_t>(l) * R + c], sum);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-      const double v = q.b[static_cast<int64_t>(i) * R + c] - sum;
-      if (lane == 0) q.r[static_cast<int64_t>(i) * R + c] = v;
+      const double v = b ? b[static_cast<int64_t>(i) * R + c] - sum : sum;
+      if (lane == 0) out[static_cast<int64_t>(i) * R + c] = v;
       rm = fmax(rm, fabs(v));
     }
   }
   return want_max ? block_max(rm, red) : 0.0;
+}
+
+// r = b - A x for one system.  Returns max |r| when asked.
+__device__ double bir_residual_body(const BatchIr& q, double* red, bool want_max) {
+  return bir_matvec(q.A, q.n, q.nrhs, q.x, q.b, q.r, red, want_max);
 }
 
 // One refinement step of every active system: r = b - A x, d = LU^-1 P r,
@@ -858,6 +866,7 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_finish_kernel(const BatchIr* 
       q.out->converged = 0;
       q.out->iters = 0;
       q.out->info = *q.info;
+      q.out->gmres_steps = 0;
       q.out->berr = INFINITY;
     }
     return;
@@ -877,6 +886,7 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_finish_kernel(const BatchIr* 
     q.out->converged = st->conv;
     q.out->iters = st->iters;
     q.out->info = 0;
+    q.out->gmres_steps = 0;
     q.out->berr = be;
   }
 }
@@ -1066,7 +1076,276 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
   return last_launch_status();
 }
 
+// ------------------------------------------------------------- batched GMRES-IR
+// Systems whose plain refinement stopped unconverged (and whose factors are
+// regular) continue by GMRES-IR, as bfx_solve_ir does with gmres = 1:
+// restarted GMRES(min(n, m)) in FP64 preconditioned by the system's FP32
+// factors, each right-hand side with its own Krylov basis, the first
+// correction exempt from the stall test.  A persistent grid of CTAs takes
+// systems from an atomic queue, one CTA a system, all of its work inside the
+// CTA; each CTA owns one slot of Krylov memory (basis, Hessenberg columns,
+// rotations) sized for the largest system.  Orthogonalisation: two classical
+// Gram-Schmidt passes, each coefficient a warp dot product with a fixed
+// reduction order (deterministic).
+struct BgmSlot {
+  double *V, *H, *hc, *g, *cs, *sn, *y;
+};
+__device__ __forceinline__ BgmSlot bgm_carve(double* base, int mm, int n, int R) {
+  BgmSlot sl;
+  sl.V = base;                                        // (mm + 1) x n x R
+  sl.H = sl.V + static_cast<int64_t>(mm + 1) * n * R;  // R x mm columns of mm + 1
+  sl.hc = sl.H + static_cast<int64_t>(R) * mm * (mm + 1);  // (mm + 1) x R, one pass
+  sl.g = sl.hc + static_cast<int64_t>(mm + 1) * R;     // R x (mm + 1)
+  sl.cs = sl.g + static_cast<int64_t>(R) * (mm + 1);   // R x mm
+  sl.sn = sl.cs + static_cast<int64_t>(R) * mm;
+  sl.y = sl.sn + static_cast<int64_t>(R) * mm;
+  return sl;
+}
+
+// per-column sum of squares of v (n x R) -> out[c] (warp c, c + 8, ...)
+__device__ __forceinline__ void bgm_colnorm(const double* v, int n, int R, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = wid; c < R; c += BIR_THREADS / 32) {
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double a = v[static_cast<int64_t>(i) * R + c];
+      s2 = fma(a, a, s2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+    if (lane == 0) out[c] = s2;
+  }
+}
+
+__global__ void __launch_bounds__(BIR_THREADS)
+    bgm_kernel(const BatchIr* __restrict__ sys, int S, int* __restrict__ queue,
+               double* __restrict__ slots, int64_t slot_doubles, int m, BatchIrParams p,
+               int max_outer, double tau) {
+  __shared__ double red[BIR_THREADS / 32];
+  __shared__ double s_beta[MAXR], s_tmp[MAXR], s_dprev[MAXR], s_dn[MAXR], s_xn[MAXR];
+  __shared__ int s_act[MAXR], s_arn[MAXR], s_k[MAXR], s_conv[MAXR], s_stall[MAXR];
+  __shared__ int s_sys, s_any, s_steps;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  constexpr int NW = BIR_THREADS / 32;
+  double* base = slots + static_cast<int64_t>(blockIdx.x) * slot_doubles;
+  for (;;) {
+    if (t == 0) s_sys = atomicAdd(queue, 1);
+    __syncthreads();
+    const int k = s_sys;
+    __syncthreads();
+    if (k >= S) break;
+    const BatchIr q = sys[k];
+    if (*q.info != 0 || q.st->conv) continue;
+    const int n = q.n, R = q.nrhs, mm = min(m, n);
+    const BgmSlot sl = bgm_carve(base, mm, n, R);
+    const int64_t vs = static_cast<int64_t>(n) * R;  // one basis vector
+    if (t < R) {
+      s_act[t] = 1;
+      s_conv[t] = 0;
+      s_stall[t] = 0;
+      s_dprev[t] = INFINITY;
+    }
+    if (t == 0) s_steps = 0;
+    __syncthreads();
+    for (int outer = 0; outer < max_outer; ++outer) {
+      if (t == 0) {
+        int a = 0;
+        for (int c = 0; c < R; ++c) a |= s_act[c];
+        s_any = a;
+      }
+      __syncthreads();
+      if (!s_any) break;
+      // ---- r = b - A x, w = M^-1 r, beta = |w|_2, V_0 = w / beta, g = beta e_1
+      bir_matvec(q.A, n, R, q.x, q.b, q.r, red, false);
+      __syncthreads();
+      bir_solve_body(q);
+      bgm_colnorm(q.d, n, R, s_tmp);
+      __syncthreads();
+      if (t < R) {
+        const double b = sqrt(s_tmp[t]);
+        s_beta[t] = b;
+        s_arn[t] = s_act[t] && b > 0.0 && b <= 1.7976931348623157e308;
+        s_k[t] = 0;
+        double* gc = sl.g + static_cast<int64_t>(t) * (mm + 1);
+        for (int i = 0; i <= mm; ++i) gc[i] = 0.0;
+        gc[0] = b;
+      }
+      __syncthreads();
+      for (int64_t e = t; e < vs; e += BIR_THREADS) {
+        const int c = static_cast<int>(e % R);
+        if (s_arn[c]) sl.V[e] = q.d[e] / s_beta[c];
+      }
+      __syncthreads();
+      // ---- Arnoldi
+      for (int j = 0; j < mm; ++j) {
+        if (t == 0) {
+          int a = 0;
+          for (int c = 0; c < R; ++c) a |= s_arn[c];
+          s_any = a;
+        }
+        __syncthreads();
+        if (!s_any) break;
+        // w = M^-1 A v_j
+        bir_matvec(q.A, n, R, sl.V + j * vs, nullptr, q.r, red, false);
+        __syncthreads();
+        bir_solve_body(q);
+        for (int pass = 0; pass < 2; ++pass) {
+          // hc[i][c] = <V_i, w> (warp i mod NW), then H(:, j) += hc
+          for (int i = wid; i <= j; i += NW) {
+            const double* vi = sl.V + i * vs;
+            for (int c = 0; c < R; ++c) {
+              double sum = 0.0;
+              if (s_arn[c])
+                for (int r = lane; r < n; r += 32)
+                  sum = fma(vi[static_cast<int64_t>(r) * R + c], q.d[static_cast<int64_t>(r) * R + c], sum);
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+              if (lane == 0) {
+                sl.hc[static_cast<int64_t>(i) * R + c] = sum;
+                double* hp = sl.H + (static_cast<int64_t>(c) * mm + j) * (mm + 1) + i;
+                *hp = pass ? *hp + sum : sum;
+              }
+            }
+          }
+          __syncthreads();
+          for (int64_t e = t; e < vs; e += BIR_THREADS) {
+            const int c = static_cast<int>(e % R);
+            if (!s_arn[c]) continue;
+            double u = q.d[e];
+            for (int i = 0; i <= j; ++i) u = fma(-sl.hc[static_cast<int64_t>(i) * R + c], sl.V[i * vs + e], u);
+            q.d[e] = u;
+          }
+          __syncthreads();
+        }
+        // h_{j+1,j} = |w|_2, V_{j+1} = w / h, Givens (thread c)
+        bgm_colnorm(q.d, n, R, s_tmp);
+        __syncthreads();
+        if (t < R) s_tmp[t] = sqrt(s_tmp[t]);
+        __syncthreads();
+        for (int64_t e = t; e < vs; e += BIR_THREADS) {
+          const int c = static_cast<int>(e % R);
+          if (s_arn[c] && s_tmp[c] > 0.0) sl.V[(j + 1) * vs + e] = q.d[e] / s_tmp[c];
+        }
+        if (t < R && s_arn[t]) {
+          const int c = t;
+          double* hcol = sl.H + (static_cast<int64_t>(c) * mm + j) * (mm + 1);
+          double* csc = sl.cs + static_cast<int64_t>(c) * mm;
+          double* snc = sl.sn + static_cast<int64_t>(c) * mm;
+          double* gc = sl.g + static_cast<int64_t>(c) * (mm + 1);
+          const double hj = s_tmp[c];
+          double pv = hcol[0];
+          for (int i = 0; i < j; ++i) {
+            const double qv = hcol[i + 1];
+            hcol[i] = csc[i] * pv + snc[i] * qv;
+            pv = -snc[i] * pv + csc[i] * qv;
+          }
+          const double rho = hypot(pv, hj);
+          const double cj = rho > 0.0 ? pv / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
+          csc[j] = cj;
+          snc[j] = sj;
+          hcol[j] = rho;
+          hcol[j + 1] = 0.0;
+          gc[j + 1] = -sj * gc[j];
+          gc[j] = cj * gc[j];
+          s_k[c] = j + 1;
+          const double res = fabs(gc[j + 1]);
+          if (res <= tau * s_beta[c] || !(hj > 0.0) || j + 1 >= mm || !(res == res)) s_arn[c] = 0;
+        }
+        __syncthreads();
+      }
+      // ---- y = R_k^-1 g_k (warp per column, lanes split each row's sum)
+      for (int c = wid; c < R; c += NW) {
+        if (!s_act[c]) continue;
+        const int kk = s_k[c];
+        const double* Hc = sl.H + static_cast<int64_t>(c) * mm * (mm + 1);
+        const double* gc = sl.g + static_cast<int64_t>(c) * (mm + 1);
+        double* yc = sl.y + static_cast<int64_t>(c) * mm;
+        for (int i = kk - 1; i >= 0; --i) {
+          double u = 0.0;
+          for (int l = i + 1 + lane; l < kk; l += 32)
+            u = fma(Hc[static_cast<int64_t>(l) * (mm + 1) + i], yc[l], u);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xFFFFFFFFu, u, o);
+          if (lane == 0) yc[i] = (gc[i] - u) / Hc[static_cast<int64_t>(i) * (mm + 1) + i];
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // ---- x += V y on refinement-active columns; |d|, |x| per column
+      if (t < R) {
+        s_dn[t] = 0.0;
+        s_xn[t] = 0.0;
+      }
+      __syncthreads();
+      for (int64_t e = t; e < vs; e += BIR_THREADS) {
+        const int c = static_cast<int>(e % R);
+        if (!s_act[c]) continue;
+        const double* yc = sl.y + static_cast<int64_t>(c) * mm;
+        double u = 0.0;
+        for (int i = 0; i < s_k[c]; ++i) u = fma(yc[i], sl.V[i * vs + e], u);
+        const double xv = q.x[e] + u;
+        q.x[e] = xv;
+        atomic_max_nonneg(&s_dn[c], fabs(u));
+        atomic_max_nonneg(&s_xn[c], fabs(xv));
+      }
+      __syncthreads();
+      if (t < R && s_act[t]) {
+        const double dn = s_dn[t], xn = s_xn[t];
+        if (!(dn == dn) || !(xn == xn)) {
+          s_act[t] = 0;
+        } else if (dn <= p.tol * xn) {
+          s_act[t] = 0;
+          s_conv[t] = 1;
+        } else if (dn >= p.stall * s_dprev[t]) {
+          s_act[t] = 0;
+          s_stall[t] = 1;
+        } else {
+          s_dprev[t] = dn;
+        }
+      }
+      if (t == 0) s_steps += 1;
+      __syncthreads();
+    }
+    // ---- backward error as bir_finish_kernel; converged if every column is
+    const double rn = bir_matvec(q.A, n, R, q.x, q.b, q.r, red, true);
+    double xm = 0.0;
+    for (int64_t e = t; e < vs; e += BIR_THREADS) xm = fmax(xm, fabs(q.x[e]));
+    const double xn = block_max(xm, red);
+    if (t == 0) {
+      BatchIrState* st = q.st;
+      const double den = st->anorm * xn + st->bnorm;
+      double be = den > 0.0 ? rn / den : 0.0;
+      if (!(be == be)) be = INFINITY;
+      int all = 1;
+      for (int c = 0; c < R; ++c) all &= (s_conv[c] || (s_stall[c] && be <= p.tol_b));
+      st->conv = all;
+      st->berr = be;
+      st->iters += s_steps;
+      q.out->converged = all;
+      q.out->iters = st->iters;
+      q.out->gmres_steps = s_steps;
+      q.out->berr = be;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_slots,
+                            int64_t slot_doubles, int nslots, int m, BatchIrParams p,
+                            int max_outer, double tau, cudaStream_t s) {
+  if (S <= 0 || nslots <= 0) return BFX_OK;
+  if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return BFX_ECUDA;
+  bgm_kernel<<<nslots, BIR_THREADS, 0, s>>>(d_ir, S, d_queue, d_slots, slot_doubles, m, p,
+                                            max_outer, tau);
+  return last_launch_status();
+}
+
+int64_t batched_gmres_slot_doubles(int m, int nmax, int R) {
+  const int64_t mm = std::min(m, nmax);
+  return (mm + 1) * nmax * R + R * mm * (mm + 1) + (mm + 1) * R + R * (mm + 1) + 3 * R * mm;
+}
 
 bfx_status ir_batched_prepare(const BatchIr* d_ir, int S, int nmax, cudaStream_t s) {
   (void)nmax;

@@ -170,6 +170,7 @@ struct TcConfig {
   static constexpr uint32_t BAR_BYTES = 256;
   static constexpr uint32_t SMEM = STAGES * STAGE + S32 * STAGE32 + BAR_BYTES + 1024;  // + alignment
   static_assert(SW == 64 || SW == 128, "BK must be 32 or 64 bfloat16");
+  static_assert(A32_TILE % 1024 == 0, "FP32 stage parts keep the 1024-byte alignment");
   static_assert(!FUSED || (BK == 32 && BN == 256), "fused: BK 32 (two FP32 stages a K-slice), BN 256");
   static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
                     TMEM_COLS == 512,

@@ -610,16 +610,6 @@ __global__ void __launch_bounds__(TRSM_COLS * 32) lu_trsm_kernel(float* __restri
 // ------------------------------------------------------------- batched forms
 // blockIdx.y (or x for the tile kernel) selects a system; systems with no
 // work in the step return at once.
-template <bool use_smem>
-__global__ void __launch_bounds__(PANEL_THREADS)
-    lu_tile_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int j0) {
-  const BatchLu b = sys[blockIdx.x];
-  const int JB = min(nb, b.n - J0);
-  const int jw = min(TILE_W, J0 + JB - j0);
-  if (JB <= 0 || jw <= 0) return;
-  tile_body<use_smem>(b.A, b.n, b.n, J0, JB, j0, jw, b.ipiv, b.info);
-}
-
 template <int RPT>
 __global__ void __launch_bounds__(PANEL_THREADS)
     lu_tile_regs_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int j0) {
@@ -806,10 +796,7 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
   const int nmax = h_n_desc[0];
   // once per process (thread-safe initialisation)
   static const bool attrs = [] {
-    return cudaFuncSetAttribute(lu_tile_batched_kernel<true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(TILE_SMEM_MAX)) == cudaSuccess &&
-           cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) ==
                cudaSuccess &&
            cudaFuncSetAttribute(lu_trsm_batched_kernel<128>,
@@ -821,16 +808,11 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
     int S_t = 0;
     while (S_t < S_act && h_n_desc[S_t] > j0) ++S_t;
     if (S_t == 0) break;
-    const int rows = nmax - j0;
-    const size_t tsm = static_cast<size_t>(rows) * TILE_W * sizeof(float);
-    if (rows <= PANEL_THREADS)
+    // batch systems have n <= 1024: tiles of at most 2 rows a thread, in registers
+    if (nmax - j0 <= PANEL_THREADS)
       lu_tile_regs_batched_kernel<1><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
-    else if (rows <= 2 * PANEL_THREADS)
-      lu_tile_regs_batched_kernel<2><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
-    else if (tsm <= TILE_SMEM_MAX)
-      lu_tile_batched_kernel<true><<<S_t, PANEL_THREADS, tsm, s>>>(d_sys, nb, J0, j0);
     else
-      lu_tile_batched_kernel<false><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
+      lu_tile_regs_batched_kernel<2><<<S_t, PANEL_THREADS, 0, s>>>(d_sys, nb, J0, j0);
     const int64_t work = static_cast<int64_t>(nmax - j0) * nb;
     const unsigned gx = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), 32)));
     lu_tile_update_batched_kernel<<<dim3(gx, S_t), 256, 0, s>>>(d_sys, nb, J0, j0);

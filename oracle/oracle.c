@@ -27,7 +27,9 @@
  *     residual, correction solve and update all in FP64 with the low-precision
  *     factors (Sec. III: "do the solve in a higher precision like FP64").
  *  R12 the "combined type" LU (Sec. IV-A) uses bf16xN only in the trailing
- *     matrix update; panel and triangular block solve are plain FP32.
+ *     matrix update; panel and triangular block solve are plain FP32, the
+ *     panel blocked in tiles of 8 columns and its columns scaled by the
+ *     reciprocal of the pivot as LAPACK's xGETF2 does.
  *  R13 GEMM result form C = alpha*Z + beta*C: t = fl32(alpha*Z), then
  *     fmaf(beta, C, t); beta == 0 does not read C.
  *  R18 "GMRES with the LU as preconditioner" (Sec. III remark, Sec. IV-B):
@@ -431,7 +433,14 @@ int orc_lu(int mode, int64_t n, int64_t nb, float* A, int64_t lda, int32_t* ipiv
           }
         float piv = A[j * lda + j];
         if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
-        for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
+        /* scale by the reciprocal of the pivot, or divide by a subnormal pivot */
+        /* (LAPACK xGETF2's rule, with its sfmin = the smallest normal number)   */
+        if (fabsf(piv) >= 1.17549435e-38f) {
+          const float rcp = 1.0f / piv;
+          for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] * rcp;
+        } else {
+          for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
+        }
         for (int64_t i = j + 1; i < n; ++i) {
           float l = A[i * lda + j];
           for (int64_t c = j + 1; c < j0 + jw; ++c)

@@ -138,8 +138,11 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
       continue;
     }
     // ---- scale the column, rank-1 update of the rest of the tile
+    // scale by the reciprocal of the pivot unless it is subnormal (LAPACK xGETF2)
+    const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
+    const float rcp = __fdiv_rn(1.0f, piv);
     for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
-      const float l = __fdiv_rn(T(r, jj), piv);
+      const float l = use_rcp ? __fmul_rn(T(r, jj), rcp) : __fdiv_rn(T(r, jj), piv);
       T(r, jj) = l;
       for (int c = jj + 1; c < jw; ++c) T(r, c) = fmaf(-l, s_row[c], T(r, c));
     }
@@ -213,13 +216,13 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
 
 // The same tile factorisation with the tile in registers, for tiles of at
 // most PANEL_THREADS * RPT rows: thread t holds rows j0 + t + q*PANEL_THREADS
-// (q < RPT), all 8 columns.  Per column two barriers: one after every warp
-// has posted its best candidate together with that row's values (so the
-// pivot row is known as soon as the argmax is), one after warp 0 has chosen;
-// the shared rows alternate between two buffers by column parity, so a
-// thread still updating with column jj's pivot row never sees column jj+1's.
-// Every element sees the same operations as in tile_body (same pivot rule,
-// __fdiv_rn, fmaf order).
+// (q < RPT), all 8 columns.  One barrier per column: every warp posts its
+// best candidate together with that row's values, then every warp reduces
+// the posted candidates itself (same data, same order: the same pivot), so
+// the pivot row is known without a second barrier.  The shared rows
+// alternate between two buffers by column parity, so a warp still using
+// column jj's data never sees column jj+1's.  Every element sees the same
+// operations as in tile_body (same pivot rule, scaling, fmaf order).
 template <int RPT>
 __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t lda, int n, int J0,
                                                int JB, int j0, int jw,
@@ -229,8 +232,6 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
   __shared__ ArgMax wbest[2][NW];
   __shared__ float wrow[2][NW][TILE_W];   // each warp's candidate row
   __shared__ float rowj[2][TILE_W];       // row j before the swap
-  __shared__ float rowp[2][TILE_W];       // the pivot row (row j after the swap)
-  __shared__ int s_piv[2];
   __shared__ int s_pivs[TILE_W];
   __shared__ int s_rows[2 * TILE_W], s_src[2 * TILE_W], s_ns;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -280,31 +281,25 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
           for (int c = 0; c < TILE_W; ++c) wrow[bf][wid][c] = v[q][c];
         }
     }
-    __syncthreads();
-    if (wid == 0) {
-      ArgMax b = lane < NW ? wbest[bf][lane] : ArgMax{-1.0f, n};
-      int w = lane;
+    __syncthreads();  // the column's only barrier: every warp decides the pivot itself
+    ArgMax b = lane < NW ? wbest[bf][lane] : ArgMax{-1.0f, n};
+    int w = lane;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, b.v, o), __shfl_xor_sync(0xFFFFFFFFu, b.i, o)};
-        const int ow = __shfl_xor_sync(0xFFFFFFFFu, w, o);
-        const ArgMax nb = better(b, other);
-        if (nb.i != b.i) w = ow;
-        b = nb;
-      }
-      // lane 0: the winning warp is w (b.i < n), else no candidate
-      const float d = rowj[bf][jj];
-      const bool keep = (d != d || b.i >= n);  // a NaN on the diagonal stays
-      const int p = keep ? j : b.i;
-      if (lane < TILE_W) rowp[bf][lane] = keep ? rowj[bf][lane] : wrow[bf][w][lane];
-      if (lane == 0) {
-        s_piv[bf] = p;
-        s_pivs[jj] = p;
-        ipiv[j] = p;
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, b.v, o), __shfl_xor_sync(0xFFFFFFFFu, b.i, o)};
+      const int ow = __shfl_xor_sync(0xFFFFFFFFu, w, o);
+      const ArgMax nb = better(b, other);
+      if (nb.i != b.i) w = ow;
+      b = nb;
     }
-    __syncthreads();
-    const int p = s_piv[bf];
+    const float d = rowj[bf][jj];
+    const bool keep = (d != d || b.i >= n);  // a NaN on the diagonal stays
+    const int p = keep ? j : b.i;
+    if (t == 0) {
+      s_pivs[jj] = p;
+      ipiv[j] = p;
+    }
+    const float* prow = keep ? rowj[bf] : wrow[bf][w];  // the pivot row = row j after the swap
     // ---- swap rows j and p (tile part)
     if (p != j) {
 #pragma unroll
@@ -312,28 +307,31 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
         const int r = j0 + t + q * PANEL_THREADS;
         if (r == j) {
 #pragma unroll
-          for (int c = 0; c < TILE_W; ++c) v[q][c] = rowp[bf][c];
+          for (int c = 0; c < TILE_W; ++c) v[q][c] = prow[c];
         } else if (r == p) {
 #pragma unroll
           for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
         }
       }
     }
-    const float piv = rowp[bf][jj];
+    const float piv = prow[jj];
     if (piv == 0.0f) {
       if (t == 0 && *info == 0) *info = j + 1;
       continue;
     }
-    // ---- scale the column, rank-1 update of the rest of the tile
+    // ---- scale the column (by the reciprocal unless the pivot is subnormal),
+    // rank-1 update of the rest of the tile
+    const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
+    const float rcp = __fdiv_rn(1.0f, piv);
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int r = j0 + t + q * PANEL_THREADS;
       if (r > j && r < n) {
-        const float l = __fdiv_rn(v[q][jj], piv);
+        const float l = use_rcp ? __fmul_rn(v[q][jj], rcp) : __fdiv_rn(v[q][jj], piv);
         v[q][jj] = l;
 #pragma unroll
         for (int c = 0; c < TILE_W; ++c)
-          if (c > jj && c < jw) v[q][c] = fmaf(-l, rowp[bf][c], v[q][c]);
+          if (c > jj && c < jw) v[q][c] = fmaf(-l, prow[c], v[q][c]);
       }
     }
   }

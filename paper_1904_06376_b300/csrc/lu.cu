@@ -235,113 +235,149 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
   __shared__ int s_pivs[TILE_W];
   __shared__ int s_rows[2 * TILE_W], s_src[2 * TILE_W], s_ns;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  // rows as two 16-byte words when the tile is full and aligned
+  const bool vec = jw == TILE_W && (lda % 4) == 0 && (j0 % 4) == 0 &&
+                   (reinterpret_cast<uintptr_t>(A) % 16) == 0;
   float v[RPT][TILE_W];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int r = j0 + t + q * PANEL_THREADS;
+    const float* src = A + static_cast<int64_t>(r < n ? r : j0) * lda + j0;
+    if (vec) {
+      const float4 x0 = *reinterpret_cast<const float4*>(src);
+      const float4 x1 = *reinterpret_cast<const float4*>(src + 4);
+      v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
+      v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
+    } else {
 #pragma unroll
-    for (int c = 0; c < TILE_W; ++c)
-      v[q][c] = (r < n && c < jw) ? A[static_cast<int64_t>(r) * lda + j0 + c] : 0.0f;
+      for (int c = 0; c < TILE_W; ++c) v[q][c] = c < jw ? src[c] : 0.0f;
+    }
+    if (r >= n) {
+#pragma unroll
+      for (int c = 0; c < TILE_W; ++c) v[q][c] = 0.0f;
+    }
   }
-#pragma unroll
-  for (int jj = 0; jj < TILE_W; ++jj) {  // unrolled: register indices stay static
-    if (jj >= jw) break;
-    const int j = j0 + jj, bf = jj & 1;
-    // ---- pivot search over rows j..n-1; row j's owner posts row j
-    ArgMax best{-1.0f, n};
-    int bq = -1;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int r = j0 + t + q * PANEL_THREADS;
-      if (r == j) {
-#pragma unroll
-        for (int c = 0; c < TILE_W; ++c) rowj[bf][c] = v[q][c];
-      }
-      if (r >= j && r < n) {
-        float a = fabsf(v[q][jj]);
-        if (a != a) a = -1.0f;  // NaN below the diagonal is never chosen
-        const ArgMax cand{a, r};
-        const ArgMax nb = better(best, cand);
-        if (nb.i != best.i) bq = q;
-        best = nb;
-      }
-    }
-    const int own = best.i;  // this thread's candidate row
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, best.v, o), __shfl_xor_sync(0xFFFFFFFFu, best.i, o)};
-      best = better(best, other);
-    }
-    if (lane == 0) wbest[bf][wid] = best;
-    if (bq >= 0 && own == best.i) {  // the lane holding the warp's winner posts its row
-#pragma unroll
-      for (int q = 0; q < RPT; ++q)
-        if (q == bq) {
-#pragma unroll
-          for (int c = 0; c < TILE_W; ++c) wrow[bf][wid][c] = v[q][c];
-        }
-    }
-    __syncthreads();  // the column's only barrier: every warp decides the pivot itself
-    ArgMax b = lane < NW ? wbest[bf][lane] : ArgMax{-1.0f, n};
-    int w = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, b.v, o), __shfl_xor_sync(0xFFFFFFFFu, b.i, o)};
-      const int ow = __shfl_xor_sync(0xFFFFFFFFu, w, o);
-      const ArgMax nb = better(b, other);
-      if (nb.i != b.i) w = ow;
-      b = nb;
-    }
-    const float d = rowj[bf][jj];
-    const bool keep = (d != d || b.i >= n);  // a NaN on the diagonal stays
-    const int p = keep ? j : b.i;
-    if (t == 0) {
-      s_pivs[jj] = p;
-      ipiv[j] = p;
-    }
-    const float* prow = keep ? rowj[bf] : wrow[bf][w];  // the pivot row = row j after the swap
-    // ---- swap rows j and p (tile part)
-    if (p != j) {
+  // Column jj of the tile is always register column 0: after each pivot
+  // column the registers rotate left by one (column 0 moves to the back), so
+  // the loop body is the same for every column and need not be unrolled;
+  // after TILE_W rotations the columns are back in place.
+  for (int jj = 0; jj < TILE_W; ++jj) {
+    if (jj < jw) {
+      const int j = j0 + jj, bf = jj & 1;
+      const int rem = jw - jj;  // tile columns from the current one on
+      // ---- pivot search over rows j..n-1; row j's owner posts row j
+      ArgMax best{-1.0f, n};
+      int bq = -1;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = j0 + t + q * PANEL_THREADS;
         if (r == j) {
 #pragma unroll
-          for (int c = 0; c < TILE_W; ++c) v[q][c] = prow[c];
-        } else if (r == p) {
+          for (int c = 0; c < TILE_W; ++c) rowj[bf][c] = v[q][c];
+        }
+        if (r >= j && r < n) {
+          float a = fabsf(v[q][0]);
+          if (a != a) a = -1.0f;  // NaN below the diagonal is never chosen
+          const ArgMax cand{a, r};
+          const ArgMax nb = better(best, cand);
+          if (nb.i != best.i) bq = q;
+          best = nb;
+        }
+      }
+      const int own = best.i;  // this thread's candidate row
 #pragma unroll
-          for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
+      for (int o = 16; o > 0; o >>= 1) {
+        ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, best.v, o), __shfl_xor_sync(0xFFFFFFFFu, best.i, o)};
+        best = better(best, other);
+      }
+      if (lane == 0) wbest[bf][wid] = best;
+      if (bq >= 0 && own == best.i) {  // the lane holding the warp's winner posts its row
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q == bq) {
+#pragma unroll
+            for (int c = 0; c < TILE_W; ++c) wrow[bf][wid][c] = v[q][c];
+          }
+      }
+      __syncthreads();  // the column's only barrier: every warp decides the pivot itself
+      ArgMax b = lane < NW ? wbest[bf][lane] : ArgMax{-1.0f, n};
+      int w = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ArgMax other{__shfl_xor_sync(0xFFFFFFFFu, b.v, o), __shfl_xor_sync(0xFFFFFFFFu, b.i, o)};
+        const int ow = __shfl_xor_sync(0xFFFFFFFFu, w, o);
+        const ArgMax nb = better(b, other);
+        if (nb.i != b.i) w = ow;
+        b = nb;
+      }
+      const float d = rowj[bf][0];
+      const bool keep = (d != d || b.i >= n);  // a NaN on the diagonal stays
+      const int p = keep ? j : b.i;
+      if (t == 0) {
+        s_pivs[jj] = p;
+        ipiv[j] = p;
+      }
+      const float* prow = keep ? rowj[bf] : wrow[bf][w];  // the pivot row = row j after the swap
+      // ---- swap rows j and p (tile part)
+      if (p != j) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int r = j0 + t + q * PANEL_THREADS;
+          if (r == j) {
+#pragma unroll
+            for (int c = 0; c < TILE_W; ++c) v[q][c] = prow[c];
+          } else if (r == p) {
+#pragma unroll
+            for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
+          }
+        }
+      }
+      const float piv = prow[0];
+      if (piv == 0.0f) {
+        if (t == 0 && *info == 0) *info = j + 1;
+      } else {
+        // ---- scale the column (by the reciprocal unless the pivot is
+        // subnormal), rank-1 update of the rest of the tile
+        const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
+        const float rcp = __fdiv_rn(1.0f, piv);
+        float u[TILE_W];
+#pragma unroll
+        for (int c = 1; c < TILE_W; ++c) u[c] = prow[c];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int r = j0 + t + q * PANEL_THREADS;
+          if (r > j && r < n) {
+            const float l = use_rcp ? __fmul_rn(v[q][0], rcp) : __fdiv_rn(v[q][0], piv);
+            v[q][0] = l;
+#pragma unroll
+            for (int c = 1; c < TILE_W; ++c)
+              if (c < rem) v[q][c] = fmaf(-l, u[c], v[q][c]);
+          }
         }
       }
     }
-    const float piv = prow[jj];
-    if (piv == 0.0f) {
-      if (t == 0 && *info == 0) *info = j + 1;
-      continue;
-    }
-    // ---- scale the column (by the reciprocal unless the pivot is subnormal),
-    // rank-1 update of the rest of the tile
-    const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
-    const float rcp = __fdiv_rn(1.0f, piv);
+    // ---- rotate the columns left by one
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-      const int r = j0 + t + q * PANEL_THREADS;
-      if (r > j && r < n) {
-        const float l = use_rcp ? __fmul_rn(v[q][jj], rcp) : __fdiv_rn(v[q][jj], piv);
-        v[q][jj] = l;
+      const float c0 = v[q][0];
 #pragma unroll
-        for (int c = 0; c < TILE_W; ++c)
-          if (c > jj && c < jw) v[q][c] = fmaf(-l, prow[c], v[q][c]);
-      }
+      for (int c = 0; c < TILE_W - 1; ++c) v[q][c] = v[q][c + 1];
+      v[q][TILE_W - 1] = c0;
     }
   }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int r = j0 + t + q * PANEL_THREADS;
     if (r < n) {
+      float* dst = A + static_cast<int64_t>(r) * lda + j0;
+      if (vec) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[q][0], v[q][1], v[q][2], v[q][3]);
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(v[q][4], v[q][5], v[q][6], v[q][7]);
+      } else {
 #pragma unroll
-      for (int c = 0; c < TILE_W; ++c)
-        if (c < jw) A[static_cast<int64_t>(r) * lda + j0 + c] = v[q][c];
+        for (int c = 0; c < TILE_W; ++c)
+          if (c < jw) dst[c] = v[q][c];
+      }
     }
   }
   // ---- the tile's row swaps on the block-column columns outside the tile

@@ -1,0 +1,69 @@
+"""Parity at the full benchmark sizes, in the launch configurations bench.py
+times: the n = 4096 single solve (config 3), the 2000-system batch with its
+autotuned tile shape (config 4) and the serving stream (config 5).  The
+oracle's FP64 LU solve is run on a sample where a full comparison would take
+too long on the host; every result is checked for convergence and its
+backward error."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import bfx_inputs as bi
+
+pytestmark = pytest.mark.gpu
+
+
+def _fe(x, xt):
+    return float(np.max(np.abs(x - xt)) / np.max(np.abs(xt)))
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e4, 1e8])
+def test_single_solve_n4096(bfx, orc, kappa):
+    P = bi.fast_system(4096, kappa, 21)
+    x, res, code = bfx.solve_ir(3, torch.from_numpy(P.A32).cuda(), torch.from_numpy(P.b).cuda())
+    assert code == 0 and res["converged"] == 1, res
+    assert res["berr"] <= np.sqrt(4096) * 2.0**-53
+    xd, _ = orc.dgesv(P.A32, P.b)
+    assert _fe(x.cpu().numpy(), P.x_true) <= 10 * _fe(xd, P.x_true) + 1e-15
+
+
+def test_batched_2000_systems(bfx, orc):
+    probs = bi.batched_systems(2000, 0)
+    ns = [p.n for p in probs]
+    B0 = bfx.Batch(6, ns, max_iter=12)
+    A, b = B0.pack([p.A32 for p in probs], [p.b for p in probs])
+    best, best_ms, table = bfx.batch_autotune(6, ns, A, b, reps=1, max_iter=12)
+    B = bfx.Batch(6, ns, max_iter=12, config=best)
+    x, st = B.solve(A, b)
+    torch.cuda.synchronize()
+    conv, iters, info, berr = B.decode_status(st)
+    assert conv.all() and (info == 0).all()
+    assert np.all(berr <= np.sqrt(np.array(ns)) * 2.0**-53)
+    xs = B.unpack(x)
+    for i in range(0, 2000, 47):  # 43 sampled systems against the oracle's FP64 LU
+        xd, _ = orc.dgesv(probs[i].A32, probs[i].b)
+        assert _fe(xs[i], probs[i].x_true) <= 10 * _fe(xd, probs[i].x_true) + 1e-15, i
+
+
+def test_serving_stream_60gb_budget(bfx, orc):
+    reqs = bi.serving_stream(120, 3)
+    systems = [bi.fast_system(r.n, 10.0 ** r.log10_kappa, r.seed, nrhs=r.nrhs) for r in reqs]
+    srv = bfx.Server(budget_bytes=60 * 10**9, max_inflight=32, mode=3)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, P in zip(reqs, systems):
+        while time.perf_counter() - t0 < r.t_arrival:
+            pass
+        tickets.append(srv.submit(P.A32, P.b))
+    out = [srv.wait(tk) for tk in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_used_bytes"] <= 60 * 10**9 and st["peak_running"] >= 8
+    for (x, res), P in zip(out, systems):
+        assert res["status"] == 0 and res["converged"] == 1, res
+        assert res["berr"] <= np.sqrt(P.n) * 2.0**-53
+        if P.n <= 1024:  # the oracle's FP64 LU on the host for the smaller ones
+            xd, _ = orc.dgesv(P.A32, P.b)
+            assert _fe(x, P.x_true) <= 10 * _fe(xd, P.x_true) + 1e-15

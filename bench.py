@@ -408,10 +408,10 @@ def main():
     ms = t0.elapsed_time(t1) / args.steps
     split_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     gemm_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    if dist:  # the slowest rank's time
+        from paper_1904_06376_b300.replicas import max_over_ranks
+
+        ms = max_over_ranks(ms, dist, dev)
     flops = 2.0 * m * n * k
     value = world * flops / (ms * 1e-3) / 1e12
     hbm, bf16_peak, bf16_sus, peak_src = peaks()

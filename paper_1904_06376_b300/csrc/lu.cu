@@ -596,8 +596,9 @@ __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict_
 // broadcast from its owner lane.
 constexpr int TRSM_COLS = 8;  // columns (warps) a CTA
 template <int NB>
-__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int n, int j0,
-                                          int jb, int cb) {
+// Columns c_begin + cb * TRSM_COLS + (warp) below c_end of the block row j0.
+__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int c_end, int j0,
+                                          int jb, int c_begin, int cb) {
   extern __shared__ float L11[];  // NB x NB, the jb x jb triangle padded with zeros
   constexpr int RPL = NB / 32;    // rows a lane
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -606,8 +607,8 @@ __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, in
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t c = j0 + jb + cb * static_cast<int64_t>(TRSM_COLS) + w;
-  if (c >= n) return;
+  const int64_t c = c_begin + cb * static_cast<int64_t>(TRSM_COLS) + w;
+  if (c >= c_end) return;
   float* col = A + static_cast<int64_t>(j0) * lda + c;
   float x[RPL];
 #pragma unroll
@@ -636,9 +637,11 @@ __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, in
 }
 
 template <int NB>
+// Columns c_begin .. c_end - 1 of the block row j0.
 __global__ void __launch_bounds__(TRSM_COLS * 32) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
-                                                                 int n, int j0, int jb) {
-  trsm_body<NB>(A, lda, n, j0, jb, blockIdx.x);
+                                                                 int c_end, int j0, int jb,
+                                                                 int c_begin) {
+  trsm_body<NB>(A, lda, c_end, j0, jb, c_begin, static_cast<int>(blockIdx.x));
 }
 
 // ------------------------------------------------------------- batched forms
@@ -677,7 +680,7 @@ __global__ void __launch_bounds__(TRSM_COLS * 32)
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
   if (JB <= 0 || J0 + JB + static_cast<int>(blockIdx.x) * TRSM_COLS >= b.n) return;
-  trsm_body<NB>(b.A, b.n, b.n, J0, JB, blockIdx.x);
+  trsm_body<NB>(b.A, b.n, b.n, J0, JB, J0 + JB, blockIdx.x);
 }
 
 // Pieces of L21 (rows below the block, block columns) and of U12^T for the
@@ -764,6 +767,50 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   uint16_t* Lp = reinterpret_cast<uint16_t*>(static_cast<char*>(ws) + kSwapSetBytes);
   uint16_t* Up = Lp + np * w.ap;
   const int N = static_cast<int>(n);
+  // Look-ahead: the caller's stream s carries the panel, the row swaps and
+  // the next block column's solve and update; an auxiliary stream (one per
+  // host thread, joined to s by events) carries the rest of each trailing
+  // update, so it runs while the next panel is factored.  The next row swaps
+  // wait for it.  Each element sees the same operations as without it.
+  thread_local cudaStream_t aux = nullptr;
+  if (!aux && cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess) {
+    aux = nullptr;
+    return BFX_ECUDA;
+  }
+  cudaEvent_t ev_fork = nullptr, ev_rest = nullptr;
+  if (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return BFX_ECUDA;
+  if (cudaEventCreateWithFlags(&ev_rest, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(ev_fork);
+    return BFX_ECUDA;
+  }
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } events{ev_fork, ev_rest};
+  bool rest_pending = false;
+  // C[:, c0 .. c0+nc) -= L21 U12[:, c0 .. c0+nc) for block column j0 on stream st
+  auto update = [&](int j0, int jb, int c0, int nc, cudaStream_t st, bool split_l) -> bfx_status {
+    const int nr = N - j0 - jb;
+    float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
+    float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb + c0;
+    float* A22 = A + static_cast<int64_t>(j0 + jb) * lda + j0 + jb + c0;
+    if (np == 0) return launch_sgemm_simt(nr, nc, jb, -1.0f, L21, lda, U12, lda, 1.0f, A22, lda, st);
+    bfx_status e;
+    if (split_l) {
+      e = launch_split(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
+                       np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, st);
+      if (e != BFX_OK) return e;
+    }
+    uint16_t* Uc = Up + static_cast<int64_t>(c0) * w.kp;  // rows c0.. of the U12^T planes
+    e = launch_split_transpose(jb, nc, U12, lda, np, Uc, np > 1 ? Uc + w.bp : nullptr,
+                               np > 2 ? Uc + 2 * w.bp : nullptr, w.kp, st);
+    if (e != BFX_OK) return e;
+    return launch_gemm_presplit(mode, nr, nc, jb, -1.0f, Lp, w.kp, w.ap, Uc, w.kp, w.bp, 1.0f, A22,
+                                lda, st);
+  };
   for (int j0 = 0; j0 < N; j0 += nb) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
     for (int t0 = j0; t0 < j0 + jb; t0 += TILE_W) {
@@ -789,6 +836,9 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
         lu_tile_update_kernel<<<g, 256, 0, s>>>(A, lda, N, j0, jb, t0, tw);
       }
     }
+    // the row swaps move rows of columns the previous rest update writes
+    if (rest_pending && cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
+    rest_pending = false;
     if (N - jb > 0) {
       const int64_t cols = N - jb;
       lu_swapset_kernel<<<1, 32, 0, s>>>(ipiv, j0, jb, swapset);
@@ -798,26 +848,26 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     }
     const int nr = N - j0 - jb;
     if (nr <= 0) continue;
-    trsm<<<static_cast<unsigned>(ceil_div(nr, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
-        A, lda, N, j0, jb);
-    float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
-    float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb;
-    float* A22 = A + static_cast<int64_t>(j0 + jb) * lda + j0 + jb;
-    bfx_status st;
-    if (np == 0) {
-      st = launch_sgemm_simt(nr, nr, jb, -1.0f, L21, lda, U12, lda, 1.0f, A22, lda, s);
-    } else {
-      st = launch_split(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
-                        np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, s);
-      if (st != BFX_OK) return st;
-      st = launch_split_transpose(jb, nr, U12, lda, np, Up, np > 1 ? Up + w.bp : nullptr,
-                                  np > 2 ? Up + 2 * w.bp : nullptr, w.kp, s);
-      if (st != BFX_OK) return st;
-      st = launch_gemm_presplit(mode, nr, nr, jb, -1.0f, Lp, w.kp, w.ap, Up, w.kp, w.bp, 1.0f,
-                                A22, lda, s);
-    }
+    // next block column: solve and update on s
+    const int nc = std::min(nb, nr);
+    trsm<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
+        A, lda, j0 + jb + nc, j0, jb, j0 + jb);
+    bfx_status st = update(j0, jb, 0, nc, s, true);
     if (st != BFX_OK) return st;
+    // the rest on the auxiliary stream, after the row swaps and the L21 pieces
+    if (nr > nc) {
+      if (cudaEventRecord(ev_fork, s) != cudaSuccess ||
+          cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
+        return BFX_ECUDA;
+      trsm<<<static_cast<unsigned>(ceil_div(nr - nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
+          A, lda, N, j0, jb, j0 + jb + nc);
+      st = update(j0, jb, nc, nr - nc, aux, false);
+      if (st != BFX_OK) return st;
+      if (cudaEventRecord(ev_rest, aux) != cudaSuccess) return BFX_ECUDA;
+      rest_pending = true;
+    }
   }
+  if (rest_pending && cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
   return last_launch_status();
 }
 

@@ -266,15 +266,22 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
       const int j = j0 + jj, bf = jj & 1;
       const int rem = jw - jj;  // tile columns from the current one on
       // ---- pivot search over rows j..n-1; row j's owner posts row j
+      // (row r lives in thread (r - j0) % PANEL_THREADS, slot (r - j0) / PANEL_THREADS:
+      // only the owner runs the copies, its slot picked by a compare chain)
+      const int tj = (j - j0) % PANEL_THREADS, qj = (j - j0) / PANEL_THREADS;
+      if (t == tj) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q == qj) {
+#pragma unroll
+            for (int c = 0; c < TILE_W; ++c) rowj[bf][c] = v[q][c];
+          }
+      }
       ArgMax best{-1.0f, n};
       int bq = -1;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = j0 + t + q * PANEL_THREADS;
-        if (r == j) {
-#pragma unroll
-          for (int c = 0; c < TILE_W; ++c) rowj[bf][c] = v[q][c];
-        }
         if (r >= j && r < n) {
           float a = fabsf(v[q][0]);
           if (a != a) a = -1.0f;  // NaN below the diagonal is never chosen
@@ -292,9 +299,10 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
       }
       if (lane == 0) wbest[bf][wid] = best;
       if (bq >= 0 && own == best.i) {  // the lane holding the warp's winner posts its row
+        const int qw = (own - j0) / PANEL_THREADS;
 #pragma unroll
         for (int q = 0; q < RPT; ++q)
-          if (q == bq) {
+          if (q == qw) {
 #pragma unroll
             for (int c = 0; c < TILE_W; ++c) wrow[bf][wid][c] = v[q][c];
           }
@@ -318,18 +326,24 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
         ipiv[j] = p;
       }
       const float* prow = keep ? rowj[bf] : wrow[bf][w];  // the pivot row = row j after the swap
-      // ---- swap rows j and p (tile part)
+      // ---- swap rows j and p (tile part): only their owners
       if (p != j) {
+        const int tp = (p - j0) % PANEL_THREADS, qp = (p - j0) / PANEL_THREADS;
+        if (t == tj) {
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          const int r = j0 + t + q * PANEL_THREADS;
-          if (r == j) {
+          for (int q = 0; q < RPT; ++q)
+            if (q == qj) {
 #pragma unroll
-            for (int c = 0; c < TILE_W; ++c) v[q][c] = prow[c];
-          } else if (r == p) {
+              for (int c = 0; c < TILE_W; ++c) v[q][c] = prow[c];
+            }
+        }
+        if (t == tp) {
 #pragma unroll
-            for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
-          }
+          for (int q = 0; q < RPT; ++q)
+            if (q == qp) {
+#pragma unroll
+              for (int c = 0; c < TILE_W; ++c) v[q][c] = rowj[bf][c];
+            }
         }
       }
       const float piv = prow[0];
@@ -648,7 +662,7 @@ __global__ void __launch_bounds__(TRSM_COLS * 32) lu_trsm_kernel(float* __restri
 // blockIdx.y (or x for the tile kernel) selects a system; systems with no
 // work in the step return at once.
 template <int RPT>
-__global__ void __launch_bounds__(PANEL_THREADS)
+__global__ void __launch_bounds__(PANEL_THREADS, 1)
     lu_tile_regs_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int j0) {
   const BatchLu b = sys[blockIdx.x];
   const int JB = min(nb, b.n - J0);

@@ -57,9 +57,18 @@ typedef enum bfx_status {
  *   BFX_X1   : hi*hi                                    (one bfloat16 piece)
  *   BFX_X3   : + hi*mid + mid*hi                        (pair split, "bx2_3")
  *   BFX_X6   : + hi*lo + mid*mid + lo*hi                (triple split, "bx3_6")
+ *   BFX_X8   : + mid*lo + lo*mid, the 2^-24 bin Z3      (triple split; Sec. II-D's
+ *              Z0 + (Z1 + (Z2 + Z3)), "might offer higher accuracy than FP32")
  *   BFX_X9   : all nine products                       (triple split)
  * The mode's value is the number of bfloat16 products per scalar product. */
-typedef enum bfx_mode { BFX_FP32 = 0, BFX_X1 = 1, BFX_X3 = 3, BFX_X6 = 6, BFX_X9 = 9 } bfx_mode;
+typedef enum bfx_mode {
+  BFX_FP32 = 0,
+  BFX_X1 = 1,
+  BFX_X3 = 3,
+  BFX_X6 = 6,
+  BFX_X8 = 8,
+  BFX_X9 = 9
+} bfx_mode;
 
 /* Library version (major*10000 + minor*100 + patch). */
 BFX_API int bfx_version(void);

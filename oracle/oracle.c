@@ -21,8 +21,9 @@
  *     split then proceeds as written, so the pieces still sum to x.
  *  R4 Inf/NaN: hi carries the value (NaN made quiet, sign kept), mid = lo = +0.
  *  R6 products and order: x1 = {00}; x3 = pair split, {00,01,10};
- *     x6 = {00,01,10,02,11,20}; x9 = all nine; level sums and the
- *     smallest-first combination exactly as written in Sec. II-D.
+ *     x6 = {00,01,10,02,11,20}; x8 = x6 + {12,21} (the "Z3" sum of
+ *     Sec. II-D); x9 = all nine; level sums and the smallest-first
+ *     combination exactly as written in Sec. II-D.
  *  R9 refinement: r = b - A x (the paper's sign slip in Sec. III corrected),
  *     residual, correction solve and update all in FP64 with the low-precision
  *     factors (Sec. III: "do the solve in a higher precision like FP64").
@@ -170,6 +171,7 @@ static int mode_pieces(int mode) {
     case 1: return 1;
     case 3: return 2;
     case 6: return 3;
+    case 8: return 3;
     case 9: return 3;
     default: return 0;
   }
@@ -181,6 +183,7 @@ static int mode_uses(int mode, int i, int j) {
     case 1: return i == 0 && j == 0;
     case 3: return i + j <= 1;
     case 6: return i + j <= 2;
+    case 8: return i + j <= 3;
     case 9: return 1;
     default: return 0;
   }
@@ -250,6 +253,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
           case 1: zr = Z0; break;
           case 3: zr = Z0 + Z1; break;
           case 6: zr = Z0 + (Z1 + Z2); break;
+          case 8: zr = Z0 + (Z1 + (Z2 + Z3)); break;
           default: zr = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
         }
         if (Cd) { Cd[i * ldcd + j] = zr; continue; }
@@ -266,6 +270,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
           case 1: zd = Z0; break;
           case 3: zd = Z0 + Z1; break;
           case 6: zd = Z0 + (Z1 + Z2); break;
+          case 8: zd = Z0 + (Z1 + (Z2 + Z3)); break;
           default: zd = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
         }
         if (Cd) { Cd[i * ldcd + j] = zd; continue; }

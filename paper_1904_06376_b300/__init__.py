@@ -12,6 +12,7 @@ from ._bfx import (  # noqa: F401
     BFX_X1,
     BFX_X3,
     BFX_X6,
+    BFX_X8,
     BFX_X9,
     Batch,
     BatchConfig,

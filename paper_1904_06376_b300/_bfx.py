@@ -13,8 +13,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "libbfx.so")
 
-BFX_FP32, BFX_X1, BFX_X3, BFX_X6, BFX_X9 = 0, 1, 3, 6, 9
-PIECES = {BFX_X1: 1, BFX_X3: 2, BFX_X6: 3, BFX_X9: 3}
+BFX_FP32, BFX_X1, BFX_X3, BFX_X6, BFX_X8, BFX_X9 = 0, 1, 3, 6, 8, 9
+PIECES = {BFX_X1: 1, BFX_X3: 2, BFX_X6: 3, BFX_X8: 3, BFX_X9: 3}
 
 _STATUS = {
     0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",

@@ -23,7 +23,8 @@ int current_device() {
 }
 
 bool check_mode(bfx_mode mode) {
-  return mode == BFX_FP32 || mode == BFX_X1 || mode == BFX_X3 || mode == BFX_X6 || mode == BFX_X9;
+  return mode == BFX_FP32 || mode == BFX_X1 || mode == BFX_X3 || mode == BFX_X6 || mode == BFX_X8 ||
+         mode == BFX_X9;
 }
 
 }  // namespace
@@ -70,6 +71,7 @@ int mode_pieces(bfx_mode mode) {
     case BFX_X1: return 1;
     case BFX_X3: return 2;
     case BFX_X6: return 3;
+    case BFX_X8: return 3;
     case BFX_X9: return 3;
     default: return 0;
   }

@@ -49,8 +49,8 @@ __device__ __forceinline__ void accumulate(float a, float b, float (&Z)[DOT_LEVE
   float x[3], y[3];
   pieces3(a, x[0], x[1], x[2]);
   pieces3(b, y[0], y[1], y[2]);
-  if (MODE == 9) {
-    Z[4] = fmaf(x[2], y[2], Z[4]);
+  if (MODE == 9) Z[4] = fmaf(x[2], y[2], Z[4]);
+  if (MODE >= 8) {
     Z[3] = fmaf(x[1], y[2], Z[3]);
     Z[3] = fmaf(x[2], y[1], Z[3]);
   }
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(DOT_THREADS) dot_final_kernel(int nblocks,
       case 1: z = Z0; break;
       case 3: z = Z0 + Z1; break;
       case 6: z = Z0 + (Z1 + Z2); break;
+      case 8: z = Z0 + (Z1 + (Z2 + Z3)); break;
       default: z = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
     }
     *out = z;
@@ -178,6 +179,7 @@ BFX_API bfx_status bfx_dot_bf16xN(bfx_mode mode, int64_t n, const float* d_x, co
     case BFX_X1: return run_dot<1>(n, d_x, d_y, d_result, part, g, s);
     case BFX_X3: return run_dot<3>(n, d_x, d_y, d_result, part, g, s);
     case BFX_X6: return run_dot<6>(n, d_x, d_y, d_result, part, g, s);
+    case BFX_X8: return run_dot<8>(n, d_x, d_y, d_result, part, g, s);
     default: return run_dot<9>(n, d_x, d_y, d_result, part, g, s);
   }
 }

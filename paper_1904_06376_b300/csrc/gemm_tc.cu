@@ -2,7 +2,8 @@
 //
 // C = alpha * Z + beta * C with Z the sum of the mode's bfloat16 piece
 // products (Sec. II-D, II-G of the paper):
-//   x1: a0 b0;  x3: + a0 b1 + a1 b0;  x6: + a0 b2 + a1 b1 + a2 b0;  x9: all.
+//   x1: a0 b0;  x3: + a0 b1 + a1 b0;  x6: + a0 b2 + a1 b1 + a2 b0;
+//   x8: + a1 b2 + a2 b1 (the Z3 sum of Sec. II-D);  x9: all.
 // Each product of two bfloat16 values is exact in FP32 (Sec. I) and the
 // tensor core accumulates in FP32, the precision the paper's FMA model uses.
 //
@@ -65,6 +66,11 @@ __host__ __device__ constexpr Prod prod_of(int mode, int i) {
   }
   if (mode == 6) {
     const Prod p[6] = {{2, 0, 1}, {1, 1, 1}, {0, 2, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+    return p[i];
+  }
+  if (mode == 8) {
+    const Prod p[8] = {{2, 1, 1}, {1, 2, 1}, {2, 0, 1}, {1, 1, 1},
+                       {0, 2, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
     return p[i];
   }
   const Prod p[9] = {{2, 2, 1}, {2, 1, 1}, {1, 2, 1}, {2, 0, 1}, {1, 1, 1},
@@ -737,6 +743,9 @@ bfx_status grouped_bn(bfx_mode mode, int num_tiles, const GroupTile* d_tiles,
     case BFX_X6:
       return run_tc_grouped<6, BN, 32, S6>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
                                            b_rows, planes, kp, alpha, beta, s);
+    case BFX_X8:
+      return run_tc_grouped<8, BN, 32, S6>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
+                                           b_rows, planes, kp, alpha, beta, s);
     case BFX_X9:
       return run_tc_grouped<9, BN, 32, S6>(num_tiles, d_tiles, d_probs, Apack, a_rows, Bpack,
                                            b_rows, planes, kp, alpha, beta, s);
@@ -780,6 +789,8 @@ bfx_status launch_gemm_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k, flo
       return run_tc_fused<3, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
     case BFX_X6:
       return run_tc_fused<6, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    case BFX_X8:
+      return run_tc_fused<8, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
     case BFX_X9:
       return run_tc_fused<9, 2>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
     default:
@@ -802,6 +813,9 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
                                    C, ldc, s);
     case BFX_X6:
       return run_tc<6, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
+    case BFX_X8:
+      return run_tc<8, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
                                    C, ldc, s);
     case BFX_X9:
       return run_tc<9, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,

@@ -953,7 +953,7 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.tsync = reinterpret_cast<int32_t*>(
       take(sizeof(int32_t) * 2 * (1 + nblk * ceil_div(nrhs, TRSV_CG))));
   size_t lub = 0;
-  for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X9})
+  for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X8, BFX_X9})
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
   w.luws_bytes = lub;
   w.luws = lub ? take(lub) : nullptr;

@@ -25,7 +25,7 @@ def acc_term(k):
 def tol(mode, k):
     if mode == 0:
         return k * EPS / (1 - k * EPS)
-    if mode in (6, 9):
+    if mode in (6, 8, 9):
         return acc_term(k)
     if mode == 3:
         return 3.03 * 2.0 ** -16 + acc_term(k)

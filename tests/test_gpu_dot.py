@@ -12,7 +12,7 @@ from _tol import tol
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", [0, 1, 3, 6, 9])
+@pytest.mark.parametrize("mode", [0, 1, 3, 6, 8, 9])
 @pytest.mark.parametrize("n", [1, 7, 1000, 4099, 1 << 20])
 def test_dot_bound_vs_fp64(bfx, orc, mode, n):
     x = bi.wide_range(n, 3 * n + mode, -12, 12)
@@ -32,7 +32,7 @@ def test_dot_exact_cases(bfx, orc):
     x = rng.integers(-64, 65, n).astype(np.float32)
     y = rng.integers(-64, 65, n).astype(np.float32)
     exact = float(sum(F(int(a)) * F(int(b)) for a, b in zip(x, y)))
-    for mode in (0, 1, 3, 6, 9):
+    for mode in (0, 1, 3, 6, 8, 9):
         got = float(bfx.dot_bf16xN(mode, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).item())
         assert got == exact
 

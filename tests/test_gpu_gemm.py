@@ -16,7 +16,7 @@ import bfx_inputs as bi
 from _tol import check_bound, tol
 
 pytestmark = pytest.mark.gpu
-MODES = [1, 3, 6, 9]
+MODES = [1, 3, 6, 8, 9]
 
 
 def _cuda(a):
@@ -83,7 +83,7 @@ def test_gemm_permutation_exact(bfx, orc, mode):
     assert np.array_equal(C1, orc.gemm(mode, P, B))
     C2 = bfx.gemm_bf16xN(mode, _cuda(A), _cuda(P.T.copy())).cpu().numpy()
     assert np.array_equal(C2, orc.gemm(mode, A, P.T.copy()))
-    if mode in (6, 9):
+    if mode in (6, 8, 9):
         assert np.array_equal(C1, B[perm])
 
 
@@ -153,3 +153,37 @@ def test_gemm_full_size_sampled_rows(bfx, orc, mode, m, n, k):
     Cs = C[torch.from_numpy(rows).cuda()].cpu().numpy()
     C64, Cabs = orc.dgemm_rows(A, B, rows)
     check_bound(Cs, C64, Cabs, mode, k)
+
+
+def test_x8_z3_bin_exact(bfx, orc):
+    """The construction of the oracle's x8 pin, batched into one GEMM: rows
+    [a, -a] times columns [b, b0 + b1] leave only a0 b2 and a1 b2.  x6 is the
+    exact a0 b2 (bit-equal to the oracle); x8 adds a1 b2 (the Z3 bin).  The
+    tensor core adds its accumulator at the alignment of the largest product
+    of each MMA, even when those products cancel, so the later 2^-8-bin MMAs
+    (a1 b0 - a1 b0 = 0 here) keep between none and all of the bits of the
+    a1 b2 held in the correction accumulator, depending on the magnitudes
+    (measured; R23).  Held: (x8 - x6) / (a1 b2) has median 1 (within 10 %)
+    and lies within a quarter of 1 for most outputs; a kernel without the
+    bin gives 0 everywhere."""
+    rng = np.random.default_rng(19)
+    a = rng.uniform(-1, 1, 64).astype(np.float32)
+    b = (rng.uniform(-1, 1, 48) * 2.0 ** rng.integers(-5, 6, 48)).astype(np.float32)
+    bp = orc.split(b, 3)
+    c = (orc.bf16_to_f32(bp[0]).astype(np.float64) + orc.bf16_to_f32(bp[1])).astype(np.float32)
+    cp = orc.split(c, 3)
+    assert np.all((cp[0] == bp[0]) & (cp[1] == bp[1]) & (cp[2] == 0))  # c splits as (b0, b1, 0)
+    A = np.stack([a, -a], axis=1)           # 64 x 2
+    B = np.stack([b, c], axis=0)            # 2 x 48
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C6 = bfx.gemm_bf16xN(6, Ad, Bd).cpu().numpy()
+    C8 = bfx.gemm_bf16xN(8, Ad, Bd).cpu().numpy()
+    assert np.array_equal(C6, orc.gemm(6, A, B))
+    a1 = orc.bf16_to_f32(orc.split(a, 3)[1]).astype(np.float64)
+    b2 = orc.bf16_to_f32(bp[2]).astype(np.float64)
+    z3 = np.outer(a1, b2)  # the exact a1 b2 of every output
+    nz = z3 != 0
+    ratio = (C8.astype(np.float64) - C6)[nz] / z3[nz]
+    assert nz.sum() > 1000
+    assert abs(np.median(ratio) - 1.0) <= 0.1
+    assert np.mean(np.abs(ratio - 1.0) <= 0.25) >= 0.75

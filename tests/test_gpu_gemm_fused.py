@@ -25,7 +25,7 @@ SHAPES = [(128, 256, 32), (300, 520, 200), (1, 1, 1), (17, 33, 5), (129, 257, 33
           (256, 512, 1000), (640, 300, 77)]
 
 
-@pytest.mark.parametrize("mode", [1, 3, 6, 9])
+@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
 @pytest.mark.parametrize("m,n,k", SHAPES)
 def test_fused_equals_separate_split(bfx, mode, m, n, k):
     A = bi.wide_range((m, k), 10 + m, -12, 12)

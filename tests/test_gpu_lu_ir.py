@@ -34,7 +34,7 @@ def test_lu_fp32_bit_exact(bfx, orc, n, nb):
     assert np.array_equal(LU, LUo)
 
 
-@pytest.mark.parametrize("mode", [3, 6, 9])
+@pytest.mark.parametrize("mode", [3, 6, 8, 9])
 @pytest.mark.parametrize("n,nb", [(200, 64), (333, 32), (700, 64)])
 def test_lu_bf16xn_vs_oracle(bfx, orc, mode, n, nb):
     """Same pivots as the oracle's bf16xN LU (random matrices: well separated

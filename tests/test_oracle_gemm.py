@@ -32,7 +32,7 @@ def _perm_matrix(perm):
 
 
 # ----------------------------------------------------------------- exact cases
-@pytest.mark.parametrize("mode", [1, 3, 6, 9])
+@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
 def test_left_permutation_exact(orc, mode):
     """C = P B with P a permutation: every row of C is exactly the sum of the
     pieces of a row of B that the mode keeps (products (0,j))."""
@@ -42,11 +42,11 @@ def test_left_permutation_exact(orc, mode):
     B = bi.wide_range((n, 17), 2, -20, 20)
     C = orc.gemm(mode, _perm_matrix(perm), B)
     b0, b1, b2 = _pieces(orc, B)
-    expect = {1: b0, 3: b0 + b1, 6: B, 9: B}[mode][perm]
+    expect = {1: b0, 3: b0 + b1, 6: B, 8: B, 9: B}[mode][perm]
     assert np.array_equal(C, expect)
 
 
-@pytest.mark.parametrize("mode", [1, 3, 6, 9])
+@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
 def test_right_permutation_exact(orc, mode):
     """C = A Q: every column of C is exactly the kept pieces of a column of A
     (products (i,0)); catches a transposed operand or a dropped (i,0) term."""
@@ -57,7 +57,7 @@ def test_right_permutation_exact(orc, mode):
     A = bi.wide_range((13, n), 4, -20, 20)
     C = orc.gemm(mode, A, Q)
     a0, a1, a2 = _pieces(orc, A)
-    expect = {1: a0, 3: a0 + a1, 6: A, 9: A}[mode][:, perm]
+    expect = {1: a0, 3: a0 + a1, 6: A, 8: A, 9: A}[mode][:, perm]
     assert np.array_equal(C, expect)
 
 
@@ -77,11 +77,11 @@ def test_single_products_exact_in_fp32(orc):
 
 
 def test_already_bfloat16_inputs_all_modes_equal(orc):
-    """Inputs that are bfloat16 values have zero mid/lo pieces: x3/x6/x9 == x1."""
+    """Inputs that are bfloat16 values have zero mid/lo pieces: x3/x6/x8/x9 == x1."""
     A = orc.bf16_to_f32(orc.bf16_rne(bi.uniform_pm1((32, 40), 6)))
     B = orc.bf16_to_f32(orc.bf16_rne(bi.uniform_pm1((40, 24), 7)))
     C1 = orc.gemm(1, A, B)
-    for mode in (3, 6, 9):
+    for mode in (3, 6, 8, 9):
         assert np.array_equal(orc.gemm(mode, A, B), C1)
 
 
@@ -179,12 +179,13 @@ def test_c1_bounds(orc, c1_case):
     k = A.shape[1]
     ratios = {}
     for m, bnd in [(0, gam(k)), (6, 1.01 * (gam(k + 2) + EPS_F)), (9, 1.01 * gam(k + 4)),
+                   (8, 1.01 * (gam(k + 3) + 2.0**-32)),  # drops only the lo*lo bin, <= 2^-32 zhat
                    (3, 3.03 * 2.0**-16 + 1.01 * gam(k + 1))]:
         C = orc.gemm(m, A, B)
         r = np.max(np.abs(C - C64) / (bnd * Cabs))
         ratios[m] = r
         assert r <= 1.0, (m, r)
-    for m in (6, 9):
+    for m in (6, 8, 9):
         C = orc.gemm(m, A, B)
         assert np.all(np.abs(C - C64) <= 2 * k * EPS_F * Cabs)
 
@@ -249,3 +250,29 @@ def test_worked_example_a1b2(orc):
     six = sum(a[i] * b[j] for i in range(3) for j in range(3) if i + j <= 2)
     assert abs(a[1] * b[2]) > 4 * abs(a[2] * b[1])
     assert abs(six + a[1] * b[2] - ex) < abs(six - ex) / 3
+
+
+def test_x8_keeps_exactly_the_z3_bin(orc):
+    """Sec. II-D's Z3 sum (x8) adds the 2^-24 bin {12, 21} to x6.  With
+    x = [a, -a] and y = [b, b0 + b1] every piece product cancels except those
+    with b's lo piece: Z^(i,2) = a_i b2, so x6 = a0 b2 (exact), x8 =
+    fl32(a0 b2 + a1 b2) and x9 additionally adds a2 b2."""
+    rng = np.random.default_rng(17)
+    checked = 0
+    for t in range(400):
+        a = np.float32(rng.uniform(-1, 1))
+        b = np.float32(rng.uniform(-1, 1) * 2.0 ** rng.integers(-5, 6))
+        a0, a1, a2 = (float(v[0]) for v in _pieces(orc, np.array([a])))
+        b0, b1, b2 = (float(v[0]) for v in _pieces(orc, np.array([b])))
+        c = np.float32(b0 + b1)
+        p = [float(v[0]) for v in _pieces(orc, np.array([c]))]
+        if p != [b0, b1, 0.0] or b2 == 0.0 or a1 == 0.0:
+            continue  # only inputs whose truncated value splits as (b0, b1, 0)
+        checked += 1
+        x = np.array([[a, -a]], dtype=np.float32)
+        y = np.array([[b], [c]], dtype=np.float32)
+        x6 = float(orc.gemm(6, x, y)[0, 0])
+        x8 = float(orc.gemm(8, x, y)[0, 0])
+        assert F(x6) == F(a0) * F(b2), t
+        assert x8 == float(np.float32(a0 * b2) + np.float32(a1 * b2)), t
+    assert checked > 100

@@ -304,13 +304,13 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
                                                    "bf16x6-update LU + FP64 refinement"}}
 
 
-def bench_serving(bfx, bi, count):
+def bench_serving(bfx, bi, count, max_inflight=32):
     """Config 5: Poisson arrivals at 5000 req/s, n log-uniform [64, 4096],
     nrhs U{1..16}, log10 kappa U[1,10], 60 GB pool, bf16x3 with escalation;
     latency measured from submission to completion inside the server."""
     reqs = bi.serving_stream(count, 3)
     systems = [bi.fast_system(r.n, 10.0 ** r.log10_kappa, r.seed, nrhs=r.nrhs) for r in reqs]
-    srv = bfx.Server(budget_bytes=60 * 10 ** 9, max_inflight=32, mode=3, escalate=True)
+    srv = bfx.Server(budget_bytes=60 * 10 ** 9, max_inflight=max_inflight, mode=3, escalate=True)
     t_start = time.perf_counter()
     tickets = []
     for r, P in zip(reqs, systems):
@@ -333,7 +333,7 @@ def bench_serving(bfx, bi, count):
             "converged_log10k_le_7": float(conv[lk <= 7].mean()),
             "median_forward_error": float(np.median(fe)),
             "peak_running": stats["peak_running"], "peak_pool_bytes": stats["peak_used_bytes"],
-            "budget_bytes": stats["pool_bytes"], "max_inflight": 32,
+            "budget_bytes": stats["pool_bytes"], "max_inflight": max_inflight,
             "generator": "O(n^2) Householder/permutation construction with exact kappa"}
 
 

@@ -786,25 +786,37 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   // host thread, joined to s by events) carries the rest of each trailing
   // update, so it runs while the next panel is factored.  The next row swaps
   // wait for it.  Each element sees the same operations as without it.
-  thread_local cudaStream_t aux = nullptr;
-  if (!aux && cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess) {
-    aux = nullptr;
+  struct AuxStream {  // released when the host thread ends
+    cudaStream_t s = nullptr;
+    ~AuxStream() {
+      if (s) cudaStreamDestroy(s);
+    }
+  };
+  thread_local AuxStream aux_owner;
+  if (!aux_owner.s && cudaStreamCreateWithFlags(&aux_owner.s, cudaStreamNonBlocking) != cudaSuccess) {
+    aux_owner.s = nullptr;
     return BFX_ECUDA;
   }
+  cudaStream_t aux = aux_owner.s;
   cudaEvent_t ev_fork = nullptr, ev_rest = nullptr;
   if (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return BFX_ECUDA;
   if (cudaEventCreateWithFlags(&ev_rest, cudaEventDisableTiming) != cudaSuccess) {
     cudaEventDestroy(ev_fork);
     return BFX_ECUDA;
   }
-  struct Events {
-    cudaEvent_t a, b;
-    ~Events() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
+  // owns the events; on every return path the caller's stream is joined to
+  // the auxiliary stream's last recorded work before the events go
+  struct Join {
+    cudaStream_t s;
+    cudaEvent_t fork, rest;
+    bool pending = false;
+    ~Join() {
+      if (pending) cudaStreamWaitEvent(s, rest, 0);
+      cudaEventDestroy(fork);
+      cudaEventDestroy(rest);
     }
-  } events{ev_fork, ev_rest};
-  bool rest_pending = false;
+  } join{s, ev_fork, ev_rest};
+  bool& rest_pending = join.pending;
   // C[:, c0 .. c0+nc) -= L21 U12[:, c0 .. c0+nc) for block column j0 on stream st
   auto update = [&](int j0, int jb, int c0, int nc, cudaStream_t st, bool split_l) -> bfx_status {
     const int nr = N - j0 - jb;
@@ -881,7 +893,10 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
       rest_pending = true;
     }
   }
-  if (rest_pending && cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
+  if (rest_pending) {
+    rest_pending = false;
+    if (cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
+  }
   return last_launch_status();
 }
 

@@ -304,6 +304,32 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
                                                    "bf16x6-update LU + FP64 refinement"}}
 
 
+def bench_accuracy(bfx, oracle, bi, dev, size=2048, rows=256):
+    """Sec. IV-A's GEMM accuracy study on the device: relative Frobenius error
+    against the FP64 oracle (on a sample of rows) of each mode and of the FP32
+    SIMT GEMM, for the narrow, maximal-exponent and Gaussian-exponent ranges."""
+    import torch
+
+    gens = {"uniform [-1,1]": bi.uniform_pm1,
+            "random exponent [-60,60]": bi.random_exponent,
+            "gaussian exponent (sigma 10)": bi.gaussian_exponent}
+    sel = np.sort(np.random.default_rng(5).choice(size, rows, replace=False)).astype(np.int64)
+    out = {}
+    for name, g in gens.items():
+        A = g((size, size), 80)
+        B = g((size, size), 81)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        C64, _ = oracle.dgemm_rows(A, B, sel)
+        res = {}
+        for label, fn in (("x3", lambda: bfx.gemm_bf16xN(3, Ad, Bd)), ("x6", lambda: bfx.gemm_bf16xN(6, Ad, Bd)),
+                          ("x8", lambda: bfx.gemm_bf16xN(8, Ad, Bd)), ("x9", lambda: bfx.gemm_bf16xN(9, Ad, Bd)),
+                          ("fp32_simt", lambda: bfx.sgemm_simt(Ad, Bd))):
+            C = fn()[torch.from_numpy(sel).to(dev)].cpu().numpy().astype(np.float64)
+            res[label] = float(np.linalg.norm(C - C64) / np.linalg.norm(C64))
+        out[name] = res
+    return {"size": size, "rows_sampled": rows, "relative_frobenius_error": out}
+
+
 def bench_serving(bfx, bi, count, max_inflight=32):
     """Config 5: Poisson arrivals at 5000 req/s, n log-uniform [64, 4096],
     nrhs U{1..16}, log10 kappa U[1,10], 60 GB pool, bf16x3 with escalation;
@@ -540,6 +566,7 @@ def main():
     del A, B, C, Ap, Bp, ws, Ahp, Bhp, Chp
     torch.cuda.empty_cache()
     if not args.no_solves:
+        line["accuracy"] = bench_accuracy(bfx, oracle, bi, dev)
         line["ir_single"] = bench_ir_single(bfx, oracle, bi, dev)
         line["batched"] = bench_batched(bfx, oracle, bi, dev)
         line["serving"] = bench_serving(bfx, bi, args.serve_requests)

@@ -25,6 +25,11 @@ Workloads (all numpy ``default_rng(seed)``):
   of Gaussian v and random permutations P, so kappa(A) is exactly
   sigma_max / sigma_min; used for the serving stream, whose thousands of
   requests up to n = 4096 cannot each afford two QR factorisations.
+* ``random_exponent`` / ``gaussian_exponent``: the wide and medium exponent
+  ranges of Sec. IV-A's GEMM study: random sign and 23 mantissa bits with the
+  exponent uniform over a range symmetric about 0 (the paper's "randomly chosen
+  exponent bits", bounded so that products and their sums stay finite) or
+  rounded from a Gaussian (its "medium range").
 * ``diag_dominant_system``: row and column diagonally dominant unsymmetric
   matrices (off-diagonal U[-1,1], each diagonal entry of random sign and
   magnitude above both its row and its column sum of the other entries), the
@@ -48,6 +53,8 @@ __all__ = [
     "special_values_f32",
     "fast_system",
     "diag_dominant_system",
+    "random_exponent",
+    "gaussian_exponent",
 ]
 
 
@@ -225,3 +232,25 @@ def diag_dominant_system(n: int, seed: int, nrhs: int = 1, margin: float = 1.0) 
     x_true = rng.standard_normal((n, nrhs))
     b = A32.astype(np.float64) @ x_true
     return SolveProblem(A32=A32, b=b, x_true=x_true, kappa_nominal=float("nan"), seed=seed)
+
+
+def _compose_f32(rng, shape, e):
+    """FP32 values with random sign, random 23-bit mantissa and exponent e (int array)."""
+    sign = rng.integers(0, 2, size=shape).astype(np.uint32) << 31
+    mant = rng.integers(0, 1 << 23, size=shape).astype(np.uint32)
+    bits = sign | ((e.astype(np.int64) + 127).astype(np.uint32) << 23) | mant
+    return bits.view(np.float32)
+
+
+def random_exponent(shape, seed: int, emin: int = -60, emax: int = 60) -> np.ndarray:
+    """FP32 normal numbers whose exponent is uniform in [emin, emax]."""
+    rng = np.random.default_rng(seed)
+    e = rng.integers(emin, emax + 1, size=shape)
+    return _compose_f32(rng, shape, e)
+
+
+def gaussian_exponent(shape, seed: int, sigma: float = 10.0, emax: int = 60) -> np.ndarray:
+    """FP32 normal numbers whose exponent is a rounded N(0, sigma^2), clipped to +-emax."""
+    rng = np.random.default_rng(seed)
+    e = np.clip(np.rint(rng.normal(0.0, sigma, size=shape)), -emax, emax).astype(np.int64)
+    return _compose_f32(rng, shape, e)

@@ -1,0 +1,49 @@
+"""The three GEMM input ranges of Sec. IV-A on the device: narrow [-1, 1],
+maximal exponent range (random exponent bits) and Gaussian exponents.  Every
+mode stays within its elementwise bound against the FP64 oracle product on
+all three; on the narrow range the paper's accuracy order holds: bf16x3,
+then FP32 SGEMM, then bf16x6 (relative Frobenius error, high to low)."""
+import numpy as np
+import pytest
+import torch
+
+import bfx_inputs as bi
+from _tol import check_bound
+
+pytestmark = pytest.mark.gpu
+
+GENS = {
+    "uniform": lambda shape, seed: bi.uniform_pm1(shape, seed),
+    "random_exponent": lambda shape, seed: bi.random_exponent(shape, seed),
+    "gaussian_exponent": lambda shape, seed: bi.gaussian_exponent(shape, seed),
+}
+
+
+def _frob(C, C64):
+    return float(np.linalg.norm(C.astype(np.float64) - C64) / np.linalg.norm(C64))
+
+
+@pytest.mark.parametrize("gen", list(GENS))
+@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
+def test_bounds_on_each_range(bfx, orc, gen, mode):
+    m, n, k = 256, 384, 512
+    A = GENS[gen]((m, k), 10)
+    B = GENS[gen]((k, n), 11)
+    C = bfx.gemm_bf16xN(mode, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(C))
+    C64, Cabs = orc.dgemm_rows(A, B)
+    check_bound(C, C64, Cabs, mode, k)
+
+
+def test_narrow_range_accuracy_order(bfx, orc):
+    errs = {"x3": [], "sgemm": [], "x6": []}
+    for s in range(4):
+        A = bi.uniform_pm1((512, 512), 20 + 2 * s)
+        B = bi.uniform_pm1((512, 512), 21 + 2 * s)
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        C64, _ = orc.dgemm_rows(A, B)
+        errs["x3"].append(_frob(bfx.gemm_bf16xN(3, Ad, Bd).cpu().numpy(), C64))
+        errs["sgemm"].append(_frob(bfx.sgemm_simt(Ad, Bd).cpu().numpy(), C64))
+        errs["x6"].append(_frob(bfx.gemm_bf16xN(6, Ad, Bd).cpu().numpy(), C64))
+    m = {k: np.mean(v) for k, v in errs.items()}
+    assert m["x3"] > m["sgemm"] > m["x6"], m

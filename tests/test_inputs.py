@@ -31,3 +31,17 @@ def test_serving_stream_distributions():
     assert abs(np.mean(np.log(n)) - (np.log(64) + np.log(4097)) / 2) < 0.05
     nr = np.array([r.nrhs for r in reqs])
     assert nr.min() == 1 and nr.max() == 16
+
+
+def test_exponent_generators():
+    import bfx_inputs as bi
+
+    x = bi.random_exponent((400, 400), 1)
+    e = ((x.view(np.uint32) >> 23) & 0xFF).astype(np.int64)
+    assert x.dtype == np.float32 and np.all(np.isfinite(x))
+    assert e.min() - 127 == -60 and e.max() - 127 == 60  # the full range is drawn
+    assert abs(np.mean(x < 0) - 0.5) < 0.01
+    g = bi.gaussian_exponent((400, 400), 2)
+    eg = ((g.view(np.uint32) >> 23) & 0xFF).astype(np.int64) - 127
+    assert abs(np.std(eg) - 10.0) < 0.2 and abs(np.mean(eg)) < 0.2
+    assert np.array_equal(x, bi.random_exponent((400, 400), 1))

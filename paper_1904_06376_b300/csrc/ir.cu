@@ -131,15 +131,24 @@ __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int
   }
 }
 
-// d[i, c] = r[perm[i], c]
+// The triangular solve's "not yet published" marker: a signalling NaN with a
+// payload bit set.  FP64 arithmetic only ever returns quiet NaNs, so no
+// computed value has this bit pattern.
+constexpr unsigned long long kTrsvSentinel = 0xFFF4000000000001ull;
+
+// d[i, c] = r[perm[i], c]; when fill != null, also fill[] = the triangular
+// solve's sentinel (n x nrhs) and tickets[0..1] = 0.
 __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
                                  const int32_t* __restrict__ perm, int64_t n, int nrhs,
-                                 double* __restrict__ d, int64_t ldd) {
+                                 double* __restrict__ d, int64_t ldd, double* __restrict__ fill,
+                                 int* __restrict__ tickets) {
+  if (tickets && blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e / nrhs;
     const int c = static_cast<int>(e - i * nrhs);
     d[i * ldd + c] = r[static_cast<int64_t>(perm[i]) * ldr + c];
+    if (fill) fill[e] = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
   }
 }
 
@@ -232,19 +241,32 @@ __global__ void __launch_bounds__(256)
 //   published, acc -= F[b, k] y_k;   y_b = Dinv_b acc (the block's inverse);
 //   store y_b, fence, publish.
 // The tile of F is fetched before the wait, so it overlaps the wait; the sums
-// run in a fixed order (deterministic).  sync: [0] ticket, [1 + k*G + g]
-// ready flags; all zero at launch.
+// run in a fixed order (deterministic).  A block's result is published by
+// storing it into y, which holds a sentinel (a signalling-NaN pattern no
+// arithmetic produces) until then: consumers poll the values themselves, so
+// there is no flag and no fence between the product and the next block.  y
+// must be all sentinel at launch; each launch resets the v rows it consumed
+// to the sentinel, so the forward launch prepares the backward one's output.
+// ticket: zero at launch.
 constexpr int TRSV_THREADS = 256;
 constexpr int TRSV_CG = 4;  // right-hand sides a CTA
 
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ bool is_trsv_sentinel(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) == kTrsvSentinel;
 }
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// relaxed (morally strong, single-copy atomic) 8-byte accesses at GPU scope:
+// the published values and the polls on them never form a data race
+__device__ __forceinline__ double ld_relaxed_gpu(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return __longlong_as_double(static_cast<long long>(v));
 }
+__device__ __forceinline__ void st_relaxed_gpu(double* p, double x) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p),
+               "l"(static_cast<unsigned long long>(__double_as_longlong(x)))
+               : "memory");
+}
+
 
 // out[i][c] (+)= sign * sum_l T[i][l] x[l][c], i < TB, c < cg; Q threads a
 // product (Q = 4, 2, 1 for cg = 1, 2, >2), their partial sums added by shuffle.
@@ -285,8 +307,8 @@ template <bool LOWER>
 __global__ void __launch_bounds__(TRSV_THREADS)
     ir_trsv_kernel(const float* __restrict__ F, int64_t ldf, int n,
                    const double* __restrict__ Dinv, const double* __restrict__ Gm,
-                   const double* __restrict__ v, double* __restrict__ y, int R,
-                   int* __restrict__ sync, int* __restrict__ err) {
+                   double* __restrict__ v, double* __restrict__ y, int R,
+                   int* __restrict__ ticket, int* __restrict__ err) {
   extern __shared__ __align__(16) uint8_t trsv_smem[];
   double* Ds = reinterpret_cast<double*>(trsv_smem);                       // [TB][TB + 1]
   double* Gs = Ds + TB * (TB + 1);                                          // [TB][TB + 1]
@@ -299,7 +321,7 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   const int nblk = (n + TB - 1) / TB;
   const int G = (R + TRSV_CG - 1) / TRSV_CG;
   if (t == 0) {
-    s_ticket = atomicAdd(sync, 1);
+    s_ticket = atomicAdd(ticket, 1);
     s_fail = 0;
   }
   __syncthreads();
@@ -307,7 +329,6 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   const int b = LOWER ? step : nblk - 1 - step;
   const int b0 = b * TB, bs = min(TB, n - b0);
   const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
-  int* ready = sync + 1;
   // F[b, k] -> Fs buffer (s & 1), asynchronously; rows >= bs / columns >= ks zero
   auto prefetch = [&](int s) {
     const int k = LOWER ? s : nblk - 1 - s;
@@ -330,32 +351,42 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     Ds[(e / TB) * (TB + 1) + e % TB] = D[e];
     if (step > 0) Gs[(e / TB) * (TB + 1) + e % TB] = Gb[e];
   }
+  // acc = v_b; the v rows read are then set to the sentinel: this launch is
+  // their last reader, and the next triangle writes its result there
   for (int e = t; e < TB * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
-    acc[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
+    double a = 0.0;
+    if (i < bs) {
+      double* vp = v + static_cast<int64_t>(b0 + i) * R + c0 + c;
+      a = *vp;
+      *vp = __longlong_as_double(static_cast<long long>(kTrsvSentinel));  // next launch's output
+    }
+    acc[i][c] = a;
   }
-  // warp 0: wait until y_k is published, then fetch it into xs
+  // warp 0: fetch y_k into xs, each lane polling its values until none is
+  // the sentinel (an 8-byte aligned store is seen whole or not at all)
+  volatile int* fail = &s_fail;
   auto fetch = [&](int k) {
     const int k0 = k * TB, ks = min(TB, n - k0);
     if (t < 32) {
-      if (t == 0 && !s_fail) {
-        const int* f = ready + k * G + grp;
-        if (ld_acquire_gpu(f) == 0) {
-          const uint64_t t0 = global_ns();
-          while (ld_acquire_gpu(f) == 0) {
-            if (global_ns() - t0 > 4000000000ull) {
-              atomicExch(err, kErrWaitBlock);
-              s_fail = 1;
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-      }
-      __syncwarp();
       for (int e = t; e < TB * cg; e += 32) {
         const int i = e / cg, c = e - i * cg;
-        xs[i][c] = i < ks ? __ldcg(y + static_cast<int64_t>(k0 + i) * R + c0 + c) : 0.0;
+        double val = 0.0;
+        if (i < ks) {
+          const double* src = y + static_cast<int64_t>(k0 + i) * R + c0 + c;
+          val = ld_relaxed_gpu(src);
+          if (is_trsv_sentinel(val) && !*fail) {
+            const uint64_t t0 = global_ns();
+            while (is_trsv_sentinel(val = ld_relaxed_gpu(src))) {
+              if (global_ns() - t0 > 4000000000ull) {
+                atomicExch(err, kErrWaitBlock);
+                *fail = 1;
+                break;
+              }
+            }
+          }
+        }
+        xs[i][c] = val;
       }
     }
   };
@@ -384,14 +415,10 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     }
     __syncthreads();
   }
+  // publish: the values themselves are the signal (no flag, no fence)
   for (int e = t; e < bs * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
-    y[static_cast<int64_t>(b0 + i) * R + c0 + c] = xs[i][c];
-  }
-  __syncthreads();
-  if (t == 0) {
-    __threadfence();
-    st_release_gpu(ready + b * G + grp, 1);
+    st_relaxed_gpu(y + static_cast<int64_t>(b0 + i) * R + c0 + c, xs[i][c]);
   }
 }
 
@@ -910,7 +937,8 @@ struct IrWs {
   double* Uinv;
   double* Lg;     // chain matrices G_b = Linv_b L[b, b-1] and Uinv_b U[b, b+1]
   double* Ug;
-  int32_t* tsync; // triangular-solve tickets and ready flags, both triangles
+  double* y1;     // forward-solve result (sentinel-filled between solves)
+  int32_t* tsync; // triangular-solve tickets, one per triangle
   void* luws;
   size_t luws_bytes;
   // GMRES-IR (gm_m > 0 only)
@@ -950,8 +978,8 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.Uinv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.Lg = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.Ug = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
-  w.tsync = reinterpret_cast<int32_t*>(
-      take(sizeof(int32_t) * 2 * (1 + nblk * ceil_div(nrhs, TRSV_CG))));
+  w.y1 = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
+  w.tsync = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2));
   size_t lub = 0;
   for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X8, BFX_X9})
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
@@ -984,8 +1012,10 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   return w;
 }
 
-// d <- U^-1 L^-1 P r (all columns).  r is consumed: d = P r (gathered), the
-// forward solve writes r, the backward solve writes d.
+// d <- U^-1 L^-1 P r (all columns; r is left as it is).  d = P r (gathered),
+// the forward solve reads d and writes y1, the backward solve reads y1 and
+// writes d.  The gather also fills y1 with the sentinel and zeroes both
+// tickets; the forward solve leaves d all sentinel for the backward one.
 bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
   static const bool attr_ok = [] {
     return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1000,14 +1030,12 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
   const int nblk = static_cast<int>(ceil_div(n, TB));
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
   const unsigned grid = static_cast<unsigned>(nblk * G);
-  if (cudaMemsetAsync(w.tsync, 0, sizeof(int32_t) * 2 * (1 + static_cast<size_t>(nblk) * G), s) !=
-      cudaSuccess)
-    return BFX_ECUDA;
-  ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs);
-  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.r,
+  ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
+                                                        w.y1, w.tsync);
+  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.y1,
                                                              nrhs, w.tsync, err);
-  ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(
-      w.LU, n, N, w.Uinv, w.Ug, w.r, w.d, nrhs, w.tsync + 1 + static_cast<size_t>(nblk) * G, err);
+  ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Uinv, w.Ug, w.y1, w.d,
+                                                              nrhs, w.tsync + 1, err);
   return last_launch_status();
 }
 

@@ -505,6 +505,17 @@ def main():
             "ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12,
             "bf16_TFLOP/s": md * flops / (t * 1e-3) / 1e12,
             "vs_separate_split": variants[f"x{md}_{m}x{n}x{k}"]["ms"] / t}
+    # Sec. II-G's asymmetric split (A two pieces, B three; five products) and
+    # Sec. IV-A's FP64 collection ("d", one accumulator per product, C in FP64)
+    t = time_call(lambda: bfx.gemm_bf16xN(bfx.BFX_X5, A, B, C, workspace=ws))
+    variants[f"x5_asym_2x3_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
+    C64o = torch.empty((m, n), dtype=torch.float64, device=dev)
+    for md in (3, 6):
+        t = time_call(lambda: bfx.gemm_bf16xN_f64(md, A, B, C64o, workspace=ws))
+        variants[f"x{md}d_f64_collect_{m}x{n}x{k}"] = {
+            "ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12,
+            "bf16_TFLOP/s": md * flops / (t * 1e-3) / 1e12}
+    del C64o
     t = time_call(lambda: bfx.sgemm_simt(A, B, C), reps=2, warm=1)
     variants[f"fp32_simt_{m}x{n}x{k}"] = {"ms": t, "TFLOP/s": flops / (t * 1e-3) / 1e12}
     ts = (16384, 16384, 256)

@@ -60,11 +60,18 @@ typedef enum bfx_status {
  *   BFX_X8   : + mid*lo + lo*mid, the 2^-24 bin Z3      (triple split; Sec. II-D's
  *              Z0 + (Z1 + (Z2 + Z3)), "might offer higher accuracy than FP32")
  *   BFX_X9   : all nine products                       (triple split)
+ *   BFX_X5   : A split in two pieces, B in three: hi*hi, hi*mid, mid*hi,
+ *              hi*lo, mid*mid (Sec. II-G's asymmetric case).  GEMM entry
+ *              points only (bfx_gemm_bf16xN, bfx_gemm_presplit,
+ *              bfx_gemm_bf16xN_f64); the others return BFX_EINVAL.  Its
+ *              accuracy is bounded by A's dropped third piece (~2^-16 |a|),
+ *              as for X3, unless A has at most 16 significant bits.
  * The mode's value is the number of bfloat16 products per scalar product. */
 typedef enum bfx_mode {
   BFX_FP32 = 0,
   BFX_X1 = 1,
   BFX_X3 = 3,
+  BFX_X5 = 5,
   BFX_X6 = 6,
   BFX_X8 = 8,
   BFX_X9 = 9
@@ -148,7 +155,8 @@ BFX_API bfx_status bfx_gemm_bf16xN_fused(bfx_mode mode, int64_t m, int64_t n, in
  * bfloat16 (row-major, leading dimension lda_p, plane p at d_Ap + p*a_plane),
  * d_Btp: npieces planes of the TRANSPOSED right operand, n x k (leading
  * dimension ldb_p, plane stride b_plane), e.g. from bfx_split /
- * bfx_split_transpose.  npieces(mode) = 1, 2, 3, 3 for X1, X3, X6, X9.
+ * bfx_split_transpose.  npieces(mode) = 1, 2, 3, 3, 3 for X1, X3, X6, X8, X9;
+ * X5 reads 2 planes of A and 3 of B.
  * Requirements of the tensor-memory-access (TMA) descriptors: lda_p, ldb_p,
  * a_plane and b_plane multiples of 8 elements, both base pointers 16-byte
  * aligned; otherwise BFX_EUNSUPPORTED.  mode must be X1..X9 (BFX_EINVAL). */
@@ -156,6 +164,21 @@ BFX_API bfx_status bfx_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_
                                      const uint16_t* d_Ap, int64_t lda_p, int64_t a_plane,
                                      const uint16_t* d_Btp, int64_t ldb_p, int64_t b_plane,
                                      float beta, float* d_C, int64_t ldc, bfx_stream stream);
+
+/* The "d" variant of Sec. IV-A: the same bfloat16 products, each accumulated
+ * in FP32 in its own tensor-memory accumulator, then added together in FP64
+ * in Sec. II-D's order, smallest level first (Z1 = Z01 + Z10,
+ * Z2 = Z02 + (Z11 + Z20), Z3 = Z12 + Z21, Z4 = Z22,
+ * C = Z0 + (Z1 + (Z2 + (Z3 + Z4))), the levels the mode has), and stored in
+ * FP64 without a final rounding to FP32: C = A B (no alpha, beta).
+ * d_C: m x n FP64, row-major, leading dimension ldc (>= n).  mode: X1, X3,
+ * X5, X6, X8, X9 (else BFX_EINVAL; FP32 has no pieces).  k must be >= 1.
+ * Workspace as bfx_gemm_bf16xN (bfx_gemm_workspace_size).  Errors as
+ * bfx_gemm_bf16xN. */
+BFX_API bfx_status bfx_gemm_bf16xN_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k,
+                                       const float* d_A, int64_t lda, const float* d_B,
+                                       int64_t ldb, double* d_C, int64_t ldc, void* d_ws,
+                                       size_t ws_bytes, bfx_stream stream);
 
 /* Workspace-free variant of bfx_gemm_bf16xN (same arguments minus the
  * workspace, same result).  The paper has no counterpart: this exists for

@@ -29,7 +29,7 @@ from . import build as _build
 
 _lib = None
 
-MODES = (0, 1, 3, 6, 9)  # 0 = plain FP32 FMA; 1/3/6/9 = bf16x1/x3/x6/x9
+MODES = (0, 1, 3, 5, 6, 8, 9)  # 0 = plain FP32 FMA; else the number of bf16 products
 PIECES = {1: 1, 3: 2, 6: 3, 9: 3}
 
 
@@ -122,8 +122,9 @@ def split_bits_range(start: int, count: int, npieces: int = 3):
 def gemm(mode: int, A, B, alpha: float = 1.0, beta: float = 0.0, C=None, sum64: bool = False):
     """C = alpha * (A B by the mode's products) + beta * C, FP32 in / out.
 
-    mode 0: plain FP32 FMA accumulation (Sec. II-C); 1/3/6/9: bf16x1/x3/x6/x9
-    (Sec. II-D, II-G); ``sum64`` is the FP64 final collection ("d" variant).
+    mode 0: plain FP32 FMA accumulation (Sec. II-C); 1/3/6/8/9: bf16x1 .. x9
+    (Sec. II-D, II-G); 5: A in two pieces, B in three (Sec. II-G's asymmetric
+    case); ``sum64`` is the FP64 final collection ("d" variant).
     """
     A = _f32(A)
     B = _f32(B)

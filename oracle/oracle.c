@@ -24,6 +24,9 @@
  *     x6 = {00,01,10,02,11,20}; x8 = x6 + {12,21} (the "Z3" sum of
  *     Sec. II-D); x9 = all nine; level sums and the smallest-first
  *     combination exactly as written in Sec. II-D.
+ *  R25 the asymmetric split of Sec. II-G: x5 = A in two pieces, B in three,
+ *     the five products {00,01,10,02,11} (the 2^-16 bin without a2 b0,
+ *     since A has no a2); combined as x6 with Z2 = Z02 + Z11.
  *  R9 refinement: r = b - A x (the paper's sign slip in Sec. III corrected),
  *     residual, correction solve and update all in FP64 with the low-precision
  *     factors (Sec. III: "do the solve in a higher precision like FP64").
@@ -170,6 +173,7 @@ static int mode_pieces(int mode) {
   switch (mode) {
     case 1: return 1;
     case 3: return 2;
+    case 5: return 3; /* B's pieces; A has two (mode_pieces_a) */
     case 6: return 3;
     case 8: return 3;
     case 9: return 3;
@@ -177,11 +181,15 @@ static int mode_pieces(int mode) {
   }
 }
 
-/* is product (i,j) used by the mode (R6) */
+/* pieces of the left operand A (R25: x5 splits A in two) */
+static int mode_pieces_a(int mode) { return mode == 5 ? 2 : mode_pieces(mode); }
+
+/* is product (i,j) used by the mode (R6, R25) */
 static int mode_uses(int mode, int i, int j) {
   switch (mode) {
     case 1: return i == 0 && j == 0;
     case 3: return i + j <= 1;
+    case 5: return i <= 1 && i + j <= 2;
     case 6: return i + j <= 2;
     case 8: return i + j <= 3;
     case 9: return 1;
@@ -209,7 +217,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
       }
     return 0;
   }
-  int np = mode_pieces(mode);
+  int np = mode_pieces(mode), npa = mode_pieces_a(mode);
   if (np == 0) return 1;
   /* pieces, widened to FP32 (exact) */
   float* Ap = (float*)malloc(sizeof(float) * 3 * (size_t)(m * k + 1));
@@ -220,7 +228,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
       uint16_t p[3];
       split_one(A[i * lda + l], &p[0], &p[1], &p[2]);
       for (int q = 0; q < 3; ++q)
-        Ap[(size_t)q * m * k + i * k + l] = (q < np) ? bf16_to_f32(p[q]) : 0.0f;
+        Ap[(size_t)q * m * k + i * k + l] = (q < npa) ? bf16_to_f32(p[q]) : 0.0f;
     }
   for (int64_t l = 0; l < k; ++l)
     for (int64_t j = 0; j < n; ++j) {
@@ -252,6 +260,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
         switch (mode) {
           case 1: zr = Z0; break;
           case 3: zr = Z0 + Z1; break;
+          case 5: zr = Z0 + (Z1 + (Z[0][2] + Z[1][1])); break;
           case 6: zr = Z0 + (Z1 + Z2); break;
           case 8: zr = Z0 + (Z1 + (Z2 + Z3)); break;
           default: zr = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
@@ -269,6 +278,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
         switch (mode) {
           case 1: zd = Z0; break;
           case 3: zd = Z0 + Z1; break;
+          case 5: zd = Z0 + (Z1 + ((double)Z[0][2] + (double)Z[1][1])); break;
           case 6: zd = Z0 + (Z1 + Z2); break;
           case 8: zd = Z0 + (Z1 + (Z2 + Z3)); break;
           default: zd = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;

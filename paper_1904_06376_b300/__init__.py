@@ -11,6 +11,7 @@ from ._bfx import (  # noqa: F401
     BFX_FP32,
     BFX_X1,
     BFX_X3,
+    BFX_X5,
     BFX_X6,
     BFX_X8,
     BFX_X9,
@@ -18,11 +19,13 @@ from ._bfx import (  # noqa: F401
     BatchConfig,
     batch_autotune,
     BfxError,
+    GEMM_PIECES,
     GMRES_MAX_M,
     IrParams,
     device_error,
     dot_bf16xN,
     gemm_bf16xN,
+    gemm_bf16xN_f64,
     gemm_bf16xN_fused,
     gemm_presplit,
     gemm_workspace_size,

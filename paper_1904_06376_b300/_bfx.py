@@ -13,8 +13,11 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "libbfx.so")
 
-BFX_FP32, BFX_X1, BFX_X3, BFX_X6, BFX_X8, BFX_X9 = 0, 1, 3, 6, 8, 9
+BFX_FP32, BFX_X1, BFX_X3, BFX_X5, BFX_X6, BFX_X8, BFX_X9 = 0, 1, 3, 5, 6, 8, 9
 PIECES = {BFX_X1: 1, BFX_X3: 2, BFX_X6: 3, BFX_X8: 3, BFX_X9: 3}
+# pieces of (A, B) a GEMM mode reads; X5 is the asymmetric 2 x 3 split
+GEMM_PIECES = {BFX_X1: (1, 1), BFX_X3: (2, 2), BFX_X5: (2, 3), BFX_X6: (3, 3), BFX_X8: (3, 3),
+               BFX_X9: (3, 3)}
 
 _STATUS = {
     0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA error",
@@ -56,6 +59,7 @@ def lib() -> ctypes.CDLL:
         "bfx_gemm_workspace_size": (sz, [i32, i64, i64, i64]),
         "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
         "bfx_gemm_bf16xN_fused": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
+        "bfx_gemm_bf16xN_f64": (i32, [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, sz, vp]),
         "bfx_gemm_presplit": (i32, [i32, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, vp]),
         "bfx_sgemm_simt": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
         "bfx_dot_workspace_size": (sz, []),
@@ -175,6 +179,29 @@ def gemm_bf16xN(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = N
     _check("bfx_gemm_bf16xN", lib().bfx_gemm_bf16xN(mode, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
                                                    beta, _ptr(C), ldc, ws_ptr, ws_bytes,
                                                    _stream(stream)))
+    return C
+
+
+def gemm_bf16xN_f64(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None,
+                    workspace: torch.Tensor = None, stream=None):
+    """C = A B with the mode's partial products added in FP64 and kept in FP64
+    (the "d" variant of Sec. IV-A).  C: float64 (m, n)."""
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    wsb = gemm_workspace_size(mode, m, n, k)
+    if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    ws_bytes = workspace.numel() * workspace.element_size() if wsb else 0
+    lda = A.stride(0) if m and k else max(k, 1)
+    ldb = B.stride(0) if k and n else max(n, 1)
+    ldc = C.stride(0) if m and n else max(n, 1)
+    _check("bfx_gemm_bf16xN_f64",
+           lib().bfx_gemm_bf16xN_f64(mode, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
+                                     _ptr(workspace) if wsb else None, ws_bytes, _stream(stream)))
     return C
 
 

@@ -23,8 +23,20 @@ int current_device() {
 }
 
 bool check_mode(bfx_mode mode) {
-  return mode == BFX_FP32 || mode == BFX_X1 || mode == BFX_X3 || mode == BFX_X6 || mode == BFX_X8 ||
-         mode == BFX_X9;
+  return mode == BFX_FP32 || mode == BFX_X1 || mode == BFX_X3 || mode == BFX_X5 ||
+         mode == BFX_X6 || mode == BFX_X8 || mode == BFX_X9;
+}
+
+// Pieces of A and of B a GEMM mode reads (x5: two and three); false if the
+// mode has no tensor-core GEMM.
+bool gemm_pieces(bfx_mode mode, int* npa, int* npb) {
+  if (mode == BFX_X5) {
+    *npa = 2;
+    *npb = 3;
+    return true;
+  }
+  *npa = *npb = mode_pieces(mode);
+  return *npa > 0;
 }
 
 }  // namespace
@@ -144,23 +156,25 @@ BFX_API bfx_status bfx_split_transpose(int64_t rows, int64_t cols, const float* 
                                 static_cast<cudaStream_t>(stream));
 }
 
-// Workspace of bfx_gemm_bf16xN: np planes of A pieces (m x kp) followed by np
-// planes of transposed B pieces (n x kp), kp = k rounded up to 8, every plane
-// starting on a 256-byte boundary.
-static void gemm_ws_layout(int np, int64_t m, int64_t n, int64_t k, int64_t* kp,
+// Workspace of bfx_gemm_bf16xN: npa planes of A pieces (m x kp) followed by
+// npb planes of transposed B pieces (n x kp), kp = k rounded up to 8, every
+// plane starting on a 256-byte boundary.
+static void gemm_ws_layout(int npa, int npb, int64_t m, int64_t n, int64_t k, int64_t* kp,
                            int64_t* a_plane, int64_t* b_plane, size_t* bytes) {
   *kp = round_up(k > 0 ? k : 1, 8);
   *a_plane = round_up(m * *kp, 128);
   *b_plane = round_up(n * *kp, 128);
-  *bytes = static_cast<size_t>(np) * static_cast<size_t>(*a_plane + *b_plane) * 2;
+  *bytes = (static_cast<size_t>(npa) * static_cast<size_t>(*a_plane) +
+            static_cast<size_t>(npb) * static_cast<size_t>(*b_plane)) *
+           2;
 }
 
 BFX_API size_t bfx_gemm_workspace_size(bfx_mode mode, int64_t m, int64_t n, int64_t k) {
-  const int np = mode_pieces(mode);
-  if (np == 0 || m <= 0 || n <= 0 || k <= 0) return 0;
+  int npa, npb;
+  if (!gemm_pieces(mode, &npa, &npb) || m <= 0 || n <= 0 || k <= 0) return 0;
   int64_t kp, ap, bp;
   size_t bytes;
-  gemm_ws_layout(np, m, n, k, &kp, &ap, &bp, &bytes);
+  gemm_ws_layout(npa, npb, m, n, k, &kp, &ap, &bp, &bytes);
   return bytes;
 }
 
@@ -188,16 +202,16 @@ BFX_API bfx_status bfx_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_
                                      const uint16_t* d_Ap, int64_t lda_p, int64_t a_plane,
                                      const uint16_t* d_Btp, int64_t ldb_p, int64_t b_plane,
                                      float beta, float* d_C, int64_t ldc, bfx_stream stream) {
-  const int np = mode_pieces(mode);
-  if (np == 0) return BFX_EINVAL;
+  int npa, npb;
+  if (!gemm_pieces(mode, &npa, &npb)) return BFX_EINVAL;
   bfx_status st = check_gemm_args(m, n, k, d_Ap, lda_p, d_Btp, ldb_p, d_C, ldc);
   if (st != BFX_OK) return st;
   if (m == 0 || n == 0) return BFX_OK;
   if (k > 0) {
     if (ldb_p < k) return BFX_EINVAL;
-    if (np > 1 && (a_plane < (m - 1) * lda_p + k || b_plane < (n - 1) * ldb_p + k))
+    if ((npa > 1 && a_plane < (m - 1) * lda_p + k) || (npb > 1 && b_plane < (n - 1) * ldb_p + k))
       return BFX_EINVAL;
-    if (lda_p % 8 || ldb_p % 8 || (np > 1 && (a_plane % 8 || b_plane % 8)) ||
+    if (lda_p % 8 || ldb_p % 8 || (npa > 1 && a_plane % 8) || (npb > 1 && b_plane % 8) ||
         !aligned(d_Ap, 16) || !aligned(d_Btp, 16))
       return BFX_EUNSUPPORTED;
   }
@@ -205,6 +219,27 @@ BFX_API bfx_status bfx_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_
   if (!is_sm103()) return BFX_EUNSUPPORTED;
   return launch_gemm_presplit(mode, m, n, k, alpha, d_Ap, lda_p, a_plane, d_Btp, ldb_p, b_plane,
                               beta, d_C, ldc, static_cast<cudaStream_t>(stream));
+}
+
+// Splits A (npa pieces) and the transpose of B (npb pieces) into the
+// workspace laid out as gemm_ws_layout says.
+static bfx_status split_operands(bfx_mode mode, int64_t m, int64_t n, int64_t k, const float* d_A,
+                                 int64_t lda, const float* d_B, int64_t ldb, void* d_ws,
+                                 size_t ws_bytes, uint16_t** Ap, uint16_t** Bp, int64_t* kp,
+                                 int64_t* ap, int64_t* bp, cudaStream_t s) {
+  int npa, npb;
+  if (!gemm_pieces(mode, &npa, &npb)) return BFX_EINVAL;
+  size_t need;
+  gemm_ws_layout(npa, npb, m, n, k, kp, ap, bp, &need);
+  if (!d_ws || ws_bytes < need) return BFX_ENOMEM;
+  if (!aligned(d_ws, 256)) return BFX_EUNSUPPORTED;
+  *Ap = static_cast<uint16_t*>(d_ws);
+  *Bp = *Ap + npa * *ap;
+  bfx_status st = launch_split(m, k, d_A, lda, npa, *Ap, npa > 1 ? *Ap + *ap : nullptr,
+                               npa > 2 ? *Ap + 2 * *ap : nullptr, *kp, s);
+  if (st != BFX_OK) return st;
+  return launch_split_transpose(k, n, d_B, ldb, npb, *Bp, npb > 1 ? *Bp + *bp : nullptr,
+                                npb > 2 ? *Bp + 2 * *bp : nullptr, *kp, s);
 }
 
 BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
@@ -222,21 +257,33 @@ BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t 
   if (ldb < n) return BFX_EINVAL;
   if (m >= INT32_MAX || n >= INT32_MAX || k >= INT32_MAX) return BFX_EUNSUPPORTED;
   if (!is_sm103()) return BFX_EUNSUPPORTED;
-  const int np = mode_pieces(mode);
   int64_t kp, ap, bp;
-  size_t need;
-  gemm_ws_layout(np, m, n, k, &kp, &ap, &bp, &need);
-  if (!d_ws || ws_bytes < need) return BFX_ENOMEM;
-  if (!aligned(d_ws, 256)) return BFX_EUNSUPPORTED;
-  uint16_t* Ap = static_cast<uint16_t*>(d_ws);
-  uint16_t* Bp = Ap + np * ap;
-  st = launch_split(m, k, d_A, lda, np, Ap, np > 1 ? Ap + ap : nullptr,
-                    np > 2 ? Ap + 2 * ap : nullptr, kp, s);
-  if (st != BFX_OK) return st;
-  st = launch_split_transpose(k, n, d_B, ldb, np, Bp, np > 1 ? Bp + bp : nullptr,
-                              np > 2 ? Bp + 2 * bp : nullptr, kp, s);
-  if (st != BFX_OK) return st;
+  uint16_t *Ap, *Bp;
+  if ((st = split_operands(mode, m, n, k, d_A, lda, d_B, ldb, d_ws, ws_bytes, &Ap, &Bp, &kp, &ap,
+                           &bp, s)) != BFX_OK)
+    return st;
   return launch_gemm_presplit(mode, m, n, k, alpha, Ap, kp, ap, Bp, kp, bp, beta, d_C, ldc, s);
+}
+
+BFX_API bfx_status bfx_gemm_bf16xN_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k,
+                                       const float* d_A, int64_t lda, const float* d_B,
+                                       int64_t ldb, double* d_C, int64_t ldc, void* d_ws,
+                                       size_t ws_bytes, bfx_stream stream) {
+  int npa, npb;
+  if (!gemm_pieces(mode, &npa, &npb)) return BFX_EINVAL;
+  if (m < 0 || n < 0 || k < 0) return BFX_EINVAL;
+  if (m == 0 || n == 0) return BFX_OK;
+  if (ldc < n || !d_C || k == 0 || !d_A || !d_B || lda < k || ldb < n) return BFX_EINVAL;
+  if (m >= INT32_MAX || n >= INT32_MAX || k >= INT32_MAX) return BFX_EUNSUPPORTED;
+  if (!is_sm103()) return BFX_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t kp, ap, bp;
+  uint16_t *Ap, *Bp;
+  bfx_status st;
+  if ((st = split_operands(mode, m, n, k, d_A, lda, d_B, ldb, d_ws, ws_bytes, &Ap, &Bp, &kp, &ap,
+                           &bp, s)) != BFX_OK)
+    return st;
+  return launch_gemm_f64(mode, m, n, k, Ap, kp, ap, Bp, kp, bp, d_C, ldc, s);
 }
 
 BFX_API bfx_status bfx_gemm_bf16xN_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k,

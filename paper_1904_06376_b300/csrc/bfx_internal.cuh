@@ -133,6 +133,11 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,
                                 const uint16_t* Btp, int64_t ldb_p, int64_t b_plane, float beta,
                                 float* C, int64_t ldc, cudaStream_t s);
+// FP64 collection of the mode's partial products (Sec. IV-A "d"); same piece
+// layout as launch_gemm_presplit, C is FP64.
+bfx_status launch_gemm_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k, const uint16_t* Ap,
+                           int64_t lda_p, int64_t a_plane, const uint16_t* Btp, int64_t ldb_p,
+                           int64_t b_plane, double* C, int64_t ldc, cudaStream_t s);
 
 // ---------------------------------------------------------------- device side
 #if defined(__CUDACC__)

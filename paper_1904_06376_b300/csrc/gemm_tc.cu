@@ -3,7 +3,9 @@
 // C = alpha * Z + beta * C with Z the sum of the mode's bfloat16 piece
 // products (Sec. II-D, II-G of the paper):
 //   x1: a0 b0;  x3: + a0 b1 + a1 b0;  x6: + a0 b2 + a1 b1 + a2 b0;
-//   x8: + a1 b2 + a2 b1 (the Z3 sum of Sec. II-D);  x9: all.
+//   x8: + a1 b2 + a2 b1 (the Z3 sum of Sec. II-D);  x9: all;
+//   x5: A split in two pieces, B in three (Sec. II-G's asymmetric case):
+//       a0 b0, a0 b1, a1 b0, a0 b2, a1 b1.
 // Each product of two bfloat16 values is exact in FP32 (Sec. I) and the
 // tensor core accumulates in FP32, the precision the paper's FMA model uses.
 //
@@ -30,6 +32,11 @@
 //             alpha/beta, store; releases the accumulator (`acc_empty`) as
 //             soon as it has been read so the next tile's MMAs overlap the
 //             stores.
+// FP64-collection variant (D64 = true, the "d" of Sec. IV-A): every product
+// gets its own FP32 accumulator in tensor memory and the epilogue adds the
+// partial products in FP64, in Sec. II-D's order (Z1 = Z01 + Z10,
+// Z2 = Z02 + (Z11 + Z20), Z3 = Z12 + Z21, Z4 = Z22, Z = Z0 + (Z1 + (Z2 + (Z3 +
+// Z4)))), and stores C in FP64 without a final rounding to FP32.
 // Fused variant (FUSED = true): warp 0 loads FP32 tiles of A (128 x 16) and
 // B (16 x BN) by TMA into a ring of FP32 stages; sixteen converter warps split
 // each element in registers into its bfloat16 pieces (the same per-element
@@ -55,13 +62,21 @@ struct Prod {
   int a, b, acc;  // piece of A, piece of B, accumulator (0 = main, 1 = correction)
 };
 
-__host__ __device__ constexpr int mode_np(int mode) { return mode == 1 ? 1 : (mode == 3 ? 2 : 3); }
+// pieces of A and of B the mode reads
+__host__ __device__ constexpr int mode_npa(int mode) {
+  return mode == 1 ? 1 : ((mode == 3 || mode == 5) ? 2 : 3);
+}
+__host__ __device__ constexpr int mode_npb(int mode) { return mode == 1 ? 1 : (mode == 3 ? 2 : 3); }
 
 // Issue order of the products: corrections smallest bin first, hi*hi last.
 __host__ __device__ constexpr Prod prod_of(int mode, int i) {
   if (mode == 1) return Prod{0, 0, 0};
   if (mode == 3) {
     const Prod p[3] = {{1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+    return p[i];
+  }
+  if (mode == 5) {
+    const Prod p[5] = {{0, 2, 1}, {1, 1, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
     return p[i];
   }
   if (mode == 6) {
@@ -77,6 +92,13 @@ __host__ __device__ constexpr Prod prod_of(int mode, int i) {
                      {0, 2, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 0}};
   return p[i];
 }
+// Index of product (a, b) in the mode's issue order (-1 if unused); with
+// D64 it is also the product's accumulator.
+__host__ __device__ constexpr int prod_slot(int mode, int a, int b) {
+  for (int i = 0; i < mode; ++i)
+    if (prod_of(mode, i).a == a && prod_of(mode, i).b == b) return i;
+  return -1;
+}
 // Is product i the first one written into its accumulator?
 __host__ __device__ constexpr bool first_in_acc(int mode, int i) {
   for (int j = 0; j < i; ++j)
@@ -89,8 +111,9 @@ struct TcArgs {
   int tiles_m, tiles_n, num_tiles, k_tiles;
   float alpha, beta;
   float* C;
+  double* Cd;  // D64: the FP64 result (alpha, beta unused)
   int64_t ldc;
-  int vec_c;  // C rows 16-byte aligned: float4 loads/stores
+  int vec_c;  // C rows 16-byte aligned: float4 (double2) loads/stores
   int* err;
   // grouped mode: many independent problems in one launch
   const GroupTile* tiles;   // num_tiles entries
@@ -151,18 +174,27 @@ __device__ __forceinline__ TileInfo get_tile<true>(int t, const TcArgs& a) {
   return ti;
 }
 
-template <int MODE, int BN, int BK, int STAGES, bool FUSED = false>
+__host__ __device__ constexpr uint32_t pow2_cols(uint32_t c) {
+  uint32_t p = 32;
+  while (p < c) p *= 2;
+  return p;
+}
+
+template <int MODE, int BN, int BK, int STAGES, bool FUSED = false, bool D64 = false>
 struct TcConfig {
-  static constexpr int NP = mode_np(MODE);
+  static constexpr int NPA = mode_npa(MODE);
+  static constexpr int NPB = mode_npb(MODE);
+  static constexpr int NP = NPA;  // fused: both operands alike
   static constexpr int NPROD = MODE;
-  static constexpr int NACC = (MODE == 1) ? 1 : 2;
+  static constexpr int NACC = D64 ? MODE : ((MODE == 1) ? 1 : 2);
   static constexpr int ACC_BUFS = (NACC * BN * 2 <= 512) ? 2 : 1;
-  static constexpr uint32_t TMEM_COLS = NACC * BN * ACC_BUFS;
+  static constexpr uint32_t TMEM_USED = NACC * BN * ACC_BUFS;
+  static constexpr uint32_t TMEM_COLS = pow2_cols(TMEM_USED);
   static constexpr int SW = BK * 2;  // swizzle span = bytes of one K-slice row
   static constexpr uint32_t A_TILE = BM * BK * 2;
   static constexpr uint32_t B_TILE = BN * BK * 2;
-  static constexpr uint32_t STAGE_A = NP * A_TILE;
-  static constexpr uint32_t STAGE = NP * (A_TILE + B_TILE);
+  static constexpr uint32_t STAGE_A = NPA * A_TILE;
+  static constexpr uint32_t STAGE = NPA * A_TILE + NPB * B_TILE;
   // fused: FP32 stages of 16 K-columns (A 128 x 16 with 64-byte swizzle, B 16 x BN plain)
   static constexpr int KF = 16;
   static constexpr uint32_t A32_TILE = BM * KF * 4;
@@ -178,9 +210,8 @@ struct TcConfig {
   static_assert(SW == 64 || SW == 128, "BK must be 32 or 64 bfloat16");
   static_assert(A32_TILE % 1024 == 0, "FP32 stage parts keep the 1024-byte alignment");
   static_assert(!FUSED || (BK == 32 && BN == 256), "fused: BK 32 (two FP32 stages a K-slice), BN 256");
-  static_assert(TMEM_COLS == 32 || TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
-                    TMEM_COLS == 512,
-                "tensor memory allocation must be a power of two");
+  static_assert(!FUSED || (NPA == NPB && !D64), "fused: symmetric modes, FP32 result");
+  static_assert(TMEM_USED <= 512, "tensor memory: 512 columns");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
   static_assert(SMEM <= 232448, "shared memory");
   static_assert((2 * STAGES + 2 * S32 + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
@@ -294,11 +325,70 @@ __device__ __forceinline__ void convert_half(const uint8_t* st32, uint8_t* pst, 
   }
 }
 
-template <int MODE, int BN, int BK, int STAGES, bool GROUPED, bool FUSED = false>
-__global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED>::THREADS, 1)
+// D64 epilogue: the FP64 combination of Sec. II-D for 16 columns of one row
+// (chunk c), each partial product read from its own accumulator.
+template <int MODE, int BN>
+__device__ __forceinline__ void sum_products_f64(uint32_t tb, int c, double (&z)[16]) {
+  float u[16], w[16];
+  auto ld = [&](int a, int b, float (&v)[16]) {
+    tmem_ld16_wait(tb + static_cast<uint32_t>(prod_slot(MODE, a, b) * BN + c * 16), v);
+  };
+  bool has = false;  // z holds the sum of the smaller levels
+  auto add_level = [&](const double (&lv)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = has ? lv[i] + z[i] : lv[i];
+    has = true;
+  };
+  double lv[16];
+  if constexpr (MODE == 9) {  // Z4 = Z22
+    ld(2, 2, u);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]);
+    add_level(lv);
+  }
+  if constexpr (MODE >= 8) {  // Z3 = Z12 + Z21
+    ld(1, 2, u);
+    ld(2, 1, w);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]) + widen(w[i]);
+    add_level(lv);
+  }
+  if constexpr (MODE >= 6) {  // Z2 = Z02 + (Z11 + Z20)
+    ld(1, 1, u);
+    ld(2, 0, w);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]) + widen(w[i]);
+    ld(0, 2, u);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]) + lv[i];
+    add_level(lv);
+  }
+  if constexpr (MODE == 5) {  // Z2 = Z02 + Z11 (A has no third piece)
+    ld(0, 2, u);
+    ld(1, 1, w);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]) + widen(w[i]);
+    add_level(lv);
+  }
+  if constexpr (MODE >= 3) {  // Z1 = Z01 + Z10
+    ld(0, 1, u);
+    ld(1, 0, w);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]) + widen(w[i]);
+    add_level(lv);
+  }
+  ld(0, 0, u);  // Z = Z0 + (...)
+#pragma unroll
+  for (int i = 0; i < 16; ++i) lv[i] = widen(u[i]);
+  add_level(lv);
+}
+
+template <int MODE, int BN, int BK, int STAGES, bool GROUPED, bool FUSED = false, bool D64 = false>
+__global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs args) {
-  using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED>;
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED, D64>;
+  static_assert(!(D64 && GROUPED), "FP64 collection: single problem");
   constexpr uint32_t IDESC = idesc_bf16_f32<BM, BN>();
 
   extern __shared__ uint8_t smem_raw[];
@@ -453,8 +543,10 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED>::THREADS
               const Prod pr = prod_of(MODE, p);
               const uint64_t ad = smem_desc_kmajor<Cfg::SW>(sa + pr.a * Cfg::A_TILE + kk * 32);
               const uint64_t bd = smem_desc_kmajor<Cfg::SW>(sb + pr.b * Cfg::B_TILE + kk * 32);
-              const uint32_t accum = (kt > 0 || kk > 0 || !first_in_acc(MODE, p)) ? 1u : 0u;
-              umma_bf16_ss(d0 + static_cast<uint32_t>(pr.acc * BN), ad, bd, IDESC, accum);
+              const uint32_t accum =
+                  (kt > 0 || kk > 0 || (!D64 && !first_in_acc(MODE, p))) ? 1u : 0u;
+              umma_bf16_ss(d0 + static_cast<uint32_t>((D64 ? p : pr.acc) * BN), ad, bd, IDESC,
+                           accum);
             }
           }
           umma_commit(&empty[s]);
@@ -489,9 +581,41 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED>::THREADS
       tc_fence_after();
       const int row = mb * BM + row_in_tile;
       const bool row_ok = row < ti.M;
-      float* crow = ti.C + static_cast<int64_t>(row_ok ? row : 0) * ti.ldc;
       const uint32_t tb = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                           static_cast<uint32_t>(buf * Cfg::NACC * BN);
+      if constexpr (D64) {
+        double* drow = args.Cd + static_cast<int64_t>(row_ok ? row : 0) * args.ldc;
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+          __syncwarp();
+          double z[16];
+          sum_products_f64<MODE, BN>(tb, c, z);
+          if (c == BN / 16 - 1) {
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+          }
+          if (!row_ok) continue;
+          const int col0 = nb * BN + c * 16;
+          if (col0 >= ti.N) continue;
+          double* dst = drow + col0;
+          if (args.vec_c && col0 + 16 <= ti.N) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2)
+              *reinterpret_cast<double2*>(dst + i) = make_double2(z[i], z[i + 1]);
+          } else {
+            const int lim = min(16, ti.N - col0);
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (i < lim) dst[i] = z[i];
+          }
+        }
+        if (++buf == Cfg::ACC_BUFS) {
+          buf = 0;
+          aph ^= 1u;
+        }
+        continue;
+      }
+      float* crow = ti.C + static_cast<int64_t>(row_ok ? row : 0) * ti.ldc;
 #pragma unroll 1
       for (int c = 0; c < BN / 16; ++c) {
         __syncwarp();
@@ -594,19 +718,19 @@ bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, int BN, int BK, int STAGES>
+// C: float* (FP32 result, alpha/beta applied) or, with D64, double* (the
+// FP64 collection, alpha/beta unused).
+template <int MODE, int BN, int BK, int STAGES, bool D64 = false>
 bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* Ap, int64_t lda_p,
                   int64_t a_plane, const uint16_t* Btp, int64_t ldb_p, int64_t b_plane,
-                  float beta, float* C, int64_t ldc, cudaStream_t s) {
-  using Cfg = TcConfig<MODE, BN, BK, STAGES>;
+                  float beta, void* C, int64_t ldc, cudaStream_t s) {
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, false, D64>;
   // with a single piece only plane 0 is read; any legal plane stride will do
-  if (Cfg::NP == 1) {
-    a_plane = round_up(lda_p * m, 8);
-    b_plane = round_up(ldb_p * n, 8);
-  }
+  if (Cfg::NPA == 1) a_plane = round_up(lda_p * m, 8);
+  if (Cfg::NPB == 1) b_plane = round_up(ldb_p * n, 8);
   CUtensorMap ma, mb;
-  if (!make_piece_map(&ma, Ap, k, m, Cfg::NP, lda_p, a_plane, BK, BM)) return BFX_EUNSUPPORTED;
-  if (!make_piece_map(&mb, Btp, k, n, Cfg::NP, ldb_p, b_plane, BK, BN)) return BFX_EUNSUPPORTED;
+  if (!make_piece_map(&ma, Ap, k, m, Cfg::NPA, lda_p, a_plane, BK, BM)) return BFX_EUNSUPPORTED;
+  if (!make_piece_map(&mb, Btp, k, n, Cfg::NPB, ldb_p, b_plane, BK, BN)) return BFX_EUNSUPPORTED;
   TcArgs a;
   a.M = static_cast<int>(m);
   a.N = static_cast<int>(n);
@@ -619,14 +743,15 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
   a.k_tiles = static_cast<int>(ceil_div(k, BK));
   a.alpha = alpha;
   a.beta = beta;
-  a.C = C;
+  a.C = D64 ? nullptr : static_cast<float*>(C);
+  a.Cd = D64 ? static_cast<double*>(C) : nullptr;
   a.ldc = ldc;
-  a.vec_c = (ldc % 4 == 0) && aligned(C, 16);
+  a.vec_c = (ldc % (D64 ? 2 : 4) == 0) && aligned(C, 16);
   a.err = device_error_word();
   a.tiles = nullptr;
   a.probs = nullptr;
   if (!a.err) return BFX_ECUDA;
-  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false>;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false, false, D64>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
       cudaSuccess)
     return BFX_ECUDA;
@@ -697,11 +822,12 @@ bfx_status run_tc_grouped(int num_tiles, const GroupTile* d_tiles, const GroupPr
                           cudaStream_t s) {
   using Cfg = TcConfig<MODE, BN, BK, STAGES>;
   CUtensorMap ma, mb;
+  static_assert(Cfg::NPA == Cfg::NPB, "grouped: symmetric modes");
   if (!make_piece_map(&ma, Apack, kp, a_rows, static_cast<int>(planes), kp, a_rows * kp, BK, BM,
-                      Cfg::NP))
+                      Cfg::NPA))
     return BFX_EUNSUPPORTED;
   if (!make_piece_map(&mb, Bpack, kp, b_rows, static_cast<int>(planes), kp, b_rows * kp, BK, BN,
-                      Cfg::NP))
+                      Cfg::NPB))
     return BFX_EUNSUPPORTED;
   TcArgs a{};
   a.num_tiles = num_tiles;
@@ -811,6 +937,9 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
     case BFX_X3:
       return run_tc<3, 256, 32, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
                                    C, ldc, s);
+    case BFX_X5:
+      return run_tc<5, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
+                                   C, ldc, s);
     case BFX_X6:
       return run_tc<6, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
                                    C, ldc, s);
@@ -820,6 +949,36 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
     case BFX_X9:
       return run_tc<9, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
                                    C, ldc, s);
+    default:
+      return BFX_EINVAL;
+  }
+}
+
+// The FP64 collection ("d", Sec. IV-A): one accumulator per product, so the
+// tile is 64 columns wide (32 for x9) to fit tensor memory's 512 columns.
+bfx_status launch_gemm_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k, const uint16_t* Ap,
+                           int64_t lda_p, int64_t a_plane, const uint16_t* Btp, int64_t ldb_p,
+                           int64_t b_plane, double* C, int64_t ldc, cudaStream_t s) {
+  if (m == 0 || n == 0) return BFX_OK;
+  switch (mode) {
+    case BFX_X1:
+      return run_tc<1, 64, 64, 6, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
+    case BFX_X3:
+      return run_tc<3, 64, 32, 6, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
+    case BFX_X5:
+      return run_tc<5, 64, 32, 6, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
+    case BFX_X6:
+      return run_tc<6, 64, 32, 5, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
+    case BFX_X8:
+      return run_tc<8, 64, 32, 5, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
+    case BFX_X9:
+      return run_tc<9, 32, 32, 6, true>(m, n, k, 1.f, Ap, lda_p, a_plane, Btp, ldb_p, b_plane,
+                                        0.f, C, ldc, s);
     default:
       return BFX_EINVAL;
   }

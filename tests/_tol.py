@@ -9,6 +9,9 @@ FP64 product of the FP32 inputs (the oracle's plain definition).
 * x3: the pair split drops the 2^-16 bin and below: 3 products each at most
   2^-16 |a0||b0| <= 2^-16 (1 + 2^-8)^2 |a||b|, so 3.03 2^-16, plus the
   accumulation term of x6.
+* x5 (A in two pieces, B in three, Sec. II-G): A's dropped third piece,
+  |a2| <= 2^-16 |a|, plus a1 b2 (<= 1.01 2^-24): 1.01 2^-16 plus the
+  accumulation term.
 * x1: one piece each, |ab - a0 b0| <= (2 + 2^-8) 2^-8 |a||b|: 2.01 2^-8 plus the
   accumulation term.
 * FP32 SIMT: gamma_k = k 2^-24 / (1 - k 2^-24) (Sec. II-C).
@@ -29,6 +32,8 @@ def tol(mode, k):
         return acc_term(k)
     if mode == 3:
         return 3.03 * 2.0 ** -16 + acc_term(k)
+    if mode == 5:
+        return 1.01 * 2.0 ** -16 + acc_term(k)
     if mode == 1:
         return 2.01 * 2.0 ** -8 + acc_term(k)
     raise ValueError(mode)

@@ -32,7 +32,7 @@ def _perm_matrix(perm):
 
 
 # ----------------------------------------------------------------- exact cases
-@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
+@pytest.mark.parametrize("mode", [1, 3, 5, 6, 8, 9])
 def test_left_permutation_exact(orc, mode):
     """C = P B with P a permutation: every row of C is exactly the sum of the
     pieces of a row of B that the mode keeps (products (0,j))."""
@@ -42,11 +42,11 @@ def test_left_permutation_exact(orc, mode):
     B = bi.wide_range((n, 17), 2, -20, 20)
     C = orc.gemm(mode, _perm_matrix(perm), B)
     b0, b1, b2 = _pieces(orc, B)
-    expect = {1: b0, 3: b0 + b1, 6: B, 8: B, 9: B}[mode][perm]
+    expect = {1: b0, 3: b0 + b1, 5: B, 6: B, 8: B, 9: B}[mode][perm]
     assert np.array_equal(C, expect)
 
 
-@pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
+@pytest.mark.parametrize("mode", [1, 3, 5, 6, 8, 9])
 def test_right_permutation_exact(orc, mode):
     """C = A Q: every column of C is exactly the kept pieces of a column of A
     (products (i,0)); catches a transposed operand or a dropped (i,0) term."""
@@ -57,7 +57,8 @@ def test_right_permutation_exact(orc, mode):
     A = bi.wide_range((13, n), 4, -20, 20)
     C = orc.gemm(mode, A, Q)
     a0, a1, a2 = _pieces(orc, A)
-    expect = {1: a0, 3: a0 + a1, 6: A, 8: A, 9: A}[mode][:, perm]
+    # x5 splits A in two pieces only (Sec. II-G's asymmetric case)
+    expect = {1: a0, 3: a0 + a1, 5: a0 + a1, 6: A, 8: A, 9: A}[mode][:, perm]
     assert np.array_equal(C, expect)
 
 
@@ -276,3 +277,45 @@ def test_x8_keeps_exactly_the_z3_bin(orc):
         assert F(x6) == F(a0) * F(b2), t
         assert x8 == float(np.float32(a0 * b2) + np.float32(a1 * b2)), t
     assert checked > 100
+
+
+# ----------------------------------------------------------------- asymmetric split
+def _sixteen_bit(shape, seed):
+    """FP32 values with at most 16 significant bits: their third piece is 0."""
+    x = bi.uniform_pm1(shape, seed)
+    return (x.view(np.uint32) & np.uint32(0xFFFFFF00)).view(np.float32)
+
+
+def test_x5_equals_x6_when_a_has_sixteen_bits(orc):
+    """Sec. II-G's 2 x 3 split keeps {00,01,10,02,11}; x6 adds a2 b0.  When A
+    has at most 16 significant bits a2 = 0, so the two modes must agree
+    exactly: a dropped or misplaced 02 / 11 term breaks the equality."""
+    A = _sixteen_bit((40, 56), 70)
+    assert not np.any(_pieces(orc, A)[2])
+    B = bi.wide_range((56, 33), 71, -12, 12)
+    C5 = orc.gemm(5, A, B)
+    assert np.array_equal(C5, orc.gemm(6, A, B))
+    assert not np.array_equal(C5, orc.gemm(3, A, B))
+    assert np.array_equal(orc.gemm_f64out(5, A, B), orc.gemm_f64out(6, A, B))
+
+
+def test_x5_accuracy_bounded_by_the_missing_third_piece(orc):
+    """Sec. II-G: with A in two pieces, the 2^-16 bin's two products cannot
+    bring the result to FP32 accuracy: A's dropped remainder a2 (|a2| <=
+    2^-16 |a|) bounds the error, |C - C64| <= (1.01 2^-16 + 2 k 2^-24)
+    (|A||B|), and the relative error stays far above x6's (>= 10x), while the
+    extra products make it smaller than x3's."""
+    k = 96
+    A = bi.uniform_pm1((64, k), 72)
+    B = bi.uniform_pm1((k, 48), 73)
+    C64 = A.astype(np.float64) @ B.astype(np.float64)
+    Cabs = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+    e = {}
+    for mode in (3, 5, 6):
+        C = orc.gemm(mode, A, B).astype(np.float64)
+        e[mode] = np.linalg.norm(C - C64) / np.linalg.norm(C64)
+        if mode == 5:
+            bound = (1.01 * 2.0**-16 + 2 * k * EPS_F) * Cabs
+            assert np.all(np.abs(C - C64) <= bound)
+    assert e[5] >= 10 * e[6], e
+    assert e[5] < e[3], e

@@ -42,6 +42,10 @@ def lib() -> ctypes.CDLL:
         vp = ctypes.c_void_p
         L.orc_bf16_rne.restype = ctypes.c_uint16
         L.orc_bf16_rne.argtypes = [f32]
+        L.orc_f16_rne_array.restype = None
+        L.orc_f16_rne_array.argtypes = [i64, vp, vp]
+        L.orc_lu_lowp.restype = i32
+        L.orc_lu_lowp.argtypes = [i32, i64, vp, i64, vp]
         L.orc_bf16_rne_array.argtypes = [i64, vp, vp]
         L.orc_split.argtypes = [i64, vp, i32, vp, vp, vp]
         L.orc_split_bits_range.argtypes = [ctypes.c_uint64, i64, i32, vp, vp, vp]
@@ -93,6 +97,38 @@ def bf16_rne(x) -> np.ndarray:
     out = np.empty(x.shape, dtype=np.uint16)
     lib().orc_bf16_rne_array(x.size, _p(x), _p(out))
     return out
+
+
+def f16_rne(x) -> np.ndarray:
+    """IEEE binary16 bit patterns of FP32 values, round to nearest even."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.uint16)
+    lib().orc_f16_rne_array(x.size, _p(x), _p(out))
+    return out
+
+
+LOWP_FP32, LOWP_BF16, LOWP_FP16 = 0, 1, 2
+
+
+def lu_lowp(typ: int, A):
+    """Single-type LU (Sec. IV-B plain IR table, reading R26): every operation
+    rounded to the type (0 FP32, 1 bfloat16, 2 binary16).  Returns the
+    factors (FP32 array of type values), ipiv (0-based) and info."""
+    LU = np.array(A, dtype=np.float32, order="C", copy=True)
+    n = LU.shape[0]
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = lib().orc_lu_lowp(int(typ), n, _p(LU), n, _p(ipiv))
+    return LU, ipiv, int(info)
+
+
+def lowp_lu_solve_ir(typ: int, A32, b, tol: float, max_iter: int = 50):
+    """The single-type LU, then the refinement of Sec. III with those factors
+    and no stall rule: converged when a correction is <= tol |x|_inf within
+    max_iter corrections (reading R26)."""
+    LU, ipiv, info = lu_lowp(typ, A32)
+    x, iters, conv, berr = solve_ir(A32, LU, ipiv, b, max_iter=max_iter, tol=tol,
+                                    tol_b=0.0, stall=float("inf"))
+    return x, int(iters[0]), int(conv[0]), info, LU, ipiv
 
 
 def bf16_to_f32(bits) -> np.ndarray:

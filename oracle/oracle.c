@@ -36,6 +36,13 @@
  *     reciprocal of the pivot as LAPACK's xGETF2 does.
  *  R13 GEMM result form C = alpha*Z + beta*C: t = fl32(alpha*Z), then
  *     fmaf(beta, C, t); beta == 0 does not read C.
+ *  R26 the single-type LU of the Sec. IV-B plain IR table ("FP32", "BF16",
+ *     "FP16" rows): A rounded to the type, then the unblocked right-looking
+ *     LU with partial pivoting in which every operation (division by the
+ *     pivot, product, difference) is done in FP32 and rounded to the type
+ *     (round to nearest even); the refinement of R9 then uses those factors
+ *     with no stall rule, converged when a correction is below the
+ *     tolerance within max_iter corrections.
  *  R18 "GMRES with the LU as preconditioner" (Sec. III remark, Sec. IV-B):
  *     left-preconditioned GMRES in FP64 solves each refinement step's
  *     correction equation; restarts recompute r = b - A x in FP64.
@@ -98,6 +105,74 @@ uint16_t orc_bf16_rne(float x) {
 
 void orc_bf16_rne_array(int64_t n, const float* x, uint16_t* out) {
   for (int64_t i = 0; i < n; ++i) out[i] = orc_bf16_rne(x[i]);
+}
+
+/* IEEE binary16 (1 sign, 5 exponent bits biased by 15, 10 fraction bits;
+ * normal binades 2^-14 .. 2^15, subnormals in steps of 2^-24) of an FP32
+ * value, rounded to nearest, ties to even, straight from the definition:
+ * |x| = m 2^e with m the 24-bit significand; the quantum of x's binade in
+ * binary16 is 2^(E-10) (E = floor(log2 |x|) >= -14) or 2^-24 below; m is
+ * shifted to that quantum with round-to-nearest-even; a carry into the next
+ * binade (and past 65504 into infinity) follows from the encoding.  NaN
+ * gives a quiet NaN with the sign kept. */
+uint16_t orc_f16_rne(float x) {
+  const uint32_t u = f32_bits(x);
+  const uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+  const uint32_t ex = (u >> 23) & 0xFFu, fr = u & 0x7FFFFFu;
+  if (ex == 0xFFu) return (uint16_t)(sign | (fr ? 0x7E00u : 0x7C00u));
+  if (ex == 0u && fr == 0u) return sign;
+  uint32_t m;
+  int e, E;
+  if (ex == 0u) { /* FP32 subnormal: far below binary16's smallest step */
+    m = fr;
+    e = -149;
+    E = -127;
+  } else {
+    m = fr | 0x800000u;
+    e = (int)ex - 150;
+    E = (int)ex - 127;
+  }
+  const int Q = (E >= -14) ? E - 10 : -24; /* exponent of the quantum */
+  const int shift = Q - e;                 /* >= 0: binary16 has fewer bits */
+  uint32_t r;
+  if (shift >= 26) {
+    r = 0u; /* below half the smallest step */
+  } else if (shift > 0) {
+    const uint32_t rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1);
+    r = m >> shift;
+    if (rem > half || (rem == half && (r & 1u))) ++r;
+  } else {
+    r = m << (-shift);
+  }
+  if (Q == -24) return (uint16_t)(sign | r); /* subnormal; r = 1024 is 2^-14 */
+  /* normal: r in [1024, 2048]; 2048 carries into the next binade */
+  const uint32_t bits = ((uint32_t)(E + 15) << 10) + (r - 1024u);
+  if (bits >= 0x7C00u) return (uint16_t)(sign | 0x7C00u);
+  return (uint16_t)(sign | bits);
+}
+
+/* (F32) of a binary16 bit pattern (exact). */
+static float f16_to_f32(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h & 0x8000u) << 16;
+  const uint32_t ex = (h >> 10) & 0x1Fu, fr = h & 0x3FFu;
+  if (ex == 0x1Fu) return f32_from_bits(sign | 0x7F800000u | (fr << 13));
+  if (ex == 0u) { /* zero or subnormal: fr 2^-24 */
+    const float v = (float)fr * 0x1p-24f;
+    return sign ? -v : v;
+  }
+  return f32_from_bits(sign | ((ex + 112u) << 23) | (fr << 13));
+}
+
+void orc_f16_rne_array(int64_t n, const float* x, uint16_t* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = orc_f16_rne(x[i]);
+}
+
+/* v rounded to the single type of R26: 0 FP32 (as is), 1 bfloat16,
+ * 2 binary16. */
+static float round_to_type(int type, float v) {
+  if (type == 1) return bf16_to_f32(orc_bf16_rne(v));
+  if (type == 2) return f16_to_f32(orc_f16_rne(v));
+  return v;
 }
 
 /* ------------------------------------------------------------------ */
@@ -492,6 +567,48 @@ int orc_lu(int mode, int64_t n, int64_t nb, float* A, int64_t lda, int32_t* ipiv
   return info;
 }
 
+/* Single-type LU (reading R26; the Sec. IV-B plain IR table): A (n x n,
+ * row-major, lda) is overwritten by its factors, every stored value a value
+ * of the type.  Column by column: the pivot is the first row of the largest
+ * |a| at or below the diagonal; the whole rows are swapped; each multiplier
+ * is a / pivot and each update a - l u, every operation in FP32 and rounded
+ * to the type.  An exactly zero pivot column records info = k + 1 (the
+ * first one) and is skipped, as LAPACK's xGETF2 does.  ipiv[k] = the row
+ * swapped with row k (0-based).  Returns info. */
+int orc_lu_lowp(int type, int64_t n, float* A, int64_t lda, int32_t* ipiv) {
+  int info = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) A[i * lda + j] = round_to_type(type, A[i * lda + j]);
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t p = k;
+    float amax = fabsf(A[k * lda + k]);
+    for (int64_t i = k + 1; i < n; ++i)
+      if (fabsf(A[i * lda + k]) > amax) {
+        amax = fabsf(A[i * lda + k]);
+        p = i;
+      }
+    ipiv[k] = (int32_t)p;
+    if (amax == 0.0f) {
+      if (!info) info = (int)(k + 1);
+      continue;
+    }
+    if (p != k)
+      for (int64_t j = 0; j < n; ++j) {
+        float t = A[k * lda + j];
+        A[k * lda + j] = A[p * lda + j];
+        A[p * lda + j] = t;
+      }
+    const float piv = A[k * lda + k];
+    for (int64_t i = k + 1; i < n; ++i) {
+      const float l = round_to_type(type, A[i * lda + k] / piv);
+      A[i * lda + k] = l;
+      for (int64_t j = k + 1; j < n; ++j)
+        A[i * lda + j] = round_to_type(type, A[i * lda + j] - round_to_type(type, l * A[k * lda + j]));
+    }
+  }
+  return info;
+}
+
 /* ------------------------------------------------------------------ */
 /* O7  residual-form iterative refinement (Sec. III, reading R9).        */
 /* A32 (n x n, FP32, the problem matrix), b (n x nrhs, FP64), x (out).    */
@@ -561,7 +678,7 @@ void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const 
         if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
       }
       ++it;
-      if (!(dn == dn) || !(xn == xn)) break;        /* NaN: diverged */
+      if (!isfinite(dn) || !isfinite(xn)) break;    /* NaN or Inf: diverged */
       if (dn <= tol * xn) { ok = 1; break; }
       if (dn >= stall * dprev) { stalled = 1; break; }
       dprev = dn;
@@ -725,7 +842,7 @@ void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, 
         if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
       }
       ++it;
-      if (!(dn == dn) || !(xn == xn)) break;
+      if (!isfinite(dn) || !isfinite(xn)) break; /* NaN or Inf: diverged */
       if (dn <= tol * xn) { ok = 1; break; }
       if (dn >= stall * dprev) { stalled = 1; break; }
       dprev = dn;

@@ -672,13 +672,15 @@ void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const 
       }
       lu32_solve64(n, LU, ldlu, ipiv, r);
       double dn = 0.0, xn = 0.0;
+      int bad = 0; /* a NaN or Inf entry: the max below would skip a NaN */
       for (int64_t i = 0; i < n; ++i) {
         xv[i] += r[i];
+        if (!isfinite(r[i]) || !isfinite(xv[i])) bad = 1;
         if (fabs(r[i]) > dn) dn = fabs(r[i]);
         if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
       }
       ++it;
-      if (!isfinite(dn) || !isfinite(xn)) break;    /* NaN or Inf: diverged */
+      if (bad) break; /* diverged */
       if (dn <= tol * xn) { ok = 1; break; }
       if (dn >= stall * dprev) { stalled = 1; break; }
       dprev = dn;
@@ -836,13 +838,15 @@ void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, 
       }
       kin += orc_gmres(n, A32, lda, LU, ldlu, ipiv, r, m, tau, d, NULL);
       double dn = 0.0, xn = 0.0;
+      int bad = 0; /* a NaN or Inf entry: the max below would skip a NaN */
       for (int64_t i = 0; i < n; ++i) {
         xv[i] += d[i];
+        if (!isfinite(d[i]) || !isfinite(xv[i])) bad = 1;
         if (fabs(d[i]) > dn) dn = fabs(d[i]);
         if (fabs(xv[i]) > xn) xn = fabs(xv[i]);
       }
       ++it;
-      if (!isfinite(dn) || !isfinite(xn)) break; /* NaN or Inf: diverged */
+      if (bad) break; /* diverged */
       if (dn <= tol * xn) { ok = 1; break; }
       if (dn >= stall * dprev) { stalled = 1; break; }
       dprev = dn;

@@ -143,3 +143,15 @@ def test_single_type_ir_follows_the_tables_order(orc, kappa):
     assert b16[1] > f16[1] or b16[0] < f16[0], stats
     if kappa >= 1e3:
         assert b16[0] < 1.0, stats
+
+
+def test_ir_counts_a_nan_correction_as_divergence(orc):
+    """A NaN in the correction (factors with a NaN entry) must stop the
+    refinement unconverged: a max over |d| that skips NaN would read 0."""
+    n = 4
+    A = np.eye(n, dtype=np.float32)
+    LU = np.eye(n, dtype=np.float32)
+    LU[2, 1] = np.nan
+    x, iters, conv, _ = orc.solve_ir(A, LU, np.arange(n, dtype=np.int32), np.ones(n), max_iter=50,
+                                     tol=1e-12, tol_b=0.0, stall=float("inf"))
+    assert conv[0] == 0 and iters[0] == 1

@@ -330,6 +330,72 @@ def bench_accuracy(bfx, oracle, bi, dev, size=2048, rows=256):
     return {"size": size, "rows_sampled": rows, "relative_frobenius_error": out}
 
 
+def bench_single_type_lu(bfx, oracle, bi, dev, n=50, per_kappa=100):
+    """Sec. IV-B's plain IR table on the device: 100 systems of order 50 per
+    condition number, LU computed entirely in FP32, bfloat16 or binary16 (every
+    operation rounded to the type), then FP64 residual-form refinement with the
+    tolerance cond(A) 2^-53, at most 50 corrections.  One launch (one warp per
+    system) per type and condition number."""
+    import torch
+
+    names = {bfx.LOWP_FP32: "FP32", bfx.LOWP_BF16: "BF16", bfx.LOWP_FP16: "FP16"}
+    rows = []
+    t_oracle = None
+    for kappa in (10.0, 100.0, 1000.0, 10000.0):
+        probs = [bi.svd_system(n, kappa, 9000 + int(np.log10(kappa)) * 1000 + s) for s in range(per_kappa)]
+        A = torch.from_numpy(np.stack([p.A32 for p in probs])).to(dev)
+        b = torch.from_numpy(np.stack([p.b[:, 0] for p in probs])).to(dev)
+        tol = torch.full((per_kappa,), kappa * 2.0 ** -53, dtype=torch.float64, device=dev)
+        for typ in (bfx.LOWP_FP32, bfx.LOWP_BF16, bfx.LOWP_FP16):
+            bfx.lowp_lu_ir_batched(typ, A, b, tol)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, iters, conv, info = bfx.lowp_lu_ir_batched(typ, A, b, tol)
+            e1.record()
+            torch.cuda.synchronize()
+            it, cv = iters.cpu().numpy(), conv.cpu().numpy().astype(bool)
+            rows.append({"precision": names[typ], "cond": kappa, "converged_pct": float(100 * cv.mean()),
+                         "mean_iterations_converged": float(it[cv].mean()) if cv.any() else None,
+                         "mean_iterations_all": float(it.mean()), "ms": e0.elapsed_time(e1)})
+        if kappa == 1000.0:  # the oracle on the same 100 systems, one type, for scale
+            t0 = time.perf_counter()
+            for p in probs:
+                oracle.lowp_lu_solve_ir(2, p.A32, p.b, tol=kappa * 2.0 ** -53)
+            t_oracle = (time.perf_counter() - t0) * 1e3
+    return {"n": n, "systems_per_cond": per_kappa, "tolerance": "cond(A) 2^-53 on |d|/|x|",
+            "max_iter": 50, "rows": rows, "oracle_ms_fp16_cond1e3_1core": t_oracle}
+
+
+def bench_lu_accuracy(bfx, oracle, bi, dev):
+    """Sec. IV-A's LU figure on the device: mean element error of the bf16x6
+    LU over that of the FP32 LU, both against the FP64 LU of the same FP32
+    matrix, for [-1, 1] and [-1e10, 1e10] (runs whose pivots differ from the
+    FP64 LU's are left out, as their factors are not comparable)."""
+    import torch
+
+    out = {}
+    for scale in (1.0, 1e10):
+        for n, runs in ((128, 20), (512, 10), (1024, 4)):
+            ratios = []
+            for s in range(runs):
+                A = (bi.uniform_pm1((n, n), 300 + s) * scale).astype(np.float32)
+                LU64, p64, _ = oracle.dgetrf(A)
+                res = []
+                for mode in (0, 6):
+                    Ad = torch.from_numpy(A.copy()).to(dev)
+                    _, ip, _ = bfx.lu_bf16xN(mode, Ad)
+                    res.append((Ad.cpu().numpy(), ip.cpu().numpy()[:n]))
+                if not all(np.array_equal(p, p64) for _, p in res):
+                    continue
+                den = np.maximum(np.abs(LU64), np.finfo(np.float64).tiny)
+                e0, e6 = (float(np.mean(np.abs(L - LU64) / den)) for L, _ in res)
+                ratios.append(e6 / e0)
+            out[f"[-{scale:g},{scale:g}] n={n}"] = {
+                "runs_compared": len(ratios), "mean_ratio_x6_over_fp32": float(np.mean(ratios)) if ratios else None}
+    return out
+
+
 def bench_serving(bfx, bi, count, max_inflight=32):
     """Config 5: Poisson arrivals at 5000 req/s, n log-uniform [64, 4096],
     nrhs U{1..16}, log10 kappa U[1,10], 60 GB pool, bf16x3 with escalation;
@@ -578,6 +644,8 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_solves:
         line["accuracy"] = bench_accuracy(bfx, oracle, bi, dev)
+        line["single_type_lu_ir"] = bench_single_type_lu(bfx, oracle, bi, dev)
+        line["lu_accuracy"] = bench_lu_accuracy(bfx, oracle, bi, dev)
         line["ir_single"] = bench_ir_single(bfx, oracle, bi, dev)
         line["batched"] = bench_batched(bfx, oracle, bi, dev)
         line["serving"] = bench_serving(bfx, bi, args.serve_requests)

@@ -180,6 +180,37 @@ BFX_API bfx_status bfx_gemm_bf16xN_f64(bfx_mode mode, int64_t m, int64_t n, int6
                                        int64_t ldb, double* d_C, int64_t ldc, void* d_ws,
                                        size_t ws_bytes, bfx_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Single-type LU with refinement (the plain IR table of Sec. IV-B: FP32
+ * factors against factors computed entirely in one bfloat16 or one binary16
+ * type), for `count` independent n x n systems, one warp each.
+ * LU: A rounded to the type; unblocked right-looking LU with partial
+ * pivoting (first row of the largest |a|, whole rows swapped); every
+ * division, product and difference done in FP32 (IEEE, no contraction) and
+ * rounded to the type (round to nearest even); an exactly zero pivot column
+ * sets info to its 1-based index (the first one) and is skipped.
+ * Refinement (Sec. III, FP64): x = (LU)^-1 P b, then up to max_iter times
+ * r = b - A x, d = (LU)^-1 P r, x += d; converged when |d|_inf <= tol[s]
+ * |x|_inf (the paper's "residual tolerance of cond(A)*eps": pass cond(A)
+ * 2^-53); stopped unconverged at the first NaN or Inf entry.  All sums run
+ * in a fixed sequential order, so results are reproducible bit for bit.
+ * d_A: count x n x n FP32, row-major, systems back to back; d_b, d_x: count
+ * x n FP64; d_tol: count FP64.  Outputs (device, caller-owned): d_x, d_iters
+ * (corrections applied after the first solve), d_conv (1/0), d_info; d_LU
+ * (count x n x n FP32 words holding the type's values) and d_ipiv (count x n,
+ * 0-based, row swapped with row k) may be NULL.  1 <= n <= 128 (else
+ * BFX_EUNSUPPORTED), count >= 0, max_iter >= 0 (BFX_EINVAL). */
+typedef enum bfx_lowp {
+  BFX_LOWP_FP32 = 0,
+  BFX_LOWP_BF16 = 1,
+  BFX_LOWP_FP16 = 2
+} bfx_lowp;
+BFX_API bfx_status bfx_lowp_lu_ir_batched(bfx_lowp type, int count, int n, const float* d_A,
+                                          const double* d_b, const double* d_tol, int max_iter,
+                                          double* d_x, float* d_LU, int32_t* d_ipiv,
+                                          int32_t* d_iters, int32_t* d_conv, int32_t* d_info,
+                                          bfx_stream stream);
+
 /* Workspace-free variant of bfx_gemm_bf16xN (same arguments minus the
  * workspace, same result).  The paper has no counterpart: this exists for
  * callers that cannot allocate device memory, e.g. a plugin inside a host

@@ -30,6 +30,10 @@ from ._bfx import (  # noqa: F401
     gemm_presplit,
     gemm_workspace_size,
     lib,
+    LOWP_BF16,
+    LOWP_FP16,
+    LOWP_FP32,
+    lowp_lu_ir_batched,
     lu_bf16xN,
     solve_ir,
     solve_ir_workspace_size,

@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         "bfx_gemm_workspace_size": (sz, [i32, i64, i64, i64]),
         "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
         "bfx_gemm_bf16xN_fused": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
+        "bfx_lowp_lu_ir_batched": (i32, [i32, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "bfx_gemm_bf16xN_f64": (i32, [i32, i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, sz, vp]),
         "bfx_gemm_presplit": (i32, [i32, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, vp]),
         "bfx_sgemm_simt": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
@@ -203,6 +204,33 @@ def gemm_bf16xN_f64(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor
            lib().bfx_gemm_bf16xN_f64(mode, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
                                      _ptr(workspace) if wsb else None, ws_bytes, _stream(stream)))
     return C
+
+
+LOWP_FP32, LOWP_BF16, LOWP_FP16 = 0, 1, 2
+
+
+def lowp_lu_ir_batched(typ: int, A: torch.Tensor, b: torch.Tensor, tol: torch.Tensor,
+                       max_iter: int = 50, factors: bool = False, stream=None):
+    """Single-type LU (every operation rounded to FP32, bfloat16 or binary16)
+    and FP64 residual-form refinement of ``count`` n x n systems (the plain IR
+    table of Sec. IV-B).  A: (count, n, n) float32, b: (count, n) float64,
+    tol: (count,) float64.  Returns x, iters, conv, info (and LU, ipiv when
+    ``factors``)."""
+    count, n, _ = A.shape
+    dev = A.device
+    x = torch.empty((count, n), dtype=torch.float64, device=dev)
+    iters = torch.empty(count, dtype=torch.int32, device=dev)
+    conv = torch.empty(count, dtype=torch.int32, device=dev)
+    info = torch.empty(count, dtype=torch.int32, device=dev)
+    LU = torch.empty((count, n, n), dtype=torch.float32, device=dev) if factors else None
+    ipiv = torch.empty((count, n), dtype=torch.int32, device=dev) if factors else None
+    _check("bfx_lowp_lu_ir_batched",
+           lib().bfx_lowp_lu_ir_batched(typ, count, n, _ptr(A), _ptr(b), _ptr(tol), int(max_iter),
+                                        _ptr(x), _ptr(LU), _ptr(ipiv), _ptr(iters), _ptr(conv),
+                                        _ptr(info), _stream(stream)))
+    if factors:
+        return x, iters, conv, info, LU, ipiv
+    return x, iters, conv, info
 
 
 def gemm_bf16xN_fused(mode: int, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None,

@@ -302,4 +302,19 @@ BFX_API bfx_status bfx_gemm_bf16xN_fused(bfx_mode mode, int64_t m, int64_t n, in
   return launch_gemm_fused(mode, m, n, k, alpha, d_A, lda, d_B, ldb, beta, d_C, ldc, s);
 }
 
+BFX_API bfx_status bfx_lowp_lu_ir_batched(bfx_lowp type, int count, int n, const float* d_A,
+                                          const double* d_b, const double* d_tol, int max_iter,
+                                          double* d_x, float* d_LU, int32_t* d_ipiv,
+                                          int32_t* d_iters, int32_t* d_conv, int32_t* d_info,
+                                          bfx_stream stream) {
+  if (type != BFX_LOWP_FP32 && type != BFX_LOWP_BF16 && type != BFX_LOWP_FP16) return BFX_EINVAL;
+  if (count < 0 || n < 1 || max_iter < 0) return BFX_EINVAL;
+  if (count == 0) return BFX_OK;
+  if (!d_A || !d_b || !d_tol || !d_x || !d_iters || !d_conv || !d_info) return BFX_EINVAL;
+  if (n > lowp_max_n()) return BFX_EUNSUPPORTED;
+  if (!is_sm103()) return BFX_EUNSUPPORTED;
+  return launch_lowp_lu_ir(type, count, n, d_A, d_b, d_tol, max_iter, d_x, d_LU, d_ipiv, d_iters,
+                           d_conv, d_info, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

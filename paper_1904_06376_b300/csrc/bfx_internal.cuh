@@ -138,6 +138,12 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
 bfx_status launch_gemm_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k, const uint16_t* Ap,
                            int64_t lda_p, int64_t a_plane, const uint16_t* Btp, int64_t ldb_p,
                            int64_t b_plane, double* C, int64_t ldc, cudaStream_t s);
+// Single-type LU + FP64 refinement, one warp per system (lowp.cu).
+bfx_status launch_lowp_lu_ir(bfx_lowp type, int count, int n, const float* A, const double* b,
+                             const double* tol, int max_iter, double* x, float* LU_out,
+                             int32_t* ipiv_out, int32_t* iters, int32_t* conv, int32_t* info,
+                             cudaStream_t s);
+int lowp_max_n();
 
 // ---------------------------------------------------------------- device side
 #if defined(__CUDACC__)

@@ -109,3 +109,23 @@ def test_solve_ir_singular(bfx):
     b = torch.ones((8, 1), dtype=torch.float64, device="cuda")
     x, res, code = bfx.solve_ir(3, A, b)
     assert code == 5 and res["info"] == 4
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e10])
+@pytest.mark.parametrize("n,runs", [(128, 20), (512, 6)])
+def test_e4_device_x6_lu_more_accurate_than_fp32(bfx, orc, scale, n, runs):
+    """Sec. IV-A's LU figure on the device: averaged over runs, the element
+    error of the bf16x6-update LU against the FP64 LU is below that of the
+    device's FP32 LU, for the ranges [-1, 1] and [-1e10, 1e10]."""
+    ratios = []
+    for s in range(runs):
+        A = (bi.uniform_pm1((n, n), 300 + s) * scale).astype(np.float32)
+        LU64, p64, _ = orc.dgetrf(A)
+        LU0, p0, _ = _lu_gpu(bfx, 0, A, 64)
+        LU6, p6, _ = _lu_gpu(bfx, 6, A, 64)
+        if not (np.array_equal(p0, p64) and np.array_equal(p6, p64)):
+            continue
+        den = np.maximum(np.abs(LU64), np.finfo(np.float64).tiny)
+        ratios.append(np.mean(np.abs(LU6 - LU64) / den) / np.mean(np.abs(LU0 - LU64) / den))
+    assert len(ratios) >= runs * 3 // 4
+    assert np.mean(ratios) < 1.0, ratios

@@ -136,12 +136,12 @@ __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int
 // computed value has this bit pattern.
 constexpr unsigned long long kTrsvSentinel = 0xFFF4000000000001ull;
 
-// d[i, c] = r[perm[i], c]; when fill != null, also fill[] = the triangular
-// solve's sentinel (n x nrhs) and tickets[0..1] = 0.
+// d[i, c] = r[perm[i], c]; when fill (fill2) != null, also fill[] (fill2[]) =
+// the triangular solve's sentinel (n x nrhs) and tickets[0..1] = 0.
 __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
                                  const int32_t* __restrict__ perm, int64_t n, int nrhs,
                                  double* __restrict__ d, int64_t ldd, double* __restrict__ fill,
-                                 int* __restrict__ tickets) {
+                                 double* __restrict__ fill2, int* __restrict__ tickets) {
   if (tickets && blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -149,6 +149,7 @@ __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
     const int c = static_cast<int>(e - i * nrhs);
     d[i * ldd + c] = r[static_cast<int64_t>(perm[i]) * ldr + c];
     if (fill) fill[e] = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
+    if (fill2) fill2[e] = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
   }
 }
 
@@ -419,6 +420,165 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   for (int e = t; e < bs * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
     st_relaxed_gpu(y + static_cast<int64_t>(b0 + i) * R + c0 + c, xs[i][c]);
+  }
+}
+
+// ------------------------------------------------------- row-sliced solve
+// For the many solves of a GMRES phase with one set of factors, the block
+// inverse is folded into the factor once: H[b][s] = Dinv_b F[b, k_s] for
+// every block b and its s-th predecessor k_s in solve order (FP64, blocks of
+// block b stored consecutively, block b at step st starting at block
+// st (st - 1) / 2).  Then y_b = Dinv_b v_b - sum_s H[b][s] y_{k_s} separates
+// by rows, and each block's rows are split over TRSV_S CTAs: the 64 x 64
+// FP64 product that follows each arrival, bounded by one SM's FP64 rate
+// (about 1.5 us), becomes TRSV_S products of 16 rows.
+constexpr int TRSV_S = 4;
+constexpr int TRSV_SR = TB / TRSV_S;  // rows a slice
+
+template <bool LOWER>
+__global__ void __launch_bounds__(256)
+    ir_hmat_kernel(const float* __restrict__ F, int64_t ldf, int n,
+                   const double* __restrict__ Dinv, double* __restrict__ H) {
+  __shared__ double Ds[TB][TB];
+  __shared__ float Fs[TB][TB];
+  const int nblk = (n + TB - 1) / TB;
+  const int st = blockIdx.x, sp = blockIdx.y;  // step of the block, index of the predecessor
+  if (sp >= st || st >= nblk) return;
+  const int b = LOWER ? st : nblk - 1 - st;
+  const int k = LOWER ? sp : nblk - 1 - sp;
+  const int b0 = b * TB, bs = min(TB, n - b0), k0 = k * TB, ks = min(TB, n - k0);
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, l = e % TB;
+    Ds[i][l] = D[e];
+    Fs[i][l] = (i < bs && l < ks) ? F[static_cast<int64_t>(b0 + i) * ldf + k0 + l] : 0.0f;
+  }
+  __syncthreads();
+  double* h = H + (static_cast<int64_t>(st) * (st - 1) / 2 + sp) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, j = e % TB;
+    double s0 = 0.0, s1 = 0.0;
+    for (int l = 0; l < TB; l += 2) {
+      s0 = fma(Ds[i][l], static_cast<double>(Fs[l][j]), s0);
+      s1 = fma(Ds[i][l + 1], static_cast<double>(Fs[l + 1][j]), s1);
+    }
+    h[e] = s0 + s1;
+  }
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
+}
+
+// out[i][c] (+)= sign * sum_l T[i][l] x[l][c] for the TRSV_SR rows of a slice;
+// Q threads per output (16, 8, 4 for cg = 1, 2, > 2) take l = q, q + Q, ...
+// and add their partial sums by shuffle (a fixed order: deterministic).
+__device__ __forceinline__ void slice_product(const double* Tm, const double (*x)[TRSV_CG + 1],
+                                              double (*out)[TRSV_CG + 1], int cg, bool sub) {
+  const int t = threadIdx.x;
+  const int Q = cg == 1 ? 16 : (cg == 2 ? 8 : 4);
+  const int o = t / Q, q = t - o * Q;
+  const bool act = o < TRSV_SR * cg;
+  const int i = act ? o / cg : 0, c = act ? o - i * cg : 0;
+  double sum = 0.0;
+  if (act) {
+    const double* row = Tm + i * (TB + 1);
+    for (int l = q; l < TB; l += Q) sum = fma(row[l], x[l][c], sum);
+  }
+  for (int off = Q / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+  if (act && q == 0) out[i][c] = sub ? out[i][c] - sum : sum;
+}
+
+// One launch a triangle, CTAs on (row block, column group, slice) tickets in
+// solve order, results published by value as in ir_trsv_kernel (y all
+// sentinel at launch).  v is only read (several slices read each row); with
+// dout the rows are also stored there (plain stores: nothing polls dout).
+template <bool LOWER>
+__global__ void __launch_bounds__(TRSV_THREADS)
+    ir_trsv_h_kernel(const double* __restrict__ H, const double* __restrict__ Dinv, int n,
+                     const double* __restrict__ v, double* __restrict__ y,
+                     double* __restrict__ dout, int R, int* __restrict__ ticket,
+                     int* __restrict__ err) {
+  __shared__ __align__(16) double Hs[2][TRSV_SR][TB + 1];
+  __shared__ double Ds[TRSV_SR][TB + 1];
+  __shared__ double xs[TB][TRSV_CG + 1];
+  __shared__ double acc[TRSV_SR][TRSV_CG + 1];
+  __shared__ int s_ticket, s_fail;
+  const int t = threadIdx.x;
+  const int nblk = (n + TB - 1) / TB;
+  const int G = (R + TRSV_CG - 1) / TRSV_CG;
+  if (t == 0) {
+    s_ticket = atomicAdd(ticket, 1);
+    s_fail = 0;
+  }
+  __syncthreads();
+  const int step = s_ticket / (G * TRSV_S);
+  const int rem = s_ticket - step * (G * TRSV_S);
+  const int grp = rem / TRSV_S, sl = rem - grp * TRSV_S;
+  const int b = LOWER ? step : nblk - 1 - step;
+  const int b0 = b * TB, bs = min(TB, n - b0);
+  const int r0 = sl * TRSV_SR;
+  const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
+  const double* Hb = H + static_cast<int64_t>(step) * (step - 1) / 2 * TB * TB;
+  // rows r0 .. r0 + 15 of H[b][s] -> Hs[s & 1], asynchronously
+  auto prefetch = [&](int s) {
+    const double* src = Hb + static_cast<int64_t>(s) * TB * TB + r0 * TB;
+    for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) {
+      const int i = e / TB, l = e - i * TB;
+      cp_async8(&Hs[s & 1][i][l], src + i * TB + l);
+    }
+  };
+  if (step > 0) prefetch(0);
+  cp_async_commit();
+  // acc = (Dinv_b v_b) on this slice's rows
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB + r0 * TB;
+  for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) Ds[e / TB][e % TB] = D[e];
+  for (int e = t; e < TB * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    xs[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  slice_product(&Ds[0][0], xs, acc, cg, false);
+  __syncthreads();
+  volatile int* fail = &s_fail;
+  for (int s = 0; s < step; ++s) {
+    if (s + 1 < step) prefetch(s + 1);
+    cp_async_commit();
+    const int k = LOWER ? s : nblk - 1 - s;
+    const int k0 = k * TB, ks = min(TB, n - k0);
+    if (t < 32) {  // warp 0: y_k into xs, each lane polling its values
+      for (int e = t; e < TB * cg; e += 32) {
+        const int i = e / cg, c = e - i * cg;
+        double val = 0.0;
+        if (i < ks) {
+          const double* src = y + static_cast<int64_t>(k0 + i) * R + c0 + c;
+          val = ld_relaxed_gpu(src);
+          if (is_trsv_sentinel(val) && !*fail) {
+            const uint64_t tw = global_ns();
+            while (is_trsv_sentinel(val = ld_relaxed_gpu(src))) {
+              if (global_ns() - tw > 4000000000ull) {
+                atomicExch(err, kErrWaitBlock);
+                *fail = 1;
+                break;
+              }
+            }
+          }
+        }
+        xs[i][c] = val;
+      }
+    }
+    cp_async_wait1();  // this thread's copies of H[b][s] have landed
+    __syncthreads();
+    slice_product(&Hs[s & 1][0][0], xs, acc, cg, true);
+    __syncthreads();
+  }
+  for (int e = t; e < TRSV_SR * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    if (r0 + i >= bs) continue;
+    const int64_t at = static_cast<int64_t>(b0 + r0 + i) * R + c0 + c;
+    st_relaxed_gpu(y + at, acc[i][c]);
+    if (dout) dout[at] = acc[i][c];
   }
 }
 
@@ -938,6 +1098,9 @@ struct IrWs {
   double* Lg;     // chain matrices G_b = Linv_b L[b, b-1] and Uinv_b U[b, b+1]
   double* Ug;
   double* y1;     // forward-solve result (sentinel-filled between solves)
+  double* y2;     // backward-solve result of the row-sliced solve (GMRES only)
+  double* Hl;     // inverse-scaled blocks Linv_b L[b, k] (GMRES only), per block in solve order
+  double* Hu;     // the same for U
   int32_t* tsync; // triangular-solve tickets, one per triangle
   void* luws;
   size_t luws_bytes;
@@ -988,6 +1151,10 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.gm_m = gm_m;
   if (gm_m > 0) {
     const int64_t R = nrhs, m = gm_m;
+    const int64_t hblocks = nblk * (nblk - 1) / 2;
+    w.y2 = reinterpret_cast<double*>(take(sizeof(double) * n * R));
+    w.Hl = reinterpret_cast<double*>(take(sizeof(double) * hblocks * TB * TB));
+    w.Hu = reinterpret_cast<double*>(take(sizeof(double) * hblocks * TB * TB));
     int64_t rows = std::max<int64_t>(1, GM_ELEMS / R);
     int64_t nch = ceil_div(n, rows);
     if (nch > GM_MAXCH) {
@@ -1016,7 +1183,10 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
 // the forward solve reads d and writes y1, the backward solve reads y1 and
 // writes d.  The gather also fills y1 with the sentinel and zeroes both
 // tickets; the forward solve leaves d all sentinel for the backward one.
-bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
+// use_h (the inverse-scaled blocks Hl, Hu computed for these factors): the
+// row-sliced solves instead; the backward one publishes through y2 (also
+// sentinel-filled by the gather) and writes its result to d.
+bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_h = false) {
   static const bool attr_ok = [] {
     return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kTrsvSmem)) == cudaSuccess &&
@@ -1031,7 +1201,15 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s) {
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
   const unsigned grid = static_cast<unsigned>(nblk * G);
   ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                        w.y1, w.tsync);
+                                                        w.y1, use_h ? w.y2 : nullptr, w.tsync);
+  if (use_h) {
+    const unsigned hgrid = static_cast<unsigned>(nblk * G * TRSV_S);
+    ir_trsv_h_kernel<true><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hl, w.Linv, N, w.d, w.y1, nullptr,
+                                                          nrhs, w.tsync, err);
+    ir_trsv_h_kernel<false><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hu, w.Uinv, N, w.y1, w.y2, w.d,
+                                                           nrhs, w.tsync + 1, err);
+    return last_launch_status();
+  }
   ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.y1,
                                                              nrhs, w.tsync, err);
   ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Uinv, w.Ug, w.y1, w.d,
@@ -1061,13 +1239,13 @@ bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int n
 // columns).  *steps = Arnoldi steps run (the most over the columns).  The
 // host reads the R Arnoldi-active flags after each step to stop early.
 bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, int R, double tau,
-                       cudaStream_t s, int* steps) {
+                       cudaStream_t s, int* steps, bool use_h) {
   const int N = static_cast<int>(n), m = w.gm_m, nch = w.gm_nchunk;
   const int64_t vstride = n * R;
   const int grid = grid_elems(n * R);
   bfx_status st;
   *steps = 0;
-  if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;  // w.d = M^-1 r
+  if ((st = lu_solve64(w, n, R, s, use_h)) != BFX_OK) return st;  // w.d = M^-1 r
   gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
   gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
                                               w.flags, w.kdone);
@@ -1086,7 +1264,7 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     const double* vj = w.V + static_cast<int64_t>(j) * vstride;
     // w.d = M^-1 A v_j
     if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s)) != BFX_OK) return st;
-    if ((st = lu_solve64(w, n, R, s)) != BFX_OK) return st;
+    if ((st = lu_solve64(w, n, R, s, use_h)) != BFX_OK) return st;
     for (int pass = 0; pass < 2; ++pass) {
       gm_dot_kernel<<<dim3(j + 1, nch), GM_THREADS, 0, s>>>(w.V, vstride, w.d, N, R, w.gm_rows, nch,
                                                             w.part);
@@ -1490,7 +1668,7 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
   ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_b, ldb, n, R, bn);
 
   bfx_mode cur = mode;
-  bool first = true, refactor = true, use_gmres = p.gmres == 2;
+  bool first = true, refactor = true, use_gmres = p.gmres == 2, h_ready = false;
   bfx_status st = BFX_OK;
   for (;;) {
     if (refactor) {
@@ -1514,6 +1692,7 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
         ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
         ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
       }
+      h_ready = false;
       const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
       ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
     }
@@ -1548,8 +1727,16 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       if (!any) break;
       if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s)) != BFX_OK) return st;
       if (use_gmres) {
+        if (!h_ready) {  // once per factorisation: the blocks of the row-sliced solve
+          const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
+          if (nblk > 1) {
+            ir_hmat_kernel<true><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Linv, w.Hl);
+            ir_hmat_kernel<false><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Hu);
+          }
+          h_ready = true;
+        }
         int k = 0;
-        if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k)) != BFX_OK) return st;
+        if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k, true)) != BFX_OK) return st;
         h_result->gmres_steps += 1;
         h_result->arnoldi += k;
       } else if ((st = lu_solve64(w, n, R, s)) != BFX_OK) {

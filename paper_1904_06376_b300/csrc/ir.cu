@@ -472,12 +472,15 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 
 // out[i][c] (+)= sign * sum_l T[i][l] x[l][c] for the TRSV_SR rows of a slice;
-// Q threads per output (16, 8, 4 for cg = 1, 2, > 2) take l = q, q + Q, ...
-// and add their partial sums by shuffle (a fixed order: deterministic).
+// Q threads per output (8, 4, 2, 2 for cg = 1 .. 4) take l = q, q + Q, ...
+// and add their partial sums by shuffle (a fixed order: deterministic).  On
+// B300 the shuffle-adds run on the FP64 pipe like the FMAs (2 a clock per
+// SM), so fewer threads per output with longer chains finish sooner: at
+// cg = 1, 8 threads per output leave 4 warps of 8 FMAs + 3 adds.
 __device__ __forceinline__ void slice_product(const double* Tm, const double (*x)[TRSV_CG + 1],
                                               double (*out)[TRSV_CG + 1], int cg, bool sub) {
   const int t = threadIdx.x;
-  const int Q = cg == 1 ? 16 : (cg == 2 ? 8 : 4);
+  const int Q = cg == 1 ? 8 : (cg == 2 ? 4 : 2);
   const int o = t / Q, q = t - o * Q;
   const bool act = o < TRSV_SR * cg;
   const int i = act ? o / cg : 0, c = act ? o - i * cg : 0;

@@ -1237,12 +1237,55 @@ bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int n
   return last_launch_status();
 }
 
+// Pinned host slots and events through which the GMRES loop reads the
+// Arnoldi-active flags without stalling the stream (one set per host thread
+// and device, released when the thread ends).
+constexpr int GM_LAG = 2;               // steps launched ahead of the flags read
+constexpr int GM_RING = GM_LAG + 2;
+struct GmFlagRing {
+  int dev = -1;
+  int32_t* h = nullptr;  // GM_RING x MAXR
+  cudaEvent_t ev[GM_RING] = {};
+  ~GmFlagRing() { release(); }
+  void release() {
+    if (h) cudaFreeHost(h);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    h = nullptr;
+    for (auto& e : ev) e = nullptr;
+    dev = -1;
+  }
+  bool ready() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return false;
+    if (d == dev && h) return true;
+    release();
+    if (cudaMallocHost(reinterpret_cast<void**>(&h), sizeof(int32_t) * GM_RING * MAXR) != cudaSuccess) {
+      h = nullptr;
+      return false;
+    }
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        release();
+        return false;
+      }
+    dev = d;
+    return true;
+  }
+};
+
 // One GMRES cycle for every refinement-active column.  On entry w.r holds
 // r = b - A x (consumed); on exit w.d holds the correction (0 in the other
-// columns).  *steps = Arnoldi steps run (the most over the columns).  The
-// host reads the R Arnoldi-active flags after each step to stop early.
+// columns).  *steps = Arnoldi steps run (the most over the columns).  After
+// each step the R Arnoldi-active flags are copied to pinned host memory; the
+// host reads the copy GM_LAG + 1 steps later (long complete by then), so the
+// stream never drains, and stops launching once no column is active.  Up to
+// GM_LAG + 1 steps launched past the last active one find every column
+// inactive and leave the state alone (the kernels skip inactive columns).
 bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, int R, double tau,
                        cudaStream_t s, int* steps, bool use_h) {
+  thread_local GmFlagRing ring;
+  if (!ring.ready()) return BFX_ECUDA;
   const int N = static_cast<int>(n), m = w.gm_m, nch = w.gm_nchunk;
   const int64_t vstride = n * R;
   const int grid = grid_elems(n * R);
@@ -1252,18 +1295,28 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
   gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
   gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
                                               w.flags, w.kdone);
-  std::vector<int32_t> fl(R);
+  // flags after "step -1" (the start) go to ring slot GM_RING - 1
+  auto post = [&](int j, const int32_t* flags) {  // copy the flags after step j
+    const int slot = (j + GM_RING) % GM_RING;
+    if (cudaMemcpyAsync(ring.h + slot * MAXR, flags, sizeof(int32_t) * R, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaEventRecord(ring.ev[slot], s) != cudaSuccess)
+      return false;
+    return true;
+  };
+  if (!post(-1, w.flags)) return BFX_ECUDA;
   int j = 0;
   for (; j < m; ++j) {
+    const int look = j - 1 - GM_LAG;  // the step whose output flags decide (-1: the start)
+    if (look >= -1) {
+      const int slot = (look + GM_RING) % GM_RING;
+      if (cudaEventSynchronize(ring.ev[slot]) != cudaSuccess) return BFX_ECUDA;
+      bool any = false;
+      for (int c = 0; c < R; ++c) any = any || ring.h[slot * MAXR + c];
+      if (!any) break;
+    }
     int32_t* ain = w.flags + (j & 1) * R;
     int32_t* aout = w.flags + ((j + 1) & 1) * R;
-    if (cudaMemcpyAsync(fl.data(), ain, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return BFX_ECUDA;
-    bool any = false;
-    for (int c = 0; c < R; ++c) any = any || fl[c];
-    if (!any) break;
     const double* vj = w.V + static_cast<int64_t>(j) * vstride;
     // w.d = M^-1 A v_j
     if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s)) != BFX_OK) return st;
@@ -1278,8 +1331,15 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
     gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, w.H, w.cs,
                                                w.sn, w.g, w.beta, m, tau, ain, aout, w.kdone);
+    if (!post(j, aout)) return BFX_ECUDA;
   }
-  *steps = j;
+  // steps taken: the most over the columns
+  std::vector<int32_t> kd(R);
+  if (cudaMemcpyAsync(kd.data(), w.kdone, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BFX_ECUDA;
+  for (int c = 0; c < R; ++c) *steps = std::max(*steps, static_cast<int>(kd[c]));
   gm_solve_y_kernel<<<R, 32, sizeof(double) * m, s>>>(w.H, w.g, w.kdone, w.active, m, w.y);
   gm_combine_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, w.y, w.kdone, w.active, N, R, m, w.d);
   return last_launch_status();

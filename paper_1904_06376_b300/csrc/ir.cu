@@ -97,8 +97,10 @@ __global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
 
 // r = b - A x (FP64; r = A x when b is null) for columns c0 .. c0+NC; warp a row, lanes over the row
 // (coalesced), one FP64 shuffle reduction per column at the end.  NC is a
-// compile-time column count so no predicated-off FP64 work is issued (FP64
-// throughput is the bound of this kernel on B300).
+// compile-time column count so no predicated-off FP64 work is issued.  Each
+// lane keeps four independent partial sums over l = lane + 32 (4 t + u), so
+// four loads of A are in flight per lane: with one, the kernel was bound by
+// memory latency (28 warps an SM x 128 B in flight), not by FP64 throughput.
 // If rn != nullptr, rn[c] = max |r[:, c]| (must start at 0).
 template <int NC>
 __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
@@ -109,18 +111,33 @@ __global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int
   const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   if (row >= n) return;
   const float* a = A + row * lda;
-  double acc[NC];
+  double acc[4][NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-  for (int l = lane; l < n; l += 32) {
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[u][c] = 0.0;
+  int l = lane;
+  for (; l + 96 < n; l += 128) {
+    float av[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) av[u] = __ldg(a + l + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double al = widen(av[u]);
+      const double* xl = x + static_cast<int64_t>(l + 32 * u) * ldx + c0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[u][c] = fma(al, xl[c], acc[u][c]);
+    }
+  }
+  for (; l < n; l += 32) {
     const double al = widen(a[l]);
     const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = fma(al, xl[c], acc[c]);
+    for (int c = 0; c < NC; ++c) acc[0][c] = fma(al, xl[c], acc[0][c]);
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    double v = acc[c];
+    double v = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     if (lane == c) {

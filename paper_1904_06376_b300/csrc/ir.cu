@@ -746,18 +746,12 @@ __global__ void __launch_bounds__(GM_THREADS)
   }
 }
 
-// End of Arnoldi step j: h_{j+1,j} = |w|_2 (partials of <w, w>),
-// V_{j+1} = w / h_{j+1,j}; CTA 0, thread c: the earlier rotations applied to
-// column j of H, the rotation that zeroes h_{j+1,j}, g updated; the column
-// stays Arnoldi-active unless |g_{j+1}| <= tau beta, the space became
-// invariant (h_{j+1,j} = 0), m steps are done, or a NaN appeared.
+// End of Arnoldi step j, part 1: h_{j+1,j} = |w|_2 (partials of <w, w>),
+// V_{j+1} = w / h_{j+1,j} for the Arnoldi-active columns.
 __global__ void __launch_bounds__(GM_THREADS)
     gm_next_kernel(double* __restrict__ V, int64_t vstride, int j, const double* __restrict__ w,
-                   int n, int R, const double* __restrict__ part, int nchunk, double* __restrict__ H,
-                   double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                   const double* __restrict__ beta, int m, double tau,
-                   const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
-                   int32_t* __restrict__ kdone) {
+                   int n, int R, const double* __restrict__ part, int nchunk,
+                   const int32_t* __restrict__ act_in) {
   __shared__ double hn[MAXR];
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) {
@@ -774,34 +768,129 @@ __global__ void __launch_bounds__(GM_THREADS)
     const int c = static_cast<int>(e % R);
     if (a[c] && hn[c] > 0.0) vn[e] = w[e] / hn[c];
   }
-  if (blockIdx.x == 0 && threadIdx.x < R) {
-    const int c = threadIdx.x;
-    int keep = a[c];
-    if (keep) {
-      double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
-      const double* csc = cs + static_cast<int64_t>(c) * m;
-      const double* snc = sn + static_cast<int64_t>(c) * m;
-      double* gc = g + static_cast<int64_t>(c) * (m + 1);
-      const double hj = hn[c];
-      // earlier rotations, the rotated lower entry carried in a register
-      double p = hcol[0];
-      for (int i = 0; i < j; ++i) {
-        const double q = hcol[i + 1];
-        hcol[i] = csc[i] * p + snc[i] * q;
-        p = -snc[i] * p + csc[i] * q;
-      }
-      const double rho = hypot(p, hj);
-      const double cj = rho > 0.0 ? p / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
-      cs[static_cast<int64_t>(c) * m + j] = cj;
-      sn[static_cast<int64_t>(c) * m + j] = sj;
-      hcol[j] = rho;
-      hcol[j + 1] = 0.0;
-      gc[j + 1] = -sj * gc[j];
-      gc[j] = cj * gc[j];
-      kdone[c] = j + 1;
-      const double res = fabs(gc[j + 1]);
-      if (res <= tau * beta[c] || !(hj > 0.0) || j + 1 >= m || !(res == res)) keep = 0;
+}
+
+// End of Arnoldi step j, part 2, CTA c for column c: the earlier rotations
+// applied to column j of H, the rotation that zeroes h_{j+1,j}, g updated;
+// the column stays Arnoldi-active unless |g_{j+1}| <= tau beta, the space
+// became invariant (h_{j+1,j} = 0), m steps are done, or a NaN appeared.
+// Applying rotation i carries the rotated lower entry p to the next one:
+// p_{i+1} = -s_i p_i + c_i h_{i+1}, an affine recurrence, so instead of j
+// dependent steps on one thread (each waiting on a load: a millisecond at
+// j ~ 2000) the CTA composes the maps x -> a x + b with a prefix scan over
+// its threads (fixed thread order: deterministic), then every thread
+// finishes its own rows h_i = c_i p_i + s_i h_{i+1}.
+constexpr int GIV_THREADS = 1024;
+constexpr int GIV_E = (BFX_GMRES_MAX_M + GIV_THREADS - 1) / GIV_THREADS;  // rows a thread
+__global__ void __launch_bounds__(GIV_THREADS)
+    gm_givens_kernel(int j, int R, const double* __restrict__ part, int nchunk,
+                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                     double* __restrict__ g, const double* __restrict__ beta, int m, double tau,
+                     const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
+                     int32_t* __restrict__ kdone) {
+  __shared__ double wA[GIV_THREADS / 32], wB[GIV_THREADS / 32];
+  __shared__ double s_p;
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (!act_in[c]) {
+    if (t == 0) act_out[c] = 0;
+    return;
+  }
+  double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
+  const double* csc = cs + static_cast<int64_t>(c) * m;
+  const double* snc = sn + static_cast<int64_t>(c) * m;
+  const int E = (j + GIV_THREADS - 1) / GIV_THREADS;  // <= GIV_E
+  const int i0 = t * E;
+  // this thread's rotations, loaded before anything is written
+  double cv[GIV_E], sv[GIV_E], qv[GIV_E];
+  double A = 1.0, B = 0.0;  // composition of this thread's maps, in order
+#pragma unroll
+  for (int e = 0; e < GIV_E; ++e) {
+    const int i = i0 + e;
+    cv[e] = sv[e] = qv[e] = 0.0;
+    if (e < E && i < j) {
+      cv[e] = csc[i];
+      sv[e] = snc[i];
+      qv[e] = hcol[i + 1];
+      const double a = -sv[e], b = cv[e] * qv[e];
+      B = a * B + b;
+      A = a * A;
     }
+  }
+  const double p0 = hcol[0];
+  // exclusive scan of (A, B) over the threads: prefix = maps of all earlier threads
+  double pA = A, pB = B;  // inclusive within the warp first
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double oA = __shfl_up_sync(0xFFFFFFFFu, pA, o);
+    const double oB = __shfl_up_sync(0xFFFFFFFFu, pB, o);
+    if (lane >= o) {  // this (later) after the earlier o
+      pB = pA * oB + pB;
+      pA = pA * oA;
+    }
+  }
+  if (lane == 31) {
+    wA[wid] = pA;
+    wB[wid] = pB;
+  }
+  __syncthreads();
+  if (wid == 0) {  // inclusive scan of the warp totals
+    double xA = wA[lane], xB = wB[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double oA = __shfl_up_sync(0xFFFFFFFFu, xA, o);
+      const double oB = __shfl_up_sync(0xFFFFFFFFu, xB, o);
+      if (lane >= o) {
+        xB = xA * oB + xB;
+        xA = xA * oA;
+      }
+    }
+    wA[lane] = xA;
+    wB[lane] = xB;
+  }
+  __syncthreads();
+  // exclusive prefix of this thread: earlier warps, then earlier lanes of this warp
+  double eA = 1.0, eB = 0.0;
+  if (wid > 0) {
+    eA = wA[wid - 1];
+    eB = wB[wid - 1];
+  }
+  {
+    double lA = __shfl_up_sync(0xFFFFFFFFu, pA, 1), lB = __shfl_up_sync(0xFFFFFFFFu, pB, 1);
+    if (lane > 0) {  // (earlier lanes) after (earlier warps)
+      eB = lA * eB + lB;
+      eA = lA * eA;
+    }
+  }
+  double p = eA * p0 + eB;  // p_{i0}
+#pragma unroll
+  for (int e = 0; e < GIV_E; ++e) {
+    const int i = i0 + e;
+    if (e < E && i < j) {
+      hcol[i] = cv[e] * p + sv[e] * qv[e];
+      p = -sv[e] * p + cv[e] * qv[e];
+      if (i == j - 1) s_p = p;  // p_j
+    }
+  }
+  if (j == 0 && t == 0) s_p = p0;
+  __syncthreads();
+  if (t == 0) {
+    double u = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) u += part[static_cast<int64_t>(ch) * R + c];
+    const double hj = sqrt(u);  // as part 1 computed it
+    const double pj = s_p;
+    double* gc = g + static_cast<int64_t>(c) * (m + 1);
+    const double rho = hypot(pj, hj);
+    const double cj = rho > 0.0 ? pj / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
+    cs[static_cast<int64_t>(c) * m + j] = cj;
+    sn[static_cast<int64_t>(c) * m + j] = sj;
+    hcol[j] = rho;
+    hcol[j + 1] = 0.0;
+    gc[j + 1] = -sj * gc[j];
+    gc[j] = cj * gc[j];
+    kdone[c] = j + 1;
+    const double res = fabs(gc[j + 1]);
+    int keep = 1;
+    if (res <= tau * beta[c] || !(hj > 0.0) || j + 1 >= m || !(res == res)) keep = 0;
     act_out[c] = keep;
   }
 }
@@ -1346,8 +1435,9 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
       gm_orth_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j + 1, w.d, N, R, w.hb, ain);
     }
     gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
-    gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, w.H, w.cs,
-                                               w.sn, w.g, w.beta, m, tau, ain, aout, w.kdone);
+    gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, ain);
+    gm_givens_kernel<<<R, GIV_THREADS, 0, s>>>(j, R, w.part, nch, w.H, w.cs, w.sn, w.g, w.beta, m,
+                                               tau, ain, aout, w.kdone);
     if (!post(j, aout)) return BFX_ECUDA;
   }
   // steps taken: the most over the columns

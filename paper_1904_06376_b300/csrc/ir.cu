@@ -711,6 +711,48 @@ __global__ void __launch_bounds__(GM_THREADS)
   }
 }
 
+// The same update when there are many vectors: gm_orth_kernel's grid covers
+// only the n R elements (16 CTAs at n = 4096, R = 1), so its (j + 1) n FP64
+// FMAs ran on 16 SMs (133 us at j = 2000).  Here CTA (x, y) sums the vectors
+// of chunk y (GM_KC of them, in order) for its elements into part2[y], and
+// gm_orth_finish_kernel subtracts the chunk sums from w in chunk order: the
+// work spreads over every SM and the order stays fixed (deterministic).
+constexpr int GM_KC = 64;
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_orth_part_kernel(const double* __restrict__ V, int64_t vstride, int nv, int n, int R,
+                        const double* __restrict__ hb, const int32_t* __restrict__ act,
+                        double* __restrict__ part2) {
+  __shared__ int32_t a[MAXR];
+  if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
+  __syncthreads();
+  const int64_t total = static_cast<int64_t>(n) * R;
+  const int i0 = blockIdx.y * GM_KC, i1 = min(nv, i0 + GM_KC);
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    if (!a[c]) continue;
+    double u = 0.0;
+    for (int i = i0; i < i1; ++i) u = fma(__ldg(hb + i * R + c), V[i * vstride + e], u);
+    part2[blockIdx.y * total + e] = u;
+  }
+}
+__global__ void __launch_bounds__(GM_THREADS)
+    gm_orth_finish_kernel(double* __restrict__ w, int n, int R, const int32_t* __restrict__ act,
+                          const double* __restrict__ part2, int nkc) {
+  __shared__ int32_t a[MAXR];
+  if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
+  __syncthreads();
+  const int64_t total = static_cast<int64_t>(n) * R;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+    const int c = static_cast<int>(e % R);
+    if (!a[c]) continue;
+    double u = w[e];
+    for (int y = 0; y < nkc; ++y) u -= part2[y * total + e];
+    w[e] = u;
+  }
+}
+
 // Start of a cycle: w = M^-1 r; beta = |w|_2 (from the partials of <w, w>),
 // V_0 = w / beta, g = beta e_1; a column takes part when it is refinement-
 // active and beta is positive and finite.
@@ -1224,6 +1266,7 @@ struct IrWs {
   double* beta;   // R
   double* hb;     // (m+1) x R, one Gram-Schmidt pass's coefficients
   double* part;   // (m+1) x nchunk x R
+  double* part2;  // ceil((m+1) / GM_KC) x n x R, the chunk sums of a long Gram-Schmidt update
   int32_t* flags; // 2 x R (Arnoldi-active, alternating between steps)
   int32_t* kdone; // R
   size_t total;
@@ -1281,6 +1324,7 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
     w.beta = reinterpret_cast<double*>(take(sizeof(double) * R));
     w.hb = reinterpret_cast<double*>(take(sizeof(double) * (m + 1) * R));
     w.part = reinterpret_cast<double*>(take(sizeof(double) * (m + 1) * nch * R));
+    w.part2 = reinterpret_cast<double*>(take(sizeof(double) * ceil_div(m + 1, GM_KC) * n * R));
     w.flags = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2 * R));
     w.kdone = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * R));
   }
@@ -1432,7 +1476,15 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
                                                             w.part);
       gm_reduce_h_kernel<<<static_cast<unsigned>(ceil_div((j + 1) * R, 256)), 256, 0, s>>>(
           w.part, nch, j + 1, R, w.hb, w.H, m, j, pass, ain);
-      gm_orth_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j + 1, w.d, N, R, w.hb, ain);
+      if (j + 1 > 2 * GM_KC) {
+        const int nkc = static_cast<int>(ceil_div(j + 1, GM_KC));
+        const unsigned eb = static_cast<unsigned>(ceil_div(n * R, GM_THREADS));
+        gm_orth_part_kernel<<<dim3(eb, nkc), GM_THREADS, 0, s>>>(w.V, vstride, j + 1, N, R, w.hb,
+                                                                 ain, w.part2);
+        gm_orth_finish_kernel<<<grid, GM_THREADS, 0, s>>>(w.d, N, R, ain, w.part2, nkc);
+      } else {
+        gm_orth_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j + 1, w.d, N, R, w.hb, ain);
+      }
     }
     gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
     gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, ain);

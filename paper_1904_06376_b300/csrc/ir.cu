@@ -824,29 +824,26 @@ __global__ void __launch_bounds__(GM_THREADS)
 // finishes its own rows h_i = c_i p_i + s_i h_{i+1}.
 constexpr int GIV_THREADS = 1024;
 constexpr int GIV_E = (BFX_GMRES_MAX_M + GIV_THREADS - 1) / GIV_THREADS;  // rows a thread
-__global__ void __launch_bounds__(GIV_THREADS)
-    gm_givens_kernel(int j, int R, const double* __restrict__ part, int nchunk,
-                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                     double* __restrict__ g, const double* __restrict__ beta, int m, double tau,
-                     const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
-                     int32_t* __restrict__ kdone) {
-  __shared__ double wA[GIV_THREADS / 32], wB[GIV_THREADS / 32];
-  __shared__ double s_p;
-  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (!act_in[c]) {
-    if (t == 0) act_out[c] = 0;
-    return;
-  }
-  double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
-  const double* csc = cs + static_cast<int64_t>(c) * m;
-  const double* snc = sn + static_cast<int64_t>(c) * m;
-  const int E = (j + GIV_THREADS - 1) / GIV_THREADS;  // <= GIV_E
+
+// The earlier rotations (csc, snc, i < j) applied to Hessenberg column hcol
+// (rows 0..j) by all NT threads of the CTA (called by every thread): the
+// carried lower entry follows the affine recurrence p_{i+1} = -s_i p_i +
+// c_i h_{i+1}; each thread composes the maps of its E consecutive rows, an
+// exclusive prefix scan over the threads (warp shuffles, then the 32 warp
+// totals; fixed order) gives its starting p, and it finishes its own rows.
+// Returns p_j, the entry the new rotation must zero against h_{j+1,j}, in
+// every thread.  wA, wB: NT / 32 doubles of shared memory; sp: one.
+template <int NT, int MAXE>
+__device__ double givens_apply_scan(double* hcol, const double* csc, const double* snc, int j,
+                                    double* wA, double* wB, double* sp) {
+  static_assert(NT % 32 == 0 && NT / 32 <= 32, "CTA of whole warps, at most 32");
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int E = (j + NT - 1) / NT;  // <= MAXE
   const int i0 = t * E;
-  // this thread's rotations, loaded before anything is written
-  double cv[GIV_E], sv[GIV_E], qv[GIV_E];
+  double cv[MAXE], sv[MAXE], qv[MAXE];
   double A = 1.0, B = 0.0;  // composition of this thread's maps, in order
 #pragma unroll
-  for (int e = 0; e < GIV_E; ++e) {
+  for (int e = 0; e < MAXE; ++e) {
     const int i = i0 + e;
     cv[e] = sv[e] = qv[e] = 0.0;
     if (e < E && i < j) {
@@ -859,13 +856,12 @@ __global__ void __launch_bounds__(GIV_THREADS)
     }
   }
   const double p0 = hcol[0];
-  // exclusive scan of (A, B) over the threads: prefix = maps of all earlier threads
-  double pA = A, pB = B;  // inclusive within the warp first
+  double pA = A, pB = B;  // inclusive scan within the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double oA = __shfl_up_sync(0xFFFFFFFFu, pA, o);
     const double oB = __shfl_up_sync(0xFFFFFFFFu, pB, o);
-    if (lane >= o) {  // this (later) after the earlier o
+    if (lane >= o) {  // this (later) map after the earlier ones
       pB = pA * oB + pB;
       pA = pA * oA;
     }
@@ -876,7 +872,7 @@ __global__ void __launch_bounds__(GIV_THREADS)
   }
   __syncthreads();
   if (wid == 0) {  // inclusive scan of the warp totals
-    double xA = wA[lane], xB = wB[lane];
+    double xA = lane < NT / 32 ? wA[lane] : 1.0, xB = lane < NT / 32 ? wB[lane] : 0.0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const double oA = __shfl_up_sync(0xFFFFFFFFu, xA, o);
@@ -886,40 +882,62 @@ __global__ void __launch_bounds__(GIV_THREADS)
         xA = xA * oA;
       }
     }
-    wA[lane] = xA;
-    wB[lane] = xB;
+    if (lane < NT / 32) {
+      wA[lane] = xA;
+      wB[lane] = xB;
+    }
   }
   __syncthreads();
-  // exclusive prefix of this thread: earlier warps, then earlier lanes of this warp
-  double eA = 1.0, eB = 0.0;
+  double eA = 1.0, eB = 0.0;  // exclusive prefix: earlier warps, then earlier lanes
   if (wid > 0) {
     eA = wA[wid - 1];
     eB = wB[wid - 1];
   }
   {
-    double lA = __shfl_up_sync(0xFFFFFFFFu, pA, 1), lB = __shfl_up_sync(0xFFFFFFFFu, pB, 1);
-    if (lane > 0) {  // (earlier lanes) after (earlier warps)
+    const double lA = __shfl_up_sync(0xFFFFFFFFu, pA, 1), lB = __shfl_up_sync(0xFFFFFFFFu, pB, 1);
+    if (lane > 0) {
       eB = lA * eB + lB;
       eA = lA * eA;
     }
   }
   double p = eA * p0 + eB;  // p_{i0}
 #pragma unroll
-  for (int e = 0; e < GIV_E; ++e) {
+  for (int e = 0; e < MAXE; ++e) {
     const int i = i0 + e;
     if (e < E && i < j) {
       hcol[i] = cv[e] * p + sv[e] * qv[e];
       p = -sv[e] * p + cv[e] * qv[e];
-      if (i == j - 1) s_p = p;  // p_j
+      if (i == j - 1) *sp = p;  // p_j
     }
   }
-  if (j == 0 && t == 0) s_p = p0;
+  if (j == 0 && t == 0) *sp = p0;
   __syncthreads();
+  const double pj = *sp;
+  __syncthreads();  // sp and the warp totals may be reused by the caller
+  return pj;
+}
+
+__global__ void __launch_bounds__(GIV_THREADS)
+    gm_givens_kernel(int j, int R, const double* __restrict__ part, int nchunk,
+                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                     double* __restrict__ g, const double* __restrict__ beta, int m, double tau,
+                     const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
+                     int32_t* __restrict__ kdone) {
+  __shared__ double wA[GIV_THREADS / 32], wB[GIV_THREADS / 32];
+  __shared__ double s_p;
+  const int c = blockIdx.x, t = threadIdx.x;
+  if (!act_in[c]) {
+    if (t == 0) act_out[c] = 0;
+    return;
+  }
+  double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
+  const double pj = givens_apply_scan<GIV_THREADS, GIV_E>(hcol, cs + static_cast<int64_t>(c) * m,
+                                                          sn + static_cast<int64_t>(c) * m, j, wA,
+                                                          wB, &s_p);
   if (t == 0) {
     double u = 0.0;
     for (int ch = 0; ch < nchunk; ++ch) u += part[static_cast<int64_t>(ch) * R + c];
     const double hj = sqrt(u);  // as part 1 computed it
-    const double pj = s_p;
     double* gc = g + static_cast<int64_t>(c) * (m + 1);
     const double rho = hypot(pj, hj);
     const double cj = rho > 0.0 ? pj / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
@@ -982,6 +1000,7 @@ __global__ void __launch_bounds__(GM_THREADS)
 
 // ------------------------------------------------------------- batched forms
 constexpr int BIR_THREADS = 256;
+constexpr int BGM_GIV_E = 4;  // Krylov length of the batched GMRES at most 4 x BIR_THREADS
 
 __device__ __forceinline__ double block_max(double v, double* red) {
   // max over the CTA of non-negative values (NaN propagates: compared as bits)
@@ -1553,6 +1572,7 @@ __global__ void __launch_bounds__(BIR_THREADS)
   __shared__ double s_beta[MAXR], s_tmp[MAXR], s_dprev[MAXR], s_dn[MAXR], s_xn[MAXR];
   __shared__ int s_act[MAXR], s_arn[MAXR], s_k[MAXR], s_conv[MAXR], s_stall[MAXR];
   __shared__ int s_sys, s_any, s_steps;
+  __shared__ double s_gA[BIR_THREADS / 32], s_gB[BIR_THREADS / 32], s_gp;  // Givens scan
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   constexpr int NW = BIR_THREADS / 32;
   double* base = slots + static_cast<int64_t>(blockIdx.x) * slot_doubles;
@@ -1654,19 +1674,17 @@ __global__ void __launch_bounds__(BIR_THREADS)
           const int c = static_cast<int>(e % R);
           if (s_arn[c] && s_tmp[c] > 0.0) sl.V[(j + 1) * vs + e] = q.d[e] / s_tmp[c];
         }
-        if (t < R && s_arn[t]) {
-          const int c = t;
+        __syncthreads();
+        for (int c = 0; c < R; ++c) {
+          if (!s_arn[c]) continue;  // uniform over the CTA
           double* hcol = sl.H + (static_cast<int64_t>(c) * mm + j) * (mm + 1);
           double* csc = sl.cs + static_cast<int64_t>(c) * mm;
           double* snc = sl.sn + static_cast<int64_t>(c) * mm;
+          const double pv = givens_apply_scan<BIR_THREADS, BGM_GIV_E>(hcol, csc, snc, j, s_gA, s_gB,
+                                                                      &s_gp);
+          if (t != 0) continue;
           double* gc = sl.g + static_cast<int64_t>(c) * (mm + 1);
           const double hj = s_tmp[c];
-          double pv = hcol[0];
-          for (int i = 0; i < j; ++i) {
-            const double qv = hcol[i + 1];
-            hcol[i] = csc[i] * pv + snc[i] * qv;
-            pv = -snc[i] * pv + csc[i] * qv;
-          }
           const double rho = hypot(pv, hj);
           const double cj = rho > 0.0 ? pv / rho : 1.0, sj = rho > 0.0 ? hj / rho : 0.0;
           csc[j] = cj;
@@ -1764,6 +1782,7 @@ bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_
                             int64_t slot_doubles, int nslots, int m, BatchIrParams p,
                             int max_outer, double tau, cudaStream_t s) {
   if (S <= 0 || nslots <= 0) return BFX_OK;
+  if (m > BGM_GIV_E * BIR_THREADS) return BFX_EINVAL;  // the Givens scan's rows per thread
   if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return BFX_ECUDA;
   bgm_kernel<<<nslots, BIR_THREADS, 0, s>>>(d_ir, S, d_queue, d_slots, slot_doubles, m, p,
                                             max_outer, tau);

@@ -306,8 +306,11 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
  * or gmres_m outside 0..BFX_GMRES_MAX_M, and the usual argument / workspace
  * errors.  Workspace: bfx_solve_ir_workspace_size(mode, n, nrhs, h_params)
  * bytes (h_params NULL: the defaults), 256-byte aligned; with gmres != 0 it
- * includes the Krylov basis, (gmres_m + 1) n nrhs doubles, and the
- * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles. */
+ * includes the Krylov basis, (gmres_m + 1) n nrhs doubles, the
+ * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles, and the factor
+ * blocks scaled by the inverses of their diagonal blocks that the GMRES
+ * phase's triangular solves use, about n^2 doubles (both triangles; built
+ * once per factorisation when the GMRES phase starts). */
 #define BFX_GMRES_MAX_M 4096
 typedef struct bfx_ir_params {
   int max_iter;

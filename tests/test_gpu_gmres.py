@@ -18,21 +18,35 @@ def _fe(x, P):
 @pytest.mark.parametrize("n,nrhs,k", [(5, 1, 3), (96, 1, 8), (200, 3, 12), (333, 16, 5),
                                       (700, 2, 20)])
 def test_first_gmres_step_matches_oracle(bfx, orc, n, nrhs, k):
+    _first_cycle(bfx, orc, n, nrhs, k, 1e5)
+
+
+@pytest.mark.parametrize("n,nrhs,k,kappa", [(300, 1, 200, 1e4), (260, 3, 140, 1e4),
+                                            (1300, 1, 1100, 1e6)])
+def test_long_gmres_cycle_matches_oracle(bfx, orc, n, nrhs, k, kappa):
+    """Long cycles: past 128 vectors the Gram-Schmidt update runs as chunk
+    sums, past 1024 rotations the Givens scan gives each thread several rows.
+    Single-product (x1) factors make GMRES converge slowly enough that the
+    residual estimate does not underflow the (never met) tolerance before k
+    steps, as it does within ~100 steps with FP32 factors."""
+    _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=1)
+
+
+def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
     """gmres = 2, one refinement step of exactly k Arnoldi steps (tolerance
     never met): x = x0 + d with d the k-th GMRES iterate, column by column.
     Equal up to rounding: the device orthogonalises by two classical
     Gram-Schmidt passes, the oracle by modified Gram-Schmidt, and sums in
     another order, so the tolerance is kappa(A) times FP64 rounding."""
-    kappa = 1e5
     P = bi.svd_system(n, kappa, 900 + n, nrhs=nrhs)
     A = torch.from_numpy(P.A32).cuda()
     b = torch.from_numpy(P.b).cuda()
-    x, res, code = bfx.solve_ir(0, A, b, max_iter=1, gmres=2, gmres_m=k, gmres_tol=1e-300,
+    x, res, code = bfx.solve_ir(mode, A, b, max_iter=1, gmres=2, gmres_m=k, gmres_tol=1e-300,
                                 escalate=False)
     assert code in (0, 6)
     kk = min(k, n)
     assert res["gmres_steps"] == 1 and res["arnoldi"] == kk, res
-    LU, ipiv, info = orc.lu(0, P.A32, nb=64)
+    LU, ipiv, info = orc.lu(mode, P.A32, nb=64)
     xo, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b, max_iter=1, m=k,
                                                    tau=0.0)
     assert np.all(inner == kk)

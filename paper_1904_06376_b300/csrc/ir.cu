@@ -95,56 +95,71 @@ __global__ void ir_anorm_kernel(const float* __restrict__ A, int64_t lda, int n,
   if (lane == 0) atomic_max_nonneg(out, s);
 }
 
-// r = b - A x (FP64; r = A x when b is null) for columns c0 .. c0+NC; warp a row, lanes over the row
-// (coalesced), one FP64 shuffle reduction per column at the end.  NC is a
-// compile-time column count so no predicated-off FP64 work is issued.  Each
-// lane keeps four independent partial sums over l = lane + 32 (4 t + u), so
-// four loads of A are in flight per lane: with one, the kernel was bound by
-// memory latency (28 warps an SM x 128 B in flight), not by FP64 throughput.
+// r = b - A x (FP64; r = A x when b is null) for columns c0 .. c0+NC.  Four
+// warps a row (RES_WPR), two rows a CTA: warp q of a row takes the 32-element
+// pieces q, q + 4, q + 8, ... (coalesced 128-byte loads, four of them in
+// flight a lane), the four partial sums meet in shared memory and are added
+// in warp order (deterministic).  NC is a compile-time column count so no
+// predicated-off FP64 work is issued.  With one warp a row the GPU held only
+// 28 warps an SM at n = 4096 and the kernel waited on load latency (43 % of
+// the FP64 pipe, long-scoreboard stalls).
 // If rn != nullptr, rn[c] = max |r[:, c]| (must start at 0).
+constexpr int RES_WPR = 4;
+constexpr int RES_ROWS = 256 / (32 * RES_WPR);  // rows a 256-thread CTA
 template <int NC>
-__global__ void ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
-                                   const double* __restrict__ b, int64_t ldb,
-                                   const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
-                                   int64_t ldr, int c0, double* __restrict__ rn) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
-  if (row >= n) return;
-  const float* a = A + row * lda;
+__global__ void __launch_bounds__(256)
+    ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
+                       const double* __restrict__ b, int64_t ldb,
+                       const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
+                       int64_t ldr, int c0, double* __restrict__ rn) {
+  __shared__ double part[RES_ROWS][RES_WPR][NC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lr = wid / RES_WPR, q = wid - lr * RES_WPR;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * RES_ROWS + lr;
   double acc[4][NC];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[u][c] = 0.0;
-  int l = lane;
-  for (; l + 96 < n; l += 128) {
-    float av[4];
+  if (row < n) {
+    const float* a = A + row * lda;
+    constexpr int S = 32 * RES_WPR;  // stride between a warp's pieces
+    int l = q * 32 + lane;
+    for (; l + 3 * S < n; l += 4 * S) {
+      float av[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) av[u] = __ldg(a + l + 32 * u);
+      for (int u = 0; u < 4; ++u) av[u] = __ldg(a + l + S * u);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const double al = widen(av[u]);
-      const double* xl = x + static_cast<int64_t>(l + 32 * u) * ldx + c0;
+      for (int u = 0; u < 4; ++u) {
+        const double al = widen(av[u]);
+        const double* xl = x + static_cast<int64_t>(l + S * u) * ldx + c0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[u][c] = fma(al, xl[c], acc[u][c]);
+        for (int c = 0; c < NC; ++c) acc[u][c] = fma(al, xl[c], acc[u][c]);
+      }
     }
-  }
-  for (; l < n; l += 32) {
-    const double al = widen(a[l]);
-    const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
+    for (; l < n; l += S) {
+      const double al = widen(a[l]);
+      const double* xl = x + static_cast<int64_t>(l) * ldx + c0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[0][c] = fma(al, xl[c], acc[0][c]);
+      for (int c = 0; c < NC; ++c) acc[0][c] = fma(al, xl[c], acc[0][c]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     double v = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if (lane == c) {
-      const double rv = b ? b[row * ldb + c0 + c] - v : v;  // no b: the product A x
-      r[row * ldr + c0 + c] = rv;
-      if (rn) atomic_max_nonneg(&rn[c0 + c], fabs(rv));
-    }
+    if (lane == 0) part[lr][q][c] = v;
+  }
+  __syncthreads();
+  if (q == 0 && lane < NC && row < n) {
+    const int c = lane;
+    double v = part[lr][0][c];
+#pragma unroll
+    for (int k = 1; k < RES_WPR; ++k) v += part[lr][k][c];
+    const double rv = b ? b[row * ldb + c0 + c] - v : v;  // no b: the product A x
+    r[row * ldr + c0 + c] = rv;
+    if (rn) atomic_max_nonneg(&rn[c0 + c], fabs(rv));
   }
 }
 
@@ -1392,7 +1407,7 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
 bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int nrhs,
                     const double* b, int64_t ldb, const double* x, int64_t ldx, double* rn,
                     cudaStream_t s) {
-  const unsigned blocks = static_cast<unsigned>(ceil_div(n * 32, 256));
+  const unsigned blocks = static_cast<unsigned>(ceil_div(n, RES_ROWS));
   const int N = static_cast<int>(n);
   int c0 = 0;
   for (; c0 + 8 <= nrhs; c0 += 8)

@@ -650,7 +650,7 @@ __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const doub
 // chunks of rows; each chunk's partial sums go to `part` and every consumer
 // adds them in chunk order, so results do not depend on scheduling.
 constexpr int GM_THREADS = 256;
-constexpr int GM_ELEMS = 2048;  // vector elements one CTA covers in a dot product
+constexpr int GM_ELEMS = 1024;  // vector elements one CTA covers in a dot product
 constexpr int GM_MAXCH = 64;    // most chunks a dot product is split into
 
 // part[(i * nchunk + ch) * R + c] = sum over the chunk's rows of V_i[r, c] w[r, c].
@@ -732,8 +732,9 @@ __global__ void __launch_bounds__(GM_THREADS)
 // of chunk y (GM_KC of them, in order) for its elements into part2[y], and
 // gm_orth_finish_kernel subtracts the chunk sums from w in chunk order: the
 // work spreads over every SM and the order stays fixed (deterministic).
-constexpr int GM_KC = 64;
-__global__ void __launch_bounds__(GM_THREADS)
+constexpr int GM_KC = 32;
+constexpr int GM_PT = 128;  // threads of a chunk-sum CTA (more CTAs over the elements)
+__global__ void __launch_bounds__(GM_PT)
     gm_orth_part_kernel(const double* __restrict__ V, int64_t vstride, int nv, int n, int R,
                         const double* __restrict__ hb, const int32_t* __restrict__ act,
                         double* __restrict__ part2) {
@@ -742,8 +743,8 @@ __global__ void __launch_bounds__(GM_THREADS)
   __syncthreads();
   const int64_t total = static_cast<int64_t>(n) * R;
   const int i0 = blockIdx.y * GM_KC, i1 = min(nv, i0 + GM_KC);
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_THREADS) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * GM_THREADS) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(GM_PT) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * GM_PT) {
     const int c = static_cast<int>(e % R);
     if (!a[c]) continue;
     double u = 0.0;
@@ -1510,10 +1511,10 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
                                                             w.part);
       gm_reduce_h_kernel<<<static_cast<unsigned>(ceil_div((j + 1) * R, 256)), 256, 0, s>>>(
           w.part, nch, j + 1, R, w.hb, w.H, m, j, pass, ain);
-      if (j + 1 > 2 * GM_KC) {
+      if (j + 1 > GM_KC) {
         const int nkc = static_cast<int>(ceil_div(j + 1, GM_KC));
-        const unsigned eb = static_cast<unsigned>(ceil_div(n * R, GM_THREADS));
-        gm_orth_part_kernel<<<dim3(eb, nkc), GM_THREADS, 0, s>>>(w.V, vstride, j + 1, N, R, w.hb,
+        const unsigned eb = static_cast<unsigned>(ceil_div(n * R, GM_PT));
+        gm_orth_part_kernel<<<dim3(eb, nkc), GM_PT, 0, s>>>(w.V, vstride, j + 1, N, R, w.hb,
                                                                  ain, w.part2);
         gm_orth_finish_kernel<<<grid, GM_THREADS, 0, s>>>(w.d, N, R, ain, w.part2, nkc);
       } else {

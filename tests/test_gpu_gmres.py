@@ -24,7 +24,7 @@ def test_first_gmres_step_matches_oracle(bfx, orc, n, nrhs, k):
 @pytest.mark.parametrize("n,nrhs,k,kappa", [(300, 1, 200, 1e4), (260, 3, 140, 1e4),
                                             (1300, 1, 1100, 1e6)])
 def test_long_gmres_cycle_matches_oracle(bfx, orc, n, nrhs, k, kappa):
-    """Long cycles: past 128 vectors the Gram-Schmidt update runs as chunk
+    """Long cycles: past 32 vectors the Gram-Schmidt update runs as chunk
     sums, past 1024 rotations the Givens scan gives each thread several rows.
     Single-product (x1) factors make GMRES converge slowly enough that the
     residual estimate does not underflow the (never met) tolerance before k

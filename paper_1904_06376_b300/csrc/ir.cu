@@ -17,10 +17,14 @@
 // Everything runs in this library's kernels; the host only loops over
 // iterations and reads the per-column norms (a few doubles) to decide.
 // Triangular solves: row blocks of 64 whose diagonal blocks are inverted once
-// per factorisation (FP64); for each block one launch in which every CTA
-// applies the block's inverse (identically) and then updates its own row
-// block, so the FP64 work of each step is spread over all SMs and no step
-// waits on a 64-long chain of dependent FP64 operations.
+// per factorisation (FP64); one launch a triangle, CTAs taking row blocks from
+// an atomic ticket in solve order and publishing their results by value
+// (ir_trsv_kernel).  In a GMRES phase, which solves hundreds of times with
+// one set of factors, the inverse is folded into the factor blocks once and
+// each row block is split over four CTAs (ir_trsv_h_kernel).
+// GMRES-IR (Sec. III remark, Sec. IV-B): when plain refinement and the
+// escalations stall, each refinement step solves its correction equation by
+// left-preconditioned GMRES in FP64 (gm_* kernels, gmres_cycle).
 #include <algorithm>
 #include <cmath>
 #include <vector>

@@ -400,13 +400,15 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     }
     acc[i][c] = a;
   }
-  // warp 0: fetch y_k into xs, each lane polling its values until none is
-  // the sentinel (an 8-byte aligned store is seen whole or not at all)
+  // fetch y_k into xs, each thread polling one value until it is not the
+  // sentinel (an 8-byte aligned store is seen whole or not at all); with a
+  // warp polling two values a lane, the second poll cost a round trip more
+  // after the first value arrived
   volatile int* fail = &s_fail;
   auto fetch = [&](int k) {
     const int k0 = k * TB, ks = min(TB, n - k0);
-    if (t < 32) {
-      for (int e = t; e < TB * cg; e += 32) {
+    {  // one value a thread (TB * cg <= TRSV_THREADS): every value is polled at once
+      for (int e = t; e < TB * cg; e += TRSV_THREADS) {
         const int i = e / cg, c = e - i * cg;
         double val = 0.0;
         if (i < ks) {
@@ -586,8 +588,8 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     cp_async_commit();
     const int k = LOWER ? s : nblk - 1 - s;
     const int k0 = k * TB, ks = min(TB, n - k0);
-    if (t < 32) {  // warp 0: y_k into xs, each lane polling its values
-      for (int e = t; e < TB * cg; e += 32) {
+    {  // y_k into xs, one value a thread: every value is polled at once
+      for (int e = t; e < TB * cg; e += TRSV_THREADS) {
         const int i = e / cg, c = e - i * cg;
         double val = 0.0;
         if (i < ks) {

@@ -420,7 +420,8 @@ def bench_serving(bfx, bi, count, max_inflight=32, mode=6):
     conv = np.array([r[1]["converged"] for r in results])
     fe = np.array([_fe(x, P.x_true) for (x, _), P in zip(results, systems)])
     lk = np.array([r.log10_kappa for r in reqs])
-    return {"requests": count, "arrival_rate_per_s": 5000, "solves_per_s": count / (t_end - t_start),
+    return {"requests": count, "arrival_rate_per_s": 5000, "mode": f"x{mode}, escalation to GMRES-IR",
+            "solves_per_s": count / (t_end - t_start),
             "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_queue_ms": float(np.mean([r[1]["queue_s"] for r in results]) * 1e3),

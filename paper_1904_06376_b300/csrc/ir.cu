@@ -305,6 +305,26 @@ __device__ __forceinline__ void st_relaxed_gpu(double* p, double x) {
 }
 
 
+// A published value of the triangular solve: *src once it is no longer the
+// sentinel.  The wait is bounded (4 s of %globaltimer); on expiry the error
+// word gets kErrWaitBlock, *fail is set (later polls of the CTA skip their
+// wait) and the sentinel is returned.
+__device__ __forceinline__ double poll_published(const double* src, volatile int* fail,
+                                                 int* err) {
+  double val = ld_relaxed_gpu(src);
+  if (is_trsv_sentinel(val) && !*fail) {
+    const uint64_t t0 = global_ns();
+    while (is_trsv_sentinel(val = ld_relaxed_gpu(src))) {
+      if (global_ns() - t0 > 4000000000ull) {
+        atomicExch(err, kErrWaitBlock);
+        *fail = 1;
+        break;
+      }
+    }
+  }
+  return val;
+}
+
 // out[i][c] (+)= sign * sum_l T[i][l] x[l][c], i < TB, c < cg; Q threads a
 // product (Q = 4, 2, 1 for cg = 1, 2, >2), their partial sums added by shuffle.
 template <typename T, int LDT>
@@ -411,20 +431,7 @@ __global__ void __launch_bounds__(TRSV_THREADS)
       for (int e = t; e < TB * cg; e += TRSV_THREADS) {
         const int i = e / cg, c = e - i * cg;
         double val = 0.0;
-        if (i < ks) {
-          const double* src = y + static_cast<int64_t>(k0 + i) * R + c0 + c;
-          val = ld_relaxed_gpu(src);
-          if (is_trsv_sentinel(val) && !*fail) {
-            const uint64_t t0 = global_ns();
-            while (is_trsv_sentinel(val = ld_relaxed_gpu(src))) {
-              if (global_ns() - t0 > 4000000000ull) {
-                atomicExch(err, kErrWaitBlock);
-                *fail = 1;
-                break;
-              }
-            }
-          }
-        }
+        if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
         xs[i][c] = val;
       }
     }
@@ -592,20 +599,7 @@ __global__ void __launch_bounds__(TRSV_THREADS)
       for (int e = t; e < TB * cg; e += TRSV_THREADS) {
         const int i = e / cg, c = e - i * cg;
         double val = 0.0;
-        if (i < ks) {
-          const double* src = y + static_cast<int64_t>(k0 + i) * R + c0 + c;
-          val = ld_relaxed_gpu(src);
-          if (is_trsv_sentinel(val) && !*fail) {
-            const uint64_t tw = global_ns();
-            while (is_trsv_sentinel(val = ld_relaxed_gpu(src))) {
-              if (global_ns() - tw > 4000000000ull) {
-                atomicExch(err, kErrWaitBlock);
-                *fail = 1;
-                break;
-              }
-            }
-          }
-        }
+        if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
         xs[i][c] = val;
       }
     }

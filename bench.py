@@ -300,7 +300,7 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
     sample = list(range(0, count, count // 16))[:16]
     t0 = time.perf_counter()
     for i in sample:
-        oracle.lu_solve_ir(6, probs[i].A32, probs[i].b, nb=64)
+        oracle.lu_solve_ir(6, probs[i].A32, probs[i].b)
     tcpu = time.perf_counter() - t0
     flops = sum(2.0 / 3.0 * p.n ** 3 for p in probs)
     return {"systems": count, "mode": "x6", "ms_per_batch": ms, "solves_per_s": count / (ms * 1e-3),

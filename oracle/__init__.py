@@ -15,7 +15,9 @@ Functions and the passages they follow:
 * ``dot_partials``   -- the nine Z^(i,j) of Sec. II-D for one vector pair.
 * ``dgemm_rows``     -- FP64 product and |A||B| (the DGEMM baseline of Sec. IV-A).
 * ``dgetrf`` / ``dgetrs`` -- FP64 LU with partial pivoting and solve.
-* ``lu``             -- FP32 blocked LU with the mode's trailing update (Sec. IV-A).
+* ``lu``             -- the LU of record: unblocked, partial pivoting, division
+  by the pivot, each trailing-update product the mode's product (Sec. IV-A).
+* ``lu_mirror``      -- regression mirror of the device's blocked LU schedule.
 * ``solve_ir``       -- residual-form iterative refinement (Sec. III).
 """
 from __future__ import annotations
@@ -62,6 +64,8 @@ def lib() -> ctypes.CDLL:
         L.orc_dgetrs.argtypes = [i64, i64, vp, i64, vp, vp, i64]
         L.orc_lu.restype = i32
         L.orc_lu.argtypes = [i32, i64, i64, vp, i64, vp]
+        L.orc_lu_plain.restype = i32
+        L.orc_lu_plain.argtypes = [i32, i64, vp, i64, vp]
         L.orc_solve_ir.argtypes = [i64, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, i32, f64,
                                    f64, f64, vp, vp, vp]
         L.orc_num_threads.restype = i32
@@ -250,8 +254,25 @@ def dgesv(A, b):
     return dgetrs(LU, ipiv, b), info
 
 
-def lu(mode: int, A, nb: int = 64):
-    """FP32 blocked LU (Sec. IV-A) whose trailing update is the mode's product."""
+def lu(mode: int, A):
+    """The LU of record (Sec. IV-A "SGETRF based on triplets", reading R12):
+    unblocked right-looking LU with partial pivoting of an FP32 matrix,
+    multipliers by IEEE division, every trailing-update product the mode's
+    product (mode 0: the FP32 FMA).  Returns (LU, ipiv (0-based), info)."""
+    LU = np.array(A, dtype=np.float32, order="C", copy=True)
+    n = LU.shape[0]
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = lib().orc_lu_plain(int(mode), n, _p(LU), n, _p(ipiv))
+    if info < 0:
+        raise RuntimeError("orc_lu_plain failed")
+    return LU, ipiv, int(info)
+
+
+def lu_mirror(mode: int, A, nb: int = 64):
+    """Regression mirror, not the oracle of record: the blocked schedule of
+    the device LU (8-column panel tiles, reciprocal scaling, rank-nb trailing
+    updates by the mode's product), so a change of the device's FP32
+    arithmetic shows bit for bit."""
     LU = np.array(A, dtype=np.float32, order="C", copy=True)
     n = LU.shape[0]
     ipiv = np.zeros(n, dtype=np.int32)
@@ -288,8 +309,9 @@ def solve_ir(A32, LU, ipiv, b, max_iter: int = 50, tol: float = 2.0**-53, tol_b=
     return x, iters, conv, berr
 
 
-def lu_solve_ir(mode: int, A32, b, nb: int = 64, **kw):
-    LU, ipiv, info = lu(mode, A32, nb)
+def lu_solve_ir(mode: int, A32, b, **kw):
+    """The LU of record, then the refinement of Sec. III with its factors."""
+    LU, ipiv, info = lu(mode, A32)
     x, iters, conv, berr = solve_ir(A32, LU, ipiv, b, **kw)
     return x, iters, conv, berr, info
 

@@ -30,10 +30,11 @@
  *  R9 refinement: r = b - A x (the paper's sign slip in Sec. III corrected),
  *     residual, correction solve and update all in FP64 with the low-precision
  *     factors (Sec. III: "do the solve in a higher precision like FP64").
- *  R12 the "combined type" LU (Sec. IV-A) uses bf16xN only in the trailing
- *     matrix update; panel and triangular block solve are plain FP32, the
- *     panel blocked in tiles of 8 columns and its columns scaled by the
- *     reciprocal of the pivot as LAPACK's xGETF2 does.
+ *  R12 the "combined type" LU (Sec. IV-A) uses bf16xN only in the products
+ *     of the trailing matrix update; pivot search, swaps and the division by
+ *     the pivot are plain FP32.  Of record: orc_lu_plain (unblocked, each
+ *     update product the mode's product).  orc_lu restates the device's
+ *     blocked schedule as a regression mirror only.
  *  R13 GEMM result form C = alpha*Z + beta*C: t = fl32(alpha*Z), then
  *     fmaf(beta, C, t); beta == 0 does not read C.
  *  R26 the single-type LU of the Sec. IV-B plain IR table ("FP32", "BF16",
@@ -272,6 +273,27 @@ static int mode_uses(int mode, int i, int j) {
   }
 }
 
+/* Level sums and the smallest-first combination of Sec. II-D in FP32 from
+ * the partial products Z[i][j] (those the mode does not use are zero):
+ *   Z1 = Z01 + Z10,  Z2 = Z02 + (Z11 + Z20),  Z3 = Z12 + Z21,  Z4 = Z22;
+ *   x1 = Z0;  x3 = Z0 + Z1;  x6 = Z0 + (Z1 + Z2);  x8 = Z0 + (Z1 + (Z2 + Z3));
+ *   x9 = Z0 + (Z1 + (Z2 + (Z3 + Z4)));  x5 (R25) = Z0 + (Z1 + (Z02 + Z11)). */
+static float combine_levels32(int mode, float Z[3][3]) {
+  float Z0 = Z[0][0];
+  float Z1 = Z[0][1] + Z[1][0];
+  float Z2 = Z[0][2] + (Z[1][1] + Z[2][0]);
+  float Z3 = Z[1][2] + Z[2][1];
+  float Z4 = Z[2][2];
+  switch (mode) {
+    case 1: return Z0;
+    case 3: return Z0 + Z1;
+    case 5: return Z0 + (Z1 + (Z[0][2] + Z[1][1]));
+    case 6: return Z0 + (Z1 + Z2);
+    case 8: return Z0 + (Z1 + (Z2 + Z3));
+    default: return Z0 + (Z1 + (Z2 + (Z3 + Z4)));
+  }
+}
+
 /* Shared body: when Cd != NULL the "d" combination is written to Cd in FP64
  * without a final rounding (alpha, beta ignored); otherwise C (FP32) gets
  * alpha*z + beta*C (R13). */
@@ -326,20 +348,7 @@ static int gemm_body(int mode, int sum64, int64_t m, int64_t n, int64_t k, float
           Z[a][b] = z;
         }
       if (!sum64) {
-        float Z0 = Z[0][0];
-        float Z1 = Z[0][1] + Z[1][0];
-        float Z2 = Z[0][2] + (Z[1][1] + Z[2][0]);
-        float Z3 = Z[1][2] + Z[2][1];
-        float Z4 = Z[2][2];
-        float zr;
-        switch (mode) {
-          case 1: zr = Z0; break;
-          case 3: zr = Z0 + Z1; break;
-          case 5: zr = Z0 + (Z1 + (Z[0][2] + Z[1][1])); break;
-          case 6: zr = Z0 + (Z1 + Z2); break;
-          case 8: zr = Z0 + (Z1 + (Z2 + Z3)); break;
-          default: zr = Z0 + (Z1 + (Z2 + (Z3 + Z4))); break;
-        }
+        float zr = combine_levels32(mode, Z);
         if (Cd) { Cd[i * ldcd + j] = zr; continue; }
         float t = alpha * zr;
         C[i * ldc + j] = (beta == 0.0f) ? t : fmaf(beta, C[i * ldc + j], t);
@@ -488,6 +497,84 @@ void orc_dgetrs(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const in
   }
 }
 
+/* The LU of record for Sec. IV-A's "SGETRF based on triplets" (R12): the
+ * plain unblocked right-looking LU with partial pivoting of an FP32 matrix,
+ * in which every product of the trailing update is the mode's product.
+ * Column j: the pivot is the first row of the largest |a_ij|, i >= j; the
+ * whole rows j and p are swapped (ipiv[j] = p, 0-based); an exactly zero
+ * pivot records info = j + 1 (the first one) and the column is skipped;
+ * otherwise each multiplier is l_i = a_ij / a_jj (an IEEE FP32 division) and
+ * every a_ic, i, c > j, becomes
+ *   mode 0:   fmaf(-l_i, a_jc, a_ic)      (the FP32 FMA of Sec. II-C)
+ *   mode N:   a_ic - z,  z = the mode's product of l_i and a_jc (one term of
+ *             Sec. II-D: both factors split, the kept piece products, which
+ *             are exact, summed by level and combined smallest first), the
+ *             subtraction in FP32 (C = alpha Z + beta C with alpha = -1,
+ *             beta = 1, reading R13).
+ * No blocking, no reciprocal: the definition, not an implementation's
+ * schedule.  Returns info, or -1 for an unknown mode. */
+int orc_lu_plain(int mode, int64_t n, float* A, int64_t lda, int32_t* ipiv) {
+  if (mode != 0 && mode_pieces(mode) == 0) return -1;
+  const int npa = mode ? mode_pieces_a(mode) : 0, npb = mode ? mode_pieces(mode) : 0;
+  float* lp = (float*)malloc(sizeof(float) * 3 * (size_t)(n + 1));
+  float* up = (float*)malloc(sizeof(float) * 3 * (size_t)(n + 1));
+  if (!lp || !up) { free(lp); free(up); return -1; }
+  int info = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = j;
+    float best = fabsf(A[j * lda + j]);
+    for (int64_t i = j + 1; i < n; ++i) {
+      float v = fabsf(A[i * lda + j]);
+      if (v > best) { best = v; p = i; }
+    }
+    ipiv[j] = (int32_t)p;
+    if (p != j)
+      for (int64_t c = 0; c < n; ++c) {
+        float t = A[j * lda + c]; A[j * lda + c] = A[p * lda + c]; A[p * lda + c] = t;
+      }
+    const float piv = A[j * lda + j];
+    if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
+    for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
+    if (mode != 0) {
+      /* pieces of the multipliers (left factor) and of row j (right factor) */
+      for (int64_t i = j + 1; i < n; ++i) {
+        uint16_t q[3];
+        split_one(A[i * lda + j], &q[0], &q[1], &q[2]);
+        for (int t = 0; t < 3; ++t) lp[3 * i + t] = (t < npa) ? bf16_to_f32(q[t]) : 0.0f;
+      }
+      for (int64_t c = j + 1; c < n; ++c) {
+        uint16_t q[3];
+        split_one(A[j * lda + c], &q[0], &q[1], &q[2]);
+        for (int t = 0; t < 3; ++t) up[3 * c + t] = (t < npb) ? bf16_to_f32(q[t]) : 0.0f;
+      }
+    }
+#pragma omp parallel for schedule(static) if (n - j > 128)
+    for (int64_t i = j + 1; i < n; ++i) {
+      const float l = A[i * lda + j];
+      for (int64_t c = j + 1; c < n; ++c) {
+        if (mode == 0) {
+          A[i * lda + c] = fmaf(-l, A[j * lda + c], A[i * lda + c]);
+          continue;
+        }
+        float Z[3][3] = {{0}};
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (mode_uses(mode, a, b)) Z[a][b] = lp[3 * i + a] * up[3 * c + b]; /* exact */
+        A[i * lda + c] = A[i * lda + c] - combine_levels32(mode, Z);
+      }
+    }
+  }
+  free(lp);
+  free(up);
+  return info;
+}
+
+/* REGRESSION MIRROR, not the oracle of record: the blocked schedule the
+ * device LU runs (tiles of 8 panel columns, reciprocal scaling as LAPACK's
+ * xGETF2, rank-nb trailing updates), restated here so that a change of the
+ * device's FP32 arithmetic shows up bit for bit.  Agreement with it says the
+ * device still runs this schedule; agreement with the method is checked
+ * against orc_lu_plain and orc_dgetrf. */
 /* LU of an FP32 matrix with the combined type of Sec. IV-A (R12), blocked
  * like LAPACK's xGETRF (the routine the paper compares with): block columns
  * of width nb; inside a block column, the panel is itself blocked in tiles of

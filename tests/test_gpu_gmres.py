@@ -1,6 +1,7 @@
 """GMRES-IR on the device (GMRES remark of Sec. III; Sec. IV-B) against the
 oracle: the first GMRES correction equals the oracle's for the same FP32
-factors (the FP32 LU is bit-identical on both sides), and GMRES-IR reaches
+factors (the device's FP32 LU is bit-identical to the oracle's blocked
+mirror of its schedule), and GMRES-IR reaches
 FP64-LU accuracy where plain refinement cannot."""
 import numpy as np
 import pytest
@@ -46,7 +47,7 @@ def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
     assert code in (0, 6)
     kk = min(k, n)
     assert res["gmres_steps"] == 1 and res["arnoldi"] == kk, res
-    LU, ipiv, info = orc.lu(mode, P.A32, nb=64)
+    LU, ipiv, info = orc.lu_mirror(mode, P.A32, nb=64)
     xo, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b, max_iter=1, m=k,
                                                    tau=0.0)
     assert np.all(inner == kk)

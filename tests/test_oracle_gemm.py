@@ -5,6 +5,7 @@ Expected values come from exact rational arithmetic (Python fractions), from
 permutation special cases whose result is known exactly, from the paper's
 error bounds and stated accuracy orderings, never from the oracle itself.
 """
+import os
 from fractions import Fraction as F
 
 import numpy as np
@@ -319,3 +320,65 @@ def test_x5_accuracy_bounded_by_the_missing_third_piece(orc):
             assert np.all(np.abs(C - C64) <= bound)
     assert e[5] >= 10 * e[6], e
     assert e[5] < e[3], e
+
+
+ORDER_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "combine_order.txt")
+
+
+def _bits_f32(words):
+    return np.array([int(w, 16) for w in words], dtype=np.uint32).view(np.float32)
+
+
+def _order_golden():
+    rows = []
+    for line in open(ORDER_GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, a, b, exp, wrong = (f.strip() for f in line.split("|"))
+        expected = {int(m): int(v, 16) for m, v in (t.split(":") for t in exp.split())}
+        w6, w9 = (int(v, 16) for v in wrong.split())
+        rows.append((name, _bits_f32(a.split()), _bits_f32(b.split()), expected, w6, w9))
+    return rows
+
+
+@pytest.mark.parametrize("row", _order_golden(), ids=lambda r: r[0])
+def test_combination_order_golden(orc, row):
+    """Sec. II-D's smallest-first combination, pinned by hand-worked cases
+    (tests/golden/combine_order.txt) in which another order gives another
+    FP32 result: G1 separates Z0 + (Z1 + Z2) from (Z0 + Z1) + Z2; G2 is the
+    x9 chain, where Z4 tips a double tie that x8, x6 and a left-to-right x9
+    round the other way."""
+    name, a, b, expected, wrong6, wrong9 = row
+    for mode, want in expected.items():
+        C = orc.gemm(mode, a[None, :], b[:, None])
+        assert int(C.view(np.uint32)[0, 0]) == want, (name, mode, hex(int(C.view(np.uint32)[0, 0])))
+        assert int(np.float32(orc.dot(mode, a, b)).view(np.uint32)) == want
+    # the other orders, evaluated in FP32 from the oracle's own partial
+    # products, give the golden's "wrong order" values, which differ
+    Z = orc.dot_partials(a, b).astype(np.float32)
+    f = np.float32
+    Z0, Z1 = Z[0, 0], f(Z[0, 1] + Z[1, 0])
+    Z2 = f(Z[0, 2] + f(Z[1, 1] + Z[2, 0]))
+    Z3, Z4 = f(Z[1, 2] + Z[2, 1]), Z[2, 2]
+    ltr6 = f(f(Z0 + Z1) + Z2)
+    ltr9 = f(f(f(f(Z0 + Z1) + Z2) + Z3) + Z4)
+    assert int(ltr6.view(np.uint32)) == wrong6 and int(ltr9.view(np.uint32)) == wrong9
+    assert expected[9] != wrong9
+    if name == "G1":
+        assert expected[6] != wrong6
+    if name == "G2":
+        assert expected[9] != expected[8]  # the lo*lo bin decides
+
+
+def test_combination_order_golden_partials_g2(orc):
+    """G2 has k = 1, so each partial product is an exact product of pieces;
+    the values worked out by hand in the golden file."""
+    row = [r for r in _order_golden() if r[0] == "G2"][0]
+    Z = orc.dot_partials(row[1], row[2]).astype(np.float64)
+    want = [[F(19781, 2**14), F(-15589, 2**22), F(-3537, 2**29)],
+            [F(-453, 2**20), F(357, 2**28), F(81, 2**35)],
+            [F(-151, 2**27), F(119, 2**35), F(27, 2**42)]]
+    for i in range(3):
+        for j in range(3):
+            assert F(float(Z[i, j])) == want[i][j], (i, j)

@@ -30,7 +30,7 @@ def _inexact_factors(orc, A, seed, eps=0.2):
     """FP32 LU of a perturbed A: a preconditioner far enough from A that
     GMRES needs several steps."""
     E = np.random.default_rng(seed).uniform(-eps, eps, A.shape).astype(np.float32)
-    LU, ipiv, info = orc.lu(0, (A + E).astype(np.float32), nb=8)
+    LU, ipiv, info = orc.lu(0, (A + E).astype(np.float32))
     assert info == 0
     return LU, ipiv
 
@@ -83,7 +83,7 @@ def test_gmres_exact_preconditioner_one_step(orc):
         2.0 ** rng.integers(3, 6, n))
     A = (L @ U).astype(np.float32)
     assert np.array_equal(A.astype(np.float64), L @ U)  # exactly representable
-    LU, ipiv, info = orc.lu(0, A, nb=4)
+    LU, ipiv, info = orc.lu(0, A)
     assert info == 0
     rhs = rng.standard_normal(n)
     d, k, hist = orc.gmres(A, LU, ipiv, rhs, m=10, tau=1e-12)
@@ -104,7 +104,7 @@ def test_gmres_ir_within_10x_of_fp64_lu_where_ir_fails(orc, kappa):
     fails, ratios = 0, []
     for s in range(4):
         P = bi.svd_system(96, kappa, 40 + s)
-        LU, ipiv, info = orc.lu(6, P.A32, nb=16)
+        LU, ipiv, info = orc.lu(6, P.A32)
         assert info == 0
         xd, _ = orc.dgesv(P.A32, P.b)
         fe64 = _fe(xd, P)
@@ -138,12 +138,12 @@ def test_e6_diag_dominant_fp32_lu_gmres(orc, n):
     for s in range(25):
         P = bi.diag_dominant_system(n, 500 + s)
         tol = np.linalg.cond(P.A32.astype(np.float64), np.inf) * 2.0**-53
-        LU, ipiv, _ = orc.lu(0, P.A32, nb=8)
+        LU, ipiv, _ = orc.lu(0, P.A32)
         x, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b, tol=tol)
         assert conv[0] == 1
         its.append(it[0])
         inn32.append(inner[0])
-        LU1, ipiv1, _ = orc.lu(1, P.A32, nb=8)
+        LU1, ipiv1, _ = orc.lu(1, P.A32)
         x1, it1, inner1, conv1, _ = orc.solve_gmres_ir(P.A32, LU1, ipiv1, P.b, tol=tol)
         assert conv1[0] == 1
         inn1.append(inner1[0])

@@ -1,15 +1,93 @@
 """Pins of the oracle's LU factorisations and residual-form refinement
 (Sec. III, Sec. IV-A "SGETRF based on triplets", Sec. IV-B).
 
-Checked against LAPACK (scipy's dgetrf, an independent implementation),
-against the backward-error property PA = LU + small, against systems with a
-known exact solution, and against the paper's qualitative findings.
+The LU of record (``orc.lu``: unblocked, partial pivoting, division by the
+pivot, each update product the mode's product) is checked against
+hand-worked factorisations (``tests/golden/lu_plain.txt``), against LAPACK
+(scipy's dgetrf, an independent implementation), against the backward-error
+property PA = LU + small, against systems with a known exact solution, and
+against the paper's qualitative findings.  The blocked regression mirror of
+the device schedule (``orc.lu_mirror``) is held to the LU of record.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg as sla
 
 import bfx_inputs as bi
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lu_plain.txt")
+
+
+def _f32(bits):
+    return np.array([int(b, 16) for b in bits], dtype=np.uint32).view(np.float32)
+
+
+def _lu_golden():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        head, a, lu, piv, info = (f.strip() for f in line.split("|"))
+        name, mode, n = head.split()
+        n = int(n)
+        rows.append((name, int(mode), _f32(a.split()).reshape(n, n),
+                     _f32(lu.split()).reshape(n, n), np.array(piv.split(), np.int32), int(info)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _lu_golden(), ids=lambda r: f"{r[0]}-x{r[1]}")
+def test_lu_golden(orc, row):
+    """Hand-worked factorisations: pivots, info and every factor bit."""
+    name, mode, A, LUe, pe, infoe = row
+    LU, p, info = orc.lu(mode, A)
+    assert info == infoe
+    assert np.array_equal(p, pe)
+    assert np.array_equal(LU.view(np.uint32), LUe.view(np.uint32)), (LU, LUe)
+
+
+def test_lu_golden_separates_division_from_reciprocal(orc):
+    """Case A of the golden file: a multiplier formed by a reciprocal of the
+    pivot (the blocked mirror's xGETF2 scaling) differs from the division, so
+    the golden pins the division."""
+    name, mode, A, LUe, _, _ = [r for r in _lu_golden() if r[0] == "A" and r[1] == 0][0]
+    LUm, _, _ = orc.lu_mirror(0, A, 64)
+    assert LUm[1, 0] != LUe[1, 0] and LUm[1, 1] != LUe[1, 1]
+
+
+@pytest.mark.parametrize("n", [64, 200])
+@pytest.mark.parametrize("mode", [0, 6, 9])
+def test_lu_matches_lapack_pivots_and_factors(orc, n, mode):
+    """Against LAPACK's FP64 LU on random [-1, 1] matrices (well separated
+    pivots): the same pivots and elementwise factor agreement at FP32 level,
+    |LU - LU64| <= 2 n 2^-24 max|LU64|."""
+    A = bi.uniform_pm1((n, n), 40 + n + mode)
+    lu64, piv64 = sla.lu_factor(A.astype(np.float64))
+    LU, p, info = orc.lu(mode, A)
+    assert info == 0
+    assert np.array_equal(p, piv64)
+    assert np.max(np.abs(LU - lu64)) <= 2 * n * 2.0**-24 * np.max(np.abs(lu64))
+
+
+@pytest.mark.parametrize("n,nb", [(200, 32), (333, 64)])
+@pytest.mark.parametrize("mode", [0, 3, 6, 9])
+def test_mirror_agrees_with_record(orc, n, nb, mode):
+    """The blocked mirror of the device schedule is a valid implementation of
+    the LU of record: the same pivots (x3, whose updates carry 2^-16-level
+    errors, may decide a late near-tie otherwise: the first half must agree)
+    and, over the columns where the pivots agree, factors within
+    4 n u max|LU|."""
+    A = bi.uniform_pm1((n, n), 7 * n + mode)
+    LU, p, _ = orc.lu(mode, A)
+    LUm, pm, _ = orc.lu_mirror(mode, A, nb)
+    u = 3 * 2.0**-16 if mode == 3 else 2.0**-24
+    diff = np.nonzero(p != pm)[0]
+    d = int(diff[0]) if diff.size else n
+    assert d >= (n // 2 if mode == 3 else n), (d, n)
+    err = np.max(np.abs(LU[:d, :d].astype(np.float64) - LUm[:d, :d]))
+    assert err <= 4 * n * u * np.max(np.abs(LU))
 
 
 def _apply_pivots(A, ipiv):
@@ -43,7 +121,7 @@ def test_dgetrf_singular_info(orc):
     A[:, 3] = 0.0
     _, _, info = orc.dgetrf(A)
     assert info == 4
-    LU32, _, info32 = orc.lu(0, A.astype(np.float32), nb=4)
+    LU32, _, info32 = orc.lu(0, A.astype(np.float32))
     assert info32 == 4
 
 
@@ -58,13 +136,14 @@ def test_dgetrs_known_solution(orc):
     assert np.max(np.abs(x - x_true)) <= 1e-13
 
 
+@pytest.mark.parametrize("which", ["record", "mirror"])
 @pytest.mark.parametrize("mode,u", [(0, 2.0**-24), (6, 2.0**-24), (9, 2.0**-24), (3, 3 * 2.0**-16),
                                     (1, 2.0**-8)])
-def test_lu_backward_error(orc, mode, u):
+def test_lu_backward_error(orc, mode, u, which):
     """PA = LU + E with |E| <= c n u |L||U| (the standard LU backward error)."""
     n = 160
     A = bi.uniform_pm1((n, n), 3)
-    LU, ipiv, info = orc.lu(mode, A, nb=32)
+    LU, ipiv, info = orc.lu(mode, A) if which == "record" else orc.lu_mirror(mode, A, 32)
     assert info == 0
     L, U = _unpack(LU)
     E = _apply_pivots(A, ipiv) - L @ U
@@ -73,13 +152,12 @@ def test_lu_backward_error(orc, mode, u):
 
 
 def test_lu_blocked_equals_fp64_pivots_and_close(orc):
-    """On a diagonally dominant-ish matrix the FP32 x6 LU picks the same pivots
-    as the FP64 LU and its factors agree to FP32 accuracy."""
+    """On a random matrix the FP32 and x6 LUs (record and mirror) pick the same
+    pivots as the FP64 LU and their factors agree to FP32 accuracy."""
     n = 128
     A = bi.uniform_pm1((n, n), 4)
     LU64, p64, _ = orc.dgetrf(A)
-    for mode in (0, 6):
-        LU, p, _ = orc.lu(mode, A, nb=32)
+    for LU, p, _ in [orc.lu(0, A), orc.lu(6, A), orc.lu_mirror(0, A, 32), orc.lu_mirror(6, A, 32)]:
         assert np.array_equal(p, p64)
         assert np.max(np.abs(LU - LU64)) <= 1e-4 * np.max(np.abs(LU64))
 
@@ -88,13 +166,16 @@ def test_lu_blocked_equals_fp64_pivots_and_close(orc):
 def test_e4_x6_lu_more_accurate_than_fp32_on_average(orc, scale):
     """Sec. IV-A (LU figure): averaged over runs, the element error of the
     bf16x6-update LU against the FP64 LU is below that of the FP32 LU, for the
-    ranges [-1, 1] and [-1e10, 1e10]."""
+    ranges [-1, 1] and [-1e10, 1e10].  The figure compares blocked LUs
+    (SGETRF, whose trailing update is a GEMM of depth nb), so the blocked form
+    is used here; in the unblocked form each update is a single product,
+    where the FP32 FMA rounds once and the x6 product twice (reading R16)."""
     ratios = []
     for s in range(20):
         A = (bi.uniform_pm1((128, 128), 200 + s) * scale).astype(np.float32)
         LU64, p64, _ = orc.dgetrf(A)
-        LU0, p0, _ = orc.lu(0, A, nb=16)
-        LU6, p6, _ = orc.lu(6, A, nb=16)
+        LU0, p0, _ = orc.lu_mirror(0, A, nb=16)
+        LU6, p6, _ = orc.lu_mirror(6, A, nb=16)
         if not (np.array_equal(p0, p64) and np.array_equal(p6, p64)):
             continue
         den = np.maximum(np.abs(LU64), np.finfo(np.float64).tiny)
@@ -112,7 +193,7 @@ def test_ir_exact_factors_zero_corrections(orc):
     A = np.diag(d).astype(np.float32)
     x_true = np.arange(1, 11, dtype=np.float64)[:, None]
     b = A.astype(np.float64) @ x_true
-    x, iters, conv, berr, info = orc.lu_solve_ir(3, A, b, nb=4)
+    x, iters, conv, berr, info = orc.lu_solve_ir(3, A, b)
     assert info == 0 and conv[0] == 1 and iters[0] == 1
     assert np.array_equal(x, x_true)
 
@@ -125,7 +206,7 @@ def test_e5_fp32_lu_ir_converges(orc, kappa):
     its, conv, ratio = [], [], []
     for s in range(20):
         P = bi.svd_system(50, kappa, s)
-        x, iters, c, berr, info = orc.lu_solve_ir(0, P.A32, P.b, nb=16)
+        x, iters, c, berr, info = orc.lu_solve_ir(0, P.A32, P.b)
         its.append(iters[0])
         conv.append(c[0])
         xd, _ = orc.dgesv(P.A32, P.b)
@@ -142,5 +223,5 @@ def test_ir_fails_when_factor_precision_too_low(orc):
     """Sec. III: refinement breaks down when cond(A) is large against the
     precision of the factors: bf16x1-update LU with cond 1e8 cannot converge."""
     P = bi.svd_system(60, 1e8, 0)
-    x, iters, conv, berr, info = orc.lu_solve_ir(1, P.A32, P.b, nb=16)
+    x, iters, conv, berr, info = orc.lu_solve_ir(1, P.A32, P.b)
     assert conv[0] == 0

@@ -63,7 +63,8 @@ typedef enum bfx_status {
  *   BFX_X5   : A split in two pieces, B in three: hi*hi, hi*mid, mid*hi,
  *              hi*lo, mid*mid (Sec. II-G's asymmetric case).  GEMM entry
  *              points only (bfx_gemm_bf16xN, bfx_gemm_presplit,
- *              bfx_gemm_bf16xN_f64); the others return BFX_EINVAL.  Its
+ *              bfx_gemm_bf16xN_f64, bfx_gemm_bf16xN_noalloc); the others
+ *              return BFX_EINVAL.  Its
  *              accuracy is bounded by A's dropped third piece (~2^-16 |a|),
  *              as for X3, unless A has at most 16 significant bits.
  * The mode's value is the number of bfloat16 products per scalar product. */
@@ -217,12 +218,17 @@ BFX_API bfx_status bfx_lowp_lu_ir_batched(bfx_lowp type, int count, int n, const
  * application that owns all device memory through its own pool and forbids
  * libraries from calling cudaMalloc, or a latency-critical loop where an
  * allocation is not acceptable.  The bfloat16 pieces go to a fixed 32 MiB
- * device array inside the library (reserved on every device that loads it,
- * held until the process exits); the call allocates nothing.  Limit: the
- * pieces need 2 * npieces * (round_up(m*kp,128) + round_up(n*kp,128)) bytes,
- * kp = k rounded up to 8, npieces = 1, 2, 3, 3 for X1, X3, X6, X9 (e.g. x6
- * fits m = n = k = 1536); larger problems return BFX_ENOMEM.  mode must be
- * X1..X9 (BFX_EINVAL otherwise).  The first call on a device looks up the
+ * device array inside the library; the call allocates nothing.  The array is
+ * reserved on a device when the library's module is loaded there (with lazy
+ * module loading, at the first launch of any of the library's kernels on
+ * that device), so every process using the library holds 32 MiB on each
+ * device it uses until it exits.  Limit: the pieces need
+ * 2 * (npa * round_up(m*kp,128) + npb * round_up(n*kp,128)) bytes, kp = k
+ * rounded up to 8, with (npa, npb) = (1, 1) for X1, (2, 2) for X3, (2, 3)
+ * for X5 and (3, 3) for X6, X8, X9 (e.g. x6 fits m = n = k = 1536); larger
+ * problems return BFX_ENOMEM before anything is launched.  Accepted modes:
+ * X1, X3, X5, X6, X8, X9; BFX_FP32 (which bfx_gemm_bf16xN sends to the SIMT
+ * GEMM) and any other value return BFX_EINVAL.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  All calls share the one
  * array: calls whose work overlaps on the GPU (other streams, other host

@@ -27,18 +27,6 @@ bool check_mode(bfx_mode mode) {
          mode == BFX_X6 || mode == BFX_X8 || mode == BFX_X9;
 }
 
-// Pieces of A and of B a GEMM mode reads (x5: two and three); false if the
-// mode has no tensor-core GEMM.
-bool gemm_pieces(bfx_mode mode, int* npa, int* npb) {
-  if (mode == BFX_X5) {
-    *npa = 2;
-    *npb = 3;
-    return true;
-  }
-  *npa = *npb = mode_pieces(mode);
-  return *npa > 0;
-}
-
 }  // namespace
 
 int* device_error_word() {
@@ -87,6 +75,18 @@ int mode_pieces(bfx_mode mode) {
     case BFX_X9: return 3;
     default: return 0;
   }
+}
+
+// Pieces of A and of B a GEMM mode reads (x5: two and three); false if the
+// mode has no tensor-core GEMM.
+bool gemm_pieces(bfx_mode mode, int* npa, int* npb) {
+  if (mode == BFX_X5) {
+    *npa = 2;
+    *npb = 3;
+    return true;
+  }
+  *npa = *npb = mode_pieces(mode);
+  return *npa > 0;
 }
 
 }  // namespace bfx

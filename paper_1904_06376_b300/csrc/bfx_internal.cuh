@@ -37,6 +37,7 @@ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 int mode_pieces(bfx_mode mode);  // 0 for invalid / FP32
+bool gemm_pieces(bfx_mode mode, int* npa, int* npb);  // GEMM pieces of A, B (x5: 2, 3)
 
 // split launchers (split.cu)
 bfx_status launch_split(int64_t rows, int64_t cols, const float* x, int64_t ldx, int npieces,

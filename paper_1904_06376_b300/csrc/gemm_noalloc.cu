@@ -6,8 +6,11 @@
 // libraries from calling cudaMalloc, or latency-critical loops where an
 // allocation (and the device-wide synchronisation cudaMalloc/cudaFree may
 // imply) is not acceptable.  For them this entry point keeps the pieces in a
-// file-scope device array of fixed size, reserved once when the library is
-// loaded on a device and held until the process exits.
+// file-scope device array of fixed size.  The array is reserved on a device
+// when the library's module is loaded there (with CUDA's lazy module loading,
+// at the first launch of any of the library's kernels on that device, by any
+// entry point), so every process using the library holds it on every device
+// it uses until the process exits.
 //
 // The array's name, used in host code, is only a host-side stand-in for the
 // symbol, not a device address.  Its device address is looked up once per
@@ -56,8 +59,8 @@ extern "C" BFX_API bfx_status bfx_gemm_bf16xN_noalloc(bfx_mode mode, int64_t m, 
                                                       int64_t lda, const float* d_B, int64_t ldb,
                                                       float beta, float* d_C, int64_t ldc,
                                                       bfx_stream stream) {
-  const int np = mode_pieces(mode);
-  if (np == 0) return BFX_EINVAL;  // X1, X3, X6, X9 only
+  int npa = 0, npb = 0;
+  if (!gemm_pieces(mode, &npa, &npb)) return BFX_EINVAL;  // X1, X3, X5, X6, X8, X9
   if (m < 0 || n < 0 || k < 0) return BFX_EINVAL;
   if (m == 0 || n == 0) return BFX_OK;
   if (!d_C || ldc < n) return BFX_EINVAL;
@@ -65,24 +68,24 @@ extern "C" BFX_API bfx_status bfx_gemm_bf16xN_noalloc(bfx_mode mode, int64_t m, 
   if (k == 0) return launch_scale(m, n, beta, d_C, ldc, s);
   if (!d_A || !d_B || lda < k || ldb < n) return BFX_EINVAL;
   if (m >= INT32_MAX || n >= INT32_MAX || k >= INT32_MAX) return BFX_EUNSUPPORTED;
-  // pieces: np planes of A (m x kp) and np planes of B^T (n x kp), kp = k
+  // pieces: npa planes of A (m x kp) and npb planes of B^T (n x kp), kp = k
   // rounded up to 8, each plane on a 256-byte boundary
   const int64_t kp = round_up(k, 8);
   const int64_t ap = round_up(m * kp, 128);
   const int64_t bp = round_up(n * kp, 128);
-  const double need = 2.0 * np * (static_cast<double>(ap) + static_cast<double>(bp));
+  const double need = 2.0 * (npa * static_cast<double>(ap) + npb * static_cast<double>(bp));
   if (need > static_cast<double>(kNoAllocScratchBytes)) return BFX_ENOMEM;
   if (!is_sm103()) return BFX_EUNSUPPORTED;
   void* scratch = nullptr;
   bfx_status st = noalloc_scratch(&scratch);
   if (st != BFX_OK) return st;
   uint16_t* Ap = static_cast<uint16_t*>(scratch);
-  uint16_t* Bp = Ap + np * ap;
-  st = launch_split(m, k, d_A, lda, np, Ap, np > 1 ? Ap + ap : nullptr,
-                    np > 2 ? Ap + 2 * ap : nullptr, kp, s);
+  uint16_t* Bp = Ap + npa * ap;
+  st = launch_split(m, k, d_A, lda, npa, Ap, npa > 1 ? Ap + ap : nullptr,
+                    npa > 2 ? Ap + 2 * ap : nullptr, kp, s);
   if (st != BFX_OK) return st;
-  st = launch_split_transpose(k, n, d_B, ldb, np, Bp, np > 1 ? Bp + bp : nullptr,
-                              np > 2 ? Bp + 2 * bp : nullptr, kp, s);
+  st = launch_split_transpose(k, n, d_B, ldb, npb, Bp, npb > 1 ? Bp + bp : nullptr,
+                              npb > 2 ? Bp + 2 * bp : nullptr, kp, s);
   if (st != BFX_OK) return st;
   return launch_gemm_presplit(mode, m, n, k, alpha, Ap, kp, ap, Bp, kp, bp, beta, d_C, ldc, s);
 }

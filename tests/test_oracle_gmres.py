@@ -152,3 +152,34 @@ def test_e6_diag_dominant_fp32_lu_gmres(orc, n):
     assert 1.0 <= np.mean(its) <= 3.0
     if n > 10:
         assert np.mean(inn1) > np.mean(inn32)
+
+
+def test_kappa_1e12_forward_error_distribution(orc):
+    """Why "within 10x of FP64 dgesv" is read over a distribution at kappa 1e12
+    (reading R22).  Over 24 systems (n = 96, config 3's generator), two FP64
+    backward-stable LU solvers, LAPACK's dgesv (scipy) and the oracle's own
+    FP64 LU, already differ in forward error by more than 10x on some systems:
+    the forward error, of order kappa times the backward error, swings with how
+    x_true falls on the smallest singular directions.  The oracle's GMRES-IR
+    (x6 factors) is held to the same distributional rule as the device: the
+    median ratio to the FP64 LU at most 10, at least 80 % of systems within
+    10x, none beyond 100x."""
+    import scipy.linalg as sla
+
+    r_gm, r_lapack = [], []
+    for s in range(24):
+        P = bi.svd_system(96, 1e12, 40 + s)
+        LU, ipiv, info = orc.lu(6, P.A32)
+        assert info == 0
+        xd, _ = orc.dgesv(P.A32, P.b)
+        fe64 = _fe(xd, P)
+        x, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b)
+        assert conv[0] == 1
+        xl = sla.solve(P.A32.astype(np.float64), P.b)
+        r_gm.append(_fe(x, P) / fe64)
+        r_lapack.append(_fe(xl, P) / fe64)
+    r_gm, r_lapack = np.array(r_gm), np.array(r_lapack)
+    assert r_lapack.max() > 10 or r_lapack.min() < 0.1  # FP64 against FP64 swings
+    assert np.median(r_gm) <= 10
+    assert np.mean(r_gm <= 10) >= 0.8
+    assert r_gm.max() <= 100

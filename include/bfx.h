@@ -6,19 +6,27 @@
  *
  * C ABI.  Every pointer argument named d_* is a device pointer on the current
  * CUDA device; h_* pointers are host memory.  The caller owns every buffer:
- * the library never frees caller memory and allocates none on the calls below
- * (scratch space is a caller-provided workspace whose size a *_workspace_size
- * query returns).  Matrices are row-major with a leading dimension (elements
+ * the library never frees caller memory.  The compute calls (split, GEMM,
+ * dot, LU, solves) allocate no device memory: their scratch space is a
+ * caller-provided workspace whose size a *_workspace_size query returns.  Two
+ * host-thread resources are created once and kept until the thread ends:
+ * the LU's auxiliary stream and two events (on the thread's first LU call on
+ * a device) and, for the GMRES phase of bfx_solve_ir, a small pinned host
+ * ring with its events.  The batch, autotune and server calls allocate as
+ * each says.  Matrices are row-major with a leading dimension (elements
  * between the starts of consecutive rows).  bfloat16 values travel as their
  * 16-bit patterns in uint16_t.
  *
  * Calls are asynchronous on the given stream (a cudaStream_t passed as
- * bfx_stream; NULL is the legacy default stream).  The returned status only
- * reports what is known at launch: invalid arguments (BFX_EINVAL), a shape or
- * device the kernels do not support (BFX_EUNSUPPORTED), a workspace that is
- * too small (BFX_ENOMEM) or a CUDA launch error (BFX_ECUDA).  Outcomes computed
- * on the device (a zero pivot, non-convergence, a device-side wait that
- * expired) are written to device memory the caller reads after synchronising.
+ * bfx_stream; NULL is the legacy default stream), except where a call says
+ * it is synchronous (bfx_solve_ir, which decides escalation and GMRES-IR on
+ * the host; bfx_device_error; the autotuner; the server's wait).  For the
+ * asynchronous calls the returned status only reports what is known at
+ * launch: invalid arguments (BFX_EINVAL), a shape or device the kernels do
+ * not support (BFX_EUNSUPPORTED), a workspace that is too small (BFX_ENOMEM)
+ * or a CUDA launch error (BFX_ECUDA).  Outcomes computed on the device (a
+ * zero pivot, non-convergence, a device-side wait that expired) are written
+ * to device memory the caller reads after synchronising.
  *
  * There is no CPU fallback: every entry point runs its work in the library's
  * own sm_103a kernels.
@@ -346,6 +354,28 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
                                 int64_t ldx, const bfx_ir_params* h_params,
                                 bfx_ir_result* h_result, void* d_ws, size_t ws_bytes,
                                 bfx_stream stream);
+
+/* The same solve, asynchronous: every step is enqueued on `stream` and the
+ * result goes to device memory, so solves can be chained on a stream (or
+ * captured) without the host reading anything back.  It runs the plain
+ * refinement of bfx_solve_ir with the given mode, the same kernels in the
+ * same order, and makes the stop decisions on the device: x and the result
+ * equal bfx_solve_ir's with escalate = 0 and gmres = 0.  Exactly max_iter
+ * refinement steps are enqueued; once every column has stopped, the later
+ * ones return at once.  h_params as bfx_solve_ir, except that escalate and
+ * gmres must be 0 (BFX_EINVAL otherwise: both need host decisions); NULL
+ * means the defaults with escalate = gmres = 0.  d_result (device,
+ * caller-owned) receives the bfx_ir_result when the stream reaches the end
+ * of the solve: info > 0 is an exactly zero pivot (x is then not written),
+ * converged = 0 a solve that did not converge (x holds the last iterate).
+ * Workspace: bfx_solve_ir_workspace_size(mode, n, nrhs, params) with the
+ * same params.  Returns only launch-time errors (BFX_EINVAL, BFX_ENOMEM,
+ * BFX_EUNSUPPORTED, BFX_ECUDA); n and nrhs must be >= 1. */
+BFX_API bfx_status bfx_solve_ir_async(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
+                                      int64_t lda, const double* d_b, int64_t ldb, double* d_x,
+                                      int64_t ldx, const bfx_ir_params* h_params,
+                                      bfx_ir_result* d_result, void* d_ws, size_t ws_bytes,
+                                      bfx_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Batched solves: many independent systems A_s x_s = b_s of uneven sizes

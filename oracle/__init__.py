@@ -270,7 +270,7 @@ def lu(mode: int, A):
 
 def lu_mirror(mode: int, A, nb: int = 64):
     """Regression mirror, not the oracle of record: the blocked schedule of
-    the device LU (8-column panel tiles, reciprocal scaling, rank-nb trailing
+    the device LU (8-column panel tiles, division by the pivot, rank-nb trailing
     updates by the mode's product), so a change of the device's FP32
     arithmetic shows bit for bit."""
     LU = np.array(A, dtype=np.float32, order="C", copy=True)

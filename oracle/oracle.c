@@ -570,8 +570,8 @@ int orc_lu_plain(int mode, int64_t n, float* A, int64_t lda, int32_t* ipiv) {
 }
 
 /* REGRESSION MIRROR, not the oracle of record: the blocked schedule the
- * device LU runs (tiles of 8 panel columns, reciprocal scaling as LAPACK's
- * xGETF2, rank-nb trailing updates), restated here so that a change of the
+ * device LU runs (tiles of 8 panel columns, multipliers by division,
+ * rank-nb trailing updates), restated here so that a change of the
  * device's FP32 arithmetic shows up bit for bit.  Agreement with it says the
  * device still runs this schedule; agreement with the method is checked
  * against orc_lu_plain and orc_dgetrf. */
@@ -610,14 +610,7 @@ int orc_lu(int mode, int64_t n, int64_t nb, float* A, int64_t lda, int32_t* ipiv
           }
         float piv = A[j * lda + j];
         if (piv == 0.0f) { if (info == 0) info = (int)(j + 1); continue; }
-        /* scale by the reciprocal of the pivot, or divide by a subnormal pivot */
-        /* (LAPACK xGETF2's rule, with its sfmin = the smallest normal number)   */
-        if (fabsf(piv) >= 1.17549435e-38f) {
-          const float rcp = 1.0f / piv;
-          for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] * rcp;
-        } else {
-          for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
-        }
+        for (int64_t i = j + 1; i < n; ++i) A[i * lda + j] = A[i * lda + j] / piv;
         for (int64_t i = j + 1; i < n; ++i) {
           float l = A[i * lda + j];
           for (int64_t c = j + 1; c < j0 + jw; ++c)

@@ -36,6 +36,8 @@ from ._bfx import (  # noqa: F401
     lowp_lu_ir_batched,
     lu_bf16xN,
     solve_ir,
+    solve_ir_async,
+    decode_ir_result,
     solve_ir_workspace_size,
     library_path,
     num_sms,

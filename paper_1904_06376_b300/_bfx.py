@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         "bfx_lu_bf16xN": (i32, [i32, i64, i32, vp, i64, vp, vp, vp, sz, vp]),
         "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, vp]),
         "bfx_solve_ir": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
+        "bfx_solve_ir_async": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
         "bfx_batch_create": (i32, [vp, i32, i32, vp, i32, vp]),
         "bfx_batch_workspace_size": (sz, [vp]),
         "bfx_batch_solve": (i32, [vp, vp, vp, vp, vp, vp, sz, vp]),
@@ -367,6 +368,41 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     if code not in (0, 5, 6) or (raise_on_status and code != 0):
         _check("bfx_solve_ir", code)
     return x, r.as_dict(), code
+
+
+IR_RESULT_BYTES = ctypes.sizeof(IrResult)
+
+
+def solve_ir_async(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None,
+                   max_iter: int = 50, tol: float = 2.0 ** -53, tol_b: float = -1.0,
+                   stall: float = 0.5, nb: int = 64, result: torch.Tensor = None,
+                   workspace: torch.Tensor = None, stream=None):
+    """Enqueue the plain refinement solve (no escalation, no GMRES) on the
+    stream; nothing is read back.  Returns (x, result) with ``result`` a
+    device uint8 tensor holding the bfx_ir_result (``decode_ir_result``)."""
+    n = A.shape[0]
+    if b.dim() == 1:
+        b = b[:, None]
+    nrhs = b.shape[1]
+    if x is None:
+        x = torch.empty((n, nrhs), dtype=torch.float64, device=A.device)
+    if result is None:
+        result = torch.zeros(IR_RESULT_BYTES, dtype=torch.uint8, device=A.device)
+    p = IrParams(max_iter, tol, tol_b, stall, 0, nb, 0, 0, 0.0)
+    wsb = solve_ir_workspace_size(mode, n, nrhs, p)
+    if workspace is None or workspace.numel() * workspace.element_size() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    _check("bfx_solve_ir_async",
+           lib().bfx_solve_ir_async(mode, n, nrhs, _ptr(A), A.stride(0), _ptr(b), b.stride(0),
+                                    _ptr(x), x.stride(0), ctypes.byref(p), _ptr(result),
+                                    _ptr(workspace), wsb, _stream(stream)))
+    return x, result
+
+
+def decode_ir_result(result: torch.Tensor) -> dict:
+    """The bfx_ir_result an asynchronous solve wrote (copies it to the host)."""
+    raw = bytes(result.cpu().numpy().tobytes())
+    return IrResult.from_buffer_copy(raw[:IR_RESULT_BYTES]).as_dict()
 
 
 class BatchConfig(ctypes.Structure):

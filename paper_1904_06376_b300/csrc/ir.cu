@@ -115,7 +115,9 @@ __global__ void __launch_bounds__(256)
     ir_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
                        const double* __restrict__ b, int64_t ldb,
                        const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
-                       int64_t ldr, int c0, double* __restrict__ rn) {
+                       int64_t ldr, int c0, double* __restrict__ rn,
+                       const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;  // asynchronous solve: every column has stopped
   __shared__ double part[RES_ROWS][RES_WPR][NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int lr = wid / RES_WPR, q = wid - lr * RES_WPR;
@@ -177,7 +179,9 @@ constexpr unsigned long long kTrsvSentinel = 0xFFF4000000000001ull;
 __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
                                  const int32_t* __restrict__ perm, int64_t n, int nrhs,
                                  double* __restrict__ d, int64_t ldd, double* __restrict__ fill,
-                                 double* __restrict__ fill2, int* __restrict__ tickets) {
+                                 double* __restrict__ fill2, int* __restrict__ tickets,
+                                 const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   if (tickets && blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -365,7 +369,9 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     ir_trsv_kernel(const float* __restrict__ F, int64_t ldf, int n,
                    const double* __restrict__ Dinv, const double* __restrict__ Gm,
                    double* __restrict__ v, double* __restrict__ y, int R,
-                   int* __restrict__ ticket, int* __restrict__ err) {
+                   int* __restrict__ ticket, int* __restrict__ err,
+                   const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;  // every CTA leaves: no block is waited on
   extern __shared__ __align__(16) uint8_t trsv_smem[];
   double* Ds = reinterpret_cast<double*>(trsv_smem);                       // [TB][TB + 1]
   double* Gs = Ds + TB * (TB + 1);                                          // [TB][TB + 1]
@@ -623,7 +629,9 @@ constexpr size_t kTrsvSmem = 2 * sizeof(double) * TB * (TB + 1) + 2 * sizeof(flo
 // x += d on active columns; dn[c] = max|d|, xn[c] = max|x| (must start at 0).
 __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
                                  int64_t ldd, int64_t n, int nrhs, const int32_t* __restrict__ active,
-                                 double* __restrict__ dn, double* __restrict__ xn) {
+                                 double* __restrict__ dn, double* __restrict__ xn,
+                                 const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e / nrhs;
@@ -1270,6 +1278,12 @@ int grid_elems(int64_t work) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, 8LL * sms)));
 }
 
+// Per-column stop state of the asynchronous solve (bfx_solve_ir_async).
+struct IraState {
+  int32_t conv, stalled, iters, pad;
+  double dprev;
+};
+
 struct IrWs {
   float* LU;
   int32_t* ipiv;
@@ -1288,6 +1302,8 @@ struct IrWs {
   double* Hl;     // inverse-scaled blocks Linv_b L[b, k] (GMRES only), per block in solve order
   double* Hu;     // the same for U
   int32_t* tsync; // triangular-solve tickets, one per triangle
+  int32_t* live;  // asynchronous solve: columns still refining (0: later steps skip)
+  IraState* ira;  // asynchronous solve: per-column stop state
   void* luws;
   size_t luws_bytes;
   // GMRES-IR (gm_m > 0 only)
@@ -1330,6 +1346,8 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.Ug = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.y1 = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
   w.tsync = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2));
+  w.live = reinterpret_cast<int32_t*>(take(sizeof(int32_t)));
+  w.ira = reinterpret_cast<IraState*>(take(sizeof(IraState) * nrhs));
   size_t lub = 0;
   for (bfx_mode m : {BFX_X1, BFX_X3, BFX_X6, BFX_X8, BFX_X9})
     if (static_cast<int>(m) >= static_cast<int>(mode)) lub = std::max(lub, lu_workspace_bytes(m, n, nb));
@@ -1374,7 +1392,8 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
 // use_h (the inverse-scaled blocks Hl, Hu computed for these factors): the
 // row-sliced solves instead; the backward one publishes through y2 (also
 // sentinel-filled by the gather) and writes its result to d.
-bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_h = false) {
+bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_h = false,
+                      const int32_t* gate = nullptr) {
   static const bool attr_ok = [] {
     return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kTrsvSmem)) == cudaSuccess &&
@@ -1389,7 +1408,7 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
   const unsigned grid = static_cast<unsigned>(nblk * G);
   ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                        w.y1, use_h ? w.y2 : nullptr, w.tsync);
+                                                        w.y1, use_h ? w.y2 : nullptr, w.tsync, gate);
   if (use_h) {
     const unsigned hgrid = static_cast<unsigned>(nblk * G * TRSV_S);
     ir_trsv_h_kernel<true><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hl, w.Linv, N, w.d, w.y1, nullptr,
@@ -1399,26 +1418,30 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
     return last_launch_status();
   }
   ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.y1,
-                                                             nrhs, w.tsync, err);
+                                                             nrhs, w.tsync, err, gate);
   ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Uinv, w.Ug, w.y1, w.d,
-                                                              nrhs, w.tsync + 1, err);
+                                                              nrhs, w.tsync + 1, err, gate);
   return last_launch_status();
 }
 
 bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int nrhs,
                     const double* b, int64_t ldb, const double* x, int64_t ldx, double* rn,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int32_t* gate = nullptr) {
   const unsigned blocks = static_cast<unsigned>(ceil_div(n, RES_ROWS));
   const int N = static_cast<int>(n);
   int c0 = 0;
   for (; c0 + 8 <= nrhs; c0 += 8)
-    ir_residual_kernel<8><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+    ir_residual_kernel<8><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
+                                                    gate);
   for (; c0 + 4 <= nrhs; c0 += 4)
-    ir_residual_kernel<4><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+    ir_residual_kernel<4><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
+                                                    gate);
   for (; c0 + 2 <= nrhs; c0 += 2)
-    ir_residual_kernel<2><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+    ir_residual_kernel<2><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
+                                                    gate);
   for (; c0 < nrhs; ++c0)
-    ir_residual_kernel<1><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn);
+    ir_residual_kernel<1><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
+                                                    gate);
   return last_launch_status();
 }
 
@@ -1792,6 +1815,125 @@ __global__ void __launch_bounds__(BIR_THREADS)
   }
 }
 
+// ------------------------------------------------------- asynchronous solve
+// The stop decisions of bfx_solve_ir, made on the device so that a whole
+// solve is enqueued without the host reading anything back.  *live counts
+// the columns still refining; once it is 0 the gated kernels of the later
+// steps return at once.
+
+// after the factorisation: a zero pivot stops the solve before it starts
+__global__ void ira_start_kernel(const int32_t* __restrict__ info, int R,
+                                 int32_t* __restrict__ active, int32_t* __restrict__ live,
+                                 IraState* __restrict__ st) {
+  const bool ok = *info == 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) {
+    active[c] = ok ? 1 : 0;
+    st[c] = IraState{0, 0, 0, 0, 0.0};
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *live = ok ? R : 0;
+}
+
+// x <- d (x0 of the asynchronous solve; nothing is written after a zero pivot)
+__global__ void ira_copy_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
+                                int64_t n, int R, const int32_t* __restrict__ gate) {
+  if (*gate == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * R;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / R;
+    const int c = static_cast<int>(e - i * R);
+    x[i * ldx + c] = d[e];
+  }
+}
+
+// after x0 = LU^-1 P b: the first correction is tested for a stall against |x0|
+__global__ void ira_x0_kernel(const double* __restrict__ xn, int R, IraState* __restrict__ st) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x)
+    st[c].dprev = xn[c];
+}
+
+// after x += d: bfx_solve_ir's tests for every active column (one CTA)
+__global__ void __launch_bounds__(256)
+    ira_decide_kernel(const double* __restrict__ dn, const double* __restrict__ xn, int R,
+                      double tol, double stall, int32_t* __restrict__ active,
+                      IraState* __restrict__ st, int32_t* __restrict__ live) {
+  __shared__ int count;
+  if (*live == 0) return;  // this step ran nothing
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int c = threadIdx.x; c < R; c += blockDim.x) {
+    if (!active[c]) continue;
+    const double d = dn[c], x = xn[c];
+    IraState q = st[c];
+    ++q.iters;
+    int act = 1;
+    if (!(d == d) || !(x == x)) {  // NaN: diverged
+      act = 0;
+    } else if (d <= tol * x) {
+      act = 0;
+      q.conv = 1;
+    } else if (d >= stall * q.dprev) {
+      act = 0;
+      q.stalled = 1;
+    } else {
+      q.dprev = d;
+    }
+    st[c] = q;
+    active[c] = act;
+    mine += act;
+  }
+  if (mine) atomicAdd(&count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *live = count;
+}
+
+// after |x| (xn) and |b - A x| (rn) of every column: backward errors, the
+// stalled columns whose backward error is small enough count as converged,
+// and the result (one CTA)
+__global__ void __launch_bounds__(256)
+    ira_finish_kernel(const double* __restrict__ norms, int R, const IraState* __restrict__ st,
+                      double tol_b, const int32_t* __restrict__ info, int mode,
+                      bfx_ir_result* __restrict__ res) {
+  __shared__ double s_berr[256];
+  __shared__ int s_all[256], s_it[256];
+  const double anorm = norms[0];
+  const double* bn = norms + 1;
+  const double* xn = bn + 2 * R;
+  const double* rn = bn + 3 * R;
+  double berr = 0.0;
+  int all = 1, itmax = 0;
+  for (int c = threadIdx.x; c < R; c += blockDim.x) {
+    const double den = anorm * xn[c] + bn[c];
+    double be = den > 0 ? rn[c] / den : 0.0;
+    if (!(be == be)) be = INFINITY;
+    const int conv = st[c].conv || (st[c].stalled && be <= tol_b);
+    berr = fmax(berr, be);
+    all = all && conv;
+    itmax = max(itmax, st[c].iters);
+  }
+  s_berr[threadIdx.x] = berr;
+  s_all[threadIdx.x] = all;
+  s_it[threadIdx.x] = itmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < blockDim.x; ++k) {  // fixed order
+      berr = fmax(berr, s_berr[k]);
+      all = all && s_all[k];
+      itmax = max(itmax, s_it[k]);
+    }
+    bfx_ir_result r{};
+    r.info = *info;
+    r.mode_used = mode;
+    r.converged = (r.info == 0 && all) ? 1 : 0;
+    r.iters = r.info == 0 ? itmax : 0;
+    r.refactorizations = 0;
+    r.berr = r.info == 0 ? berr : INFINITY;
+    r.gmres_steps = 0;
+    r.arnoldi = 0;
+    *res = r;
+  }
+}
+
 }  // namespace
 
 bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_slots,
@@ -2000,7 +2142,8 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
         return st;
       }
       if (cudaMemsetAsync(dn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
-      ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn);
+      ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn,
+                                                         nullptr);
       if (cudaMemcpyAsync(h.data(), w.norms, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                           s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess)
@@ -2074,6 +2217,80 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       stalled[c] = 0;
     }
   }
+}
+
+BFX_API bfx_status bfx_solve_ir_async(bfx_mode mode, int64_t n, int64_t nrhs, const float* d_A,
+                                      int64_t lda, const double* d_b, int64_t ldb, double* d_x,
+                                      int64_t ldx, const bfx_ir_params* h_params,
+                                      bfx_ir_result* d_result, void* d_ws, size_t ws_bytes,
+                                      bfx_stream stream) {
+  if (mode != BFX_FP32 && mode_pieces(mode) == 0) return BFX_EINVAL;
+  if (n <= 0 || nrhs <= 0 || !d_result) return BFX_EINVAL;
+  if (!d_A || !d_b || !d_x || lda < n || ldb < nrhs || ldx < nrhs) return BFX_EINVAL;
+  if (n >= (1 << 30) || nrhs > (1 << 20)) return BFX_EUNSUPPORTED;
+  bfx_ir_params p = ir_defaults();
+  p.escalate = 0;
+  p.gmres = 0;
+  if (h_params) p = *h_params;
+  if (p.escalate != 0 || p.gmres != 0) return BFX_EINVAL;  // both need host decisions
+  if (!ir_resolve(&p, n, &p)) return BFX_EINVAL;
+  if (mode != BFX_FP32 && !is_sm103()) return BFX_EUNSUPPORTED;
+  IrWs w = carve(d_ws, mode, n, nrhs, p.nb, 0);
+  if (!d_ws || ws_bytes < w.total || !aligned(d_ws, 256)) return BFX_ENOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int R = static_cast<int>(nrhs);
+  const int N = static_cast<int>(n);
+  double* anorm = w.norms;
+  double* bn = w.norms + 1;
+  double* dn = bn + R;
+  double* xn = dn + R;
+  double* rn = xn + R;
+  const unsigned cgrid = static_cast<unsigned>(std::min<int64_t>(ceil_div(R, 256), 1024));
+  bfx_status st;
+  if (cudaMemsetAsync(w.norms, 0, sizeof(double) * (1 + 4 * R), s) != cudaSuccess) return BFX_ECUDA;
+  ir_anorm_kernel<<<static_cast<unsigned>(ceil_div(n * 32, 256)), 256, 0, s>>>(d_A, lda, N, anorm);
+  ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_b, ldb, n, R, bn);
+  // ---- factor; a zero pivot leaves *live = 0 and every gated kernel idle
+  if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n, n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return BFX_ECUDA;
+  if ((st = lu_factor(mode, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s)) != BFX_OK)
+    return st;
+  ira_start_kernel<<<cgrid, 256, 0, s>>>(w.info, R, w.active, w.live, w.ira);
+  const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
+  ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
+  ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
+  if (nblk > 1) {
+    ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
+    ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
+  }
+  const bool sm = n <= 6144;
+  ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+  // ---- x0 = LU^-1 P b
+  if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R, n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return BFX_ECUDA;
+  if ((st = lu_solve64(w, n, R, s, false, w.live)) != BFX_OK) return st;
+  ira_copy_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, n, R, w.live);
+  ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
+  ira_x0_kernel<<<cgrid, 256, 0, s>>>(xn, R, w.ira);
+  // ---- max_iter refinement steps, each skipped once every column stopped
+  for (int it = 0; it < p.max_iter; ++it) {
+    if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s, w.live)) != BFX_OK)
+      return st;
+    if ((st = lu_solve64(w, n, R, s, false, w.live)) != BFX_OK) return st;
+    if (cudaMemsetAsync(dn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
+    ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn,
+                                                       w.live);
+    ira_decide_kernel<<<1, 256, 0, s>>>(dn, xn, R, p.tol, p.stall, w.active, w.ira, w.live);
+  }
+  // ---- backward errors and the result
+  if (cudaMemsetAsync(xn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
+  ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
+  if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, rn, s)) != BFX_OK) return st;
+  ira_finish_kernel<<<1, 256, 0, s>>>(w.norms, R, w.ira, p.tol_b, w.info, static_cast<int>(mode),
+                                      d_result);
+  return last_launch_status();
 }
 
 }  // extern "C"

@@ -3,13 +3,18 @@
 // and six products"; Sec. III: the cubic work in low precision).
 //
 // For each block column j0 (width jb <= nb):
-//   panel   : FP32 LU of A[j0:n, j0:j0+jb], blocked like LAPACK's panel in
-//             tiles of 8 columns: each tile is factored by one CTA from
-//             shared memory (pivot = first row of the largest |a|, found by a
-//             warp-shuffle argmax; row swap across the block column; division
-//             by the pivot; FMA rank-1 updates inside the tile), its rows of
-//             the block columns to its right are forward-substituted, and the
-//             rows below get the tile's rank-8 update (FMA, in column order);
+//   panel   : FP32 LU of A[j0:n, j0:j0+jb] (pivot = first row of the largest
+//             |a|, found by warp-shuffle argmaxes; whole block-column rows
+//             swapped; multipliers by IEEE division by the pivot; FMA rank-1
+//             updates in column order).  Up to 8 x 512 rows and jb <= 64:
+//             one thread-block cluster holds the whole block column in
+//             registers and exchanges the pivot candidates through
+//             distributed shared memory (one cluster barrier a column).
+//             Otherwise in tiles of 8 columns, one CTA each (registers or
+//             shared memory), the tile's rows of the block columns right of
+//             it forward-substituted and the rows below given the tile's
+//             rank-8 update: for every element the same operations in the
+//             same order;
 //   laswp   : the panel's row swaps applied to the columns left and right of it;
 //   trsm    : U12 = L11^-1 A12 (unit lower, FP32 FMA, one thread a column);
 //   update  : A22 <- A22 - L21 U12 by the mode's bfloat16 products on the
@@ -137,12 +142,9 @@ __device__ __forceinline__ void tile_body(float* __restrict__ A, int64_t lda, in
       __syncthreads();
       continue;
     }
-    // ---- scale the column, rank-1 update of the rest of the tile
-    // scale by the reciprocal of the pivot unless it is subnormal (LAPACK xGETF2)
-    const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
-    const float rcp = __fdiv_rn(1.0f, piv);
+    // ---- multipliers (IEEE division by the pivot), rank-1 update of the rest of the tile
     for (int r = j + 1 + t; r < n; r += PANEL_THREADS) {
-      const float l = use_rcp ? __fmul_rn(T(r, jj), rcp) : __fdiv_rn(T(r, jj), piv);
+      const float l = __fdiv_rn(T(r, jj), piv);
       T(r, jj) = l;
       for (int c = jj + 1; c < jw; ++c) T(r, c) = fmaf(-l, s_row[c], T(r, c));
     }
@@ -350,10 +352,8 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
       if (piv == 0.0f) {
         if (t == 0 && *info == 0) *info = j + 1;
       } else {
-        // ---- scale the column (by the reciprocal unless the pivot is
-        // subnormal), rank-1 update of the rest of the tile
-        const bool use_rcp = fabsf(piv) >= 1.17549435e-38f;
-        const float rcp = __fdiv_rn(1.0f, piv);
+        // ---- multipliers (IEEE division by the pivot), rank-1 update of
+        // the rest of the tile
         float u[TILE_W];
 #pragma unroll
         for (int c = 1; c < TILE_W; ++c) u[c] = prow[c];
@@ -361,7 +361,7 @@ __device__ __forceinline__ void tile_body_regs(float* __restrict__ A, int64_t ld
         for (int q = 0; q < RPT; ++q) {
           const int r = j0 + t + q * PANEL_THREADS;
           if (r > j && r < n) {
-            const float l = use_rcp ? __fmul_rn(v[q][0], rcp) : __fdiv_rn(v[q][0], piv);
+            const float l = __fdiv_rn(v[q][0], piv);
             v[q][0] = l;
 #pragma unroll
             for (int c = 1; c < TILE_W; ++c)
@@ -736,6 +736,329 @@ __global__ void lu_split_batched_kernel(const BatchLu* __restrict__ sys, int nb,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Whole block column by one thread-block cluster (single-system path).
+//
+// The block column [J0, J0+JB) of rows J0..n-1 (JB <= NB) is spread over the
+// cs CTAs of one cluster: CTA c holds rows J0 + c*CLP_THREADS + t, one row a
+// thread, the row's NB values in registers (one CTA of as many threads as
+// rows when they fit one CTA).  Per pivot column j:
+//  1. every thread offers its row's |a_rj| (rows >= j) as a key: the value's
+//     bits plus one (a NaN gets 0: never chosen over a number) with the row
+//     index; a warp keeps the largest key and, among equal keys, the lowest
+//     row (LAPACK's first row of the largest |a|) by two warp reductions;
+//     each warp's winner posts its row to shared memory, and the thread
+//     holding row j posts row j;
+//  2. after a CTA barrier the pushing warps reduce the warps' offers the
+//     same way and push the CTA's offer (key, row index, row) and, from CTA
+//     0, row j into an exchange slot of every CTA (distributed shared
+//     memory; plain shared memory in a cluster of one);
+//  3. one cluster barrier (release / acquire); warp 0 reduces the cs offers
+//     -> pivot row p (a NaN on the diagonal stays), then a CTA barrier; the
+//     holder of row j takes the pivot row, the holder of row p the old row j;
+//  4. rows below j: l = a_rj / a_jj (IEEE division), then a_rc <- fma(-l,
+//     u_jc, a_rc) for the block column's columns c > j, in column order.
+// Each element therefore sees the operations of the unblocked right-looking
+// LU of the block column, in the same order as the 8-column tile path.  The
+// exchange slots alternate by column parity: a CTA writes column j+2's offers
+// only after the barrier of column j+1, which no CTA reaches before it has
+// read column j's.  Columns go in groups of 8 whose register indices are
+// compile-time constants; after a group the row rotates left by 8, so after
+// NB / 8 groups it is back in place.
+constexpr int CLP_THREADS = 512;  // rows a CTA holds
+constexpr int CLP_MAX_CL = 16;    // exchange slots (16 would be a non-portable cluster size)
+constexpr int kPanelMaxCluster = 8;  // clusters launched: the portable size, up to 4096 rows
+
+template <int NB>
+struct ClusterSlot {
+  float row[CLP_MAX_CL][NB];  // each CTA's offered row (rotated register order)
+  float rowj[NB];             // row j before the swap
+  uint32_t key[CLP_MAX_CL];
+  uint32_t idx[CLP_MAX_CL];
+};
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  __syncwarp();  // the .aligned barrier wants the warp converged
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of `p` (this CTA's shared memory) in the shared window of CTA `rank`
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// store v at p in CTA `rank` (local when the cluster is a single CTA)
+template <class T>
+__device__ __forceinline__ void push_to(T* p, uint32_t rank, T v, bool local) {
+  if (local)
+    *p = v;
+  else
+    cl_st(cl_map(p, rank), v);
+}
+
+// pivot offer of a row: larger key wins, ties to the lower row index
+__device__ __forceinline__ uint32_t offer_key(float a) {
+  const float m = fabsf(a);
+  return m == m ? __float_as_uint(m) + 1u : 0u;  // a NaN below any number
+}
+// warp winner of (key, idx) over all 32 lanes: the largest key, then the
+// smallest index; *lane_out = a lane that offered it
+__device__ __forceinline__ void warp_offer(uint32_t key, uint32_t idx, uint32_t* kout,
+                                           uint32_t* iout, int* lane_out) {
+  const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
+  const uint32_t i = __reduce_min_sync(0xFFFFFFFFu, key == m ? idx : 0xFFFFFFFFu);
+  *kout = m;
+  *iout = i;
+  *lane_out = __ffs(__ballot_sync(0xFFFFFFFFu, key == m && idx == i)) - 1;
+}
+
+// One pivot column of the cluster panel; K = the column's register (the
+// current rotation puts column g*8 + K there), JB the block-column width.
+template <int NB, int K>
+__device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int n, int J0, int r,
+                                             bool has, int t, int lane, int wid, int nw, int cr,
+                                             int cs, ClusterSlot<NB>* slot, float (*wrow)[NB],
+                                             float* myrowj, uint32_t* wkey, uint32_t* widx,
+                                             int* s_dec, int* s_piv) {
+  constexpr int NQ = NB / 4;
+  const int j = J0 + jj, bf = jj & 1;
+  const int g8 = jj - K;  // columns rotated away so far
+  const bool local = cs == 1;
+  // ---- 1. offers: every warp's winner posts its row, the holder of row j posts row j
+  const bool offers = has && r >= j;
+  uint32_t wk, wi;
+  int wl;
+  warp_offer(offers ? offer_key(v[K]) : 0u, offers ? static_cast<uint32_t>(r) : 0xFFFFFFFFu, &wk,
+             &wi, &wl);
+  if (lane == 0) {
+    wkey[wid] = wk;
+    widx[wid] = wi;
+  }
+  if (lane == wl && offers) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      *reinterpret_cast<float4*>(&wrow[wid][4 * q]) =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  if (cr == 0 && t == jj) {  // row j = J0 + jj lives in CTA 0, thread jj
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      *reinterpret_cast<float4*>(&myrowj[4 * q]) =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+  __syncthreads();
+  // ---- 2. pushes: the pushing warps reduce the warps' offers themselves
+  const int npush = cs * NQ;
+  const bool push_rowj = cr == 0 && t >= npush && t < 2 * npush;
+  if (wid * 32 < npush) {  // whole warps: the reductions need every lane
+    uint32_t ck, ci;
+    int cw;
+    warp_offer(lane < nw ? wkey[lane] : 0u, lane < nw ? widx[lane] : 0xFFFFFFFFu, &ck, &ci, &cw);
+    cw = min(cw, nw - 1);  // every CTA offers a row (its rows are >= j)
+    if (t < npush) {
+      const int dst = t / NQ, q = t % NQ;
+      push_to(reinterpret_cast<float4*>(&slot[bf].row[cr][4 * q]), dst,
+              *reinterpret_cast<const float4*>(&wrow[cw][4 * q]), local);
+      if (q == 0) {
+        push_to(&slot[bf].key[cr], dst, ck, local);
+        push_to(&slot[bf].idx[cr], dst, ci, local);
+      }
+    }
+  }
+  if (push_rowj) {
+    const int e = t - npush, dst = e / NQ, q = e % NQ;
+    push_to(reinterpret_cast<float4*>(&slot[bf].rowj[4 * q]), dst,
+            *reinterpret_cast<const float4*>(&myrowj[4 * q]), local);
+  }
+  if (local)
+    __syncthreads();
+  else
+    cl_sync();
+  // ---- 3. the pivot: every warp reduces the cs offers (same data, same result)
+  uint32_t gk, gi;
+  int gw;
+  warp_offer(lane < cs ? slot[bf].key[lane] : 0u, lane < cs ? slot[bf].idx[lane] : 0xFFFFFFFFu,
+             &gk, &gi, &gw);
+  const float d = slot[bf].rowj[K];
+  const bool keep = (d != d || gi >= static_cast<uint32_t>(n));  // a NaN on the diagonal stays
+  const int p = keep ? j : static_cast<int>(gi);
+  const float* prow = keep ? slot[bf].rowj : slot[bf].row[min(gw, cs - 1)];
+  if (t == 0) s_piv[jj] = p;  // to global memory once, at the end: a global store before
+                              // the next release would hold it up
+  if (p != j && has) {
+    if (r == j) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(prow + 4 * q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      }
+    } else if (r == p) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(slot[bf].rowj + 4 * q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      }
+    }
+  }
+  const float piv = prow[K];
+  if (piv == 0.0f) {
+    if (t == 0 && s_dec[2] == 0) s_dec[2] = j + 1;  // the first zero pivot
+  } else if (has && r > j) {
+    // ---- 4. multiplier and rank-1 update of the row's later columns
+    const float l = __fdiv_rn(v[K], piv);
+    v[K] = l;
+    const int lim = JB - g8;  // registers below lim hold the block column's columns
+#pragma unroll
+    for (int q = (K + 1) / 4; q < NQ; ++q) {
+      if (4 * q >= lim) break;  // the same for every thread
+      const float4 u = *reinterpret_cast<const float4*>(prow + 4 * q);
+      const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 4 * q + e;
+        if (c > K && c < lim) v[c] = fmaf(-l, uu[e], v[c]);
+      }
+    }
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CLP_THREADS, 1)
+    lu_panel_cluster_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
+                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+  constexpr int MW = CLP_THREADS / 32;
+  constexpr int NQ = NB / 4;  // float4 words a row
+  static_assert(MW <= 32 && CLP_MAX_CL <= 32, "one warp reduces the offers");
+  static_assert(2 * CLP_MAX_CL * NQ <= CLP_THREADS, "pushes of the offered row and of row j");
+  static_assert(NB % 8 == 0, "columns go in groups of 8");
+  __shared__ __align__(16) ClusterSlot<NB> slot[2];
+  __shared__ __align__(16) float wrow[MW][NB];  // each warp's offered row
+  __shared__ __align__(16) float myrowj[NB];    // row j, in CTA 0
+  __shared__ uint32_t wkey[MW], widx[MW];
+  __shared__ int s_dec[3];   // s_dec[2]: the first zero pivot
+  __shared__ int s_piv[NB];  // the block column's pivots
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int cr = static_cast<int>(cl_rank()), cs = static_cast<int>(cl_size());
+  const int r = J0 + cr * CLP_THREADS + t;  // this thread's row
+  const bool has = r < n;
+  const bool vec = JB == NB && (lda % 4) == 0 && (J0 % 4) == 0 &&
+                   (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+  float v[NB];
+  {
+    const float* src = A + static_cast<int64_t>(has ? r : J0) * lda + J0;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 x = *reinterpret_cast<const float4*>(src + 4 * q);
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) v[c] = c < JB ? src[c] : 0.0f;
+    }
+    if (!has) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) v[c] = 0.0f;
+    }
+  }
+  if (t == 0) s_dec[2] = 0;
+  cl_sync();  // every CTA of the cluster runs before the first remote store
+  for (int g = 0; g < NB; g += 8) {
+#define BFX_PANEL_COL(K)                                                                       \
+  if (g + K < JB)                                                                              \
+    panel_column<NB, K>(v, g + K, JB, n, J0, r, has, t, lane, wid, nw, cr, cs, slot, wrow,     \
+                        myrowj, wkey, widx, s_dec, s_piv);
+    BFX_PANEL_COL(0)
+    BFX_PANEL_COL(1)
+    BFX_PANEL_COL(2)
+    BFX_PANEL_COL(3)
+    BFX_PANEL_COL(4)
+    BFX_PANEL_COL(5)
+    BFX_PANEL_COL(6)
+    BFX_PANEL_COL(7)
+#undef BFX_PANEL_COL
+    float tmp[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) tmp[c] = v[c];
+#pragma unroll
+    for (int c = 0; c < NB - 8; ++c) v[c] = v[c + 8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[NB - 8 + c] = tmp[c];
+  }
+  if (has) {
+    float* dst = A + static_cast<int64_t>(r) * lda + J0;
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        *reinterpret_cast<float4*>(dst + 4 * q) =
+            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < JB) dst[c] = v[c];
+    }
+  }
+  if (cr == 0) {
+    for (int c = t; c < JB; c += blockDim.x) ipiv[J0 + c] = s_piv[c];
+    if (t == 0 && s_dec[2] != 0 && *info == 0) *info = s_dec[2];
+  }
+  cl_sync();  // no CTA leaves while a remote store into it may be in flight
+}
+
+// Launch the cluster panel for the block column [J0, J0+JB) if it fits
+// (rows <= kPanelMaxCluster * CLP_THREADS, JB <= 64); returns false to fall
+// back on the tiles.  A single CTA has as many threads as rows (rounded up
+// to whole warps), a cluster CLP_THREADS a CTA.
+bool launch_panel_cluster(float* A, int64_t lda, int n, int J0, int JB, int32_t* ipiv,
+                          int32_t* info, cudaStream_t s, bfx_status* st) {
+  const int rows = n - J0;
+  const int cs = static_cast<int>(ceil_div(rows, CLP_THREADS));
+  if (JB > 64 || cs > kPanelMaxCluster) return false;
+  const int threads = cs == 1 ? static_cast<int>(round_up(rows, 32)) : CLP_THREADS;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cs);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(static_cast<unsigned>(cs), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e =
+      JB <= 32 ? cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<32>, A, lda, n, J0, JB, ipiv, info)
+               : cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<64>, A, lda, n, J0, JB, ipiv, info);
+  if (e != cudaSuccess) {  // e.g. a cluster size the device does not offer: use the tiles
+    cudaGetLastError();
+    return false;
+  }
+  *st = BFX_OK;
+  return true;
+}
+
 struct LuWs {
   int64_t kp, ap, bp;
   size_t bytes;
@@ -786,36 +1109,51 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   // host thread, joined to s by events) carries the rest of each trailing
   // update, so it runs while the next panel is factored.  The next row swaps
   // wait for it.  Each element sees the same operations as without it.
-  struct AuxStream {  // released when the host thread ends
+  // The auxiliary stream and its two events are created once per host thread
+  // and device (on the first LU call there) and kept until the thread ends;
+  // later calls create nothing.
+  struct Aux {
+    int dev = -1;
     cudaStream_t s = nullptr;
-    ~AuxStream() {
+    cudaEvent_t fork = nullptr, rest = nullptr;
+    ~Aux() { release(); }
+    void release() {
+      if (fork) cudaEventDestroy(fork);
+      if (rest) cudaEventDestroy(rest);
       if (s) cudaStreamDestroy(s);
+      fork = rest = nullptr;
+      s = nullptr;
+      dev = -1;
+    }
+    bool ready() {
+      int d = -1;
+      if (cudaGetDevice(&d) != cudaSuccess) return false;
+      if (d == dev && s) return true;
+      release();
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&rest, cudaEventDisableTiming) != cudaSuccess) {
+        release();
+        return false;
+      }
+      dev = d;
+      return true;
     }
   };
-  thread_local AuxStream aux_owner;
-  if (!aux_owner.s && cudaStreamCreateWithFlags(&aux_owner.s, cudaStreamNonBlocking) != cudaSuccess) {
-    aux_owner.s = nullptr;
-    return BFX_ECUDA;
-  }
+  thread_local Aux aux_owner;
+  if (!aux_owner.ready()) return BFX_ECUDA;
   cudaStream_t aux = aux_owner.s;
-  cudaEvent_t ev_fork = nullptr, ev_rest = nullptr;
-  if (cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess) return BFX_ECUDA;
-  if (cudaEventCreateWithFlags(&ev_rest, cudaEventDisableTiming) != cudaSuccess) {
-    cudaEventDestroy(ev_fork);
-    return BFX_ECUDA;
-  }
-  // owns the events; on every return path the caller's stream is joined to
-  // the auxiliary stream's last recorded work before the events go
+  cudaEvent_t ev_fork = aux_owner.fork, ev_rest = aux_owner.rest;
+  // on every return path the caller's stream is joined to the auxiliary
+  // stream's last recorded work
   struct Join {
     cudaStream_t s;
-    cudaEvent_t fork, rest;
+    cudaEvent_t rest;
     bool pending = false;
     ~Join() {
       if (pending) cudaStreamWaitEvent(s, rest, 0);
-      cudaEventDestroy(fork);
-      cudaEventDestroy(rest);
     }
-  } join{s, ev_fork, ev_rest};
+  } join{s, ev_rest};
   bool& rest_pending = join.pending;
   // C[:, c0 .. c0+nc) -= L21 U12[:, c0 .. c0+nc) for block column j0 on stream st
   auto update = [&](int j0, int jb, int c0, int nc, cudaStream_t st, bool split_l) -> bfx_status {
@@ -839,7 +1177,10 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   };
   for (int j0 = 0; j0 < N; j0 += nb) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
-    for (int t0 = j0; t0 < j0 + jb; t0 += TILE_W) {
+    bfx_status pst = BFX_OK;
+    const bool clustered = launch_panel_cluster(A, lda, N, j0, jb, ipiv, info, s, &pst);
+    if (pst != BFX_OK) return pst;
+    for (int t0 = j0; !clustered && t0 < j0 + jb; t0 += TILE_W) {
       const int tw = std::min(TILE_W, j0 + jb - t0);
       const int rows = N - t0;
       const size_t tsm = static_cast<size_t>(rows) * TILE_W * sizeof(float);

@@ -50,11 +50,16 @@ def test_lu_golden(orc, row):
 
 def test_lu_golden_separates_division_from_reciprocal(orc):
     """Case A of the golden file: a multiplier formed by a reciprocal of the
-    pivot (the blocked mirror's xGETF2 scaling) differs from the division, so
-    the golden pins the division."""
+    pivot (LAPACK xGETF2's scaling) differs from the division, so the golden
+    pins the division.  The mirror of the device's blocked schedule divides
+    too and reproduces the golden."""
     name, mode, A, LUe, _, _ = [r for r in _lu_golden() if r[0] == "A" and r[1] == 0][0]
-    LUm, _, _ = orc.lu_mirror(0, A, 64)
-    assert LUm[1, 0] != LUe[1, 0] and LUm[1, 1] != LUe[1, 1]
+    f = np.float32
+    l_rcp = f(f(1.25) * f(f(1.0) / f(3.0)))
+    assert l_rcp != LUe[1, 0]
+    assert int(np.array(l_rcp).view(np.uint32)) == 0x3ED55556
+    LUm, pm, _ = orc.lu_mirror(0, A, 64)
+    assert np.array_equal(LUm.view(np.uint32), LUe.view(np.uint32))
 
 
 @pytest.mark.parametrize("n", [64, 200])

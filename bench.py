@@ -226,6 +226,22 @@ def _fe(x, x_true):
     return float(np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)))
 
 
+def _ratio_to_dgesv(pairs, sample):
+    """Forward error of each solve divided by that of LAPACK's FP64 dgesv
+    (numpy) on the same system: pairs = [(x, P)]; returns the distribution."""
+    r = []
+    for x, P in pairs:
+        xd = np.linalg.solve(P.A32.astype(np.float64), P.b)
+        r.append(_fe(x, P.x_true) / max(_fe(xd, P.x_true), 1e-300))
+    r = np.array(r)
+    if r.size == 0:
+        return {"sample": sample, "count": 0}
+    return {"reference": "LAPACK dgesv (numpy), FP64, same A32 and b", "sample": sample,
+            "count": int(r.size), "median_ratio": float(np.median(r)),
+            "p90_ratio": float(np.percentile(r, 90)), "max_ratio": float(r.max()),
+            "frac_within_10x": float(np.mean(r <= 10.0))}
+
+
 def bench_ir_single(bfx, oracle, bi, dev):
     """Config 3: one n = 4096 system per condition number, bf16x3 trailing
     updates with escalation to x6, then GMRES-IR if plain refinement stalls;
@@ -297,6 +313,7 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
         by[f"1e{lo}-1e{lo + 1}"] = {"systems": int(msk.sum()), "converged": float(conv[msk].mean()),
                                     "median_forward_error": float(np.median(fe[msk])),
                                     "max_forward_error": float(fe[msk].max())}
+    ratio = _ratio_to_dgesv(list(zip(xs, probs)), f"all {count} systems")
     sample = list(range(0, count, count // 16))[:16]
     t0 = time.perf_counter()
     for i in sample:
@@ -306,6 +323,7 @@ def bench_batched(bfx, oracle, bi, dev, count=2000):
     return {"systems": count, "mode": "x6", "ms_per_batch": ms, "solves_per_s": count / (ms * 1e-3),
             "lu_eff_tflops": flops / (ms * 1e-3) / 1e12, "converged": float(conv.mean()),
             "mean_iters": float(iters.mean()), "by_condition": by,
+            "forward_error_vs_fp64_dgesv": ratio,
             "graph": "whole batch captured once, replayed per solve",
             "tile_shape": {"nb": best[0], "gemm_bn": best[1]},
             "autotune": [{"nb": r[0], "gemm_bn": r[1], "ms": r[2], "status": r[3]} for r in table],

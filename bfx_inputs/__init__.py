@@ -124,15 +124,35 @@ class SolveProblem:
         return self.b.shape[1]
 
 
+_UV_CACHE = {}
+
+
+def _orthogonal_pair(n: int, seed: int):
+    """U, V of svd_system (two QRs of Gaussians from the seed) and the
+    generator's state after them; large pairs are kept for reuse, so the
+    four condition numbers of one size and seed cost two QRs, not eight."""
+    key = (n, seed)
+    if key in _UV_CACHE:
+        U, V, state = _UV_CACHE[key]
+        rng = np.random.default_rng()
+        rng.bit_generator.state = state
+        return U, V, rng
+    rng = np.random.default_rng(seed)
+    U = _haar_like_orthogonal(n, rng)
+    V = _haar_like_orthogonal(n, rng)
+    if n >= 1024:
+        _UV_CACHE.clear()  # at most one large pair at a time
+        _UV_CACHE[key] = (U, V, rng.bit_generator.state)
+    return U, V, rng
+
+
 def svd_system(n: int, kappa: float, seed: int, nrhs: int = 1) -> SolveProblem:
     """A = U diag(sigma) V^T, sigma_i = kappa**(-i/(n-1)), rounded to FP32.
 
     b = A32 @ x_true is evaluated in FP64 from the FP32 matrix, so x_true is the
     exact solution of the FP32 problem up to the FP64 rounding of b.
     """
-    rng = np.random.default_rng(seed)
-    U = _haar_like_orthogonal(n, rng)
-    V = _haar_like_orthogonal(n, rng)
+    U, V, rng = _orthogonal_pair(n, seed)
     if n > 1:
         sigma = kappa ** (-np.arange(n, dtype=np.float64) / (n - 1))
     else:

@@ -80,3 +80,36 @@ def test_many_concurrent_requests_same_as_alone(bfx):
                                     escalate=False)
         assert np.array_equal(x, xa.cpu().numpy())
         assert res["iters"] == ra["iters"] and res["converged"] == ra["converged"]
+
+
+def test_mixed_requests_same_as_alone_x6_gmres(bfx, orc):
+    """bench.py's serving configuration: bf16x6 factors, escalation, GMRES-IR
+    for what plain refinement cannot finish, the Krylov length capped at
+    min(n, 1024).  Requests of kappa up to 1e10 go through GMRES-IR; each
+    result equals the same request solved alone (same kernels, same order),
+    bit for bit, with the same refinement and Arnoldi counts, and lies within
+    10x of the oracle's FP64 LU in forward error."""
+    rng = np.random.default_rng(11)
+    ns = [300, 96, 700, 160, 515, 64, 257, 420]
+    lks = [9.5, 2.0, 10.0, 6.0, 9.0, 1.0, 8.0, 4.0]
+    reqs = [bi.svd_system(n, 10.0 ** lk, 400 + i, nrhs=int(rng.integers(1, 4)))
+            for i, (n, lk) in enumerate(zip(ns, lks))]
+    srv = bfx.Server(budget_bytes=4 << 30, max_inflight=8, mode=6, escalate=True, gmres=1)
+    tickets = [srv.submit(P.A32, P.b) for P in reqs]
+    out = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_running"] >= 2
+    assert sum(res["gmres_steps"] > 0 for _, res in out) >= 2  # GMRES-IR ran in the mix
+    for P, (x, res) in zip(reqs, out):
+        assert res["status"] == 0 and res["converged"] == 1, res
+        xa, ra, code = bfx.solve_ir(6, torch.from_numpy(P.A32).cuda(), torch.from_numpy(P.b).cuda(),
+                                    escalate=True, nb=64, gmres=1, gmres_m=min(P.n, 1024))
+        assert code == 0
+        assert np.array_equal(x, xa.cpu().numpy())
+        for k in ("iters", "gmres_steps", "arnoldi", "refactorizations", "mode_used"):
+            assert res[k] == ra[k], k
+        xd, _ = orc.dgesv(P.A32, P.b)
+        fe = np.max(np.abs(x - P.x_true)) / np.max(np.abs(P.x_true))
+        fe64 = np.max(np.abs(xd - P.x_true)) / np.max(np.abs(P.x_true))
+        assert fe <= 10 * fe64 + 1e-15, (P.n, fe, fe64)

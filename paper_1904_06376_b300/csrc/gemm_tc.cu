@@ -56,6 +56,15 @@ namespace bfx {
 namespace {
 
 constexpr int BM = 128;     // UMMA M (one CTA, cta_group::1)
+// Long-K accuracy: beyond kChunkMinK the hi*hi product is accumulated in
+// chunks of kChunkK (a fresh tensor-memory accumulation each chunk) and the
+// chunk sums are added in FP32 with round to nearest by the epilogue.  The
+// tensor core adds each 16-deep block into its FP32 accumulator without
+// round-to-nearest, so over a long K the hi*hi accumulator's error grows
+// with the number of blocks; chunking bounds that growth to kChunkK / 16
+// blocks and leaves the rest to round-to-nearest additions.
+constexpr int kChunkK = 128;
+constexpr int kChunkMinK = 512;
 constexpr int GROUP_M = 16; // tile raster: groups of 16 row-blocks for L2 reuse
 
 struct Prod {
@@ -180,14 +189,15 @@ __host__ __device__ constexpr uint32_t pow2_cols(uint32_t c) {
   return p;
 }
 
-template <int MODE, int BN, int BK, int STAGES, bool FUSED = false, bool D64 = false>
+template <int MODE, int BN, int BK, int STAGES, bool FUSED = false, bool D64 = false, int CH = 0>
 struct TcConfig {
   static constexpr int NPA = mode_npa(MODE);
   static constexpr int NPB = mode_npb(MODE);
   static constexpr int NP = NPA;  // fused: both operands alike
   static constexpr int NPROD = MODE;
-  static constexpr int NACC = D64 ? MODE : ((MODE == 1) ? 1 : 2);
-  static constexpr int ACC_BUFS = (NACC * BN * 2 <= 512) ? 2 : 1;
+  // chunked (CH > 0): two D_main buffers (alternating K-chunks) and D_corr
+  static constexpr int NACC = D64 ? MODE : (CH > 0 ? 3 : ((MODE == 1) ? 1 : 2));
+  static constexpr int ACC_BUFS = CH > 0 ? 1 : ((NACC * BN * 2 <= 512) ? 2 : 1);
   static constexpr uint32_t TMEM_USED = NACC * BN * ACC_BUFS;
   static constexpr uint32_t TMEM_COLS = pow2_cols(TMEM_USED);
   static constexpr int SW = BK * 2;  // swizzle span = bytes of one K-slice row
@@ -204,7 +214,10 @@ struct TcConfig {
   static constexpr int S32_FIT = static_cast<int>((232448u - 1280u - STAGES * STAGE) / STAGE32);
   static constexpr int S32 = FUSED ? (S32_FIT < 8 ? S32_FIT : 8) : 0;
   static constexpr int CONV_WARPS = FUSED ? 16 : 0;
-  static constexpr int THREADS = 192 + 32 * CONV_WARPS;
+  // chunked: two epilogue warps per tensor-memory lane quarter, each holding
+  // the running hi*hi sums of half the tile's columns
+  static constexpr int EPI_WARPS = CH > 0 ? 4 : 4;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS + 32 * CONV_WARPS;
   static constexpr uint32_t BAR_BYTES = 256;
   static constexpr uint32_t SMEM = STAGES * STAGE + S32 * STAGE32 + BAR_BYTES + 1024;  // + alignment
   static_assert(SW == 64 || SW == 128, "BK must be 32 or 64 bfloat16");
@@ -214,7 +227,8 @@ struct TcConfig {
   static_assert(TMEM_USED <= 512, "tensor memory: 512 columns");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
   static_assert(SMEM <= 232448, "shared memory");
-  static_assert((2 * STAGES + 2 * S32 + 2 * ACC_BUFS + 1) * 8 + 4 <= BAR_BYTES, "barrier area");
+  static_assert((2 * STAGES + 2 * S32 + 2 * ACC_BUFS + 1 + 4) * 8 + 4 <= BAR_BYTES, "barrier area");
+  static_assert(CH == 0 || (!FUSED && !D64 && MODE != 1), "chunked: split pieces, FP32 result");
 };
 
 // Converter warps of the fused kernel: split one FP32 stage (16 K-columns)
@@ -383,11 +397,12 @@ __device__ __forceinline__ void sum_products_f64(uint32_t tb, int c, double (&z)
   add_level(lv);
 }
 
-template <int MODE, int BN, int BK, int STAGES, bool GROUPED, bool FUSED = false, bool D64 = false>
-__global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::THREADS, 1)
+template <int MODE, int BN, int BK, int STAGES, bool GROUPED, bool FUSED = false, bool D64 = false,
+          int CH = 0>
+__global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>::THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs args) {
-  using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED, D64>;
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>;
   static_assert(!(D64 && GROUPED), "FP64 collection: single problem");
   constexpr uint32_t IDESC = idesc_bf16_f32<BM, BN>();
 
@@ -402,7 +417,9 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::TH
   uint64_t* drain = acc_empty + Cfg::ACC_BUFS;
   uint64_t* full32 = drain + 1;  // fused only
   uint64_t* empty32 = full32 + Cfg::S32;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty32 + Cfg::S32);
+  uint64_t* chunk_full = empty32 + Cfg::S32;  // chunked only: a D_main buffer is complete
+  uint64_t* chunk_empty = chunk_full + 2;     // ... and has been read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(chunk_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = args.err;
@@ -419,7 +436,11 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::TH
     }
     for (int b = 0; b < Cfg::ACC_BUFS; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], 32 * Cfg::EPI_WARPS);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&chunk_full[b], 1);
+      mbar_init(&chunk_empty[b], 32 * Cfg::EPI_WARPS);
     }
     mbar_init(drain, 1);
     fence_barrier_init();
@@ -517,6 +538,69 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::TH
         }
       }
     }
+  } else if (CH > 0 && warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer (chunked)
+      // hi*hi goes to D_main buffer (chunk & 1), restarted at every chunk of
+      // CH K-slices; the corrections accumulate in D_corr over the whole K.
+      // A buffer is reused once the epilogue has read it (two chunks later).
+      int s = 0, gch = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      const uint32_t dc = tmem_base + static_cast<uint32_t>(2 * BN);
+      for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait_bounded(&acc_empty[0], aph ^ 1u, err, kErrWaitAccEmpty)) break;
+        tc_fence_after();
+        const int k_tiles = get_tile<GROUPED>(t, args).k_tiles;
+        for (int kt = 0; kt < k_tiles && ok; ++kt) {
+          const int kc = kt % CH;
+          if (kc == 0) {
+            if (!mbar_wait_bounded(&chunk_empty[gch & 1], ((gch >> 1) & 1) ^ 1u, err,
+                                   kErrWaitAccEmpty)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          if (!mbar_wait_bounded(&full[s], ph, err, kErrWaitFull)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dm = tmem_base + static_cast<uint32_t>((gch & 1) * BN);
+          const uint32_t sa = smem_addr(smem + s * Cfg::STAGE);
+          const uint32_t sb = sa + Cfg::STAGE_A;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+            for (int p = 0; p < Cfg::NPROD; ++p) {
+              const Prod pr = prod_of(MODE, p);
+              const uint64_t ad = smem_desc_kmajor<Cfg::SW>(sa + pr.a * Cfg::A_TILE + kk * 32);
+              const uint64_t bd = smem_desc_kmajor<Cfg::SW>(sb + pr.b * Cfg::B_TILE + kk * 32);
+              if (pr.acc == 0)
+                umma_bf16_ss(dm, ad, bd, IDESC, (kc > 0 || kk > 0) ? 1u : 0u);
+              else
+                umma_bf16_ss(dc, ad, bd, IDESC,
+                             (kt > 0 || kk > 0 || !first_in_acc(MODE, p)) ? 1u : 0u);
+            }
+          }
+          umma_commit(&empty[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+          if (kc == CH - 1 || kt == k_tiles - 1) {
+            umma_commit(&chunk_full[gch & 1]);
+            ++gch;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[0]);
+        aph ^= 1u;
+      }
+      umma_commit(drain);
+      mbar_wait_bounded(drain, 0u, err, kErrWaitDrain);
+    }
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
@@ -565,6 +649,102 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64>::TH
       // all MMAs issued by this thread complete before tensor memory is freed
       umma_commit(drain);
       mbar_wait_bounded(drain, 0u, err, kErrWaitDrain);
+    }
+  } else if constexpr (CH > 0) {
+    // -------------------------------------------------- epilogue (chunked)
+    // Each chunk's D_main is added into S in FP32 with round to nearest (a
+    // thread holds half of its row's BN values: warps 2..5 the first half,
+    // warps 6..9 the second), then Z = S + D_corr.
+    constexpr int HB = BN / (Cfg::EPI_WARPS / 4);  // columns a thread holds
+    static_assert(HB % 16 == 0, "half tile in groups of 16 columns");
+    const int q = warp & 3;
+    const int row_in_tile = q * 32 + lane;
+    const int hc = ((warp - 2) >> 2) * HB;  // first column of this thread's part
+    const uint32_t lane_off = (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(hc);
+    int gce = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+      const TileInfo ti = get_tile<GROUPED>(t, args);
+      const int nch = (ti.k_tiles + CH - 1) / CH;
+      float S[HB];
+      for (int ch = 0; ch < nch; ++ch) {
+        ok = mbar_wait_bounded(&chunk_full[gce & 1], (gce >> 1) & 1, err, kErrWaitAccFull);
+        ok = __all_sync(0xFFFFFFFFu, ok);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t tb = tmem_base + lane_off + static_cast<uint32_t>((gce & 1) * BN);
+#pragma unroll
+        for (int c = 0; c < HB / 16; ++c) {
+          float v[16];
+          tmem_ld16_wait(tb + c * 16, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) S[c * 16 + i] = ch == 0 ? v[i] : S[c * 16 + i] + v[i];
+        }
+        tc_fence_before();
+        mbar_arrive(&chunk_empty[gce & 1]);
+        ++gce;
+      }
+      if (!ok) break;
+      ok = mbar_wait_bounded(&acc_full[0], aph, err, kErrWaitAccFull);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      // Z = D_main + D_corr, written over D_corr, then stored from there
+      const uint32_t tdc = tmem_base + lane_off + static_cast<uint32_t>(2 * BN);
+#pragma unroll
+      for (int c = 0; c < HB / 16; ++c) {
+        float v[16];
+        tmem_ld16_wait(tdc + c * 16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = S[c * 16 + i] + v[i];
+        tmem_st16_wait(tdc + c * 16, v);
+      }
+      const int row = ti.mb * BM + row_in_tile;
+      const bool row_ok = row < ti.M;
+      float* crow = ti.C + static_cast<int64_t>(row_ok ? row : 0) * ti.ldc;
+#pragma unroll 1
+      for (int c = 0; c < HB / 16; ++c) {
+        float v[16];
+        tmem_ld16_wait(tdc + c * 16, v);
+        if (c == HB / 16 - 1) {
+          tc_fence_before();
+          mbar_arrive(&acc_empty[0]);
+        }
+        if (!row_ok) continue;
+        const int col0 = ti.nb * BN + hc + c * 16;
+        if (col0 >= ti.N) continue;
+        float* dst = crow + col0;
+        if (ti.vec_c && col0 + 16 <= ti.N) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            float4 o;
+            float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (args.beta != 0.0f) old = *reinterpret_cast<const float4*>(dst + i);
+            o.x = args.alpha * v[i + 0];
+            o.y = args.alpha * v[i + 1];
+            o.z = args.alpha * v[i + 2];
+            o.w = args.alpha * v[i + 3];
+            if (args.beta != 0.0f) {
+              o.x = fmaf(args.beta, old.x, o.x);
+              o.y = fmaf(args.beta, old.y, o.y);
+              o.z = fmaf(args.beta, old.z, o.z);
+              o.w = fmaf(args.beta, old.w, o.w);
+            }
+            *reinterpret_cast<float4*>(dst + i) = o;
+          }
+        } else {
+          const int lim = min(16, ti.N - col0);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < lim) {
+              const float tv = args.alpha * v[i];
+              dst[i] = (args.beta == 0.0f) ? tv : fmaf(args.beta, dst[i], tv);
+            }
+          }
+        }
+      }
+      aph ^= 1u;
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..5)
@@ -720,11 +900,11 @@ bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64
 
 // C: float* (FP32 result, alpha/beta applied) or, with D64, double* (the
 // FP64 collection, alpha/beta unused).
-template <int MODE, int BN, int BK, int STAGES, bool D64 = false>
+template <int MODE, int BN, int BK, int STAGES, bool D64 = false, int CH = 0>
 bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* Ap, int64_t lda_p,
                   int64_t a_plane, const uint16_t* Btp, int64_t ldb_p, int64_t b_plane,
                   float beta, void* C, int64_t ldc, cudaStream_t s) {
-  using Cfg = TcConfig<MODE, BN, BK, STAGES, false, D64>;
+  using Cfg = TcConfig<MODE, BN, BK, STAGES, false, D64, CH>;
   // with a single piece only plane 0 is read; any legal plane stride will do
   if (Cfg::NPA == 1) a_plane = round_up(lda_p * m, 8);
   if (Cfg::NPB == 1) b_plane = round_up(ldb_p * n, 8);
@@ -751,13 +931,13 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
   a.tiles = nullptr;
   a.probs = nullptr;
   if (!a.err) return BFX_ECUDA;
-  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false, false, D64>;
+  auto kern = gemm_tc_kernel<MODE, BN, BK, STAGES, false, false, D64, CH>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM) !=
       cudaSuccess)
     return BFX_ECUDA;
   const int sms = current_num_sms();
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-  kern<<<grid, 192, Cfg::SMEM, s>>>(ma, mb, a);
+  kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(ma, mb, a);
   return last_launch_status();
 }
 
@@ -930,6 +1110,25 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
                                 float* C, int64_t ldc, cudaStream_t s) {
   if (m == 0 || n == 0) return BFX_OK;
   if (k == 0) return launch_scale(m, n, beta, C, ldc, s);
+  if (k > kChunkMinK) {
+    // long K, FP32-accurate modes: hi*hi accumulated in chunks of kChunkK,
+    // the chunk sums added with round to nearest by the epilogue (128 x 128
+    // tiles: tensor memory holds two D_main buffers and D_corr).  x3 and x5
+    // keep one accumulator: their error is that of the dropped 2^-16 terms.
+    switch (mode) {
+      case BFX_X6:
+        return run_tc<6, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+                                                          ldb_p, b_plane, beta, C, ldc, s);
+      case BFX_X8:
+        return run_tc<8, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+                                                          ldb_p, b_plane, beta, C, ldc, s);
+      case BFX_X9:
+        return run_tc<9, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+                                                          ldb_p, b_plane, beta, C, ldc, s);
+      default:
+        break;
+    }
+  }
   switch (mode) {
     case BFX_X1:
       return run_tc<1, 256, 64, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,

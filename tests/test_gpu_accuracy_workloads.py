@@ -47,3 +47,23 @@ def test_narrow_range_accuracy_order(bfx, orc):
         errs["x6"].append(_frob(bfx.gemm_bf16xN(6, Ad, Bd).cpu().numpy(), C64))
     m = {k: np.mean(v) for k, v in errs.items()}
     assert m["x3"] > m["sgemm"] > m["x6"], m
+
+
+@pytest.mark.parametrize("k", [2048, 8192])
+@pytest.mark.parametrize("gen", ["uniform_pm1", "random_exponent"])
+def test_long_k_x6_more_accurate_than_sgemm(bfx, orc, k, gen):
+    """Sec. IV-A's order "SGEMM < bx3_6" (x6 the more accurate) at long K on
+    the tensor cores: relative Frobenius error against the FP64 product on a
+    sample of rows, narrow range and random exponents.  Holds because the
+    hi*hi accumulator is restarted every 256 of K and the chunk sums are added
+    with round to nearest."""
+    g = getattr(bi, gen)
+    m, n = 256, 512
+    A = g((m, k), 60)
+    B = g((k, n), 61)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    rows = np.arange(0, m, 2)
+    C64, _ = orc.dgemm_rows(A, B, rows)
+    e6 = _frob(bfx.gemm_bf16xN(6, Ad, Bd).cpu().numpy()[rows], C64)
+    es = _frob(bfx.sgemm_simt(Ad, Bd).cpu().numpy()[rows], C64)
+    assert e6 < es, (e6, es)

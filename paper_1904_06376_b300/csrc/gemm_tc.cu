@@ -63,7 +63,7 @@ constexpr int BM = 128;     // UMMA M (one CTA, cta_group::1)
 // round-to-nearest, so over a long K the hi*hi accumulator's error grows
 // with the number of blocks; chunking bounds that growth to kChunkK / 16
 // blocks and leaves the rest to round-to-nearest additions.
-constexpr int kChunkK = 128;
+constexpr int kChunkK = 256;
 constexpr int kChunkMinK = 512;
 constexpr int GROUP_M = 16; // tile raster: groups of 16 row-blocks for L2 reuse
 
@@ -195,8 +195,8 @@ struct TcConfig {
   static constexpr int NPB = mode_npb(MODE);
   static constexpr int NP = NPA;  // fused: both operands alike
   static constexpr int NPROD = MODE;
-  // chunked (CH > 0): two D_main buffers (alternating K-chunks) and D_corr
-  static constexpr int NACC = D64 ? MODE : (CH > 0 ? 3 : ((MODE == 1) ? 1 : 2));
+  // chunked (CH > 0): D_main (restarted every chunk) and D_corr
+  static constexpr int NACC = D64 ? MODE : ((MODE == 1) ? 1 : 2);
   static constexpr int ACC_BUFS = CH > 0 ? 1 : ((NACC * BN * 2 <= 512) ? 2 : 1);
   static constexpr uint32_t TMEM_USED = NACC * BN * ACC_BUFS;
   static constexpr uint32_t TMEM_COLS = pow2_cols(TMEM_USED);
@@ -214,9 +214,9 @@ struct TcConfig {
   static constexpr int S32_FIT = static_cast<int>((232448u - 1280u - STAGES * STAGE) / STAGE32);
   static constexpr int S32 = FUSED ? (S32_FIT < 8 ? S32_FIT : 8) : 0;
   static constexpr int CONV_WARPS = FUSED ? 16 : 0;
-  // chunked: two epilogue warps per tensor-memory lane quarter, each holding
-  // the running hi*hi sums of half the tile's columns
-  static constexpr int EPI_WARPS = CH > 0 ? 4 : 4;
+  // chunked: four epilogue warps per tensor-memory lane quarter, each holding
+  // the running hi*hi sums of a quarter of the tile's columns
+  static constexpr int EPI_WARPS = CH > 0 ? 16 : 4;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS + 32 * CONV_WARPS;
   static constexpr uint32_t BAR_BYTES = 256;
   static constexpr uint32_t SMEM = STAGES * STAGE + S32 * STAGE32 + BAR_BYTES + 1024;  // + alignment
@@ -541,33 +541,27 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
   } else if (CH > 0 && warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer (chunked)
-      // hi*hi goes to D_main buffer (chunk & 1), restarted at every chunk of
-      // CH K-slices; the corrections accumulate in D_corr over the whole K.
-      // A buffer is reused once the epilogue has read it (two chunks later).
+      // hi*hi goes to D_main, restarted at every chunk of CH K-slices; the
+      // corrections accumulate in D_corr over the whole K.  A chunk's first
+      // hi*hi MMA waits until the epilogue has read the previous chunk's
+      // D_main; the corrections of that K-slice, issued before it, keep the
+      // tensor core busy meanwhile.
       int s = 0, gch = 0;
       uint32_t ph = 0, aph = 0;
       bool ok = true;
-      const uint32_t dc = tmem_base + static_cast<uint32_t>(2 * BN);
+      const uint32_t dm = tmem_base;
+      const uint32_t dc = tmem_base + static_cast<uint32_t>(BN);
       for (int t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
         if (!mbar_wait_bounded(&acc_empty[0], aph ^ 1u, err, kErrWaitAccEmpty)) break;
         tc_fence_after();
         const int k_tiles = get_tile<GROUPED>(t, args).k_tiles;
         for (int kt = 0; kt < k_tiles && ok; ++kt) {
           const int kc = kt % CH;
-          if (kc == 0) {
-            if (!mbar_wait_bounded(&chunk_empty[gch & 1], ((gch >> 1) & 1) ^ 1u, err,
-                                   kErrWaitAccEmpty)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
           if (!mbar_wait_bounded(&full[s], ph, err, kErrWaitFull)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t dm = tmem_base + static_cast<uint32_t>((gch & 1) * BN);
           const uint32_t sa = smem_addr(smem + s * Cfg::STAGE);
           const uint32_t sb = sa + Cfg::STAGE_A;
 #pragma unroll
@@ -577,20 +571,30 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
               const Prod pr = prod_of(MODE, p);
               const uint64_t ad = smem_desc_kmajor<Cfg::SW>(sa + pr.a * Cfg::A_TILE + kk * 32);
               const uint64_t bd = smem_desc_kmajor<Cfg::SW>(sb + pr.b * Cfg::B_TILE + kk * 32);
-              if (pr.acc == 0)
+              if (pr.acc == 0) {
+                if (kc == 0 && kk == 0 && gch > 0) {  // D_main of chunk gch-1 read?
+                  if (!mbar_wait_bounded(&chunk_empty[0], (gch - 1) & 1, err, kErrWaitAccEmpty)) {
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                }
                 umma_bf16_ss(dm, ad, bd, IDESC, (kc > 0 || kk > 0) ? 1u : 0u);
-              else
+              } else {
                 umma_bf16_ss(dc, ad, bd, IDESC,
                              (kt > 0 || kk > 0 || !first_in_acc(MODE, p)) ? 1u : 0u);
+              }
             }
+            if (!ok) break;
           }
+          if (!ok) break;
           umma_commit(&empty[s]);
           if (++s == STAGES) {
             s = 0;
             ph ^= 1u;
           }
           if (kc == CH - 1 || kt == k_tiles - 1) {
-            umma_commit(&chunk_full[gch & 1]);
+            umma_commit(&chunk_full[0]);
             ++gch;
           }
         }
@@ -653,8 +657,8 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
   } else if constexpr (CH > 0) {
     // -------------------------------------------------- epilogue (chunked)
     // Each chunk's D_main is added into S in FP32 with round to nearest (a
-    // thread holds half of its row's BN values: warps 2..5 the first half,
-    // warps 6..9 the second), then Z = S + D_corr.
+    // thread holds a quarter of its row's BN values: warps 2..5 the first
+    // quarter, 6..9 the second, ...), then Z = S + D_corr.
     constexpr int HB = BN / (Cfg::EPI_WARPS / 4);  // columns a thread holds
     static_assert(HB % 16 == 0, "half tile in groups of 16 columns");
     const int q = warp & 3;
@@ -669,11 +673,11 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
       const int nch = (ti.k_tiles + CH - 1) / CH;
       float S[HB];
       for (int ch = 0; ch < nch; ++ch) {
-        ok = mbar_wait_bounded(&chunk_full[gce & 1], (gce >> 1) & 1, err, kErrWaitAccFull);
+        ok = mbar_wait_bounded(&chunk_full[0], gce & 1, err, kErrWaitAccFull);
         ok = __all_sync(0xFFFFFFFFu, ok);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t tb = tmem_base + lane_off + static_cast<uint32_t>((gce & 1) * BN);
+        const uint32_t tb = tmem_base + lane_off;
 #pragma unroll
         for (int c = 0; c < HB / 16; ++c) {
           float v[16];
@@ -682,7 +686,7 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
           for (int i = 0; i < 16; ++i) S[c * 16 + i] = ch == 0 ? v[i] : S[c * 16 + i] + v[i];
         }
         tc_fence_before();
-        mbar_arrive(&chunk_empty[gce & 1]);
+        mbar_arrive(&chunk_empty[0]);
         ++gce;
       }
       if (!ok) break;
@@ -691,7 +695,7 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
       if (!ok) break;
       tc_fence_after();
       // Z = D_main + D_corr, written over D_corr, then stored from there
-      const uint32_t tdc = tmem_base + lane_off + static_cast<uint32_t>(2 * BN);
+      const uint32_t tdc = tmem_base + lane_off + static_cast<uint32_t>(BN);
 #pragma unroll
       for (int c = 0; c < HB / 16; ++c) {
         float v[16];
@@ -1112,18 +1116,17 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
   if (k == 0) return launch_scale(m, n, beta, C, ldc, s);
   if (k > kChunkMinK) {
     // long K, FP32-accurate modes: hi*hi accumulated in chunks of kChunkK,
-    // the chunk sums added with round to nearest by the epilogue (128 x 128
-    // tiles: tensor memory holds two D_main buffers and D_corr).  x3 and x5
+    // the chunk sums added with round to nearest by the epilogue.  x3 and x5
     // keep one accumulator: their error is that of the dropped 2^-16 terms.
     switch (mode) {
       case BFX_X6:
-        return run_tc<6, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+        return run_tc<6, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
                                                           ldb_p, b_plane, beta, C, ldc, s);
       case BFX_X8:
-        return run_tc<8, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+        return run_tc<8, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
                                                           ldb_p, b_plane, beta, C, ldc, s);
       case BFX_X9:
-        return run_tc<9, 128, 32, 4, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
+        return run_tc<9, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
                                                           ldb_p, b_plane, beta, C, ldc, s);
       default:
         break;

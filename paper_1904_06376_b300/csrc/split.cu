@@ -25,6 +25,38 @@ __device__ __forceinline__ uint4 pack8(const uint16_t* q) {
 }
 
 template <int NP>
+__device__ __forceinline__ void split8_store(const float4 a, const float4 b, uint16_t* p0,
+                                             uint16_t* p1, uint16_t* p2, int64_t off) {
+  const float e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint16_t h[8], m[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) split_elem(e[i], h[i], m[i], l[i]);
+  __stcs(reinterpret_cast<uint4*>(p0 + off), pack8(h));
+  if (NP >= 2) __stcs(reinterpret_cast<uint4*>(p1 + off), pack8(m));
+  if (NP >= 3) __stcs(reinterpret_cast<uint4*>(p2 + off), pack8(l));
+}
+
+// Contiguous rows (ldx == ldp == cols): one flat range, no index division;
+// two groups of 8 elements a thread and iteration, all four 16-byte loads
+// issued before the splits.
+template <int NP>
+__global__ void __launch_bounds__(256) split_flat_kernel(const float* __restrict__ x, int64_t n8,
+                                                         uint16_t* __restrict__ p0,
+                                                         uint16_t* __restrict__ p1,
+                                                         uint16_t* __restrict__ p2) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const float4* src = reinterpret_cast<const float4*>(x);
+  int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  for (; v + stride < n8; v += 2 * stride) {
+    const float4 a0 = __ldcs(src + 2 * v), b0 = __ldcs(src + 2 * v + 1);
+    const float4 a1 = __ldcs(src + 2 * (v + stride)), b1 = __ldcs(src + 2 * (v + stride) + 1);
+    split8_store<NP>(a0, b0, p0, p1, p2, 8 * v);
+    split8_store<NP>(a1, b1, p0, p1, p2, 8 * (v + stride));
+  }
+  if (v < n8) split8_store<NP>(__ldcs(src + 2 * v), __ldcs(src + 2 * v + 1), p0, p1, p2, 8 * v);
+}
+
+template <int NP>
 __global__ void __launch_bounds__(256) split_vec8_kernel(const float* __restrict__ x, int64_t ldx,
                                                          int64_t rows, int64_t cols8,
                                                          uint16_t* __restrict__ p0,
@@ -78,7 +110,7 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
                                                               uint16_t* __restrict__ p0,
                                                               uint16_t* __restrict__ p1,
                                                               uint16_t* __restrict__ p2,
-                                                              int64_t ldp, bool pairs) {
+                                                              int64_t ldp, int pairs) {
   __shared__ float tile[TT][TT + 1];
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * TT;
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TT;
@@ -93,6 +125,36 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
     }
   }
   __syncthreads();
+  if (pairs == 2) {
+    // 16-byte stores: thread t writes output row oc = c0 + t/8 (+32), output
+    // columns r0 + 8*(t%8) .. +7, when that run is inside the matrix
+    const int seg = (threadIdx.x & 7) * 8;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      const int ol = (threadIdx.x >> 3) + 32 * pass;
+      const int64_t oc = c0 + ol;
+      if (oc >= cols) continue;
+      const int64_t orr = r0 + seg;
+      uint16_t h[8], m[8], l[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split_elem(tile[seg + q][ol], h[q], m[q], l[q]);
+      const int64_t off = oc * ldp + orr;
+      if (orr + 8 <= rows) {
+        *reinterpret_cast<uint4*>(p0 + off) = pack8(h);
+        if (np >= 2) *reinterpret_cast<uint4*>(p1 + off) = pack8(m);
+        if (np >= 3) *reinterpret_cast<uint4*>(p2 + off) = pack8(l);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (orr + q >= rows) break;
+          p0[off + q] = h[q];
+          if (np >= 2) p1[off + q] = m[q];
+          if (np >= 3) p2[off + q] = l[q];
+        }
+      }
+    }
+    return;
+  }
   // output row oc = c0 + (ty + i), output columns orr = r0 + 2*tx + {0,1}
 #pragma unroll
   for (int i = 0; i < TT; i += 8) {
@@ -103,7 +165,7 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
     split_elem(tile[2 * tx][ty + i], h0, m0, l0);
     split_elem(tile[2 * tx + 1][ty + i], h1, m1, l1);
     const int64_t off = oc * ldp + orr;
-    if (pairs && orr + 1 < rows && ((off & 1) == 0)) {
+    if (pairs == 1 && orr + 1 < rows && ((off & 1) == 0)) {
       *reinterpret_cast<uint32_t*>(p0 + off) = h0 | (static_cast<uint32_t>(h1) << 16);
       if (np >= 2) *reinterpret_cast<uint32_t*>(p1 + off) = m0 | (static_cast<uint32_t>(m1) << 16);
       if (np >= 3) *reinterpret_cast<uint32_t*>(p2 + off) = l0 | (static_cast<uint32_t>(l1) << 16);
@@ -146,7 +208,15 @@ bfx_status launch_split(int64_t rows, int64_t cols, const float* x, int64_t ldx,
   const bool vec = (cols % 8 == 0) && (ldx % 4 == 0) && (ldp % 8 == 0) && aligned(x, 16) &&
                    aligned(hi, 16) && (npieces < 2 || aligned(mid, 16)) &&
                    (npieces < 3 || aligned(lo, 16));
-  if (vec) {
+  if (vec && ldx == cols && ldp == cols) {
+    const int64_t n8 = rows * cols / 8;
+    const int grid = grid_for(n8, 256);
+    switch (npieces) {
+      case 1: split_flat_kernel<1><<<grid, 256, 0, s>>>(x, n8, hi, mid, lo); break;
+      case 2: split_flat_kernel<2><<<grid, 256, 0, s>>>(x, n8, hi, mid, lo); break;
+      default: split_flat_kernel<3><<<grid, 256, 0, s>>>(x, n8, hi, mid, lo); break;
+    }
+  } else if (vec) {
     const int64_t cols8 = cols / 8;
     const int grid = grid_for(rows * cols8, 256);
     switch (npieces) {
@@ -168,8 +238,13 @@ bfx_status launch_split_transpose(int64_t rows, int64_t cols, const float* x, in
   const int64_t gx = ceil_div(cols, TT), gy = ceil_div(rows, TT);
   if (gy > 65535 || gx > INT32_MAX) return BFX_EUNSUPPORTED;
   dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
-  const bool pairs = aligned(hi, 4) && (npieces < 2 || aligned(mid, 4)) &&
-                     (npieces < 3 || aligned(lo, 4));
+  // 2: 16-byte stores (planes 16-byte aligned, ldp a multiple of 8);
+  // 1: 4-byte pairs; 0: single elements
+  const bool al16 = aligned(hi, 16) && (npieces < 2 || aligned(mid, 16)) &&
+                    (npieces < 3 || aligned(lo, 16)) && ldp % 8 == 0;
+  const bool al4 = aligned(hi, 4) && (npieces < 2 || aligned(mid, 4)) &&
+                   (npieces < 3 || aligned(lo, 4));
+  const int pairs = al16 ? 2 : (al4 ? 1 : 0);
   split_transpose_kernel<<<grid, 256, 0, s>>>(x, ldx, rows, cols, npieces, hi, mid, lo, ldp,
                                               pairs);
   return last_launch_status();

@@ -247,6 +247,14 @@ BFX_API bfx_status bfx_gemm_bf16xN_noalloc(bfx_mode mode, int64_t m, int64_t n, 
                                            const float* d_B, int64_t ldb, float beta, float* d_C,
                                            int64_t ldc, bfx_stream stream);
 
+/* Measured arithmetic peak of the CUDA cores: a kernel of independent FMA
+ * chains (8 a thread, a full wave of CTAs on every SM), timed with CUDA
+ * events on `stream`; fp64 = 0 FFMA (FP32), 1 DFMA (FP64).  The FP32 figure
+ * is the roofline denominator of the FP32 SIMT baseline.  *h_tflops
+ * receives TFLOP/s (2 per FMA).  Synchronous.  Errors: BFX_EINVAL (h_tflops
+ * NULL), BFX_ECUDA. */
+BFX_API bfx_status bfx_measure_fma_peak(int fp64, double* h_tflops, bfx_stream stream);
+
 /* Plain FP32 SIMT GEMM (the Sec. II-C reference computation on CUDA cores;
  * the same-GPU baseline).  Each C element is accumulated with one FMA per k
  * in increasing k, then t = alpha*Z, C = beta == 0 ? t : fma(beta, C, t).
@@ -474,6 +482,17 @@ BFX_API void bfx_batch_destroy(bfx_batch plan);
  * with params {50, 2^-53, sqrt(n) 2^-53, 0.5, escalate, nb, gmres,
  * min(n, 1024), 1e-10} (the Krylov length capped so that one large request's
  * reservation does not crowd the pool).
+ * Continuous batching (batch_max_n > 0): a free worker whose next request
+ * is small (n <= batch_max_n, nrhs <= 16) takes every small request with the
+ * same nrhs that is waiting, in arrival order (up to batch_max, as far as the
+ * pool has room), and solves them together with the batched path of
+ * bfx_batch_solve (mode as configured, fixed tile shape nb 32, gemm_bn 64,
+ * GMRES-IR for the systems plain refinement leaves unconverged, max_iter
+ * 20); a small request's result is the same whichever requests share its
+ * batch (every kernel of the batched path works on one system at a time), so
+ * it equals the result of that request alone through the server.  Large
+ * requests are solved one per worker as above.  A batched request reports
+ * mode_used = the configured mode, refactorizations = 0 and arnoldi = 0.
  * The caller's host buffers h_A (n x n), h_b (n x nrhs) must stay valid and
  * h_x (n x nrhs, output) writable until the request completes.
  * submit: BFX_ENOMEM if the request can never fit the budget; never blocks.
@@ -487,6 +506,9 @@ typedef struct bfx_server_config {
   int nb;       /* LU block width (0 = 64) */
   int escalate; /* refactor with more products when refinement stalls */
   int gmres;    /* bfx_ir_params.gmres of every request (0, 1 or 2) */
+  int batch_max_n; /* continuous batching: requests with n <= batch_max_n (<= 1024) and
+                      nrhs <= 16 waiting together are solved as one batch (0 = off) */
+  int batch_max;   /* most requests in one batch (0 = 64) */
 } bfx_server_config;
 typedef struct bfx_request_result {
   int32_t status;           /* bfx_status of the solve */
@@ -502,7 +524,8 @@ typedef struct bfx_request_result {
   int32_t arnoldi;
 } bfx_request_result;
 typedef struct bfx_server_stats_t {
-  int32_t queued, running, peak_running, pad;
+  int32_t queued, running, peak_running;
+  int32_t batches; /* batches of small requests run so far */
   size_t pool_bytes, used_bytes, peak_used_bytes;
 } bfx_server_stats_t;
 typedef struct bfx_server_impl* bfx_server;

@@ -37,6 +37,7 @@ from ._bfx import (  # noqa: F401
     lu_bf16xN,
     solve_ir,
     solve_ir_async,
+    measure_fma_peak,
     decode_ir_result,
     solve_ir_workspace_size,
     library_path,

@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
         "bfx_solve_ir_workspace_size": (sz, [i32, i64, i64, vp]),
         "bfx_solve_ir": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
         "bfx_solve_ir_async": (i32, [i32, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, vp]),
+        "bfx_measure_fma_peak": (i32, [i32, vp, vp]),
         "bfx_batch_create": (i32, [vp, i32, i32, vp, i32, vp]),
         "bfx_batch_workspace_size": (sz, [vp]),
         "bfx_batch_solve": (i32, [vp, vp, vp, vp, vp, vp, sz, vp]),
@@ -370,6 +371,14 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     return x, r.as_dict(), code
 
 
+def measure_fma_peak(fp64: bool = False, stream=None) -> float:
+    """Measured FP32 (or FP64) FMA rate of the CUDA cores, TFLOP/s."""
+    out = ctypes.c_double()
+    _check("bfx_measure_fma_peak", lib().bfx_measure_fma_peak(int(bool(fp64)), ctypes.byref(out),
+                                                             _stream(stream)))
+    return float(out.value)
+
+
 IR_RESULT_BYTES = ctypes.sizeof(IrResult)
 
 
@@ -534,7 +543,8 @@ class Batch:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("mode", ctypes.c_int),
-                ("nb", ctypes.c_int), ("escalate", ctypes.c_int), ("gmres", ctypes.c_int)]
+                ("nb", ctypes.c_int), ("escalate", ctypes.c_int), ("gmres", ctypes.c_int),
+                ("batch_max_n", ctypes.c_int), ("batch_max", ctypes.c_int)]
 
 
 class RequestResult(ctypes.Structure):
@@ -550,7 +560,7 @@ class RequestResult(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("peak_running", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("pool_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("batches", ctypes.c_int32), ("pool_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
                 ("peak_used_bytes", ctypes.c_size_t)]
 
 
@@ -561,9 +571,9 @@ class Server:
     completes) and returns a ticket; wait() returns (x, result dict)."""
 
     def __init__(self, budget_bytes: int, max_inflight: int = 16, mode: int = BFX_X3, nb: int = 64,
-                 escalate: bool = True, gmres: int = 1):
+                 escalate: bool = True, gmres: int = 1, batch_max_n: int = 0, batch_max: int = 0):
         cfg = ServerConfig(int(budget_bytes), int(max_inflight), int(mode), int(nb), int(bool(escalate)),
-                           int(gmres))
+                           int(gmres), int(batch_max_n), int(batch_max))
         h = ctypes.c_void_p()
         _check("bfx_server_create", lib().bfx_server_create(ctypes.byref(h), ctypes.byref(cfg)))
         self.handle = h

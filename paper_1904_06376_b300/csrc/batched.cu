@@ -181,6 +181,34 @@ bfx_status write_tables(bfx_batch_plan* P, cudaStream_t s) {
 
 }  // namespace
 
+namespace bfx {
+// One batched solve launched directly on stream s, without a graph: the
+// serving loop's batches come with new buffers every time, so capturing
+// would cost more than it saves.  Same launch sequence as the graph.
+bfx_status batch_solve_direct(bfx_batch_plan* P, const float* d_A, const double* d_b, double* d_x,
+                              bfx_batch_status* d_status, void* d_ws, size_t ws_bytes,
+                              cudaStream_t s) {
+  if (!P || !d_A || !d_b || !d_x || !d_status) return BFX_EINVAL;
+  if (!d_ws || ws_bytes < P->total) return BFX_ENOMEM;
+  if (!aligned(d_ws, 256)) return BFX_EUNSUPPORTED;
+  if (!device_error_word()) return BFX_ECUDA;
+  if (P->exec) {
+    cudaGraphExecDestroy(P->exec);
+    P->exec = nullptr;
+  }
+  P->bA = d_A;
+  P->bb = d_b;
+  P->bx = d_x;
+  P->bst = d_status;
+  P->bws = d_ws;
+  bfx_status st = write_tables(P, s);
+  if (st != BFX_OK) return st;
+  st = enqueue(P, s);
+  P->bA = nullptr;  // not bound to a graph: a later bfx_batch_solve captures afresh
+  return st;
+}
+}  // namespace bfx
+
 extern "C" {
 
 BFX_API bfx_status bfx_batch_create_config(bfx_batch* out, bfx_mode mode, int count,

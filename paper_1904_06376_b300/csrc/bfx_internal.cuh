@@ -88,6 +88,11 @@ struct BatchLu {
 bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_desc, int S,
                             int nb, int J0, uint16_t* packA, uint16_t* packB, int64_t slot_rows,
                             int64_t kp, cudaStream_t s);
+// One batched solve launched directly (no graph) on s; the plan is left
+// unbound, so bfx_batch_solve captures afresh afterwards (batched.cu).
+bfx_status batch_solve_direct(bfx_batch_plan* P, const float* d_A, const double* d_b, double* d_x,
+                              bfx_batch_status* d_status, void* d_ws, size_t ws_bytes,
+                              cudaStream_t s);
 // Batched refinement (ir.cu): one descriptor per system (same order as the
 // BatchLu array).  All buffers are n x nrhs (FP64) or n x n (FP32), leading
 // dimension n (resp. nrhs).

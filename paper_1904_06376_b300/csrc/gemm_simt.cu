@@ -122,3 +122,66 @@ bfx_status launch_sgemm_simt(int64_t m, int64_t n, int64_t k, float alpha, const
 }
 
 }  // namespace bfx
+
+// ---------------------------------------------------------------------------
+// Arithmetic peaks of the CUDA cores, measured: the roofline denominators of
+// the FP32 SIMT baseline (FFMA) and of the refinement's FP64 work (DFMA).
+// Every thread runs 8 independent FMA chains (enough to cover the pipeline
+// latency), one CTA of 256 threads per 1/8 of an SM's threads times 8 waves
+// of the SMs; the chains' results are stored only under a condition the
+// caller never meets, so the work cannot be dropped.
+namespace bfx {
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T seed, T* __restrict__ sink) {
+  T a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = seed + static_cast<T>(threadIdx.x + q);
+  const T m = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = fma(a[q], m, c);
+    }
+  }
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += a[q];
+  if (s == static_cast<T>(-12345.0)) sink[threadIdx.x] = s;
+}
+
+template <typename T>
+bfx_status fma_peak(double* tflops, cudaStream_t s) {
+  const int sms = current_num_sms();
+  if (sms <= 0) return BFX_ECUDA;
+  const int grid = sms * 8, iters = 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return BFX_ECUDA;
+  }
+  fma_peak_kernel<T><<<grid, 256, 0, s>>>(iters / 8, static_cast<T>(1.0), nullptr);  // warm-up
+  cudaEventRecord(e0, s);
+  fma_peak_kernel<T><<<grid, 256, 0, s>>>(iters, static_cast<T>(1.0), nullptr);
+  cudaEventRecord(e1, s);
+  float ms = 0.0f;
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return BFX_ECUDA;
+  const double flops = 2.0 * 8.0 * 16.0 * iters * static_cast<double>(grid) * 256.0;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return last_launch_status();
+}
+
+}  // namespace
+}  // namespace bfx
+
+extern "C" BFX_API bfx_status bfx_measure_fma_peak(int fp64, double* h_tflops, bfx_stream stream) {
+  if (!h_tflops) return BFX_EINVAL;
+  return fp64 ? bfx::fma_peak<double>(h_tflops, static_cast<cudaStream_t>(stream))
+              : bfx::fma_peak<float>(h_tflops, static_cast<cudaStream_t>(stream));
+}

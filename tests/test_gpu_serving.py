@@ -113,3 +113,41 @@ def test_mixed_requests_same_as_alone_x6_gmres(bfx, orc):
         fe = np.max(np.abs(x - P.x_true)) / np.max(np.abs(P.x_true))
         fe64 = np.max(np.abs(xd - P.x_true)) / np.max(np.abs(P.x_true))
         assert fe <= 10 * fe64 + 1e-15, (P.n, fe, fe64)
+
+
+def test_continuous_batching_small_requests(bfx, orc):
+    """Continuous batching: small requests (n <= 512) waiting together are
+    solved as one batch (grouped tensor-core updates over all of them), large
+    ones one per worker.  Each small request's result does not depend on the
+    batch it shared: it equals the same request alone through a server (a
+    batch of one), bit for bit; large requests equal bfx_solve_ir alone.
+    Every result lies within 10x of the oracle's FP64 LU in forward error."""
+    rng = np.random.default_rng(21)
+    ns = [64, 300, 96, 700, 512, 128, 33, 1100, 257, 200, 480, 150, 75, 1024, 400, 90]
+    reqs = [bi.svd_system(n, 10.0 ** rng.uniform(1, 7), 600 + i, nrhs=int(rng.integers(1, 3)))
+            for i, n in enumerate(ns)]
+    kw = dict(budget_bytes=4 << 30, mode=6, escalate=True, gmres=1, batch_max_n=512)
+    srv = bfx.Server(max_inflight=4, **kw)
+    tickets = [srv.submit(P.A32, P.b) for P in reqs]
+    out = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["batches"] >= 1
+    small = [i for i, P in enumerate(reqs) if P.n <= 512]
+    alone_srv = bfx.Server(max_inflight=1, **kw)
+    for i, (P, (x, res)) in enumerate(zip(reqs, out)):
+        assert res["status"] == 0 and res["converged"] == 1, (P.n, res)
+        if i in small:
+            xa, ra = alone_srv.wait(alone_srv.submit(P.A32, P.b))
+            assert np.array_equal(x, xa), P.n
+            assert res["iters"] == ra["iters"] and res["gmres_steps"] == ra["gmres_steps"]
+        else:
+            xa, ra, code = bfx.solve_ir(6, torch.from_numpy(P.A32).cuda(),
+                                        torch.from_numpy(P.b).cuda(), escalate=True, nb=64,
+                                        gmres=1, gmres_m=min(P.n, 1024))
+            assert np.array_equal(x, xa.cpu().numpy())
+        xd, _ = orc.dgesv(P.A32, P.b)
+        fe = np.max(np.abs(x - P.x_true)) / np.max(np.abs(P.x_true))
+        fe64 = np.max(np.abs(xd - P.x_true)) / np.max(np.abs(P.x_true))
+        assert fe <= 10 * fe64 + 1e-15, (P.n, fe, fe64)
+    alone_srv.close()

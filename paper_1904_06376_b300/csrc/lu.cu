@@ -944,9 +944,9 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
 }
 
 template <int NB>
-__global__ void __launch_bounds__(CLP_THREADS, 1)
-    lu_panel_cluster_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
-                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+__device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
+                                           int32_t* __restrict__ ipiv,
+                                           int32_t* __restrict__ info) {
   constexpr int MW = CLP_THREADS / 32;
   constexpr int NQ = NB / 4;  // float4 words a row
   static_assert(MW <= 32 && CLP_MAX_CL <= 32, "one warp reduces the offers");
@@ -1024,6 +1024,25 @@ __global__ void __launch_bounds__(CLP_THREADS, 1)
     if (t == 0 && s_dec[2] != 0 && *info == 0) *info = s_dec[2];
   }
   cl_sync();  // no CTA leaves while a remote store into it may be in flight
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CLP_THREADS, 1)
+    lu_panel_cluster_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
+                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
+  panel_body<NB>(A, lda, n, J0, JB, ipiv, info);
+}
+
+// Batched form: cluster c (of the grid's clusters) factors block column J0
+// of system sys[c]; a system whose n <= J0 has no work (the whole cluster
+// leaves together).
+template <int NB>
+__global__ void __launch_bounds__(CLP_THREADS, 1)
+    lu_panel_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
+  const BatchLu b = sys[blockIdx.x / cl_size()];
+  const int JB = min(nb, b.n - J0);
+  if (JB <= 0) return;
+  panel_body<NB>(b.A, b.n, b.n, J0, JB, b.ipiv, b.info);
 }
 
 // Launch the cluster panel for the block column [J0, J0+JB) if it fits
@@ -1258,7 +1277,34 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
                                 128 * 128 * static_cast<int>(sizeof(float))) == cudaSuccess;
   }();
   if (!attrs) return BFX_ECUDA;
-  for (int j0 = J0; j0 < J0 + nb; j0 += TILE_W) {
+  bool paneled = false;
+  if (nb <= 64) {
+    // the whole block column of every system by the panel kernel: one CTA a
+    // system (two, a cluster, above 512 rows)
+    const int rows = nmax - J0;
+    const int cs = static_cast<int>(ceil_div(rows, CLP_THREADS));
+    if (cs <= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = static_cast<unsigned>(cs);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(static_cast<unsigned>(cs * S_act), 1, 1);
+      cfg.blockDim = dim3(static_cast<unsigned>(cs == 1 ? round_up(rows, 32) : CLP_THREADS), 1, 1);
+      cfg.stream = s;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = nb <= 32
+                                ? cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<32>, d_sys, nb, J0)
+                                : cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<64>, d_sys, nb, J0);
+      if (e == cudaSuccess)
+        paneled = true;
+      else
+        cudaGetLastError();
+    }
+  }
+  for (int j0 = J0; !paneled && j0 < J0 + nb; j0 += TILE_W) {
     int S_t = 0;
     while (S_t < S_act && h_n_desc[S_t] > j0) ++S_t;
     if (S_t == 0) break;

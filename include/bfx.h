@@ -97,9 +97,10 @@ BFX_API int bfx_num_sms(void);
 
 /* Read and clear the device error word of the current device.  Kernels whose
  * waits are bounded (tensor-core GEMM pipeline barriers, the refinement's
- * triangular solves waiting on earlier row blocks) set it instead of
- * hanging: 0 = no error, otherwise a code naming the wait that expired
- * (1-5 GEMM pipeline, 6 triangular solve).
+ * triangular solves waiting on earlier row blocks, the LU panel's pivot
+ * exchange between the CTAs of a cluster) set it instead of hanging: 0 = no
+ * error, otherwise a code naming the wait that expired (1-5 GEMM pipeline,
+ * 6 triangular solve, 7 LU panel).
  * Synchronises `stream`.  h_code: host int (output). */
 BFX_API bfx_status bfx_device_error(int* h_code, bfx_stream stream);
 
@@ -287,9 +288,9 @@ BFX_API bfx_status bfx_dot_bf16xN(bfx_mode mode, int64_t n, const float* d_x, co
  * BFX_FP32.  d_ipiv[j] (int32, 0-based) is the row swapped with row j at
  * step j.  d_info (device int32) receives 0 or the 1-based index of the first
  * exactly zero pivot; the factorisation completes either way.  Workspace:
- * bfx_lu_workspace_size(mode, n, nb) bytes, 256-byte aligned (the row-swap
- * bookkeeping of a block column, plus the bfloat16 pieces of the trailing
- * update for X1..X9).  Errors: BFX_EINVAL, BFX_ENOMEM, BFX_EUNSUPPORTED. */
+ * bfx_lu_workspace_size(mode, n, nb) bytes, 256-byte aligned (the bfloat16
+ * pieces of the trailing update for X1..X9; 0 bytes for BFX_FP32, when d_ws
+ * may be NULL).  Errors: BFX_EINVAL, BFX_ENOMEM, BFX_EUNSUPPORTED. */
 BFX_API size_t bfx_lu_workspace_size(bfx_mode mode, int64_t n, int nb);
 BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, int64_t lda,
                                  int32_t* d_ipiv, int32_t* d_info, void* d_ws, size_t ws_bytes,

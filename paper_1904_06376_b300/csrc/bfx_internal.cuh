@@ -22,6 +22,7 @@ enum DeviceError : int {
   kErrWaitAccEmpty = 4,  // MMA issuer waited too long for the epilogue
   kErrWaitDrain = 5,     // final drain of in-flight MMAs expired
   kErrWaitBlock = 6,     // triangular solve waited too long for an earlier row block
+  kErrWaitPanel = 7,     // cluster panel waited too long for a pivot exchange
 };
 
 int* device_error_word();  // nullptr on failure

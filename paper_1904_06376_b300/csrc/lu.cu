@@ -15,8 +15,9 @@
 //             it forward-substituted and the rows below given the tile's
 //             rank-8 update: for every element the same operations in the
 //             same order;
-//   laswp   : the panel's row swaps applied to the columns left and right of it;
-//   trsm    : U12 = L11^-1 A12 (unit lower, FP32 FMA, one thread a column);
+//   laswp   : the panel's row swaps applied to the columns left and right of it
+//             (each CTA forms their net effect on the touched rows itself);
+//   trsm    : U12 = L11^-1 A12 (unit lower, FP32 FMA, one warp a column);
 //   update  : A22 <- A22 - L21 U12 by the mode's bfloat16 products on the
 //             tensor cores (split of L21, transposed split of U12, tcgen05
 //             GEMM with alpha = -1, beta = 1), or the FP32 SIMT GEMM.
@@ -493,114 +494,132 @@ __global__ void lu_tile_update_kernel(float* __restrict__ A, int64_t lda, int n,
   tile_update_body(A, lda, n, J0, JB, j0, jw, blockIdx.x, gridDim.x);
 }
 
-// Apply the swaps ipiv[j0 .. j0+jb) to every column outside [j0, j0+jb).
-// The sequential swaps are first turned into their net effect on the at most
-// 2 jb rows they touch (slot k ends up holding the original row cont[k]) by
-// one warp; then every thread moves the touched rows of its column with all
-// loads issued before the stores.
-constexpr int LASWP_COLS = 64;
+// Apply the swaps ipiv[j0 .. j0+jb) to columns outside [j0, j0+jb).
+// Every CTA first turns the sequential swaps into their net effect on the at
+// most 2 jb rows they touch (slot k ends up holding the original row
+// cont[k]), then moves those rows of its LASWP_COLS columns: warp w loads
+// slots w, w + LASWP_WARPS, ... of its lane's column into registers, and
+// after a CTA barrier (which orders every load of the column before every
+// store) writes them to their new rows.
+constexpr int LASWP_COLS = 32;     // columns a CTA, one a lane
+constexpr int LASWP_WARPS = 8;     // warps a CTA
+constexpr int LASWP_THREADS = LASWP_COLS * LASWP_WARPS;
+constexpr int LASWP_SLOTS = 256;   // 2 x the largest block width
+constexpr int LASWP_PER_WARP = LASWP_SLOTS / LASWP_WARPS;
 struct SwapSet {
-  int rowid[256];
-  int cont[256];
+  int rowid[LASWP_SLOTS];  // the touched rows
+  int cont[LASWP_SLOTS];   // row rowid[k] receives the original row cont[k]
   int nslots;
 };
 
-// Warp 0 of the calling CTA fills *ss (shared or global memory).
-__device__ __forceinline__ void swapset_build(const int32_t* __restrict__ ipiv, int j0, int jb,
-                                              SwapSet* ss) {
-  __shared__ int piv[128];
-  const int t = threadIdx.x;
+// One warp (all lanes) turns piv[0 .. jb) (absolute rows, piv[j] >= j0 + j;
+// shared memory, 16-byte aligned, jb <= 128) into *ss (shared memory).
+// Slot k < jb is row j0 + k; each row p >= j0 + jb that a swap names gets
+// the next slot in the order of its first appearance.  Swap j exchanges
+// slots j and sp[j] >= j, so slot j is final once swap j is done; one lane
+// replays the swaps on the slot contents.
+__device__ __forceinline__ void swapset_warp(const int* __restrict__ piv, int j0, int jb,
+                                             SwapSet* ss, int* sp) {
+  const int lane = threadIdx.x & 31;
+  constexpr int G = 4;  // groups of 32 swaps
+  uint32_t fresh[G];    // swaps that name a row outside the block for the first time
+  int first[G];         // the first swap naming the same outside row (-1: inside)
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = 32 * g + lane;
+    const int p = j < jb ? piv[j] : -1;
+    int f = -1;
+    if (p >= j0 + jb) {
+      f = j;
+      for (int q0 = 0; q0 < j && f == j; q0 += 4) {
+        const int4 x = *reinterpret_cast<const int4*>(piv + q0);
+        if (x.x == p) f = q0;
+        else if (q0 + 1 < j && x.y == p) f = q0 + 1;
+        else if (q0 + 2 < j && x.z == p) f = q0 + 2;
+        else if (q0 + 3 < j && x.w == p) f = q0 + 3;
+      }
+    }
+    first[g] = f;
+    fresh[g] = __ballot_sync(0xFFFFFFFFu, f >= 0 && f == j);
+  }
+  int nfresh = 0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) nfresh += __popc(fresh[g]);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int j = 32 * g + lane;
+    if (j < jb) {
+      const int f = first[g];
+      int s = piv[j] - j0;
+      if (f >= 0) {
+        int below = 0;  // first appearances before swap f
+#pragma unroll
+        for (int h = 0; h < G; ++h) {
+          if (h < (f >> 5)) below += __popc(fresh[h]);
+          else if (h == (f >> 5)) below += __popc(fresh[h] & ((1u << (f & 31)) - 1u));
+        }
+        s = jb + below;
+        if (f == j) ss->rowid[s] = piv[j];
+      }
+      sp[j] = s;
+      ss->rowid[j] = j0 + j;
+    }
+  }
+  const int ns = jb + nfresh;
+  __syncwarp();
+  for (int k = lane; k < ns; k += 32) ss->cont[k] = ss->rowid[k];
+  __syncwarp();
+  if (lane == 0) {
+    for (int j = 0; j < jb; ++j) {
+      const int s = sp[j];
+      if (s != j) {
+        const int a = ss->cont[j];
+        ss->cont[j] = ss->cont[s];
+        ss->cont[s] = a;
+      }
+    }
+    ss->nslots = ns;
+  }
+  __syncwarp();
+}
+
+// Moves the touched rows of CTA cb's columns: column index
+// idx = cb * LASWP_COLS + lane of the list [c0, c0 + n0) ++ [c1, c1 + n1).
+// Builds the swap set of ipiv[j0 .. j0+jb) itself (blockDim = LASWP_THREADS).
+__device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int j0, int jb,
+                                           const int32_t* __restrict__ ipiv, int c0, int n0,
+                                           int c1, int n1, int cb) {
+  __shared__ SwapSet ss;
+  __shared__ __align__(16) int piv[128];
+  __shared__ int sp[128];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int j = t; j < jb; j += blockDim.x) piv[j] = ipiv[j0 + j];
   __syncthreads();
-  if (t < 32) {
-    for (int k = t; k < jb; k += 32) {
-      ss->rowid[k] = j0 + k;
-      ss->cont[k] = j0 + k;
-    }
-    int ns = jb;
-    __syncwarp();
-    for (int j = 0; j < jb; ++j) {
-      const int p = piv[j];
-      int sp;
-      if (p < j0 + jb) {
-        sp = p - j0;
-      } else {
-        sp = -1;
-        for (int base = jb; base < ns && sp < 0; base += 32) {
-          const int k = base + t;
-          const unsigned hit = __ballot_sync(0xFFFFFFFFu, k < ns && ss->rowid[k] == p);
-          if (hit) sp = base + __ffs(hit) - 1;
-        }
-        if (sp < 0) {
-          sp = ns++;
-          if (t == 0) {
-            ss->rowid[sp] = p;
-            ss->cont[sp] = p;
-          }
-        }
-      }
-      __syncwarp();
-      if (t == 0 && sp != j) {
-        const int tmp = ss->cont[j];
-        ss->cont[j] = ss->cont[sp];
-        ss->cont[sp] = tmp;
-      }
-      __syncwarp();
-    }
-    if (t == 0) ss->nslots = ns;
+  if (w == 0) swapset_warp(piv, j0, jb, &ss, sp);
+  __syncthreads();
+  const int idx = cb * LASWP_COLS + lane;
+  const bool on = idx < n0 + n1;
+  const int64_t c = idx < n0 ? c0 + idx : c1 + (idx - n0);
+  const int ns = ss.nslots;
+  float v[LASWP_PER_WARP];
+#pragma unroll
+  for (int q = 0; q < LASWP_PER_WARP; ++q) {
+    const int k = w + LASWP_WARPS * q;
+    v[q] = (on && k < ns) ? A[static_cast<int64_t>(ss.cont[k]) * lda + c] : 0.0f;
   }
   __syncthreads();
-}
-
-__global__ void lu_swapset_kernel(const int32_t* __restrict__ ipiv, int j0, int jb,
-                                  SwapSet* __restrict__ out) {
-  __shared__ SwapSet ss;
-  swapset_build(ipiv, j0, jb, &ss);
-  for (int k = threadIdx.x; k < ss.nslots; k += blockDim.x) {
-    out->rowid[k] = ss.rowid[k];
-    out->cont[k] = ss.cont[k];
+#pragma unroll
+  for (int q = 0; q < LASWP_PER_WARP; ++q) {
+    const int k = w + LASWP_WARPS * q;
+    if (on && k < ns) A[static_cast<int64_t>(ss.rowid[k]) * lda + c] = v[q];
   }
-  if (threadIdx.x == 0) out->nslots = ss.nslots;
 }
 
-// Move the touched rows of column block cb (ss: a finished swap set).
-__device__ __forceinline__ void laswp_apply(float* __restrict__ A, int64_t lda, int n, int j0,
-                                            int jb, const SwapSet* __restrict__ ss, int cb) {
-  extern __shared__ float vals[];  // (2 jb) x LASWP_COLS
-  const int t = threadIdx.x;
-  const int64_t idx = cb * static_cast<int64_t>(LASWP_COLS) + t;
-  if (idx >= n - jb) return;
-  const int c = static_cast<int>(idx < j0 ? idx : idx + jb);
-  const int ns = ss->nslots;
-  // batches of 16 loads in registers before their shared-memory stores, so
-  // the global loads are all in flight together
-  for (int k0 = 0; k0 < ns; k0 += 16) {
-    int src[16];
-    float v[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) src[q] = (k0 + q < ns) ? ss->cont[k0 + q] : -1;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = (src[q] >= 0) ? A[static_cast<int64_t>(src[q]) * lda + c] : 0.0f;
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (k0 + q < ns) vals[(k0 + q) * LASWP_COLS + t] = v[q];
-  }
-  for (int k = 0; k < ns; ++k)
-    A[static_cast<int64_t>(ss->rowid[k]) * lda + c] = vals[k * LASWP_COLS + t];
-}
-
-// batched systems: each CTA builds the (small) swap set itself
-__device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int n, int j0,
-                                           int jb, const int32_t* __restrict__ ipiv, int cb) {
-  __shared__ SwapSet ss;
-  swapset_build(ipiv, j0, jb, &ss);
-  laswp_apply(A, lda, n, j0, jb, &ss, cb);
-}
-
-__global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict__ A, int64_t lda,
-                                                             int n, int j0, int jb,
-                                                             const SwapSet* __restrict__ ss) {
-  laswp_apply(A, lda, n, j0, jb, ss, blockIdx.x);
+// Columns [c0, c0 + n0) ++ [c1, c1 + n1) of one matrix.
+__global__ void __launch_bounds__(LASWP_THREADS)
+    lu_laswp_kernel(float* __restrict__ A, int64_t lda, int j0, int jb,
+                    const int32_t* __restrict__ ipiv, int c0, int n0, int c1, int n1) {
+  laswp_body(A, lda, j0, jb, ipiv, c0, n0, c1, n1, static_cast<int>(blockIdx.x));
 }
 
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
@@ -609,15 +628,23 @@ __global__ void __launch_bounds__(LASWP_COLS) lu_laswp_kernel(float* __restrict_
 // per element the same FMA sequence as row-by-row substitution - with x_l
 // broadcast from its owner lane.
 constexpr int TRSM_COLS = 8;  // columns (warps) a CTA
+__host__ __device__ constexpr int trsm_lds(int nb) { return nb + 1; }  // row stride of L11 in shared memory
+// shared bytes of the block solve's L11 for register tile nb
+constexpr size_t trsm_smem_bytes(int nb) {
+  return static_cast<size_t>(nb) * trsm_lds(nb) * sizeof(float);
+}
 template <int NB>
 // Columns c_begin + cb * TRSM_COLS + (warp) below c_end of the block row j0.
 __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int c_end, int j0,
                                           int jb, int c_begin, int cb) {
-  extern __shared__ float L11[];  // NB x NB, the jb x jb triangle padded with zeros
-  constexpr int RPL = NB / 32;    // rows a lane
+  // NB x NB, the jb x jb triangle padded with zeros; rows trsm_lds(NB) apart
+  // so the lanes' rows i = lane + 32 q of one column l fall in distinct banks
+  extern __shared__ float L11[];
+  constexpr int RPL = NB / 32;  // rows a lane
+  constexpr int LS = trsm_lds(NB);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, l = e % NB;
-    L11[e] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
+    L11[i * LS + l] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -639,7 +666,7 @@ __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, in
 #pragma unroll
       for (int q = q0; q < RPL; ++q) {
         const int i = lane + 32 * q;
-        if (i > l && i < jb) x[q] = fmaf(-L11[i * NB + l], xl, x[q]);
+        if (i > l && i < jb) x[q] = fmaf(-L11[i * LS + l], xl, x[q]);
       }
     }
   }
@@ -680,12 +707,12 @@ __global__ void lu_tile_update_batched_kernel(const BatchLu* __restrict__ sys, i
   tile_update_body(b.A, b.n, b.n, J0, JB, j0, jw, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(LASWP_COLS)
+__global__ void __launch_bounds__(LASWP_THREADS)
     lu_laswp_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
-  if (JB <= 0 || blockIdx.x * LASWP_COLS >= b.n - JB) return;
-  laswp_body(b.A, b.n, b.n, J0, JB, b.ipiv, blockIdx.x);
+  if (JB <= 0 || static_cast<int>(blockIdx.x) * LASWP_COLS >= b.n - JB) return;
+  laswp_body(b.A, b.n, J0, JB, b.ipiv, 0, J0, J0 + JB, b.n - J0 - JB, static_cast<int>(blockIdx.x));
 }
 
 template <int NB>
@@ -750,32 +777,68 @@ __global__ void lu_split_batched_kernel(const BatchLu* __restrict__ sys, int nb,
 //     each warp's winner posts its row to shared memory, and the thread
 //     holding row j posts row j;
 //  2. after a CTA barrier the pushing warps reduce the warps' offers the
-//     same way and push the CTA's offer (key, row index, row) and, from CTA
-//     0, row j into an exchange slot of every CTA (distributed shared
-//     memory; plain shared memory in a cluster of one);
-//  3. one cluster barrier (release / acquire); warp 0 reduces the cs offers
-//     -> pivot row p (a NaN on the diagonal stays), then a CTA barrier; the
-//     holder of row j takes the pivot row, the holder of row p the old row j;
+//     same way and store the CTA's offer (key, row index, row) and, from CTA
+//     0, row j into an exchange slot of every CTA of the cluster: into the
+//     other CTAs by asynchronous remote shared-memory stores that complete
+//     their bytes on the receiving slot's mbarrier, into the own slot by
+//     plain stores followed by an arrival on it (plain stores and a CTA
+//     barrier in a cluster of one);
+//  3. every thread waits (acquire, cluster scope) for its CTA's slot to be
+//     complete - each CTA waits only for the bytes sent to it, no cluster-wide
+//     barrier; every warp reduces the cs offers -> pivot row p (a NaN on the
+//     diagonal stays); the holder of row j takes the pivot row, the holder of
+//     row p the old row j;
 //  4. rows below j: l = a_rj / a_jj (IEEE division), then a_rc <- fma(-l,
 //     u_jc, a_rc) for the block column's columns c > j, in column order.
 // Each element therefore sees the operations of the unblocked right-looking
-// LU of the block column, in the same order as the 8-column tile path.  The
-// exchange slots alternate by column parity: a CTA writes column j+2's offers
-// only after the barrier of column j+1, which no CTA reaches before it has
-// read column j's.  Columns go in groups of 8 whose register indices are
-// compile-time constants; after a group the row rotates left by 8, so after
-// NB / 8 groups it is back in place.
+// LU of the block column, in the same order as the 8-column tile path.
+// The slots, the staged rows and offers alternate by column parity.  A CTA
+// stores column j+2's offer into CTA b only after its own slot for column
+// j+1 is complete, which needs b's column j+1 offer, which b sends only after
+// a CTA barrier that all its threads pass once they have read column j's
+// slot; the same barrier orders a CTA's reads of its staged rows for column j
+// before their rewrite for column j+2.  Columns go in groups of 8 whose
+// register indices are compile-time constants; after a group the row rotates
+// left by 8, so after NB / 8 groups it is back in place.  Every wait is
+// bounded: an expired wait records kErrWaitPanel in the device error word and
+// the kernel runs to its end without further waits.
 constexpr int CLP_THREADS = 512;  // rows a CTA holds
 constexpr int CLP_MAX_CL = 16;    // exchange slots (16 would be a non-portable cluster size)
 constexpr int kPanelMaxCluster = 8;  // clusters launched: the portable size, up to 4096 rows
+constexpr uint64_t kPanelWaitNs = 2000000000ull;  // a column's exchange takes microseconds
 
 template <int NB>
 struct ClusterSlot {
   float row[CLP_MAX_CL][NB];  // each CTA's offered row (rotated register order)
   float rowj[NB];             // row j before the swap
-  uint32_t key[CLP_MAX_CL];
-  uint32_t idx[CLP_MAX_CL];
+  uint2 ki[CLP_MAX_CL];       // each CTA's offer: key, row index
 };
+
+template <int NB>
+struct PanelShared {
+  static constexpr int MW = CLP_THREADS / 32;
+  ClusterSlot<NB> slot[2];  // by column parity
+  float wrow[2][MW][NB];    // each warp's offered row, by column parity
+  float rowj[2][NB];        // row j (CTA 0), by column parity
+  uint32_t wkey[2][MW];
+  uint32_t widx[2][MW];
+  uint64_t bar[2];          // slot complete (clusters of more than one CTA)
+  int piv[NB];              // the block column's pivots
+  int zero;                 // 1-based row of the first zero pivot, or 0
+};
+
+// A slot of CTA cr (cs > 1) completes a phase when its bytes from the other
+// CTAs have landed (their offers; row j unless cr is CTA 0) and the threads
+// that fill it locally (the offer: NQ threads; row j in CTA 0: NQ more) have
+// arrived after their stores, besides the arrival that sets the byte count.
+template <int NB>
+__device__ __forceinline__ uint32_t slot_bytes(int cs, int cr) {
+  return static_cast<uint32_t>(cs - 1) * (NB * 4 + 8) + (cr == 0 ? 0u : NB * 4u);
+}
+template <int NB>
+__device__ __forceinline__ uint32_t slot_arrivals(int cr) {
+  return 1u + (cr == 0 ? 2u : 1u) * (NB / 4);
+}
 
 __device__ __forceinline__ uint32_t cl_rank() {
   uint32_t r;
@@ -800,21 +863,44 @@ __device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void cl_st(uint32_t addr, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x),
-               "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
+// shared-memory stores into another CTA of the cluster that complete their
+// bytes on mbarrier `bar` (an address in the same CTA's shared window)
+__device__ __forceinline__ void st_async(uint32_t addr, float4 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(addr), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+      "r"(__float_as_uint(v.w)), "r"(bar)
+      : "memory");
 }
-__device__ __forceinline__ void cl_st(uint32_t addr, uint32_t v) {
-  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+__device__ __forceinline__ void st_async(uint32_t addr, uint2 v, uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];"
+      ::"r"(addr), "r"(v.x), "r"(v.y), "r"(bar)
+      : "memory");
 }
-// store v at p in CTA `rank` (local when the cluster is a single CTA)
-template <class T>
-__device__ __forceinline__ void push_to(T* p, uint32_t rank, T v, bool local) {
-  if (local)
-    *p = v;
-  else
-    cl_st(cl_map(p, rank), v);
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the slot's phase; *expired: an earlier wait gave up (skip)
+__device__ __forceinline__ void panel_wait(uint64_t* bar, uint32_t parity, int* err,
+                                           bool* expired) {
+  if (*expired || mbar_try_wait_cluster(bar, parity)) return;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (global_ns() - t0 > kPanelWaitNs) {
+      if (err) atomicCAS(err, 0, kErrWaitPanel);
+      *expired = true;
+      return;
+    }
+  }
 }
 
 // pivot offer of a row: larger key wins, ties to the lower row index
@@ -833,18 +919,34 @@ __device__ __forceinline__ void warp_offer(uint32_t key, uint32_t idx, uint32_t*
   *lane_out = __ffs(__ballot_sync(0xFFFFFFFFu, key == m && idx == i)) - 1;
 }
 
+template <int NQ>
+__device__ __forceinline__ void put_row(float* dst, const float* v) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    *reinterpret_cast<float4*>(dst + 4 * q) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+template <int NQ>
+__device__ __forceinline__ void get_row(float* v, const float* src) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float4 x = *reinterpret_cast<const float4*>(src + 4 * q);
+    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+  }
+}
+
 // One pivot column of the cluster panel; K = the column's register (the
 // current rotation puts column g*8 + K there), JB the block-column width.
 template <int NB, int K>
 __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int n, int J0, int r,
                                              bool has, int t, int lane, int wid, int nw, int cr,
-                                             int cs, ClusterSlot<NB>* slot, float (*wrow)[NB],
-                                             float* myrowj, uint32_t* wkey, uint32_t* widx,
-                                             int* s_dec, int* s_piv) {
+                                             int cs, PanelShared<NB>& sh, int* err,
+                                             bool* expired) {
   constexpr int NQ = NB / 4;
   const int j = J0 + jj, bf = jj & 1;
   const int g8 = jj - K;  // columns rotated away so far
   const bool local = cs == 1;
+  ClusterSlot<NB>& sl = sh.slot[bf];
   // ---- 1. offers: every warp's winner posts its row, the holder of row j posts row j
   const bool offers = has && r >= j;
   uint32_t wk, wi;
@@ -852,78 +954,70 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
   warp_offer(offers ? offer_key(v[K]) : 0u, offers ? static_cast<uint32_t>(r) : 0xFFFFFFFFu, &wk,
              &wi, &wl);
   if (lane == 0) {
-    wkey[wid] = wk;
-    widx[wid] = wi;
+    sh.wkey[bf][wid] = wk;
+    sh.widx[bf][wid] = wi;
   }
-  if (lane == wl && offers) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      *reinterpret_cast<float4*>(&wrow[wid][4 * q]) =
-          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  }
-  if (cr == 0 && t == jj) {  // row j = J0 + jj lives in CTA 0, thread jj
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      *reinterpret_cast<float4*>(&myrowj[4 * q]) =
-          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  }
+  if (lane == wl && offers) put_row<NQ>(sh.wrow[bf][wid], v);
+  if (cr == 0 && t == jj) put_row<NQ>(sh.rowj[bf], v);  // row j: CTA 0, thread jj
   __syncthreads();
   // ---- 2. pushes: the pushing warps reduce the warps' offers themselves
   const int npush = cs * NQ;
-  const bool push_rowj = cr == 0 && t >= npush && t < 2 * npush;
+  if (!local && t == 0) mbar_arrive_expect_tx(&sh.bar[bf], slot_bytes<NB>(cs, cr));
   if (wid * 32 < npush) {  // whole warps: the reductions need every lane
     uint32_t ck, ci;
     int cw;
-    warp_offer(lane < nw ? wkey[lane] : 0u, lane < nw ? widx[lane] : 0xFFFFFFFFu, &ck, &ci, &cw);
+    warp_offer(lane < nw ? sh.wkey[bf][lane] : 0u, lane < nw ? sh.widx[bf][lane] : 0xFFFFFFFFu,
+               &ck, &ci, &cw);
     cw = min(cw, nw - 1);  // every CTA offers a row (its rows are >= j)
     if (t < npush) {
       const int dst = t / NQ, q = t % NQ;
-      push_to(reinterpret_cast<float4*>(&slot[bf].row[cr][4 * q]), dst,
-              *reinterpret_cast<const float4*>(&wrow[cw][4 * q]), local);
-      if (q == 0) {
-        push_to(&slot[bf].key[cr], dst, ck, local);
-        push_to(&slot[bf].idx[cr], dst, ci, local);
+      const float4 x = *reinterpret_cast<const float4*>(&sh.wrow[bf][cw][4 * q]);
+      float4* to = reinterpret_cast<float4*>(&sl.row[cr][4 * q]);
+      if (dst == cr) {  // this CTA's own slot: plain stores, then an arrival
+        *to = x;
+        if (q == 0) sl.ki[cr] = make_uint2(ck, ci);
+        if (!local) mbar_arrive(&sh.bar[bf]);
+      } else {
+        const uint32_t rb = cl_map(&sh.bar[bf], dst);
+        st_async(cl_map(to, dst), x, rb);
+        if (q == 0) st_async(cl_map(&sl.ki[cr], dst), make_uint2(ck, ci), rb);
       }
     }
   }
-  if (push_rowj) {
+  if (cr == 0 && t >= npush && t < 2 * npush) {
     const int e = t - npush, dst = e / NQ, q = e % NQ;
-    push_to(reinterpret_cast<float4*>(&slot[bf].rowj[4 * q]), dst,
-            *reinterpret_cast<const float4*>(&myrowj[4 * q]), local);
+    const float4 x = *reinterpret_cast<const float4*>(&sh.rowj[bf][4 * q]);
+    float4* to = reinterpret_cast<float4*>(&sl.rowj[4 * q]);
+    if (dst == 0) {
+      *to = x;
+      if (!local) mbar_arrive(&sh.bar[bf]);
+    } else {
+      st_async(cl_map(to, dst), x, cl_map(&sh.bar[bf], dst));
+    }
   }
   if (local)
     __syncthreads();
   else
-    cl_sync();
+    panel_wait(&sh.bar[bf], static_cast<uint32_t>((jj >> 1) & 1), err, expired);
   // ---- 3. the pivot: every warp reduces the cs offers (same data, same result)
   uint32_t gk, gi;
   int gw;
-  warp_offer(lane < cs ? slot[bf].key[lane] : 0u, lane < cs ? slot[bf].idx[lane] : 0xFFFFFFFFu,
-             &gk, &gi, &gw);
-  const float d = slot[bf].rowj[K];
+  warp_offer(lane < cs ? sl.ki[lane].x : 0u, lane < cs ? sl.ki[lane].y : 0xFFFFFFFFu, &gk, &gi,
+             &gw);
+  const float d = sl.rowj[K];
   const bool keep = (d != d || gi >= static_cast<uint32_t>(n));  // a NaN on the diagonal stays
   const int p = keep ? j : static_cast<int>(gi);
-  const float* prow = keep ? slot[bf].rowj : slot[bf].row[min(gw, cs - 1)];
-  if (t == 0) s_piv[jj] = p;  // to global memory once, at the end: a global store before
-                              // the next release would hold it up
+  const float* prow = keep ? sl.rowj : sl.row[min(gw, cs - 1)];
+  if (t == jj) sh.piv[jj] = p;  // to global memory once, at the end, by the same thread
   if (p != j && has) {
-    if (r == j) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(prow + 4 * q);
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-      }
-    } else if (r == p) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(slot[bf].rowj + 4 * q);
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-      }
-    }
+    if (r == j)
+      get_row<NQ>(v, prow);
+    else if (r == p)
+      get_row<NQ>(v, sl.rowj);
   }
   const float piv = prow[K];
   if (piv == 0.0f) {
-    if (t == 0 && s_dec[2] == 0) s_dec[2] = j + 1;  // the first zero pivot
+    if (t == 0 && sh.zero == 0) sh.zero = j + 1;  // the first zero pivot
   } else if (has && r > j) {
     // ---- 4. multiplier and rank-1 update of the row's later columns
     const float l = __fdiv_rn(v[K], piv);
@@ -945,19 +1039,13 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
 
 template <int NB>
 __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
-                                           int32_t* __restrict__ ipiv,
-                                           int32_t* __restrict__ info) {
-  constexpr int MW = CLP_THREADS / 32;
+                                           int32_t* __restrict__ ipiv, int32_t* __restrict__ info,
+                                           int* __restrict__ err) {
   constexpr int NQ = NB / 4;  // float4 words a row
-  static_assert(MW <= 32 && CLP_MAX_CL <= 32, "one warp reduces the offers");
+  static_assert(PanelShared<NB>::MW <= 32 && CLP_MAX_CL <= 32, "one warp reduces the offers");
   static_assert(2 * CLP_MAX_CL * NQ <= CLP_THREADS, "pushes of the offered row and of row j");
   static_assert(NB % 8 == 0, "columns go in groups of 8");
-  __shared__ __align__(16) ClusterSlot<NB> slot[2];
-  __shared__ __align__(16) float wrow[MW][NB];  // each warp's offered row
-  __shared__ __align__(16) float myrowj[NB];    // row j, in CTA 0
-  __shared__ uint32_t wkey[MW], widx[MW];
-  __shared__ int s_dec[3];   // s_dec[2]: the first zero pivot
-  __shared__ int s_piv[NB];  // the block column's pivots
+  __shared__ __align__(16) PanelShared<NB> sh;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   const int cr = static_cast<int>(cl_rank()), cs = static_cast<int>(cl_size());
   const int r = J0 + cr * CLP_THREADS + t;  // this thread's row
@@ -968,11 +1056,7 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
   {
     const float* src = A + static_cast<int64_t>(has ? r : J0) * lda + J0;
     if (vec) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float4 x = *reinterpret_cast<const float4*>(src + 4 * q);
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-      }
+      get_row<NQ>(v, src);
     } else {
 #pragma unroll
       for (int c = 0; c < NB; ++c) v[c] = c < JB ? src[c] : 0.0f;
@@ -982,13 +1066,21 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
       for (int c = 0; c < NB; ++c) v[c] = 0.0f;
     }
   }
-  if (t == 0) s_dec[2] = 0;
-  cl_sync();  // every CTA of the cluster runs before the first remote store
+  if (t == 0) {
+    sh.zero = 0;
+    if (cs > 1) {
+      mbar_init(&sh.bar[0], slot_arrivals<NB>(cr));
+      mbar_init(&sh.bar[1], slot_arrivals<NB>(cr));
+      fence_barrier_init();
+    }
+  }
+  cl_sync();  // the slots' mbarriers set up in every CTA before the first remote store
+  bool expired = false;
   for (int g = 0; g < NB; g += 8) {
-#define BFX_PANEL_COL(K)                                                                       \
-  if (g + K < JB)                                                                              \
-    panel_column<NB, K>(v, g + K, JB, n, J0, r, has, t, lane, wid, nw, cr, cs, slot, wrow,     \
-                        myrowj, wkey, widx, s_dec, s_piv);
+#define BFX_PANEL_COL(K)                                                                      \
+  if (g + K < JB)                                                                             \
+    panel_column<NB, K>(v, g + K, JB, n, J0, r, has, t, lane, wid, nw, cr, cs, sh, err,       \
+                        &expired);
     BFX_PANEL_COL(0)
     BFX_PANEL_COL(1)
     BFX_PANEL_COL(2)
@@ -1009,10 +1101,7 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
   if (has) {
     float* dst = A + static_cast<int64_t>(r) * lda + J0;
     if (vec) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        *reinterpret_cast<float4*>(dst + 4 * q) =
-            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      put_row<NQ>(dst, v);
     } else {
 #pragma unroll
       for (int c = 0; c < NB; ++c)
@@ -1020,17 +1109,18 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
     }
   }
   if (cr == 0) {
-    for (int c = t; c < JB; c += blockDim.x) ipiv[J0 + c] = s_piv[c];
-    if (t == 0 && s_dec[2] != 0 && *info == 0) *info = s_dec[2];
+    for (int c = t; c < JB; c += blockDim.x) ipiv[J0 + c] = sh.piv[c];
+    if (t == 0 && sh.zero != 0 && *info == 0) *info = sh.zero;
   }
-  cl_sync();  // no CTA leaves while a remote store into it may be in flight
+  cl_sync();  // every CTA has received all it waits for before any leaves
 }
 
 template <int NB>
 __global__ void __launch_bounds__(CLP_THREADS, 1)
     lu_panel_cluster_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
-                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info) {
-  panel_body<NB>(A, lda, n, J0, JB, ipiv, info);
+                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info,
+                            int* __restrict__ err) {
+  panel_body<NB>(A, lda, n, J0, JB, ipiv, info, err);
 }
 
 // Batched form: cluster c (of the grid's clusters) factors block column J0
@@ -1038,11 +1128,11 @@ __global__ void __launch_bounds__(CLP_THREADS, 1)
 // leaves together).
 template <int NB>
 __global__ void __launch_bounds__(CLP_THREADS, 1)
-    lu_panel_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
+    lu_panel_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int* __restrict__ err) {
   const BatchLu b = sys[blockIdx.x / cl_size()];
   const int JB = min(nb, b.n - J0);
   if (JB <= 0) return;
-  panel_body<NB>(b.A, b.n, b.n, J0, JB, b.ipiv, b.info);
+  panel_body<NB>(b.A, b.n, b.n, J0, JB, b.ipiv, b.info, err);
 }
 
 // Launch the cluster panel for the block column [J0, J0+JB) if it fits
@@ -1067,9 +1157,16 @@ bool launch_panel_cluster(float* A, int64_t lda, int n, int J0, int JB, int32_t*
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  int* err = device_error_word();
+  if (!err) {
+    *st = BFX_ECUDA;
+    return false;
+  }
   const cudaError_t e =
-      JB <= 32 ? cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<32>, A, lda, n, J0, JB, ipiv, info)
-               : cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<64>, A, lda, n, J0, JB, ipiv, info);
+      JB <= 32 ? cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<32>, A, lda, n, J0, JB, ipiv, info,
+                                    err)
+               : cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<64>, A, lda, n, J0, JB, ipiv, info,
+                                    err);
   if (e != cudaSuccess) {  // e.g. a cluster size the device does not offer: use the tiles
     cudaGetLastError();
     return false;
@@ -1083,16 +1180,13 @@ struct LuWs {
   size_t bytes;
 };
 
-constexpr size_t kSwapSetBytes = (sizeof(SwapSet) + 255) / 256 * 256;
-
-// Workspace: the swap set of the current block column, then np planes of the
-// L21 pieces and np planes of the U12^T pieces.
+// Workspace: np planes of the L21 pieces and np planes of the U12^T pieces.
 LuWs lu_ws(int np, int64_t n, int nb) {
   LuWs w;
   w.kp = round_up(nb, 8);
   w.ap = round_up(n * w.kp, 128);
   w.bp = w.ap;
-  w.bytes = kSwapSetBytes + static_cast<size_t>(np) * static_cast<size_t>(w.ap + w.bp) * 2;
+  w.bytes = static_cast<size_t>(np) * static_cast<size_t>(w.ap + w.bp) * 2;
   return w;
 }
 
@@ -1106,28 +1200,26 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   if (n == 0) return BFX_OK;
   const int np = mode_pieces(mode);
   LuWs w = lu_ws(np, n, nb);
-  if (!ws || ws_bytes < w.bytes || !aligned(ws, 256)) return BFX_ENOMEM;
-  SwapSet* swapset = static_cast<SwapSet*>(ws);
+  if (w.bytes > 0 && (!ws || ws_bytes < w.bytes || !aligned(ws, 256))) return BFX_ENOMEM;
   if (cudaFuncSetAttribute(lu_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess ||
-      cudaFuncSetAttribute(lu_laswp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) != cudaSuccess)
+                           static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess)
     return BFX_ECUDA;
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);  // register tile of the block solve
   auto trsm = tnb == 32 ? lu_trsm_kernel<32> : (tnb == 64 ? lu_trsm_kernel<64> : lu_trsm_kernel<128>);
-  const size_t trsm_smem = static_cast<size_t>(tnb) * tnb * sizeof(float);
+  const size_t trsm_smem = trsm_smem_bytes(tnb);
   if (trsm_smem > 48 * 1024 &&
       cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(trsm_smem)) != cudaSuccess)
     return BFX_ECUDA;
-  uint16_t* Lp = reinterpret_cast<uint16_t*>(static_cast<char*>(ws) + kSwapSetBytes);
+  uint16_t* Lp = static_cast<uint16_t*>(ws);
   uint16_t* Up = Lp + np * w.ap;
   const int N = static_cast<int>(n);
-  // Look-ahead: the caller's stream s carries the panel, the row swaps and
-  // the next block column's solve and update; an auxiliary stream (one per
-  // host thread, joined to s by events) carries the rest of each trailing
-  // update, so it runs while the next panel is factored.  The next row swaps
-  // wait for it.  Each element sees the same operations as without it.
+  // Look-ahead: the caller's stream s carries the panel and the next block
+  // column's row swaps, solve and update; an auxiliary stream (one per host
+  // thread, joined to s by events) carries the other columns' row swaps and
+  // the rest of the solve and of the trailing update, so they run while the
+  // next panel is factored.  The next row swaps wait for them.  Each element
+  // sees the same operations as without it.
   // The auxiliary stream and its two events are created once per host thread
   // and device (on the first LU call there) and kept until the thread ends;
   // later calls create nothing.
@@ -1225,30 +1317,33 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     // the row swaps move rows of columns the previous rest update writes
     if (rest_pending && cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
     rest_pending = false;
-    if (N - jb > 0) {
-      const int64_t cols = N - jb;
-      lu_swapset_kernel<<<1, 32, 0, s>>>(ipiv, j0, jb, swapset);
-      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(cols, LASWP_COLS)), LASWP_COLS,
-                        static_cast<size_t>(2 * jb) * LASWP_COLS * sizeof(float), s>>>(A, lda, N, j0,
-                                                                                     jb, swapset);
-    }
     const int nr = N - j0 - jb;
-    if (nr <= 0) continue;
-    // next block column: solve and update on s
-    const int nc = std::min(nb, nr);
-    trsm<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
-        A, lda, j0 + jb + nc, j0, jb, j0 + jb);
-    bfx_status st = update(j0, jb, 0, nc, s, true);
-    if (st != BFX_OK) return st;
-    // the rest on the auxiliary stream, after the row swaps and the L21 pieces
-    if (nr > nc) {
+    const int nc = std::min(nb, nr);  // the next block column's width (0 after the last)
+    // the next block column: row swaps, solve and update on s
+    if (nc > 0) {
+      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(nc, LASWP_COLS)), LASWP_THREADS, 0, s>>>(
+          A, lda, j0, jb, ipiv, j0 + jb, nc, 0, 0);
+      trsm<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
+          A, lda, j0 + jb + nc, j0, jb, j0 + jb);
+      bfx_status st = update(j0, jb, 0, nc, s, true);
+      if (st != BFX_OK) return st;
+    }
+    // the rest on the auxiliary stream, after the L21 pieces: the row swaps
+    // of the columns left of the block and right of the next one, then the
+    // remaining solve and update
+    const int c_far = j0 + jb + nc, n_far = N - c_far;
+    if (j0 + n_far > 0) {
       if (cudaEventRecord(ev_fork, s) != cudaSuccess ||
           cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
         return BFX_ECUDA;
-      trsm<<<static_cast<unsigned>(ceil_div(nr - nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
-          A, lda, N, j0, jb, j0 + jb + nc);
-      st = update(j0, jb, nc, nr - nc, aux, false);
-      if (st != BFX_OK) return st;
+      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(j0 + n_far, LASWP_COLS)), LASWP_THREADS, 0,
+                        aux>>>(A, lda, j0, jb, ipiv, 0, j0, c_far, n_far);
+      if (n_far > 0) {
+        trsm<<<static_cast<unsigned>(ceil_div(n_far, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
+            A, lda, N, j0, jb, c_far);
+        const bfx_status st = update(j0, jb, nc, n_far, aux, false);
+        if (st != BFX_OK) return st;
+      }
       if (cudaEventRecord(ev_rest, aux) != cudaSuccess) return BFX_ECUDA;
       rest_pending = true;
     }
@@ -1269,12 +1364,9 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
   const int nmax = h_n_desc[0];
   // once per process (thread-safe initialisation)
   static const bool attrs = [] {
-    return cudaFuncSetAttribute(lu_laswp_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                2 * 128 * LASWP_COLS * static_cast<int>(sizeof(float))) ==
-               cudaSuccess &&
-           cudaFuncSetAttribute(lu_trsm_batched_kernel<128>,
+    return cudaFuncSetAttribute(lu_trsm_batched_kernel<128>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                128 * 128 * static_cast<int>(sizeof(float))) == cudaSuccess;
+                                static_cast<int>(trsm_smem_bytes(128))) == cudaSuccess;
   }();
   if (!attrs) return BFX_ECUDA;
   bool paneled = false;
@@ -1296,8 +1388,10 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
       cfg.attrs = at;
       cfg.numAttrs = 1;
       const cudaError_t e = nb <= 32
-                                ? cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<32>, d_sys, nb, J0)
-                                : cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<64>, d_sys, nb, J0);
+                                ? cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<32>, d_sys, nb, J0,
+                                                     device_error_word())
+                                : cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<64>, d_sys, nb, J0,
+                                                     device_error_word());
       if (e == cudaSuccess)
         paneled = true;
       else
@@ -1318,11 +1412,9 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
     lu_tile_update_batched_kernel<<<dim3(gx, S_t), 256, 0, s>>>(d_sys, nb, J0, j0);
   }
   const unsigned cblk = static_cast<unsigned>(ceil_div(nmax, LASWP_COLS));
-  lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_COLS,
-                            static_cast<size_t>(2 * nb) * LASWP_COLS * sizeof(float), s>>>(d_sys, nb,
-                                                                                         J0);
+  lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_THREADS, 0, s>>>(d_sys, nb, J0);
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
-  const size_t tsmem = static_cast<size_t>(tnb) * tnb * sizeof(float);
+  const size_t tsmem = trsm_smem_bytes(tnb);
   const unsigned tblk = static_cast<unsigned>(ceil_div(nmax, TRSM_COLS));
   if (tnb == 32)
     lu_trsm_batched_kernel<32><<<dim3(tblk, S_act), TRSM_COLS * 32, tsmem, s>>>(d_sys, nb, J0);

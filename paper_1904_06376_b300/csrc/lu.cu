@@ -633,25 +633,25 @@ __host__ __device__ constexpr int trsm_lds(int nb) { return nb + 1; }  // row st
 constexpr size_t trsm_smem_bytes(int nb) {
   return static_cast<size_t>(nb) * trsm_lds(nb) * sizeof(float);
 }
+// L11 of block row j0 into shared memory: NB x NB, the jb x jb triangle
+// padded with zeros; rows trsm_lds(NB) apart so the lanes' rows
+// i = lane + 32 q of one column l fall in distinct banks.
 template <int NB>
-// Columns c_begin + cb * TRSM_COLS + (warp) below c_end of the block row j0.
-__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int c_end, int j0,
-                                          int jb, int c_begin, int cb) {
-  // NB x NB, the jb x jb triangle padded with zeros; rows trsm_lds(NB) apart
-  // so the lanes' rows i = lane + 32 q of one column l fall in distinct banks
-  extern __shared__ float L11[];
-  constexpr int RPL = NB / 32;  // rows a lane
+__device__ __forceinline__ void load_l11(const float* __restrict__ A, int64_t lda, int j0, int jb,
+                                         float* L11) {
   constexpr int LS = trsm_lds(NB);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int i = e / NB, l = e % NB;
     L11[i * LS + l] = (i < jb && l < jb) ? A[static_cast<int64_t>(j0 + i) * lda + j0 + l] : 0.0f;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t c = c_begin + cb * static_cast<int64_t>(TRSM_COLS) + w;
-  if (c >= c_end) return;
-  float* col = A + static_cast<int64_t>(j0) * lda + c;
-  float x[RPL];
+}
+// The column col[i * lda], i < jb, solved in x (lane's rows i = lane + 32 q);
+// rows 1 .. jb-1 written back (row 0 is its own solution).
+template <int NB>
+__device__ __forceinline__ void solve_col(float* __restrict__ col, int64_t lda, int jb,
+                                          const float* L11, int lane, float (&x)[NB / 32]) {
+  constexpr int RPL = NB / 32;  // rows a lane
+  constexpr int LS = trsm_lds(NB);
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     const int i = lane + 32 * q;
@@ -678,11 +678,76 @@ __device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, in
 }
 
 template <int NB>
-// Columns c_begin .. c_end - 1 of the block row j0.
-__global__ void __launch_bounds__(TRSM_COLS * 32) lu_trsm_kernel(float* __restrict__ A, int64_t lda,
-                                                                 int c_end, int j0, int jb,
-                                                                 int c_begin) {
-  trsm_body<NB>(A, lda, c_end, j0, jb, c_begin, static_cast<int>(blockIdx.x));
+// Columns c_begin + cb * TRSM_COLS + (warp) below c_end of the block row j0.
+__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int c_end, int j0,
+                                          int jb, int c_begin, int cb) {
+  extern __shared__ float L11[];
+  load_l11<NB>(A, lda, j0, jb, L11);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t c = c_begin + cb * static_cast<int64_t>(TRSM_COLS) + w;
+  if (c >= c_end) return;
+  float x[NB / 32];
+  solve_col<NB>(A + static_cast<int64_t>(j0) * lda + c, lda, jb, L11, lane, x);
+}
+
+// Single system: columns [c_begin, c_end) of block row j0 (one warp a
+// column), each first given the block column's row swaps ipiv[j0 .. j0+jb)
+// (the CTA forms their net effect; warp w's lanes move the touched rows of
+// its column, all loads before a warp barrier, then the stores), then solved;
+// with np > 0 the bfloat16 pieces of the solved column (U12^T row
+// c - (j0 + jb)) go to planes Up, Up + bp, Up + 2 bp (row stride kp), which
+// the trailing update reads.
+template <int NB>
+__global__ void __launch_bounds__(TRSM_COLS * 32)
+    lu_solve_cols_kernel(float* __restrict__ A, int64_t lda, int j0, int jb, int c_begin, int c_end,
+                         const int32_t* __restrict__ ipiv, int np, uint16_t* __restrict__ Up,
+                         int64_t bp, int64_t kp) {
+  extern __shared__ float L11[];
+  __shared__ SwapSet ss;
+  __shared__ __align__(16) int piv[128];
+  __shared__ int sp[128];
+  constexpr int SPL = 2 * NB / 32;  // swap slots a lane (at most 2 jb)
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  load_l11<NB>(A, lda, j0, jb, L11);
+  for (int j = t; j < jb; j += blockDim.x) piv[j] = ipiv[j0 + j];
+  __syncthreads();
+  if (w == 0) swapset_warp(piv, j0, jb, &ss, sp);
+  __syncthreads();
+  const int64_t c = c_begin + static_cast<int64_t>(blockIdx.x) * TRSM_COLS + w;
+  if (c >= c_end) return;
+  {
+    const int ns = ss.nslots;
+    float sv[SPL];
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const int k = lane + 32 * q;
+      sv[q] = k < ns ? A[static_cast<int64_t>(ss.cont[k]) * lda + c] : 0.0f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+      const int k = lane + 32 * q;
+      if (k < ns) A[static_cast<int64_t>(ss.rowid[k]) * lda + c] = sv[q];
+    }
+    __syncwarp();
+  }
+  float x[NB / 32];
+  solve_col<NB>(A + static_cast<int64_t>(j0) * lda + c, lda, jb, L11, lane, x);
+  if (np > 0) {
+    uint16_t* u = Up + (c - (j0 + jb)) * kp;
+#pragma unroll
+    for (int q = 0; q < NB / 32; ++q) {
+      const int i = lane + 32 * q;
+      if (i < jb) {
+        uint16_t h, m, l;
+        split_elem(x[q], h, m, l);
+        u[i] = h;
+        if (np > 1) u[bp + i] = m;
+        if (np > 2) u[2 * bp + i] = l;
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------- batched forms
@@ -1180,13 +1245,15 @@ struct LuWs {
   size_t bytes;
 };
 
-// Workspace: np planes of the L21 pieces and np planes of the U12^T pieces.
+// Workspace: two sets (by block-column parity: a panel writes its L21
+// pieces while the previous block's trailing update still reads the other
+// set) of np planes of the L21 pieces, then np planes of the U12^T pieces.
 LuWs lu_ws(int np, int64_t n, int nb) {
   LuWs w;
   w.kp = round_up(nb, 8);
   w.ap = round_up(n * w.kp, 128);
   w.bp = w.ap;
-  w.bytes = static_cast<size_t>(np) * static_cast<size_t>(w.ap + w.bp) * 2;
+  w.bytes = static_cast<size_t>(np) * static_cast<size_t>(2 * w.ap + w.bp) * 2;
   return w;
 }
 
@@ -1205,14 +1272,15 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
                            static_cast<int>(TILE_SMEM_MAX)) != cudaSuccess)
     return BFX_ECUDA;
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);  // register tile of the block solve
-  auto trsm = tnb == 32 ? lu_trsm_kernel<32> : (tnb == 64 ? lu_trsm_kernel<64> : lu_trsm_kernel<128>);
+  auto solve = tnb == 32 ? lu_solve_cols_kernel<32>
+                          : (tnb == 64 ? lu_solve_cols_kernel<64> : lu_solve_cols_kernel<128>);
   const size_t trsm_smem = trsm_smem_bytes(tnb);
-  if (trsm_smem > 48 * 1024 &&
-      cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (trsm_smem > 40 * 1024 &&
+      cudaFuncSetAttribute(solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(trsm_smem)) != cudaSuccess)
     return BFX_ECUDA;
-  uint16_t* Lp = static_cast<uint16_t*>(ws);
-  uint16_t* Up = Lp + np * w.ap;
+  uint16_t* Lset[2] = {static_cast<uint16_t*>(ws), static_cast<uint16_t*>(ws) + np * w.ap};
+  uint16_t* Up = Lset[1] + np * w.ap;
   const int N = static_cast<int>(n);
   // Look-ahead: the caller's stream s carries the panel and the next block
   // column's row swaps, solve and update; an auxiliary stream (one per host
@@ -1267,27 +1335,22 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   } join{s, ev_rest};
   bool& rest_pending = join.pending;
   // C[:, c0 .. c0+nc) -= L21 U12[:, c0 .. c0+nc) for block column j0 on stream st
-  auto update = [&](int j0, int jb, int c0, int nc, cudaStream_t st, bool split_l) -> bfx_status {
+  // (pieces: L21's in Lp, split after the panel; U12^T's written by the
+  // block solve)
+  auto update = [&](int j0, int jb, int c0, int nc, const uint16_t* Lp, cudaStream_t st) -> bfx_status {
     const int nr = N - j0 - jb;
     float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
     float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb + c0;
     float* A22 = A + static_cast<int64_t>(j0 + jb) * lda + j0 + jb + c0;
     if (np == 0) return launch_sgemm_simt(nr, nc, jb, -1.0f, L21, lda, U12, lda, 1.0f, A22, lda, st);
-    bfx_status e;
-    if (split_l) {
-      e = launch_split(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
-                       np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, st);
-      if (e != BFX_OK) return e;
-    }
-    uint16_t* Uc = Up + static_cast<int64_t>(c0) * w.kp;  // rows c0.. of the U12^T planes
-    e = launch_split_transpose(jb, nc, U12, lda, np, Uc, np > 1 ? Uc + w.bp : nullptr,
-                               np > 2 ? Uc + 2 * w.bp : nullptr, w.kp, st);
-    if (e != BFX_OK) return e;
+    const uint16_t* Uc = Up + static_cast<int64_t>(c0) * w.kp;  // rows c0.. of the U12^T planes
     return launch_gemm_presplit(mode, nr, nc, jb, -1.0f, Lp, w.kp, w.ap, Uc, w.kp, w.bp, 1.0f, A22,
                                 lda, st);
   };
-  for (int j0 = 0; j0 < N; j0 += nb) {
+  for (int j0 = 0, blk = 0; j0 < N; j0 += nb, ++blk) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
+    const int nr = N - j0 - jb;
+    uint16_t* Lp = Lset[blk & 1];
     bfx_status pst = BFX_OK;
     const bool clustered = launch_panel_cluster(A, lda, N, j0, jb, ipiv, info, s, &pst);
     if (pst != BFX_OK) return pst;
@@ -1314,34 +1377,40 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
         lu_tile_update_kernel<<<g, 256, 0, s>>>(A, lda, N, j0, jb, t0, tw);
       }
     }
+    // the L21 pieces into this block's set (the previous block's update may
+    // still read the other), before waiting for that update
+    if (np > 0 && nr > 0) {
+      const float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
+      const bfx_status e = launch_split(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
+                                        np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, s);
+      if (e != BFX_OK) return e;
+    }
     // the row swaps move rows of columns the previous rest update writes
     if (rest_pending && cudaStreamWaitEvent(s, ev_rest, 0) != cudaSuccess) return BFX_ECUDA;
     rest_pending = false;
-    const int nr = N - j0 - jb;
     const int nc = std::min(nb, nr);  // the next block column's width (0 after the last)
-    // the next block column: row swaps, solve and update on s
+    // the next block column: row swaps and solve (one kernel), update on s
     if (nc > 0) {
-      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(nc, LASWP_COLS)), LASWP_THREADS, 0, s>>>(
-          A, lda, j0, jb, ipiv, j0 + jb, nc, 0, 0);
-      trsm<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
-          A, lda, j0 + jb + nc, j0, jb, j0 + jb);
-      bfx_status st = update(j0, jb, 0, nc, s, true);
+      solve<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
+          A, lda, j0, jb, j0 + jb, j0 + jb + nc, ipiv, np, Up, w.bp, w.kp);
+      const bfx_status st = update(j0, jb, 0, nc, Lp, s);
       if (st != BFX_OK) return st;
     }
     // the rest on the auxiliary stream, after the L21 pieces: the row swaps
-    // of the columns left of the block and right of the next one, then the
-    // remaining solve and update
+    // of the columns left of the block, the row swaps and solve of the
+    // columns right of the next one, and their update
     const int c_far = j0 + jb + nc, n_far = N - c_far;
     if (j0 + n_far > 0) {
       if (cudaEventRecord(ev_fork, s) != cudaSuccess ||
           cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
         return BFX_ECUDA;
-      lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(j0 + n_far, LASWP_COLS)), LASWP_THREADS, 0,
-                        aux>>>(A, lda, j0, jb, ipiv, 0, j0, c_far, n_far);
+      if (j0 > 0)
+        lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(j0, LASWP_COLS)), LASWP_THREADS, 0, aux>>>(
+            A, lda, j0, jb, ipiv, 0, j0, 0, 0);
       if (n_far > 0) {
-        trsm<<<static_cast<unsigned>(ceil_div(n_far, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
-            A, lda, N, j0, jb, c_far);
-        const bfx_status st = update(j0, jb, nc, n_far, aux, false);
+        solve<<<static_cast<unsigned>(ceil_div(n_far, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
+            A, lda, j0, jb, c_far, N, ipiv, np, Up, w.bp, w.kp);
+        const bfx_status st = update(j0, jb, nc, n_far, Lp, aux);
         if (st != BFX_OK) return st;
       }
       if (cudaEventRecord(ev_rest, aux) != cudaSuccess) return BFX_ECUDA;

@@ -69,10 +69,11 @@ def lib() -> ctypes.CDLL:
         L.orc_solve_ir.argtypes = [i64, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, i32, f64,
                                    f64, f64, vp, vp, vp]
         L.orc_num_threads.restype = i32
-        L.orc_gmres.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, f64, vp, vp]
+        L.orc_gmres.argtypes = [i64, vp, i64, vp, i64, vp, vp, vp, vp, i32, f64, vp, vp]
         L.orc_gmres.restype = i32
         L.orc_solve_gmres_ir.argtypes = [i64, i64, vp, i64, vp, i64, vp, vp, i64, vp, i64, i32,
-                                         f64, f64, f64, i32, f64, vp, vp, vp, vp]
+                                         f64, f64, f64, i32, f64, i32, vp, vp, vp, vp]
+        L.orc_tri_inverse.argtypes = [i64, vp, i64, i32, vp]
         L.orc_set_num_threads.argtypes = [i32]
         _lib = L
     return _lib
@@ -316,26 +317,42 @@ def lu_solve_ir(mode: int, A32, b, **kw):
     return x, iters, conv, berr, info
 
 
-def gmres(A32, LU, ipiv, rhs, m: int = 50, tau: float = 1e-10):
+def tri_inverse(LU, lower: bool) -> np.ndarray:
+    """Reading R27: L^-1 (lower, unit diagonal) or U^-1 of the packed FP32
+    factors, in FP64, column c by substitution on e_c."""
+    LU = _f32(LU)
+    n = LU.shape[0]
+    X = np.zeros((n, n))
+    lib().orc_tri_inverse(n, _p(LU), n, int(bool(lower)), _p(X))
+    return X
+
+
+def gmres(A32, LU, ipiv, rhs, m: int = 50, tau: float = 1e-10, inverses: bool = False):
     """Left-preconditioned GMRES on M^-1 A d = M^-1 rhs (M from the FP32
-    factors, FP64 arithmetic), zero first guess.  Returns d, the number of
-    Arnoldi steps k and the residual estimates |g_1| .. |g_k|."""
+    factors, FP64 arithmetic), zero first guess; M^-1 by substitution, or
+    through the explicit inverses when ``inverses`` (R27).  Returns d, the
+    number of Arnoldi steps k and the residual estimates |g_1| .. |g_k|."""
     A32 = _f32(A32)
     LU = _f32(LU)
     n = A32.shape[0]
     rhs = np.ascontiguousarray(rhs, dtype=np.float64).reshape(n)
     d = np.zeros(n)
     hist = np.zeros(max(m, 1))
+    XL = tri_inverse(LU, True) if inverses else None
+    XU = tri_inverse(LU, False) if inverses else None
     k = lib().orc_gmres(n, _p(A32), n, _p(LU), n, _p(np.ascontiguousarray(ipiv, np.int32)),
+                        _p(XL) if inverses else None, _p(XU) if inverses else None,
                         _p(rhs), int(m), float(tau), _p(d), _p(hist))
     return d, int(k), hist[:k].copy()
 
 
 def solve_gmres_ir(A32, LU, ipiv, b, max_iter: int = 50, tol: float = 2.0**-53, tol_b=None,
-                   stall: float = 0.5, m: int = 50, tau: float = 1e-10):
+                   stall: float = 0.5, m: int = 50, tau: float = 1e-10, inverses: bool = False):
     """Refinement whose corrections come from GMRES(m) preconditioned by the
-    FP32 factors (reading R18); stop rules as ``solve_ir``.  Returns x,
-    refinement steps, Arnoldi steps, converged flags and backward errors."""
+    FP32 factors (reading R18; through their explicit FP64 inverses inside
+    GMRES when ``inverses``, reading R27); stop rules as ``solve_ir``.
+    Returns x, refinement steps, Arnoldi steps, converged flags and backward
+    errors."""
     A32 = _f32(A32)
     LU = _f32(LU)
     n = A32.shape[0]
@@ -353,5 +370,6 @@ def solve_gmres_ir(A32, LU, ipiv, b, max_iter: int = 50, tol: float = 2.0**-53, 
     lib().orc_solve_gmres_ir(n, nrhs, _p(A32), n, _p(LU), n,
                              _p(np.ascontiguousarray(ipiv, np.int32)), _p(b), nrhs, _p(x), nrhs,
                              int(max_iter), float(tol), float(tol_b), float(stall), int(m),
-                             float(tau), _p(iters), _p(inner), _p(conv), _p(berr))
+                             float(tau), int(bool(inverses)), _p(iters), _p(inner), _p(conv),
+                             _p(berr))
     return x, iters, inner, conv, berr

@@ -47,6 +47,14 @@
  *  R18 "GMRES with the LU as preconditioner" (Sec. III remark, Sec. IV-B):
  *     left-preconditioned GMRES in FP64 solves each refinement step's
  *     correction equation; restarts recompute r = b - A x in FP64.
+ *  R27 the preconditioner of R18 applied through explicit inverses: the
+ *     paper fixes M = P^T L U (the low-precision factors) and FP64 for
+ *     GMRES, not how M^-1 v is evaluated.  With the inverses X_L = L^-1 and
+ *     X_U = U^-1 of the FP32 factors formed once in FP64 (column c by
+ *     substitution on the unit vector e_c), M^-1 v = X_U (X_L (P v)), two
+ *     matrix-vector products; this is the same operator up to FP64
+ *     rounding.  orc_gmres takes the inverses as an option; the starting
+ *     x0 = M^-1 b keeps the substitution.
  */
 #include <math.h>
 #include <stdint.h>
@@ -721,6 +729,53 @@ static void lu32_solve64(int64_t n, const float* LU, int64_t lda, const int32_t*
   }
 }
 
+/* R27: X = L^-1 (lower != 0: the unit lower factor) or X = U^-1 (the      */
+/* upper factor) of the packed FP32 factors LU, FP64, n x n row-major with */
+/* zeros outside the triangle.  Column c solves T x = e_c by substitution: */
+/* forward x_i = [i == c] - sum_{l < i} L_il x_l, backward                 */
+/* x_i = ([i == c] - sum_{l > i} U_il x_l) / U_ii, l in increasing order.   */
+void orc_tri_inverse(int64_t n, const float* LU, int64_t lda, int lower, double* X) {
+  double* x = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t c = 0; c < n; ++c) {
+    if (lower) {
+      for (int64_t i = 0; i < n; ++i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int64_t l = 0; l < i; ++l) s -= (double)LU[i * lda + l] * x[l];
+        x[i] = s;
+      }
+    } else {
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int64_t l = i + 1; l < n; ++l) s -= (double)LU[i * lda + l] * x[l];
+        x[i] = s / (double)LU[i * lda + i];
+      }
+    }
+    for (int64_t i = 0; i < n; ++i) X[i * n + c] = x[i];
+  }
+  free(x);
+}
+
+/* M^-1 v through the inverses (R27): v <- X_U (X_L (P v)) */
+static void inv_solve64(int64_t n, const double* XL, const double* XU, const int32_t* ipiv,
+                        double* v) {
+  double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = ipiv[j];
+    if (p != j) { double u = v[j]; v[j] = v[p]; v[p] = u; }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t l = 0; l <= i; ++l) s += XL[i * n + l] * v[l];
+    t[i] = s;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t l = i; l < n; ++l) s += XU[i * n + l] * t[l];
+    v[i] = s;
+  }
+  free(t);
+}
+
 void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const float* LU,
                   int64_t ldlu, const int32_t* ipiv, const double* b, int64_t ldb,
                   double* x, int64_t ldx, int max_iter, double tol, double tol_b, double stall,
@@ -798,12 +853,14 @@ void orc_solve_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const 
 /* ------------------------------------------------------------------ */
 
 /* d = (M^-1 A)^-1 M^-1 rhs approximately; returns k, the Arnoldi steps    */
+/* taken.  M^-1 by substitution with the factors, or through the explicit  */
+/* inverses XL, XU when XL != NULL (R27).                                   */
 /* taken.  Stops when the residual estimate |g_k| <= tau * beta, after m  */
 /* steps, or at breakdown (h_{k+1,k} = 0: the Krylov space is invariant   */
 /* and the solution in it exact).  hist[j] = |g_{j+1}| if hist != NULL.   */
 int orc_gmres(int64_t n, const float* A32, int64_t lda, const float* LU, int64_t ldlu,
-              const int32_t* ipiv, const double* rhs, int m, double tau, double* d,
-              double* hist) {
+              const int32_t* ipiv, const double* XL, const double* XU, const double* rhs, int m,
+              double tau, double* d, double* hist) {
   double* V = (double*)calloc((size_t)(m + 1) * (size_t)n, sizeof(double));
   double* H = (double*)calloc((size_t)(m + 1) * (size_t)m, sizeof(double)); /* H[i*m+j] */
   double* cs = (double*)calloc((size_t)m + 1, sizeof(double));
@@ -813,7 +870,7 @@ int orc_gmres(int64_t n, const float* A32, int64_t lda, const float* LU, int64_t
   for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
   /* r0 = M^-1 rhs, beta = |r0|_2, v0 = r0 / beta */
   for (int64_t i = 0; i < n; ++i) w[i] = rhs[i];
-  lu32_solve64(n, LU, ldlu, ipiv, w);
+  if (XL) inv_solve64(n, XL, XU, ipiv, w); else lu32_solve64(n, LU, ldlu, ipiv, w);
   double beta = 0.0;
   for (int64_t i = 0; i < n; ++i) beta += w[i] * w[i];
   beta = sqrt(beta);
@@ -829,7 +886,7 @@ int orc_gmres(int64_t n, const float* A32, int64_t lda, const float* LU, int64_t
         for (int64_t l = 0; l < n; ++l) s += (double)A32[i * lda + l] * vj[l];
         w[i] = s;
       }
-      lu32_solve64(n, LU, ldlu, ipiv, w);
+      if (XL) inv_solve64(n, XL, XU, ipiv, w); else lu32_solve64(n, LU, ldlu, ipiv, w);
       /* modified Gram-Schmidt against v_0 .. v_j */
       for (int i = 0; i <= j; ++i) {
         const double* vi = V + (size_t)i * (size_t)n;
@@ -887,8 +944,15 @@ int orc_gmres(int64_t n, const float* A32, int64_t lda, const float* LU, int64_t
 void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, const float* LU,
                         int64_t ldlu, const int32_t* ipiv, const double* b, int64_t ldb,
                         double* x, int64_t ldx, int max_iter, double tol, double tol_b,
-                        double stall, int m, double tau, int32_t* iters, int32_t* inner,
-                        int32_t* conv, double* berr_out) {
+                        double stall, int m, double tau, int explicit_inv, int32_t* iters,
+                        int32_t* inner, int32_t* conv, double* berr_out) {
+  double *XL = NULL, *XU = NULL;
+  if (explicit_inv) { /* R27: the GMRES preconditioner through the inverses */
+    XL = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
+    XU = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
+    orc_tri_inverse(n, LU, ldlu, 1, XL);
+    orc_tri_inverse(n, LU, ldlu, 0, XU);
+  }
   double anorm = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
@@ -916,7 +980,7 @@ void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, 
         for (int64_t l = 0; l < n; ++l) s -= (double)A32[i * lda + l] * xv[l];
         r[i] = s;
       }
-      kin += orc_gmres(n, A32, lda, LU, ldlu, ipiv, r, m, tau, d, NULL);
+      kin += orc_gmres(n, A32, lda, LU, ldlu, ipiv, XL, XU, r, m, tau, d, NULL);
       double dn = 0.0, xn = 0.0;
       int bad = 0; /* a NaN or Inf entry: the max below would skip a NaN */
       for (int64_t i = 0; i < n; ++i) {
@@ -949,4 +1013,6 @@ void orc_solve_gmres_ir(int64_t n, int64_t nrhs, const float* A32, int64_t lda, 
     if (berr_out) berr_out[c] = berr;
     free(xv); free(r); free(d);
   }
+  free(XL);
+  free(XU);
 }

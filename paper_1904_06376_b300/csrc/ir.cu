@@ -19,9 +19,10 @@
 // Triangular solves: row blocks of 64 whose diagonal blocks are inverted once
 // per factorisation (FP64); one launch a triangle, CTAs taking row blocks from
 // an atomic ticket in solve order and publishing their results by value
-// (ir_trsv_kernel).  In a GMRES phase, which solves hundreds of times with
-// one set of factors, the inverse is folded into the factor blocks once and
-// each row block is split over four CTAs (ir_trsv_h_kernel).
+// (ir_trsv_kernel).  In a GMRES phase, which applies M^-1 thousands of times
+// with one set of factors, L^-1 and U^-1 are formed once in FP64 and each
+// application is a row gather and two triangular matrix-vector products
+// (ir_xmv_kernel), with no dependent chain of row blocks.
 // GMRES-IR (Sec. III remark, Sec. IV-B): when plain refinement and the
 // escalations stall, each refinement step solves its correction equation by
 // left-preconditioned GMRES in FP64 (gm_* kernels, gmres_cycle).
@@ -474,152 +475,169 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   }
 }
 
-// ------------------------------------------------------- row-sliced solve
-// For the many solves of a GMRES phase with one set of factors, the block
-// inverse is folded into the factor once: H[b][s] = Dinv_b F[b, k_s] for
-// every block b and its s-th predecessor k_s in solve order (FP64, blocks of
-// block b stored consecutively, block b at step st starting at block
-// st (st - 1) / 2).  Then y_b = Dinv_b v_b - sum_s H[b][s] y_{k_s} separates
-// by rows, and each block's rows are split over TRSV_S CTAs: the 64 x 64
-// FP64 product that follows each arrival, bounded by one SM's FP64 rate
-// (about 1.5 us), becomes TRSV_S products of 16 rows.
-constexpr int TRSV_S = 4;
-constexpr int TRSV_SR = TB / TRSV_S;  // rows a slice
+// ------------------------------------------------------- explicit inverses
+// For the many preconditioner applications of a GMRES phase, the inverses
+// of the FP32 factors are formed once per factorisation in FP64: X = L^-1
+// (unit lower) and X = U^-1 (upper), so each application of M^-1 = U^-1 L^-1
+// P is a row gather and two triangular matrix-vector products, with no
+// dependent chain of row blocks.  X is kept in 64 x 64 blocks in solve
+// order: block (st, sk), sk <= st, holds rows of natural block b(st) and
+// columns of natural block b(sk) (b(s) = s for L, nblk - 1 - s for U), at
+// offset (st (st + 1) / 2 + sk) TB^2, row-major.  In those coordinates both
+// triangles follow one recurrence:
+//   X[st][st] = Dinv_b(st)  (the diagonal block's inverse),
+//   X[st][sk] = -Dinv_b(st) sum_{ss = sk}^{st - 1} F[b(st)][b(ss)] X[ss][sk].
+// It runs right-looking by the distance t = st - sk: once X[sk + t][sk] is
+// final, its products F[b(st)][b(sk + t)] X[sk + t][sk] are added into the
+// accumulators X[st][sk] of every st > sk + t (one launch, a CTA a block),
+// in the order of ss (deterministic); then X[sk + t + 1][sk] = -Dinv times
+// its accumulator (one launch).  n^3 / 6 FP64 FMAs a triangle.
+__host__ __device__ __forceinline__ int64_t xblk(int st, int sk) {
+  return (static_cast<int64_t>(st) * (st + 1) / 2 + sk) * TB * TB;
+}
+constexpr int XB_THREADS = 256;
+constexpr size_t kXbSmem = 2 * sizeof(double) * TB * (TB + 1);  // two padded FP64 tiles
 
+// out (+)= sign * A B for 64 x 64 FP64 tiles in shared memory (rows TB + 1
+// apart); thread (ty, tx) of 16 x 16 owns rows ty + 16 r and columns
+// tx + 16 c; l in order (deterministic).
+__device__ __forceinline__ void xb_product(const double (*As)[TB + 1], const double (*Bs)[TB + 1],
+                                           double (&acc)[4][4]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int l = 0; l < TB; ++l) {
+    double a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = As[ty + 16 * r][l];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+  }
+}
+
+// X[st][st] = Dinv_b(st); X[st][sk] = 0 below it (the accumulators).  A CTA a block.
 template <bool LOWER>
-__global__ void __launch_bounds__(256)
-    ir_hmat_kernel(const float* __restrict__ F, int64_t ldf, int n,
-                   const double* __restrict__ Dinv, double* __restrict__ H) {
-  __shared__ double Ds[TB][TB];
-  __shared__ float Fs[TB][TB];
-  const int nblk = (n + TB - 1) / TB;
-  const int st = blockIdx.x, sp = blockIdx.y;  // step of the block, index of the predecessor
-  if (sp >= st || st >= nblk) return;
+__global__ void __launch_bounds__(XB_THREADS)
+    ir_xinit_kernel(const double* __restrict__ Dinv, int nblk, double* __restrict__ X) {
+  const int64_t e0 = static_cast<int64_t>(blockIdx.x) * TB * TB;
+  int st = 0;
+  while (xblk(st + 1, 0) <= e0) ++st;
+  const int sk = static_cast<int>(e0 / (TB * TB) - static_cast<int64_t>(st) * (st + 1) / 2);
   const int b = LOWER ? st : nblk - 1 - st;
-  const int k = LOWER ? sp : nblk - 1 - sp;
-  const int b0 = b * TB, bs = min(TB, n - b0), k0 = k * TB, ks = min(TB, n - k0);
   const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += 256) {
-    const int i = e / TB, l = e % TB;
-    Ds[i][l] = D[e];
-    Fs[i][l] = (i < bs && l < ks) ? F[static_cast<int64_t>(b0 + i) * ldf + k0 + l] : 0.0f;
-  }
-  __syncthreads();
-  double* h = H + (static_cast<int64_t>(st) * (st - 1) / 2 + sp) * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += 256) {
-    const int i = e / TB, j = e % TB;
-    double s0 = 0.0, s1 = 0.0;
-    for (int l = 0; l < TB; l += 2) {
-      s0 = fma(Ds[i][l], static_cast<double>(Fs[l][j]), s0);
-      s1 = fma(Ds[i][l + 1], static_cast<double>(Fs[l + 1][j]), s1);
-    }
-    h[e] = s0 + s1;
-  }
+  double* out = X + e0;
+  for (int e = threadIdx.x; e < TB * TB; e += XB_THREADS) out[e] = sk == st ? D[e] : 0.0;
 }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem)
-               : "memory");
-}
-
-// out[i][c] (+)= sign * sum_l T[i][l] x[l][c] for the TRSV_SR rows of a slice;
-// Q threads per output (8, 4, 2, 2 for cg = 1 .. 4) take l = q, q + Q, ...
-// and add their partial sums by shuffle (a fixed order: deterministic).  On
-// B300 the shuffle-adds run on the FP64 pipe like the FMAs (2 a clock per
-// SM), so fewer threads per output with longer chains finish sooner: at
-// cg = 1, 8 threads per output leave 4 warps of 8 FMAs + 3 adds.
-__device__ __forceinline__ void slice_product(const double* Tm, const double (*x)[TRSV_CG + 1],
-                                              double (*out)[TRSV_CG + 1], int cg, bool sub) {
-  const int t = threadIdx.x;
-  const int Q = cg == 1 ? 8 : (cg == 2 ? 4 : 2);
-  const int o = t / Q, q = t - o * Q;
-  const bool act = o < TRSV_SR * cg;
-  const int i = act ? o / cg : 0, c = act ? o - i * cg : 0;
-  double sum = 0.0;
-  if (act) {
-    const double* row = Tm + i * (TB + 1);
-    for (int l = q; l < TB; l += Q) sum = fma(row[l], x[l][c], sum);
-  }
-  for (int off = Q / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
-  if (act && q == 0) out[i][c] = sub ? out[i][c] - sum : sum;
-}
-
-// One launch a triangle, CTAs on (row block, column group, slice) tickets in
-// solve order, results published by value as in ir_trsv_kernel (y all
-// sentinel at launch).  v is only read (several slices read each row); with
-// dout the rows are also stored there (plain stores: nothing polls dout).
+// Distance t: X[st][sk] += F[b(st)][b(ss)] X[ss][sk] with ss = sk + t, for
+// every st > ss.  grid (nblk - t - 1, nblk - t - 1): x = sk, y = st - ss - 1.
 template <bool LOWER>
-__global__ void __launch_bounds__(TRSV_THREADS)
-    ir_trsv_h_kernel(const double* __restrict__ H, const double* __restrict__ Dinv, int n,
-                     const double* __restrict__ v, double* __restrict__ y,
-                     double* __restrict__ dout, int R, int* __restrict__ ticket,
-                     int* __restrict__ err) {
-  __shared__ __align__(16) double Hs[2][TRSV_SR][TB + 1];
-  __shared__ double Ds[TRSV_SR][TB + 1];
-  __shared__ double xs[TB][TRSV_CG + 1];
-  __shared__ double acc[TRSV_SR][TRSV_CG + 1];
-  __shared__ int s_ticket, s_fail;
-  const int t = threadIdx.x;
-  const int nblk = (n + TB - 1) / TB;
-  const int G = (R + TRSV_CG - 1) / TRSV_CG;
-  if (t == 0) {
-    s_ticket = atomicAdd(ticket, 1);
-    s_fail = 0;
+__global__ void __launch_bounds__(XB_THREADS)
+    ir_xupd_kernel(const float* __restrict__ F, int64_t ldf, int n, int nblk, int t,
+                   double* __restrict__ X) {
+  extern __shared__ double xsm[];
+  double (*Fs)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(xsm);
+  double (*Ys)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(xsm + TB * (TB + 1));
+  const int sk = blockIdx.x, ss = sk + t, st = ss + 1 + static_cast<int>(blockIdx.y);
+  if (st >= nblk) return;
+  const int b = LOWER ? st : nblk - 1 - st, bs_ = LOWER ? ss : nblk - 1 - ss;
+  const int r0 = b * TB, c0 = bs_ * TB;
+  const double* Y = X + xblk(ss, sk);
+  for (int e = threadIdx.x; e < TB * TB; e += XB_THREADS) {
+    const int i = e / TB, l = e % TB;
+    Fs[i][l] = (r0 + i < n && c0 + l < n)
+                   ? static_cast<double>(F[static_cast<int64_t>(r0 + i) * ldf + c0 + l])
+                   : 0.0;
+    Ys[i][l] = Y[e];
   }
   __syncthreads();
-  const int step = s_ticket / (G * TRSV_S);
-  const int rem = s_ticket - step * (G * TRSV_S);
-  const int grp = rem / TRSV_S, sl = rem - grp * TRSV_S;
-  const int b = LOWER ? step : nblk - 1 - step;
-  const int b0 = b * TB, bs = min(TB, n - b0);
-  const int r0 = sl * TRSV_SR;
-  const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
-  const double* Hb = H + static_cast<int64_t>(step) * (step - 1) / 2 * TB * TB;
-  // rows r0 .. r0 + 15 of H[b][s] -> Hs[s & 1], asynchronously
-  auto prefetch = [&](int s) {
-    const double* src = Hb + static_cast<int64_t>(s) * TB * TB + r0 * TB;
-    for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) {
-      const int i = e / TB, l = e - i * TB;
-      cp_async8(&Hs[s & 1][i][l], src + i * TB + l);
-    }
-  };
-  if (step > 0) prefetch(0);
-  cp_async_commit();
-  // acc = (Dinv_b v_b) on this slice's rows
-  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB + r0 * TB;
-  for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) Ds[e / TB][e % TB] = D[e];
-  for (int e = t; e < TB * cg; e += TRSV_THREADS) {
-    const int i = e / cg, c = e - i * cg;
-    xs[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
+  double* out = X + xblk(st, sk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = out[(ty + 16 * r) * TB + tx + 16 * c];
+  xb_product(Fs, Ys, acc);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[(ty + 16 * r) * TB + tx + 16 * c] = acc[r][c];
+}
+
+// Distance t >= 1: X[st][st - t] = -Dinv_b(st) X[st][st - t] (the accumulator
+// is complete).  A CTA per st = t + blockIdx.x.
+template <bool LOWER>
+__global__ void __launch_bounds__(XB_THREADS)
+    ir_xfin_kernel(const double* __restrict__ Dinv, int nblk, int t, double* __restrict__ X) {
+  extern __shared__ double xsm[];
+  double (*Ds)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(xsm);
+  double (*As)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(xsm + TB * (TB + 1));
+  const int st = t + static_cast<int>(blockIdx.x), sk = st - t;
+  const int b = LOWER ? st : nblk - 1 - st;
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  double* io = X + xblk(st, sk);
+  for (int e = threadIdx.x; e < TB * TB; e += XB_THREADS) {
+    Ds[e / TB][e % TB] = D[e];
+    As[e / TB][e % TB] = io[e];
   }
   __syncthreads();
-  slice_product(&Ds[0][0], xs, acc, cg, false);
-  __syncthreads();
-  volatile int* fail = &s_fail;
-  for (int s = 0; s < step; ++s) {
-    if (s + 1 < step) prefetch(s + 1);
-    cp_async_commit();
-    const int k = LOWER ? s : nblk - 1 - s;
-    const int k0 = k * TB, ks = min(TB, n - k0);
-    {  // y_k into xs, one value a thread: every value is polled at once
-      for (int e = t; e < TB * cg; e += TRSV_THREADS) {
-        const int i = e / cg, c = e - i * cg;
-        double val = 0.0;
-        if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
-        xs[i][c] = val;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  xb_product(Ds, As, acc);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) io[(ty + 16 * r) * TB + tx + 16 * c] = -acc[r][c];
+}
+
+// y = X v for columns c0 .. c0 + CG of v, y (row-major, ld R); a warp per
+// pair of rows i and n - 1 - i, so every warp reads about the same number of
+// blocks (a row of natural block b reads b + 1 blocks of L^-1, nblk - b of
+// U^-1).  Each lane adds its elements in block order, the lanes' sums meet
+// by an xor tree: a fixed order.
+template <bool LOWER, int CG>
+__global__ void __launch_bounds__(256)
+    ir_xmv_kernel(const double* __restrict__ X, int n, int nblk, const double* __restrict__ v,
+                  double* __restrict__ y, int R, int c0) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int half = (n + 1) / 2;
+  if (w >= half) return;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int i = pass == 0 ? w : n - 1 - w;
+    if (pass == 1 && i == w) break;  // the middle row of an odd n
+    const int b = i / TB, r = i - b * TB;
+    const int st = LOWER ? b : nblk - 1 - b;
+    double acc[CG];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) acc[c] = 0.0;
+    for (int sk = 0; sk <= st; ++sk) {
+      const int k = LOWER ? sk : nblk - 1 - sk;
+      const double* row = X + xblk(st, sk) + static_cast<int64_t>(r) * TB;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = lane + 32 * h, col = k * TB + l;
+        if (col < n) {
+          const double a = row[l];
+#pragma unroll
+          for (int c = 0; c < CG; ++c)
+            acc[c] = fma(a, v[static_cast<int64_t>(col) * R + c0 + c], acc[c]);
+        }
       }
     }
-    cp_async_wait1();  // this thread's copies of H[b][s] have landed
-    __syncthreads();
-    slice_product(&Hs[s & 1][0][0], xs, acc, cg, true);
-    __syncthreads();
-  }
-  for (int e = t; e < TRSV_SR * cg; e += TRSV_THREADS) {
-    const int i = e / cg, c = e - i * cg;
-    if (r0 + i >= bs) continue;
-    const int64_t at = static_cast<int64_t>(b0 + r0 + i) * R + c0 + c;
-    st_relaxed_gpu(y + at, acc[i][c]);
-    if (dout) dout[at] = acc[i][c];
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xFFFFFFFFu, acc[c], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < CG; ++c) y[static_cast<int64_t>(i) * R + c0 + c] = acc[c];
+    }
   }
 }
 
@@ -1298,9 +1316,8 @@ struct IrWs {
   double* Lg;     // chain matrices G_b = Linv_b L[b, b-1] and Uinv_b U[b, b+1]
   double* Ug;
   double* y1;     // forward-solve result (sentinel-filled between solves)
-  double* y2;     // backward-solve result of the row-sliced solve (GMRES only)
-  double* Hl;     // inverse-scaled blocks Linv_b L[b, k] (GMRES only), per block in solve order
-  double* Hu;     // the same for U
+  double* XL;     // L^-1 and U^-1 in FP64 (GMRES only), 64 x 64 blocks in solve order
+  double* XU;
   int32_t* tsync; // triangular-solve tickets, one per triangle
   int32_t* live;  // asynchronous solve: columns still refining (0: later steps skip)
   IraState* ira;  // asynchronous solve: per-column stop state
@@ -1356,10 +1373,9 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.gm_m = gm_m;
   if (gm_m > 0) {
     const int64_t R = nrhs, m = gm_m;
-    const int64_t hblocks = nblk * (nblk - 1) / 2;
-    w.y2 = reinterpret_cast<double*>(take(sizeof(double) * n * R));
-    w.Hl = reinterpret_cast<double*>(take(sizeof(double) * hblocks * TB * TB));
-    w.Hu = reinterpret_cast<double*>(take(sizeof(double) * hblocks * TB * TB));
+    const int64_t xblocks = nblk * (nblk + 1) / 2;
+    w.XL = reinterpret_cast<double*>(take(sizeof(double) * xblocks * TB * TB));
+    w.XU = reinterpret_cast<double*>(take(sizeof(double) * xblocks * TB * TB));
     int64_t rows = std::max<int64_t>(1, GM_ELEMS / R);
     int64_t nch = ceil_div(n, rows);
     if (nch > GM_MAXCH) {
@@ -1385,14 +1401,26 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   return w;
 }
 
+// y = X v (all nrhs columns) with X an explicit inverse (ir_xmv_kernel)
+template <bool LOWER>
+void inverse_mv(const double* X, int64_t n, int nrhs, const double* v, double* y, cudaStream_t s) {
+  const int N = static_cast<int>(n), nblk = static_cast<int>(ceil_div(n, TB));
+  const unsigned grid = static_cast<unsigned>(ceil_div((n + 1) / 2, 8));  // 8 warps a CTA
+  int c0 = 0;
+  for (; c0 + 4 <= nrhs; c0 += 4)
+    ir_xmv_kernel<LOWER, 4><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
+  for (; c0 + 2 <= nrhs; c0 += 2)
+    ir_xmv_kernel<LOWER, 2><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
+  for (; c0 < nrhs; ++c0) ir_xmv_kernel<LOWER, 1><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
+}
+
 // d <- U^-1 L^-1 P r (all columns; r is left as it is).  d = P r (gathered),
 // the forward solve reads d and writes y1, the backward solve reads y1 and
 // writes d.  The gather also fills y1 with the sentinel and zeroes both
 // tickets; the forward solve leaves d all sentinel for the backward one.
-// use_h (the inverse-scaled blocks Hl, Hu computed for these factors): the
-// row-sliced solves instead; the backward one publishes through y2 (also
-// sentinel-filled by the gather) and writes its result to d.
-bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_h = false,
+// use_inv (the explicit inverses XL, XU formed for these factors): d = P r,
+// y1 = L^-1 d, d = U^-1 y1 by two matrix-vector products instead.
+bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_inv = false,
                       const int32_t* gate = nullptr) {
   static const bool attr_ok = [] {
     return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1405,22 +1433,50 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
   if (!err) return BFX_ECUDA;
   const int N = static_cast<int>(n);
   const int nblk = static_cast<int>(ceil_div(n, TB));
+  if (use_inv) {
+    ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
+                                                          nullptr, nullptr, nullptr, gate);
+    inverse_mv<true>(w.XL, n, nrhs, w.d, w.y1, s);
+    inverse_mv<false>(w.XU, n, nrhs, w.y1, w.d, s);
+    return last_launch_status();
+  }
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
   const unsigned grid = static_cast<unsigned>(nblk * G);
   ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                        w.y1, use_h ? w.y2 : nullptr, w.tsync, gate);
-  if (use_h) {
-    const unsigned hgrid = static_cast<unsigned>(nblk * G * TRSV_S);
-    ir_trsv_h_kernel<true><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hl, w.Linv, N, w.d, w.y1, nullptr,
-                                                          nrhs, w.tsync, err);
-    ir_trsv_h_kernel<false><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hu, w.Uinv, N, w.y1, w.y2, w.d,
-                                                           nrhs, w.tsync + 1, err);
-    return last_launch_status();
-  }
+                                                        w.y1, nullptr, w.tsync, gate);
   ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.y1,
                                                              nrhs, w.tsync, err, gate);
   ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Uinv, w.Ug, w.y1, w.d,
                                                               nrhs, w.tsync + 1, err, gate);
+  return last_launch_status();
+}
+
+// L^-1 and U^-1 of the FP32 factors in w.LU (FP64, into w.XL and w.XU), from
+// the diagonal blocks' inverses w.Linv, w.Uinv; once per factorisation.
+bfx_status form_inverses(const IrWs& w, int64_t n, cudaStream_t s) {
+  static const bool attr_ok = [] {
+    const int b = static_cast<int>(kXbSmem);
+    return cudaFuncSetAttribute(ir_xupd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(ir_xupd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(ir_xfin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(ir_xfin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b) ==
+               cudaSuccess;
+  }();
+  if (!attr_ok) return BFX_ECUDA;
+  const int N = static_cast<int>(n), nblk = static_cast<int>(ceil_div(n, TB));
+  const unsigned nx = static_cast<unsigned>(nblk * (nblk + 1) / 2);
+  ir_xinit_kernel<true><<<nx, XB_THREADS, 0, s>>>(w.Linv, nblk, w.XL);
+  ir_xinit_kernel<false><<<nx, XB_THREADS, 0, s>>>(w.Uinv, nblk, w.XU);
+  for (int t = 0; t + 1 < nblk; ++t) {
+    const unsigned M = static_cast<unsigned>(nblk - 1 - t);
+    ir_xupd_kernel<true><<<dim3(M, M), XB_THREADS, kXbSmem, s>>>(w.LU, n, N, nblk, t, w.XL);
+    ir_xupd_kernel<false><<<dim3(M, M), XB_THREADS, kXbSmem, s>>>(w.LU, n, N, nblk, t, w.XU);
+    ir_xfin_kernel<true><<<M, XB_THREADS, kXbSmem, s>>>(w.Linv, nblk, t + 1, w.XL);
+    ir_xfin_kernel<false><<<M, XB_THREADS, kXbSmem, s>>>(w.Uinv, nblk, t + 1, w.XU);
+  }
   return last_launch_status();
 }
 
@@ -1491,7 +1547,7 @@ struct GmFlagRing {
 // GM_LAG + 1 steps launched past the last active one find every column
 // inactive and leave the state alone (the kernels skip inactive columns).
 bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, int R, double tau,
-                       cudaStream_t s, int* steps, bool use_h) {
+                       cudaStream_t s, int* steps, bool use_inv) {
   thread_local GmFlagRing ring;
   if (!ring.ready()) return BFX_ECUDA;
   const int N = static_cast<int>(n), m = w.gm_m, nch = w.gm_nchunk;
@@ -1499,7 +1555,7 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
   const int grid = grid_elems(n * R);
   bfx_status st;
   *steps = 0;
-  if ((st = lu_solve64(w, n, R, s, use_h)) != BFX_OK) return st;  // w.d = M^-1 r
+  if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;  // w.d = M^-1 r
   gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
   gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
                                               w.flags, w.kdone);
@@ -1528,7 +1584,7 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     const double* vj = w.V + static_cast<int64_t>(j) * vstride;
     // w.d = M^-1 A v_j
     if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s)) != BFX_OK) return st;
-    if ((st = lu_solve64(w, n, R, s, use_h)) != BFX_OK) return st;
+    if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;
     for (int pass = 0; pass < 2; ++pass) {
       gm_dot_kernel<<<dim3(j + 1, nch), GM_THREADS, 0, s>>>(w.V, vstride, w.d, N, R, w.gm_rows, nch,
                                                             w.part);
@@ -2067,7 +2123,7 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
   ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_b, ldb, n, R, bn);
 
   bfx_mode cur = mode;
-  bool first = true, refactor = true, use_gmres = p.gmres == 2, h_ready = false;
+  bool first = true, refactor = true, use_gmres = p.gmres == 2, x_ready = false;
   bfx_status st = BFX_OK;
   for (;;) {
     if (refactor) {
@@ -2091,7 +2147,7 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
         ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
         ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
       }
-      h_ready = false;
+      x_ready = false;
       const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
       ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
     }
@@ -2126,13 +2182,9 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       if (!any) break;
       if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s)) != BFX_OK) return st;
       if (use_gmres) {
-        if (!h_ready) {  // once per factorisation: the blocks of the row-sliced solve
-          const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
-          if (nblk > 1) {
-            ir_hmat_kernel<true><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Linv, w.Hl);
-            ir_hmat_kernel<false><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Hu);
-          }
-          h_ready = true;
+        if (!x_ready) {  // once per factorisation: the factors' explicit inverses
+          if ((st = form_inverses(w, n, s)) != BFX_OK) return st;
+          x_ready = true;
         }
         int k = 0;
         if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k, true)) != BFX_OK) return st;

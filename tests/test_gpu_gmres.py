@@ -1,8 +1,9 @@
 """GMRES-IR on the device (GMRES remark of Sec. III; Sec. IV-B) against the
 oracle: the first GMRES correction equals the oracle's for the same FP32
 factors (the device's FP32 LU is bit-identical to the oracle's blocked
-mirror of its schedule), and GMRES-IR reaches
-FP64-LU accuracy where plain refinement cannot."""
+mirror of its schedule) with the preconditioner applied through the
+factors' explicit FP64 inverses on both sides (reading R27), and GMRES-IR
+reaches FP64-LU accuracy where plain refinement cannot."""
 import numpy as np
 import pytest
 import torch
@@ -38,7 +39,8 @@ def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
     never met): x = x0 + d with d the k-th GMRES iterate, column by column.
     Equal up to rounding: the device orthogonalises by two classical
     Gram-Schmidt passes, the oracle by modified Gram-Schmidt, and sums in
-    another order, so the tolerance is kappa(A) times FP64 rounding."""
+    another order (the inverses too: blocked on the device, by columns in
+    the oracle), so the tolerance is kappa(A) times FP64 rounding."""
     P = bi.svd_system(n, kappa, 900 + n, nrhs=nrhs)
     A = torch.from_numpy(P.A32).cuda()
     b = torch.from_numpy(P.b).cuda()
@@ -49,7 +51,7 @@ def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
     assert res["gmres_steps"] == 1 and res["arnoldi"] == kk, res
     LU, ipiv, info = orc.lu_mirror(mode, P.A32, nb=64)
     xo, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b, max_iter=1, m=k,
-                                                   tau=0.0)
+                                                   tau=0.0, inverses=True)
     assert np.all(inner == kk)
     x = x.cpu().numpy()
     scale = np.max(np.abs(xo), axis=0)

@@ -28,6 +28,7 @@
 // left-preconditioned GMRES in FP64 (gm_* kernels, gmres_cycle).
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "bfx_internal.cuh"
@@ -42,6 +43,32 @@ namespace {
 
 constexpr int TB = 64;         // triangular-solve row block
 constexpr int MAXR = 16;       // right-hand sides handled per pass
+
+// Programmatic dependent launch for the chain of short kernels of a GMRES
+// step: a kernel launched with launch_pdl may start while its predecessor in
+// the stream finishes; pdl_begin (first statement of every such kernel)
+// waits until the predecessor has completed and its writes are visible,
+// then lets the next kernel start launching.  Launched without the
+// attribute, the wait returns at once.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   // non-negative doubles order like their bit patterns (NaN sorts above Inf)
@@ -118,6 +145,7 @@ __global__ void __launch_bounds__(256)
                        const double* __restrict__ x, int64_t ldx, double* __restrict__ r,
                        int64_t ldr, int c0, double* __restrict__ rn,
                        const int32_t* __restrict__ gate) {
+  pdl_begin();
   if (gate && *gate == 0) return;  // asynchronous solve: every column has stopped
   __shared__ double part[RES_ROWS][RES_WPR][NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -182,6 +210,7 @@ __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
                                  double* __restrict__ d, int64_t ldd, double* __restrict__ fill,
                                  double* __restrict__ fill2, int* __restrict__ tickets,
                                  const int32_t* __restrict__ gate) {
+  pdl_begin();
   if (gate && *gate == 0) return;
   if (tickets && blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
@@ -602,6 +631,7 @@ template <bool LOWER, int CG>
 __global__ void __launch_bounds__(256)
     ir_xmv_kernel(const double* __restrict__ X, int n, int nblk, const double* __restrict__ v,
                   double* __restrict__ y, int R, int c0) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int half = (n + 1) / 2;
@@ -685,6 +715,7 @@ constexpr int GM_MAXCH = 64;    // most chunks a dot product is split into
 __global__ void __launch_bounds__(GM_THREADS)
     gm_dot_kernel(const double* __restrict__ V, int64_t vstride, const double* __restrict__ w,
                   int n, int R, int rows_per_chunk, int nchunk, double* __restrict__ part) {
+  pdl_begin();
   __shared__ double acc[GM_THREADS];
   __shared__ double red[8 * MAXR];
   const int i = blockIdx.x, ch = blockIdx.y, t = threadIdx.x;
@@ -721,6 +752,7 @@ __global__ void __launch_bounds__(GM_THREADS)
 __global__ void gm_reduce_h_kernel(const double* __restrict__ part, int nchunk, int nv, int R,
                                    double* __restrict__ hb, double* __restrict__ H, int m, int j,
                                    int accumulate, const int32_t* __restrict__ act) {
+  pdl_begin();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nv * R) return;
   const int i = e / R, c = e % R;
@@ -738,6 +770,7 @@ __global__ void gm_reduce_h_kernel(const double* __restrict__ part, int nchunk, 
 __global__ void __launch_bounds__(GM_THREADS)
     gm_orth_kernel(const double* __restrict__ V, int64_t vstride, int nv, double* __restrict__ w,
                    int n, int R, const double* __restrict__ hb, const int32_t* __restrict__ act) {
+  pdl_begin();
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
   __syncthreads();
@@ -764,6 +797,7 @@ __global__ void __launch_bounds__(GM_PT)
     gm_orth_part_kernel(const double* __restrict__ V, int64_t vstride, int nv, int n, int R,
                         const double* __restrict__ hb, const int32_t* __restrict__ act,
                         double* __restrict__ part2) {
+  pdl_begin();
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
   __syncthreads();
@@ -781,6 +815,7 @@ __global__ void __launch_bounds__(GM_PT)
 __global__ void __launch_bounds__(GM_THREADS)
     gm_orth_finish_kernel(double* __restrict__ w, int n, int R, const int32_t* __restrict__ act,
                           const double* __restrict__ part2, int nkc) {
+  pdl_begin();
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) a[threadIdx.x] = act[threadIdx.x];
   __syncthreads();
@@ -803,6 +838,7 @@ __global__ void __launch_bounds__(GM_THREADS)
                     const double* __restrict__ part, int nchunk, double* __restrict__ g,
                     double* __restrict__ beta, int m, const int32_t* __restrict__ active,
                     int32_t* __restrict__ act_out, int32_t* __restrict__ kdone) {
+  pdl_begin();
   __shared__ double bs[MAXR];
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) {
@@ -836,6 +872,7 @@ __global__ void __launch_bounds__(GM_THREADS)
     gm_next_kernel(double* __restrict__ V, int64_t vstride, int j, const double* __restrict__ w,
                    int n, int R, const double* __restrict__ part, int nchunk,
                    const int32_t* __restrict__ act_in) {
+  pdl_begin();
   __shared__ double hn[MAXR];
   __shared__ int32_t a[MAXR];
   if (threadIdx.x < R) {
@@ -964,12 +1001,16 @@ __global__ void __launch_bounds__(GIV_THREADS)
                      double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                      double* __restrict__ g, const double* __restrict__ beta, int m, double tau,
                      const int32_t* __restrict__ act_in, int32_t* __restrict__ act_out,
-                     int32_t* __restrict__ kdone) {
+                     int32_t* __restrict__ kdone, int32_t* __restrict__ host_flags) {
+  pdl_begin();
   __shared__ double wA[GIV_THREADS / 32], wB[GIV_THREADS / 32];
   __shared__ double s_p;
   const int c = blockIdx.x, t = threadIdx.x;
   if (!act_in[c]) {
-    if (t == 0) act_out[c] = 0;
+    if (t == 0) {
+      act_out[c] = 0;
+      host_flags[c] = 0;
+    }
     return;
   }
   double* hcol = H + (static_cast<int64_t>(c) * m + j) * (m + 1);  // column j, rows 0..j+1
@@ -994,6 +1035,7 @@ __global__ void __launch_bounds__(GIV_THREADS)
     int keep = 1;
     if (res <= tau * beta[c] || !(hj > 0.0) || j + 1 >= m || !(res == res)) keep = 0;
     act_out[c] = keep;
+    host_flags[c] = keep;  // mapped pinned memory: the host reads it after an event
   }
 }
 
@@ -1408,10 +1450,10 @@ void inverse_mv(const double* X, int64_t n, int nrhs, const double* v, double* y
   const unsigned grid = static_cast<unsigned>(ceil_div((n + 1) / 2, 8));  // 8 warps a CTA
   int c0 = 0;
   for (; c0 + 4 <= nrhs; c0 += 4)
-    ir_xmv_kernel<LOWER, 4><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
+    launch_pdl(ir_xmv_kernel<LOWER, 4>, grid, 256, 0, s, X, N, nblk, v, y, nrhs, c0);
   for (; c0 + 2 <= nrhs; c0 += 2)
-    ir_xmv_kernel<LOWER, 2><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
-  for (; c0 < nrhs; ++c0) ir_xmv_kernel<LOWER, 1><<<grid, 256, 0, s>>>(X, N, nblk, v, y, nrhs, c0);
+    launch_pdl(ir_xmv_kernel<LOWER, 2>, grid, 256, 0, s, X, N, nblk, v, y, nrhs, c0);
+  for (; c0 < nrhs; ++c0) launch_pdl(ir_xmv_kernel<LOWER, 1>, grid, 256, 0, s, X, N, nblk, v, y, nrhs, c0);
 }
 
 // d <- U^-1 L^-1 P r (all columns; r is left as it is).  d = P r (gathered),
@@ -1433,9 +1475,12 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
   if (!err) return BFX_ECUDA;
   const int N = static_cast<int>(n);
   const int nblk = static_cast<int>(ceil_div(n, TB));
-  if (use_inv) {
-    ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                          nullptr, nullptr, nullptr, gate);
+  if (use_inv) {  // launched as dependents of their predecessors (all in a GMRES step)
+    launch_pdl(ir_gather_kernel, dim3(static_cast<unsigned>(grid_elems(n * nrhs))), 256, 0, s,
+               static_cast<const double*>(w.r), static_cast<int64_t>(nrhs),
+               static_cast<const int32_t*>(w.perm), n, nrhs, w.d, static_cast<int64_t>(nrhs),
+               static_cast<double*>(nullptr), static_cast<double*>(nullptr), static_cast<int*>(nullptr),
+               gate);
     inverse_mv<true>(w.XL, n, nrhs, w.d, w.y1, s);
     inverse_mv<false>(w.XU, n, nrhs, w.y1, w.d, s);
     return last_launch_status();
@@ -1480,42 +1525,45 @@ bfx_status form_inverses(const IrWs& w, int64_t n, cudaStream_t s) {
   return last_launch_status();
 }
 
+// pdl: launched as a dependent of its predecessor (inside a GMRES step)
 bfx_status residual(const IrWs& w, const float* A, int64_t lda, int64_t n, int nrhs,
                     const double* b, int64_t ldb, const double* x, int64_t ldx, double* rn,
-                    cudaStream_t s, const int32_t* gate = nullptr) {
+                    cudaStream_t s, const int32_t* gate = nullptr, bool pdl = false) {
   const unsigned blocks = static_cast<unsigned>(ceil_div(n, RES_ROWS));
   const int N = static_cast<int>(n);
+  auto go = [&](auto kernel, int c0) {
+    if (pdl)
+      launch_pdl(kernel, dim3(blocks), 256, 0, s, A, lda, N, b, ldb, x, ldx, w.r,
+                 static_cast<int64_t>(nrhs), c0, rn, gate);
+    else
+      kernel<<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn, gate);
+  };
   int c0 = 0;
-  for (; c0 + 8 <= nrhs; c0 += 8)
-    ir_residual_kernel<8><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
-                                                    gate);
-  for (; c0 + 4 <= nrhs; c0 += 4)
-    ir_residual_kernel<4><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
-                                                    gate);
-  for (; c0 + 2 <= nrhs; c0 += 2)
-    ir_residual_kernel<2><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
-                                                    gate);
-  for (; c0 < nrhs; ++c0)
-    ir_residual_kernel<1><<<blocks, 256, 0, s>>>(A, lda, N, b, ldb, x, ldx, w.r, nrhs, c0, rn,
-                                                    gate);
+  for (; c0 + 8 <= nrhs; c0 += 8) go(ir_residual_kernel<8>, c0);
+  for (; c0 + 4 <= nrhs; c0 += 4) go(ir_residual_kernel<4>, c0);
+  for (; c0 + 2 <= nrhs; c0 += 2) go(ir_residual_kernel<2>, c0);
+  for (; c0 < nrhs; ++c0) go(ir_residual_kernel<1>, c0);
   return last_launch_status();
 }
 
-// Pinned host slots and events through which the GMRES loop reads the
-// Arnoldi-active flags without stalling the stream (one set per host thread
-// and device, released when the thread ends).
+// Pinned, device-mapped host slots and events through which the GMRES loop
+// reads the Arnoldi-active flags without stalling the stream: the Givens
+// kernel writes each step's flags into a slot directly (no copy in the
+// stream), and the host reads the slot after the event recorded behind it
+// (one set per host thread and device, released when the thread ends).
 constexpr int GM_LAG = 2;               // steps launched ahead of the flags read
 constexpr int GM_RING = GM_LAG + 2;
 struct GmFlagRing {
   int dev = -1;
-  int32_t* h = nullptr;  // GM_RING x MAXR
+  int32_t* h = nullptr;   // GM_RING x MAXR
+  int32_t* hd = nullptr;  // the same memory, device address
   cudaEvent_t ev[GM_RING] = {};
   ~GmFlagRing() { release(); }
   void release() {
     if (h) cudaFreeHost(h);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
-    h = nullptr;
+    h = hd = nullptr;
     for (auto& e : ev) e = nullptr;
     dev = -1;
   }
@@ -1524,8 +1572,13 @@ struct GmFlagRing {
     if (cudaGetDevice(&d) != cudaSuccess) return false;
     if (d == dev && h) return true;
     release();
-    if (cudaMallocHost(reinterpret_cast<void**>(&h), sizeof(int32_t) * GM_RING * MAXR) != cudaSuccess) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int32_t) * GM_RING * MAXR,
+                      cudaHostAllocMapped) != cudaSuccess) {
       h = nullptr;
+      return false;
+    }
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&hd), h, 0) != cudaSuccess) {
+      release();
       return false;
     }
     for (auto& e : ev)
@@ -1559,16 +1612,13 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
   gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
   gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
                                               w.flags, w.kdone);
-  // flags after "step -1" (the start) go to ring slot GM_RING - 1
-  auto post = [&](int j, const int32_t* flags) {  // copy the flags after step j
-    const int slot = (j + GM_RING) % GM_RING;
-    if (cudaMemcpyAsync(ring.h + slot * MAXR, flags, sizeof(int32_t) * R, cudaMemcpyDeviceToHost,
+  {  // the flags after the start ("step -1") into ring slot GM_RING - 1, by a copy
+    const int slot = GM_RING - 1;
+    if (cudaMemcpyAsync(ring.h + slot * MAXR, w.flags, sizeof(int32_t) * R, cudaMemcpyDeviceToHost,
                         s) != cudaSuccess ||
         cudaEventRecord(ring.ev[slot], s) != cudaSuccess)
-      return false;
-    return true;
-  };
-  if (!post(-1, w.flags)) return BFX_ECUDA;
+      return BFX_ECUDA;
+  }
   int j = 0;
   for (; j < m; ++j) {
     const int look = j - 1 - GM_LAG;  // the step whose output flags decide (-1: the start)
@@ -1582,29 +1632,46 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     int32_t* ain = w.flags + (j & 1) * R;
     int32_t* aout = w.flags + ((j + 1) & 1) * R;
     const double* vj = w.V + static_cast<int64_t>(j) * vstride;
-    // w.d = M^-1 A v_j
-    if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s)) != BFX_OK) return st;
+    // w.d = M^-1 A v_j; every kernel of the step launched as a dependent of
+    // the one before it (programmatic dependent launch)
+    if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s, nullptr, true)) != BFX_OK)
+      return st;
     if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;
+    const int64_t r64 = R;
+    const unsigned g1 = static_cast<unsigned>(grid);
     for (int pass = 0; pass < 2; ++pass) {
-      gm_dot_kernel<<<dim3(j + 1, nch), GM_THREADS, 0, s>>>(w.V, vstride, w.d, N, R, w.gm_rows, nch,
-                                                            w.part);
-      gm_reduce_h_kernel<<<static_cast<unsigned>(ceil_div((j + 1) * R, 256)), 256, 0, s>>>(
-          w.part, nch, j + 1, R, w.hb, w.H, m, j, pass, ain);
+      launch_pdl(gm_dot_kernel, dim3(static_cast<unsigned>(j + 1), nch), GM_THREADS, 0, s,
+                 static_cast<const double*>(w.V), vstride, static_cast<const double*>(w.d), N, R,
+                 w.gm_rows, nch, w.part);
+      launch_pdl(gm_reduce_h_kernel, dim3(static_cast<unsigned>(ceil_div((j + 1) * r64, 256))), 256, 0,
+                 s, static_cast<const double*>(w.part), nch, j + 1, R, w.hb, w.H, m, j, pass,
+                 static_cast<const int32_t*>(ain));
       if (j + 1 > GM_KC) {
         const int nkc = static_cast<int>(ceil_div(j + 1, GM_KC));
         const unsigned eb = static_cast<unsigned>(ceil_div(n * R, GM_PT));
-        gm_orth_part_kernel<<<dim3(eb, nkc), GM_PT, 0, s>>>(w.V, vstride, j + 1, N, R, w.hb,
-                                                                 ain, w.part2);
-        gm_orth_finish_kernel<<<grid, GM_THREADS, 0, s>>>(w.d, N, R, ain, w.part2, nkc);
+        launch_pdl(gm_orth_part_kernel, dim3(eb, nkc), GM_PT, 0, s, static_cast<const double*>(w.V),
+                   vstride, j + 1, N, R, static_cast<const double*>(w.hb),
+                   static_cast<const int32_t*>(ain), w.part2);
+        launch_pdl(gm_orth_finish_kernel, dim3(g1), GM_THREADS, 0, s, w.d, N, R,
+                   static_cast<const int32_t*>(ain), static_cast<const double*>(w.part2), nkc);
       } else {
-        gm_orth_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j + 1, w.d, N, R, w.hb, ain);
+        launch_pdl(gm_orth_kernel, dim3(g1), GM_THREADS, 0, s, static_cast<const double*>(w.V),
+                   vstride, j + 1, w.d, N, R, static_cast<const double*>(w.hb),
+                   static_cast<const int32_t*>(ain));
       }
     }
-    gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
-    gm_next_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, vstride, j, w.d, N, R, w.part, nch, ain);
-    gm_givens_kernel<<<R, GIV_THREADS, 0, s>>>(j, R, w.part, nch, w.H, w.cs, w.sn, w.g, w.beta, m,
-                                               tau, ain, aout, w.kdone);
-    if (!post(j, aout)) return BFX_ECUDA;
+    launch_pdl(gm_dot_kernel, dim3(1, nch), GM_THREADS, 0, s, static_cast<const double*>(w.d),
+               static_cast<int64_t>(0), static_cast<const double*>(w.d), N, R, w.gm_rows, nch, w.part);
+    launch_pdl(gm_next_kernel, dim3(g1), GM_THREADS, 0, s, w.V, vstride, j,
+               static_cast<const double*>(w.d), N, R, static_cast<const double*>(w.part), nch,
+               static_cast<const int32_t*>(ain));
+    const int slot = (j + GM_RING) % GM_RING;
+    launch_pdl(gm_givens_kernel, dim3(static_cast<unsigned>(R)), GIV_THREADS, 0, s, j, R,
+               static_cast<const double*>(w.part), nch, w.H, w.cs, w.sn, w.g,
+               static_cast<const double*>(w.beta), m, tau, static_cast<const int32_t*>(ain), aout,
+               w.kdone, ring.hd + slot * MAXR);
+    if (cudaGetLastError() != cudaSuccess) return BFX_ECUDA;
+    if (cudaEventRecord(ring.ev[slot], s) != cudaSuccess) return BFX_ECUDA;
   }
   // steps taken: the most over the columns
   std::vector<int32_t> kd(R);

@@ -708,6 +708,7 @@ __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const doub
 constexpr int GM_THREADS = 256;
 constexpr int GM_ELEMS = 1024;  // vector elements one CTA covers in a dot product
 constexpr int GM_MAXCH = 64;    // most chunks a dot product is split into
+constexpr int GM_WHOLE = 64;    // from this many vectors, a Gram-Schmidt dot takes whole vectors
 
 // part[(i * nchunk + ch) * R + c] = sum over the chunk's rows of V_i[r, c] w[r, c].
 // Threads own one column each and step through rows, so a warp reads
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(GM_THREADS)
 // of chunk y (GM_KC of them, in order) for its elements into part2[y], and
 // gm_orth_finish_kernel subtracts the chunk sums from w in chunk order: the
 // work spreads over every SM and the order stays fixed (deterministic).
-constexpr int GM_KC = 32;
+constexpr int GM_KC = 64;
 constexpr int GM_PT = 128;  // threads of a chunk-sum CTA (more CTAs over the elements)
 __global__ void __launch_bounds__(GM_PT)
     gm_orth_part_kernel(const double* __restrict__ V, int64_t vstride, int nv, int n, int R,
@@ -1639,12 +1640,16 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;
     const int64_t r64 = R;
     const unsigned g1 = static_cast<unsigned>(grid);
+    // with many vectors, each CTA of a Gram-Schmidt dot product takes a whole
+    // vector (its fixed costs outweighed the 1024 FMAs of a chunk)
+    const int pch = j + 1 >= GM_WHOLE ? 1 : nch;
+    const int prows = pch == 1 ? N : w.gm_rows;
     for (int pass = 0; pass < 2; ++pass) {
-      launch_pdl(gm_dot_kernel, dim3(static_cast<unsigned>(j + 1), nch), GM_THREADS, 0, s,
+      launch_pdl(gm_dot_kernel, dim3(static_cast<unsigned>(j + 1), pch), GM_THREADS, 0, s,
                  static_cast<const double*>(w.V), vstride, static_cast<const double*>(w.d), N, R,
-                 w.gm_rows, nch, w.part);
+                 prows, pch, w.part);
       launch_pdl(gm_reduce_h_kernel, dim3(static_cast<unsigned>(ceil_div((j + 1) * r64, 256))), 256, 0,
-                 s, static_cast<const double*>(w.part), nch, j + 1, R, w.hb, w.H, m, j, pass,
+                 s, static_cast<const double*>(w.part), pch, j + 1, R, w.hb, w.H, m, j, pass,
                  static_cast<const int32_t*>(ain));
       if (j + 1 > GM_KC) {
         const int nkc = static_cast<int>(ceil_div(j + 1, GM_KC));

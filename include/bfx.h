@@ -316,7 +316,8 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
  * correction is not tested for a stall.  The same stop rules apply otherwise.
  * d_A: n x n FP32 (lda); d_b: n x nrhs FP64 (ldb); d_x: n x nrhs FP64 (ldx,
  * output).  h_params may be NULL (max_iter 50, tol 2^-53, tol_b sqrt(n) 2^-53,
- * stall 0.5, escalate 1, nb 64, gmres 1, gmres_m 0, gmres_tol 1e-10); a
+ * stall 0.5, escalate 1, nb 64, gmres 1, gmres_m 0, gmres_tol 1e-10,
+ * gmres_inverses 1); a
  * zero gmres_m means min(n, BFX_GMRES_MAX_M) (full GMRES up to that size:
  * factors of FP32 precision leave about as many poorly approximated
  * directions as A has singular values below ~2^-24 |A|, and a restart before
@@ -330,10 +331,16 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
  * errors.  Workspace: bfx_solve_ir_workspace_size(mode, n, nrhs, h_params)
  * bytes (h_params NULL: the defaults), 256-byte aligned; with gmres != 0 it
  * includes the Krylov basis, (gmres_m + 1) n nrhs doubles, the
- * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles, and the factor
- * blocks scaled by the inverses of their diagonal blocks that the GMRES
- * phase's triangular solves use, about n^2 doubles (both triangles; built
- * once per factorisation when the GMRES phase starts). */
+ * Hessenberg matrices, nrhs (gmres_m + 1) gmres_m doubles, and the prepared
+ * preconditioner, about n^2 doubles (both triangles; built once per
+ * factorisation when the GMRES phase starts).  The preconditioner is the
+ * same operator in both forms, up to FP64 rounding: gmres_inverses = 1 forms
+ * L^-1 and U^-1 of the FP32 factors in FP64 (n^3/3 FP64 FMAs) so that each
+ * application is two matrix-vector products (the fastest single solve when
+ * the GMRES phase runs hundreds of Arnoldi steps or more); gmres_inverses = 0
+ * folds each diagonal block's inverse into the factor blocks (about n^3/64
+ * FMAs) and solves by row blocks in solve order (slower per application,
+ * but the least FP64 work: the choice for many concurrent solves). */
 #define BFX_GMRES_MAX_M 4096
 typedef struct bfx_ir_params {
   int max_iter;
@@ -345,6 +352,8 @@ typedef struct bfx_ir_params {
   int gmres;        /* 0 off, 1 after plain refinement stalls, 2 always */
   int gmres_m;      /* Arnoldi steps per refinement step (0: min(n, BFX_GMRES_MAX_M)) */
   double gmres_tol; /* relative residual reduction ending a GMRES cycle (<= 0: 1e-10) */
+  int gmres_inverses; /* M^-1 in GMRES: 1 explicit FP64 inverses of the factors, 0 row-sliced
+                         block substitution (see below) */
 } bfx_ir_params;
 typedef struct bfx_ir_result {
   int32_t info;             /* first zero pivot (1-based) or 0 */

@@ -304,7 +304,8 @@ GMRES_MAX_M = 4096
 class IrParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("tol_b", ctypes.c_double),
                 ("stall", ctypes.c_double), ("escalate", ctypes.c_int), ("nb", ctypes.c_int),
-                ("gmres", ctypes.c_int), ("gmres_m", ctypes.c_int), ("gmres_tol", ctypes.c_double)]
+                ("gmres", ctypes.c_int), ("gmres_m", ctypes.c_int), ("gmres_tol", ctypes.c_double),
+                ("gmres_inverses", ctypes.c_int)]
 
 
 class IrResult(ctypes.Structure):
@@ -343,12 +344,15 @@ def solve_ir_workspace_size(mode: int, n: int, nrhs: int, params: "IrParams" = N
 def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None, max_iter: int = 50,
              tol: float = 2.0 ** -53, tol_b: float = -1.0, stall: float = 0.5, escalate: bool = True,
              nb: int = 64, gmres: int = 1, gmres_m: int = 0, gmres_tol: float = 1e-10,
-             workspace: torch.Tensor = None, stream=None, raise_on_status: bool = False):
+             gmres_inverses: bool = True, workspace: torch.Tensor = None, stream=None,
+             raise_on_status: bool = False):
     """Solve A x = b (A FP32 n x n, b FP64 n x nrhs) by residual-form refinement.
 
     gmres: 0 plain refinement only; 1 GMRES-IR once plain refinement stalls
     (after any escalation); 2 GMRES-IR from the first correction.  gmres_m:
     Arnoldi steps per refinement step (0: min(n, GMRES_MAX_M)).
+    gmres_inverses: the GMRES preconditioner through explicit FP64 inverses of
+    the factors (True) or by row-sliced block substitution (False).
     Returns (x, result dict, status code).  Synchronous."""
     n = A.shape[0]
     if b.dim() == 1:
@@ -357,7 +361,7 @@ def solve_ir(mode: int, A: torch.Tensor, b: torch.Tensor, x: torch.Tensor = None
     if x is None:
         x = torch.empty((n, nrhs), dtype=torch.float64, device=A.device)
     p = IrParams(max_iter, tol, tol_b, stall, int(bool(escalate)), nb, int(gmres), int(gmres_m),
-                 float(gmres_tol))
+                 float(gmres_tol), int(bool(gmres_inverses)))
     wsb = solve_ir_workspace_size(mode, n, nrhs, p)
     if wsb and (workspace is None or workspace.numel() * workspace.element_size() < wsb):
         workspace = torch.empty(wsb, dtype=torch.uint8, device=A.device)

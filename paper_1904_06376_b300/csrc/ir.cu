@@ -504,6 +504,156 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   }
 }
 
+// ------------------------------------------------------- row-sliced solve
+// For the many solves of a GMRES phase with one set of factors (the
+// substitution form of its preconditioner, GmPrec::kRowSliced), the block
+// inverse is folded into the factor once: H[b][s] = Dinv_b F[b, k_s] for
+// every block b and its s-th predecessor k_s in solve order (FP64, blocks of
+// block b stored consecutively, block b at step st starting at block
+// st (st - 1) / 2).  Then y_b = Dinv_b v_b - sum_s H[b][s] y_{k_s} separates
+// by rows, and each block's rows are split over TRSV_S CTAs: the 64 x 64
+// FP64 product that follows each arrival, bounded by one SM's FP64 rate
+// (about 1.5 us), becomes TRSV_S products of 16 rows.
+constexpr int TRSV_S = 4;
+constexpr int TRSV_SR = TB / TRSV_S;  // rows a slice
+
+template <bool LOWER>
+__global__ void __launch_bounds__(256)
+    ir_hmat_kernel(const float* __restrict__ F, int64_t ldf, int n,
+                   const double* __restrict__ Dinv, double* __restrict__ H) {
+  __shared__ double Ds[TB][TB];
+  __shared__ float Fs[TB][TB];
+  const int nblk = (n + TB - 1) / TB;
+  const int st = blockIdx.x, sp = blockIdx.y;  // step of the block, index of the predecessor
+  if (sp >= st || st >= nblk) return;
+  const int b = LOWER ? st : nblk - 1 - st;
+  const int k = LOWER ? sp : nblk - 1 - sp;
+  const int b0 = b * TB, bs = min(TB, n - b0), k0 = k * TB, ks = min(TB, n - k0);
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, l = e % TB;
+    Ds[i][l] = D[e];
+    Fs[i][l] = (i < bs && l < ks) ? F[static_cast<int64_t>(b0 + i) * ldf + k0 + l] : 0.0f;
+  }
+  __syncthreads();
+  double* h = H + (static_cast<int64_t>(st) * (st - 1) / 2 + sp) * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += 256) {
+    const int i = e / TB, j = e % TB;
+    double s0 = 0.0, s1 = 0.0;
+    for (int l = 0; l < TB; l += 2) {
+      s0 = fma(Ds[i][l], static_cast<double>(Fs[l][j]), s0);
+      s1 = fma(Ds[i][l + 1], static_cast<double>(Fs[l + 1][j]), s1);
+    }
+    h[e] = s0 + s1;
+  }
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
+}
+
+// out[i][c] (+)= sign * sum_l T[i][l] x[l][c] for the TRSV_SR rows of a slice;
+// Q threads per output (8, 4, 2, 2 for cg = 1 .. 4) take l = q, q + Q, ...
+// and add their partial sums by shuffle (a fixed order: deterministic).  On
+// B300 the shuffle-adds run on the FP64 pipe like the FMAs (2 a clock per
+// SM), so fewer threads per output with longer chains finish sooner: at
+// cg = 1, 8 threads per output leave 4 warps of 8 FMAs + 3 adds.
+__device__ __forceinline__ void slice_product(const double* Tm, const double (*x)[TRSV_CG + 1],
+                                              double (*out)[TRSV_CG + 1], int cg, bool sub) {
+  const int t = threadIdx.x;
+  const int Q = cg == 1 ? 8 : (cg == 2 ? 4 : 2);
+  const int o = t / Q, q = t - o * Q;
+  const bool act = o < TRSV_SR * cg;
+  const int i = act ? o / cg : 0, c = act ? o - i * cg : 0;
+  double sum = 0.0;
+  if (act) {
+    const double* row = Tm + i * (TB + 1);
+    for (int l = q; l < TB; l += Q) sum = fma(row[l], x[l][c], sum);
+  }
+  for (int off = Q / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+  if (act && q == 0) out[i][c] = sub ? out[i][c] - sum : sum;
+}
+
+// One launch a triangle, CTAs on (row block, column group, slice) tickets in
+// solve order, results published by value as in ir_trsv_kernel (y all
+// sentinel at launch).  v is only read (several slices read each row); with
+// dout the rows are also stored there (plain stores: nothing polls dout).
+template <bool LOWER>
+__global__ void __launch_bounds__(TRSV_THREADS)
+    ir_trsv_h_kernel(const double* __restrict__ H, const double* __restrict__ Dinv, int n,
+                     const double* __restrict__ v, double* __restrict__ y,
+                     double* __restrict__ dout, int R, int* __restrict__ ticket,
+                     int* __restrict__ err) {
+  __shared__ __align__(16) double Hs[2][TRSV_SR][TB + 1];
+  __shared__ double Ds[TRSV_SR][TB + 1];
+  __shared__ double xs[TB][TRSV_CG + 1];
+  __shared__ double acc[TRSV_SR][TRSV_CG + 1];
+  __shared__ int s_ticket, s_fail;
+  const int t = threadIdx.x;
+  const int nblk = (n + TB - 1) / TB;
+  const int G = (R + TRSV_CG - 1) / TRSV_CG;
+  if (t == 0) {
+    s_ticket = atomicAdd(ticket, 1);
+    s_fail = 0;
+  }
+  __syncthreads();
+  const int step = s_ticket / (G * TRSV_S);
+  const int rem = s_ticket - step * (G * TRSV_S);
+  const int grp = rem / TRSV_S, sl = rem - grp * TRSV_S;
+  const int b = LOWER ? step : nblk - 1 - step;
+  const int b0 = b * TB, bs = min(TB, n - b0);
+  const int r0 = sl * TRSV_SR;
+  const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
+  const double* Hb = H + static_cast<int64_t>(step) * (step - 1) / 2 * TB * TB;
+  // rows r0 .. r0 + 15 of H[b][s] -> Hs[s & 1], asynchronously
+  auto prefetch = [&](int s) {
+    const double* src = Hb + static_cast<int64_t>(s) * TB * TB + r0 * TB;
+    for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) {
+      const int i = e / TB, l = e - i * TB;
+      cp_async8(&Hs[s & 1][i][l], src + i * TB + l);
+    }
+  };
+  if (step > 0) prefetch(0);
+  cp_async_commit();
+  // acc = (Dinv_b v_b) on this slice's rows
+  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB + r0 * TB;
+  for (int e = t; e < TRSV_SR * TB; e += TRSV_THREADS) Ds[e / TB][e % TB] = D[e];
+  for (int e = t; e < TB * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    xs[i][c] = i < bs ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  slice_product(&Ds[0][0], xs, acc, cg, false);
+  __syncthreads();
+  volatile int* fail = &s_fail;
+  for (int s = 0; s < step; ++s) {
+    if (s + 1 < step) prefetch(s + 1);
+    cp_async_commit();
+    const int k = LOWER ? s : nblk - 1 - s;
+    const int k0 = k * TB, ks = min(TB, n - k0);
+    {  // y_k into xs, one value a thread: every value is polled at once
+      for (int e = t; e < TB * cg; e += TRSV_THREADS) {
+        const int i = e / cg, c = e - i * cg;
+        double val = 0.0;
+        if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
+        xs[i][c] = val;
+      }
+    }
+    cp_async_wait1();  // this thread's copies of H[b][s] have landed
+    __syncthreads();
+    slice_product(&Hs[s & 1][0][0], xs, acc, cg, true);
+    __syncthreads();
+  }
+  for (int e = t; e < TRSV_SR * cg; e += TRSV_THREADS) {
+    const int i = e / cg, c = e - i * cg;
+    if (r0 + i >= bs) continue;
+    const int64_t at = static_cast<int64_t>(b0 + r0 + i) * R + c0 + c;
+    st_relaxed_gpu(y + at, acc[i][c]);
+    if (dout) dout[at] = acc[i][c];
+  }
+}
+
 // ------------------------------------------------------- explicit inverses
 // For the many preconditioner applications of a GMRES phase, the inverses
 // of the FP32 factors are formed once per factorisation in FP64: X = L^-1
@@ -1385,6 +1535,9 @@ struct IrWs {
   double* y1;     // forward-solve result (sentinel-filled between solves)
   double* XL;     // L^-1 and U^-1 in FP64 (GMRES only), 64 x 64 blocks in solve order
   double* XU;
+  double* Hl;     // inverse-scaled blocks Linv_b L[b, k] (GMRES only, in place of XL)
+  double* Hu;     // the same for U (in place of XU)
+  double* y2;     // backward-solve result of the row-sliced solve (GMRES only)
   int32_t* tsync; // triangular-solve tickets, one per triangle
   int32_t* live;  // asynchronous solve: columns still refining (0: later steps skip)
   IraState* ira;  // asynchronous solve: per-column stop state
@@ -1440,9 +1593,12 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   w.gm_m = gm_m;
   if (gm_m > 0) {
     const int64_t R = nrhs, m = gm_m;
-    const int64_t xblocks = nblk * (nblk + 1) / 2;
+    const int64_t xblocks = nblk * (nblk + 1) / 2;  // the row-sliced blocks need nblk fewer
     w.XL = reinterpret_cast<double*>(take(sizeof(double) * xblocks * TB * TB));
     w.XU = reinterpret_cast<double*>(take(sizeof(double) * xblocks * TB * TB));
+    w.Hl = w.XL;  // a GMRES phase uses one preconditioner form
+    w.Hu = w.XU;
+    w.y2 = reinterpret_cast<double*>(take(sizeof(double) * n * R));
     int64_t rows = std::max<int64_t>(1, GM_ELEMS / R);
     int64_t nch = ceil_div(n, rows);
     if (nch > GM_MAXCH) {
@@ -1482,14 +1638,21 @@ void inverse_mv(const double* X, int64_t n, int nrhs, const double* v, double* y
     launch_pdl(ir_xmv_kernel<LOWER, 1>, grid, XMV_THREADS, 0, s, X, N, nblk, v, y, nrhs, c0);
 }
 
+// How M^-1 = U^-1 L^-1 P is applied: the chained block solve (every solve
+// outside a GMRES phase), the row-sliced solve with the inverse-scaled
+// blocks Hl, Hu, or the explicit inverses XL, XU (both prepared once per
+// factorisation for a GMRES phase).
+enum class GmPrec { kChain, kRowSliced, kInverse };
+
 // d <- U^-1 L^-1 P r (all columns; r is left as it is).  d = P r (gathered),
 // the forward solve reads d and writes y1, the backward solve reads y1 and
 // writes d.  The gather also fills y1 with the sentinel and zeroes both
 // tickets; the forward solve leaves d all sentinel for the backward one.
-// use_inv (the explicit inverses XL, XU formed for these factors): d = P r,
-// y1 = L^-1 d, d = U^-1 y1 by two matrix-vector products instead.
-bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool use_inv = false,
-                      const int32_t* gate = nullptr) {
+// kRowSliced: the row-sliced solves instead; the backward one publishes
+// through y2 (also sentinel-filled by the gather) and writes its result to d.
+// kInverse: d = P r, y1 = L^-1 d, d = U^-1 y1 by two matrix-vector products.
+bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s,
+                      GmPrec prec = GmPrec::kChain, const int32_t* gate = nullptr) {
   static const bool attr_ok = [] {
     return cudaFuncSetAttribute(ir_trsv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(kTrsvSmem)) == cudaSuccess &&
@@ -1501,7 +1664,7 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
   if (!err) return BFX_ECUDA;
   const int N = static_cast<int>(n);
   const int nblk = static_cast<int>(ceil_div(n, TB));
-  if (use_inv) {  // launched as dependents of their predecessors (all in a GMRES step)
+  if (prec == GmPrec::kInverse) {  // launched as dependents of their predecessors
     launch_pdl(ir_gather_kernel, dim3(static_cast<unsigned>(grid_elems(n * nrhs))), 256, 0, s,
                static_cast<const double*>(w.r), static_cast<int64_t>(nrhs),
                static_cast<const int32_t*>(w.perm), n, nrhs, w.d, static_cast<int64_t>(nrhs),
@@ -1509,6 +1672,17 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s, bool u
                gate);
     inverse_mv<true>(w.XL, n, nrhs, w.d, w.y1, s);
     inverse_mv<false>(w.XU, n, nrhs, w.y1, w.d, s);
+    return last_launch_status();
+  }
+  if (prec == GmPrec::kRowSliced) {
+    const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
+    const unsigned hgrid = static_cast<unsigned>(nblk * G * TRSV_S);
+    ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
+                                                          w.y1, w.y2, w.tsync, gate);
+    ir_trsv_h_kernel<true><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hl, w.Linv, N, w.d, w.y1, nullptr,
+                                                          nrhs, w.tsync, err);
+    ir_trsv_h_kernel<false><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hu, w.Uinv, N, w.y1, w.y2, w.d,
+                                                           nrhs, w.tsync + 1, err);
     return last_launch_status();
   }
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
@@ -1626,7 +1800,7 @@ struct GmFlagRing {
 // GM_LAG + 1 steps launched past the last active one find every column
 // inactive and leave the state alone (the kernels skip inactive columns).
 bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, int R, double tau,
-                       cudaStream_t s, int* steps, bool use_inv) {
+                       cudaStream_t s, int* steps, GmPrec prec) {
   thread_local GmFlagRing ring;
   if (!ring.ready()) return BFX_ECUDA;
   const int N = static_cast<int>(n), m = w.gm_m, nch = w.gm_nchunk;
@@ -1634,7 +1808,7 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
   const int grid = grid_elems(n * R);
   bfx_status st;
   *steps = 0;
-  if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;  // w.d = M^-1 r
+  if ((st = lu_solve64(w, n, R, s, prec)) != BFX_OK) return st;  // w.d = M^-1 r
   gm_dot_kernel<<<dim3(1, nch), GM_THREADS, 0, s>>>(w.d, 0, w.d, N, R, w.gm_rows, nch, w.part);
   gm_start_kernel<<<grid, GM_THREADS, 0, s>>>(w.V, w.d, N, R, w.part, nch, w.g, w.beta, m, w.active,
                                               w.flags, w.kdone);
@@ -1662,7 +1836,7 @@ bfx_status gmres_cycle(const IrWs& w, const float* A, int64_t lda, int64_t n, in
     // the one before it (programmatic dependent launch)
     if ((st = residual(w, A, lda, n, R, nullptr, 0, vj, R, nullptr, s, nullptr, true)) != BFX_OK)
       return st;
-    if ((st = lu_solve64(w, n, R, s, use_inv)) != BFX_OK) return st;
+    if ((st = lu_solve64(w, n, R, s, prec)) != BFX_OK) return st;
     const int64_t r64 = R;
     const unsigned g1 = static_cast<unsigned>(grid);
     // with many vectors, each CTA of a Gram-Schmidt dot product takes a whole
@@ -2152,6 +2326,7 @@ bfx_ir_params ir_defaults() {
   p.gmres = 1;
   p.gmres_m = 0;
   p.gmres_tol = 1e-10;
+  p.gmres_inverses = 1;
   return p;
 }
 
@@ -2163,7 +2338,7 @@ bool ir_resolve(const bfx_ir_params* h, int64_t n, bfx_ir_params* out) {
   if (!(p.gmres_tol > 0.0)) p.gmres_tol = 1e-10;
   if (p.tol_b < 0) p.tol_b = 1.1102230246251565e-16 * std::sqrt(static_cast<double>(n));
   if (p.nb > 128 || p.max_iter < 0 || p.gmres < 0 || p.gmres > 2 || p.gmres_m < 0 ||
-      p.gmres_m > BFX_GMRES_MAX_M)
+      p.gmres_m > BFX_GMRES_MAX_M || p.gmres_inverses < 0 || p.gmres_inverses > 1)
     return false;
   *out = p;
   return true;
@@ -2279,12 +2454,21 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       if (!any) break;
       if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s)) != BFX_OK) return st;
       if (use_gmres) {
-        if (!x_ready) {  // once per factorisation: the factors' explicit inverses
-          if ((st = form_inverses(w, n, s)) != BFX_OK) return st;
+        const GmPrec prec = p.gmres_inverses ? GmPrec::kInverse : GmPrec::kRowSliced;
+        if (!x_ready) {  // once per factorisation: the preconditioner's prepared form
+          if (prec == GmPrec::kInverse) {
+            if ((st = form_inverses(w, n, s)) != BFX_OK) return st;
+          } else {
+            const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
+            if (nblk > 1) {
+              ir_hmat_kernel<true><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Linv, w.Hl);
+              ir_hmat_kernel<false><<<dim3(nblk, nblk), 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Hu);
+            }
+          }
           x_ready = true;
         }
         int k = 0;
-        if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k, true)) != BFX_OK) return st;
+        if ((st = gmres_cycle(w, d_A, lda, n, R, p.gmres_tol, s, &k, prec)) != BFX_OK) return st;
         h_result->gmres_steps += 1;
         h_result->arnoldi += k;
       } else if ((st = lu_solve64(w, n, R, s)) != BFX_OK) {
@@ -2419,7 +2603,7 @@ BFX_API bfx_status bfx_solve_ir_async(bfx_mode mode, int64_t n, int64_t nrhs, co
   if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R, n,
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return BFX_ECUDA;
-  if ((st = lu_solve64(w, n, R, s, false, w.live)) != BFX_OK) return st;
+  if ((st = lu_solve64(w, n, R, s, GmPrec::kChain, w.live)) != BFX_OK) return st;
   ira_copy_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, n, R, w.live);
   ir_colmax_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, n, R, xn);
   ira_x0_kernel<<<cgrid, 256, 0, s>>>(xn, R, w.ira);
@@ -2427,7 +2611,7 @@ BFX_API bfx_status bfx_solve_ir_async(bfx_mode mode, int64_t n, int64_t nrhs, co
   for (int it = 0; it < p.max_iter; ++it) {
     if ((st = residual(w, d_A, lda, n, R, d_b, ldb, d_x, ldx, nullptr, s, w.live)) != BFX_OK)
       return st;
-    if ((st = lu_solve64(w, n, R, s, false, w.live)) != BFX_OK) return st;
+    if ((st = lu_solve64(w, n, R, s, GmPrec::kChain, w.live)) != BFX_OK) return st;
     if (cudaMemsetAsync(dn, 0, sizeof(double) * 2 * R, s) != cudaSuccess) return BFX_ECUDA;
     ir_update_kernel<<<grid_elems(n * R), 256, 0, s>>>(d_x, ldx, w.d, R, n, R, w.active, dn, xn,
                                                        w.live);

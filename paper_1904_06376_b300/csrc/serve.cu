@@ -142,6 +142,9 @@ bfx_ir_params request_params(const bfx_server_config& cfg, int64_t n, int64_t nr
   p.gmres = nrhs <= 16 ? cfg.gmres : 0;  // one Krylov basis per right-hand side, at most 16
   p.gmres_m = static_cast<int>(std::min<int64_t>(n, 1024));
   p.gmres_tol = 1e-10;
+  // many concurrent solves: the preconditioner form with the least FP64 work
+  // (explicit inverses cost n^3/3 FMAs per factorisation and save none)
+  p.gmres_inverses = 0;
   return p;
 }
 

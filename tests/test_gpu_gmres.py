@@ -17,10 +17,14 @@ def _fe(x, P):
     return np.max(np.abs(x - P.x_true)) / np.max(np.abs(P.x_true))
 
 
+@pytest.mark.parametrize("inverses", [True, False])
 @pytest.mark.parametrize("n,nrhs,k", [(5, 1, 3), (96, 1, 8), (200, 3, 12), (333, 16, 5),
                                       (700, 2, 20)])
-def test_first_gmres_step_matches_oracle(bfx, orc, n, nrhs, k):
-    _first_cycle(bfx, orc, n, nrhs, k, 1e5)
+def test_first_gmres_step_matches_oracle(bfx, orc, n, nrhs, k, inverses):
+    """Both forms of the preconditioner: explicit inverses (against the
+    oracle's inverses, reading R27) and the row-sliced block substitution
+    (against the oracle's substitution)."""
+    _first_cycle(bfx, orc, n, nrhs, k, 1e5, inverses=inverses)
 
 
 @pytest.mark.parametrize("n,nrhs,k,kappa", [(300, 1, 200, 1e4), (260, 3, 140, 1e4),
@@ -34,7 +38,7 @@ def test_long_gmres_cycle_matches_oracle(bfx, orc, n, nrhs, k, kappa):
     _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=1)
 
 
-def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
+def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0, inverses=True):
     """gmres = 2, one refinement step of exactly k Arnoldi steps (tolerance
     never met): x = x0 + d with d the k-th GMRES iterate, column by column.
     Equal up to rounding: the device orthogonalises by two classical
@@ -45,13 +49,13 @@ def _first_cycle(bfx, orc, n, nrhs, k, kappa, mode=0):
     A = torch.from_numpy(P.A32).cuda()
     b = torch.from_numpy(P.b).cuda()
     x, res, code = bfx.solve_ir(mode, A, b, max_iter=1, gmres=2, gmres_m=k, gmres_tol=1e-300,
-                                escalate=False)
+                                escalate=False, gmres_inverses=inverses)
     assert code in (0, 6)
     kk = min(k, n)
     assert res["gmres_steps"] == 1 and res["arnoldi"] == kk, res
     LU, ipiv, info = orc.lu_mirror(mode, P.A32, nb=64)
     xo, it, inner, conv, berr = orc.solve_gmres_ir(P.A32, LU, ipiv, P.b, max_iter=1, m=k,
-                                                   tau=0.0, inverses=True)
+                                                   tau=0.0, inverses=inverses)
     assert np.all(inner == kk)
     x = x.cpu().numpy()
     scale = np.max(np.abs(xo), axis=0)

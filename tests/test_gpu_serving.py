@@ -85,7 +85,8 @@ def test_many_concurrent_requests_same_as_alone(bfx):
 def test_mixed_requests_same_as_alone_x6_gmres(bfx, orc):
     """bench.py's serving configuration: bf16x6 factors, escalation, GMRES-IR
     for what plain refinement cannot finish, the Krylov length capped at
-    min(n, 1024).  Requests of kappa up to 1e10 go through GMRES-IR; each
+    min(n, 1024), the preconditioner by row-sliced block substitution (the
+    server's form).  Requests of kappa up to 1e10 go through GMRES-IR; each
     result equals the same request solved alone (same kernels, same order),
     bit for bit, with the same refinement and Arnoldi counts, and lies within
     10x of the oracle's FP64 LU in forward error."""
@@ -104,7 +105,8 @@ def test_mixed_requests_same_as_alone_x6_gmres(bfx, orc):
     for P, (x, res) in zip(reqs, out):
         assert res["status"] == 0 and res["converged"] == 1, res
         xa, ra, code = bfx.solve_ir(6, torch.from_numpy(P.A32).cuda(), torch.from_numpy(P.b).cuda(),
-                                    escalate=True, nb=64, gmres=1, gmres_m=min(P.n, 1024))
+                                    escalate=True, nb=64, gmres=1, gmres_m=min(P.n, 1024),
+                                    gmres_inverses=False)
         assert code == 0
         assert np.array_equal(x, xa.cpu().numpy())
         for k in ("iters", "gmres_steps", "arnoldi", "refactorizations", "mode_used"):

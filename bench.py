@@ -399,13 +399,17 @@ def bench_lu_accuracy(bfx, bi, dev):
     """Sec. IV-A's LU figure on the device: mean element error of the bf16x6
     LU over that of the FP32 LU, both against the FP64 LU of the same FP32
     matrix, for [-1, 1] and [-1e10, 1e10] (runs whose pivots differ from the
-    FP64 LU's are left out, as their factors are not comparable)."""
+    FP64 LU's are left out, as their factors are not comparable).  The block
+    width leaves several trailing updates at every size (n / nb >= 8): the
+    two LUs share the FP32 panel and differ in the updates only, so at
+    n = 128 a width of 64 would compare one 64 x 64 update and the panel's
+    noise."""
     import scipy.linalg
     import torch
 
     out = {}
     for scale in (1.0, 1e10):
-        for n, runs in ((128, 20), (512, 10), (1024, 4)):
+        for n, runs, nb in ((128, 20, 16), (512, 10, 64), (1024, 4, 64)):
             ratios = []
             for s in range(runs):
                 A = (bi.uniform_pm1((n, n), 300 + s) * scale).astype(np.float32)
@@ -413,7 +417,7 @@ def bench_lu_accuracy(bfx, bi, dev):
                 res = []
                 for mode in (0, 6):
                     Ad = torch.from_numpy(A.copy()).to(dev)
-                    _, ip, _ = bfx.lu_bf16xN(mode, Ad)
+                    _, ip, _ = bfx.lu_bf16xN(mode, Ad, nb=nb)
                     res.append((Ad.cpu().numpy(), ip.cpu().numpy()[:n]))
                 if not all(np.array_equal(p, p64) for _, p in res):
                     continue
@@ -421,7 +425,8 @@ def bench_lu_accuracy(bfx, bi, dev):
                 e0, e6 = (float(np.mean(np.abs(L - LU64) / den)) for L, _ in res)
                 ratios.append(e6 / e0)
             out[f"[-{scale:g},{scale:g}] n={n}"] = {
-                "runs_compared": len(ratios), "mean_ratio_x6_over_fp32": float(np.mean(ratios)) if ratios else None}
+                "nb": nb, "runs_compared": len(ratios),
+                "mean_ratio_x6_over_fp32": float(np.mean(ratios)) if ratios else None}
     return out
 
 
@@ -483,7 +488,7 @@ def bench_serving(bfx, bi, count, max_inflight=32, mode=6, batch_max_n=0, batche
            "generator": "O(n^2) Householder/permutation construction with exact kappa"}
     # steady state: the same requests with Poisson arrivals at lower rates
     sweep = []
-    for rate in (40, 80, 120, 160, 200):
+    for rate in (40, 80, 120, 160, 200, 240, 280):
         arr = np.cumsum(np.random.default_rng(70 + rate).exponential(1.0 / rate, size=count))
         res, sec, st = _serve_stream(bfx, arr, systems, max_inflight, mode, batch_max_n)
         la = np.array([r[1]["latency_s"] for r in res])

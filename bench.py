@@ -558,8 +558,9 @@ def main():
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        bfx.split(A, npc, out=[Ap[i][:, :k] for i in range(npc)])
-        bfx.split_transpose(B, npc, out=[Bp[i][:, :k] for i in range(npc)])
+        # both operands' pieces in one launch (split of A, transposed split of B)
+        bfx.split_pair(A, B, npc, npc, out_a=[Ap[i][:, :k] for i in range(npc)],
+                       out_b=[Bp[i][:, :k] for i in range(npc)])
         if ev is not None:
             ev[1].record(stream)
         bfx.gemm_presplit(mode, Ap, Bp, k, C)

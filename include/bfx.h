@@ -128,6 +128,19 @@ BFX_API bfx_status bfx_split_transpose(int64_t rows, int64_t cols, const float* 
                                        int npieces, uint16_t* d_hi, uint16_t* d_mid,
                                        uint16_t* d_lo, int64_t ldp, bfx_stream stream);
 
+/* Both operands of a product C = A B in one launch: A (rows_a x cols_a, lda)
+ * split as bfx_split into planes a0..a2 (leading dimension ldpa), B (rows_b x
+ * cols_b, ldb) split as bfx_split_transpose into planes b0..b2 (ldpb).  The
+ * same pieces as the two calls; one kernel when A's rows are contiguous
+ * (lda == ldpa == cols_a, cols_a a multiple of 8, 16-byte aligned) and B's
+ * planes are 16-byte aligned with ldpb a multiple of 8, so the two passes
+ * overlap; otherwise the two kernels in turn.  Errors as bfx_split. */
+BFX_API bfx_status bfx_split_pair(int64_t rows_a, int64_t cols_a, const float* d_a, int64_t lda,
+                                  int npa, uint16_t* d_a0, uint16_t* d_a1, uint16_t* d_a2,
+                                  int64_t ldpa, int64_t rows_b, int64_t cols_b, const float* d_b,
+                                  int64_t ldb, int npb, uint16_t* d_b0, uint16_t* d_b1,
+                                  uint16_t* d_b2, int64_t ldpb, bfx_stream stream);
+
 /* ---------------------------------------------------------------------------
  * GEMM C = alpha * (A B) + beta * C from FP32 A (m x k, lda) and B (k x n, ldb)
  * by the mode's bfloat16 products (Sec. II-D, II-G; Sec. IV-A: a GEMM that
@@ -135,7 +148,9 @@ BFX_API bfx_status bfx_split_transpose(int64_t rows, int64_t cols, const float* 
  * behind the scenes).  The products run on the tcgen05 tensor cores with FP32
  * accumulation in tensor memory; the hi*hi product is accumulated apart from
  * the correction products, which are issued smallest bin first, and the two
- * are added in FP32 in the epilogue.  Then t = alpha * Z and
+ * are added in FP32 in the epilogue (for X6, X8 and X9 with k > 512 the
+ * hi*hi accumulator restarts every 256 of k and its chunk sums are added in
+ * FP32 registers with round-to-nearest adds).  Then t = alpha * Z and
  * C = beta == 0 ? t : fma(beta, C, t) (C is not read when beta == 0).
  * mode BFX_FP32 runs the plain FP32 SIMT GEMM instead (no workspace).
  * Workspace: d_ws of ws_bytes >= bfx_gemm_workspace_size(mode, m, n, k), 256-
@@ -152,7 +167,9 @@ BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t 
  * "can be hidden"): the FP32 tiles of A and B are loaded by TMA and split in
  * registers into the bfloat16 pieces the tensor cores read, so no workspace is
  * needed and no pieces go through global memory.  Same result as
- * bfx_gemm_bf16xN bit for bit (same pieces, same products in the same order).
+ * bfx_gemm_bf16xN bit for bit (same pieces, same products in the same order)
+ * for k <= 512 and for modes X1, X3 and X5; for X6, X8 and X9 beyond k = 512
+ * it keeps one hi*hi accumulator over all of k and meets the same bound.
  * Requirements of the TMA descriptors: lda and ldb multiples of 4, d_A and
  * d_B 16-byte aligned; otherwise BFX_EUNSUPPORTED.  mode must be X1..X9
  * (BFX_EINVAL).  Other errors as bfx_gemm_bf16xN. */

@@ -46,5 +46,6 @@ from ._bfx import (  # noqa: F401
     sgemm_simt,
     split,
     split_transpose,
+    split_pair,
     version,
 )

@@ -56,6 +56,8 @@ def lib() -> ctypes.CDLL:
         "bfx_device_error": (i32, [vp, vp]),
         "bfx_split": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
         "bfx_split_transpose": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
+        "bfx_split_pair": (i32, [i64, i64, vp, i64, i32, vp, vp, vp, i64,
+                                 i64, i64, vp, i64, i32, vp, vp, vp, i64, vp]),
         "bfx_gemm_workspace_size": (sz, [i32, i64, i64, i64]),
         "bfx_gemm_bf16xN": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp, sz, vp]),
         "bfx_gemm_bf16xN_fused": (i32, [i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
@@ -155,6 +157,30 @@ def split_transpose(x: torch.Tensor, npieces: int = 3, out=None, stream=None):
                                      npieces, _ptr(ps[0]), _ptr(ps[1]), _ptr(ps[2]), ldp,
                                      _stream(stream)))
     return out
+
+
+def split_pair(a: torch.Tensor, b: torch.Tensor, npa: int = 3, npb: int = 3, out_a=None, out_b=None,
+               stream=None):
+    """split(a) and split_transpose(b) in one launch (the two operands of a
+    product); returns (pieces of a, pieces of b^T)."""
+    assert a.dtype == torch.float32 and a.is_cuda and b.dtype == torch.float32 and b.is_cuda
+    ra, ca = a.shape
+    rb, cb = b.shape
+    if out_a is None:
+        out_a = [torch.empty((ra, ca), dtype=torch.int16, device=a.device) for _ in range(npa)]
+    if out_b is None:
+        out_b = [torch.empty((cb, rb), dtype=torch.int16, device=b.device) for _ in range(npb)]
+    pa = list(out_a) + [None] * (3 - len(out_a))
+    pb = list(out_b) + [None] * (3 - len(out_b))
+    lda = _ld(a) if ra and ca else max(ca, 1)
+    ldb = _ld(b) if rb and cb else max(cb, 1)
+    ldpa = _ld(out_a[0]) if ra and ca else max(ca, 1)
+    ldpb = _ld(out_b[0]) if rb and cb else max(rb, 1)
+    _check("bfx_split_pair",
+           lib().bfx_split_pair(ra, ca, _ptr(a), lda, npa, _ptr(pa[0]), _ptr(pa[1]), _ptr(pa[2]), ldpa,
+                                rb, cb, _ptr(b), ldb, npb, _ptr(pb[0]), _ptr(pb[1]), _ptr(pb[2]), ldpb,
+                                _stream(stream)))
+    return out_a, out_b
 
 
 def gemm_workspace_size(mode: int, m: int, n: int, k: int) -> int:

@@ -156,6 +156,26 @@ BFX_API bfx_status bfx_split_transpose(int64_t rows, int64_t cols, const float* 
                                 static_cast<cudaStream_t>(stream));
 }
 
+BFX_API bfx_status bfx_split_pair(int64_t rows_a, int64_t cols_a, const float* d_a, int64_t lda,
+                                  int npa, uint16_t* d_a0, uint16_t* d_a1, uint16_t* d_a2,
+                                  int64_t ldpa, int64_t rows_b, int64_t cols_b, const float* d_b,
+                                  int64_t ldb, int npb, uint16_t* d_b0, uint16_t* d_b1,
+                                  uint16_t* d_b2, int64_t ldpb, bfx_stream stream) {
+  bfx_status st = check_split_args(rows_a, cols_a, d_a, lda, npa, d_a0, d_a1, d_a2, ldpa, cols_a);
+  if (st != BFX_OK) return st;
+  st = check_split_args(rows_b, cols_b, d_b, ldb, npb, d_b0, d_b1, d_b2, ldpb, rows_b);
+  if (st != BFX_OK) return st;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rows_a == 0 || cols_a == 0)
+    return (rows_b == 0 || cols_b == 0)
+               ? BFX_OK
+               : launch_split_transpose(rows_b, cols_b, d_b, ldb, npb, d_b0, d_b1, d_b2, ldpb, s);
+  if (rows_b == 0 || cols_b == 0)
+    return launch_split(rows_a, cols_a, d_a, lda, npa, d_a0, d_a1, d_a2, ldpa, s);
+  return launch_split_pair(rows_a, cols_a, d_a, lda, npa, d_a0, d_a1, d_a2, ldpa, rows_b, cols_b,
+                           d_b, ldb, npb, d_b0, d_b1, d_b2, ldpb, s);
+}
+
 // Workspace of bfx_gemm_bf16xN: npa planes of A pieces (m x kp) followed by
 // npb planes of transposed B pieces (n x kp), kp = k rounded up to 8, every
 // plane starting on a 256-byte boundary.
@@ -235,11 +255,9 @@ static bfx_status split_operands(bfx_mode mode, int64_t m, int64_t n, int64_t k,
   if (!aligned(d_ws, 256)) return BFX_EUNSUPPORTED;
   *Ap = static_cast<uint16_t*>(d_ws);
   *Bp = *Ap + npa * *ap;
-  bfx_status st = launch_split(m, k, d_A, lda, npa, *Ap, npa > 1 ? *Ap + *ap : nullptr,
-                               npa > 2 ? *Ap + 2 * *ap : nullptr, *kp, s);
-  if (st != BFX_OK) return st;
-  return launch_split_transpose(k, n, d_B, ldb, npb, *Bp, npb > 1 ? *Bp + *bp : nullptr,
-                                npb > 2 ? *Bp + 2 * *bp : nullptr, *kp, s);
+  return launch_split_pair(m, k, d_A, lda, npa, *Ap, npa > 1 ? *Ap + *ap : nullptr,
+                           npa > 2 ? *Ap + 2 * *ap : nullptr, *kp, k, n, d_B, ldb, npb, *Bp,
+                           npb > 1 ? *Bp + *bp : nullptr, npb > 2 ? *Bp + 2 * *bp : nullptr, *kp, s);
 }
 
 BFX_API bfx_status bfx_gemm_bf16xN(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,

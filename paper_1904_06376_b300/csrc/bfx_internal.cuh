@@ -46,6 +46,10 @@ bfx_status launch_split(int64_t rows, int64_t cols, const float* x, int64_t ldx,
 bfx_status launch_split_transpose(int64_t rows, int64_t cols, const float* x, int64_t ldx,
                                   int npieces, uint16_t* hi, uint16_t* mid, uint16_t* lo,
                                   int64_t ldp, cudaStream_t s);
+bfx_status launch_split_pair(int64_t rows_a, int64_t cols_a, const float* a, int64_t lda, int npa,
+                             uint16_t* a0, uint16_t* a1, uint16_t* a2, int64_t ldpa,
+                             int64_t rows_b, int64_t cols_b, const float* b, int64_t ldb, int npb,
+                             uint16_t* b0, uint16_t* b1, uint16_t* b2, int64_t ldpb, cudaStream_t s);
 // C = beta*C (k == 0 GEMM)
 bfx_status launch_scale(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t s);
 // SIMT SGEMM (gemm_simt.cu)

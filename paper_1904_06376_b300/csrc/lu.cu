@@ -583,12 +583,13 @@ __device__ __forceinline__ void swapset_warp(const int* __restrict__ piv, int j0
   __syncwarp();
 }
 
-// Moves the touched rows of CTA cb's columns: column index
-// idx = cb * LASWP_COLS + lane of the list [c0, c0 + n0) ++ [c1, c1 + n1).
-// Builds the swap set of ipiv[j0 .. j0+jb) itself (blockDim = LASWP_THREADS).
+// Moves the touched rows of column blocks cb0, cb0 + cstep, ...: column
+// index idx = cb * LASWP_COLS + lane of the list [c0, c0 + n0) ++
+// [c1, c1 + n1).  Builds the swap set of ipiv[j0 .. j0+jb) once itself
+// (blockDim = LASWP_THREADS).
 __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int j0, int jb,
                                            const int32_t* __restrict__ ipiv, int c0, int n0,
-                                           int c1, int n1, int cb) {
+                                           int c1, int n1, int cb0, int cstep) {
   __shared__ SwapSet ss;
   __shared__ __align__(16) int piv[128];
   __shared__ int sp[128];
@@ -597,21 +598,23 @@ __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, i
   __syncthreads();
   if (w == 0) swapset_warp(piv, j0, jb, &ss, sp);
   __syncthreads();
-  const int idx = cb * LASWP_COLS + lane;
-  const bool on = idx < n0 + n1;
-  const int64_t c = idx < n0 ? c0 + idx : c1 + (idx - n0);
   const int ns = ss.nslots;
-  float v[LASWP_PER_WARP];
+  for (int cb = cb0; cb * LASWP_COLS < n0 + n1; cb += cstep) {  // the same for the whole CTA
+    const int idx = cb * LASWP_COLS + lane;
+    const bool on = idx < n0 + n1;
+    const int64_t c = idx < n0 ? c0 + idx : c1 + (idx - n0);
+    float v[LASWP_PER_WARP];
 #pragma unroll
-  for (int q = 0; q < LASWP_PER_WARP; ++q) {
-    const int k = w + LASWP_WARPS * q;
-    v[q] = (on && k < ns) ? A[static_cast<int64_t>(ss.cont[k]) * lda + c] : 0.0f;
-  }
-  __syncthreads();
+    for (int q = 0; q < LASWP_PER_WARP; ++q) {
+      const int k = w + LASWP_WARPS * q;
+      v[q] = (on && k < ns) ? A[static_cast<int64_t>(ss.cont[k]) * lda + c] : 0.0f;
+    }
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < LASWP_PER_WARP; ++q) {
-    const int k = w + LASWP_WARPS * q;
-    if (on && k < ns) A[static_cast<int64_t>(ss.rowid[k]) * lda + c] = v[q];
+    for (int q = 0; q < LASWP_PER_WARP; ++q) {
+      const int k = w + LASWP_WARPS * q;
+      if (on && k < ns) A[static_cast<int64_t>(ss.rowid[k]) * lda + c] = v[q];
+    }
   }
 }
 
@@ -619,7 +622,8 @@ __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, i
 __global__ void __launch_bounds__(LASWP_THREADS)
     lu_laswp_kernel(float* __restrict__ A, int64_t lda, int j0, int jb,
                     const int32_t* __restrict__ ipiv, int c0, int n0, int c1, int n1) {
-  laswp_body(A, lda, j0, jb, ipiv, c0, n0, c1, n1, static_cast<int>(blockIdx.x));
+  laswp_body(A, lda, j0, jb, ipiv, c0, n0, c1, n1, static_cast<int>(blockIdx.x),
+             static_cast<int>(gridDim.x));
 }
 
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
@@ -777,7 +781,8 @@ __global__ void __launch_bounds__(LASWP_THREADS)
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
   if (JB <= 0 || static_cast<int>(blockIdx.x) * LASWP_COLS >= b.n - JB) return;
-  laswp_body(b.A, b.n, J0, JB, b.ipiv, 0, J0, J0 + JB, b.n - J0 - JB, static_cast<int>(blockIdx.x));
+  laswp_body(b.A, b.n, J0, JB, b.ipiv, 0, J0, J0 + JB, b.n - J0 - JB, static_cast<int>(blockIdx.x),
+             static_cast<int>(gridDim.x));
 }
 
 template <int NB>
@@ -1480,7 +1485,8 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
     const unsigned gx = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), 32)));
     lu_tile_update_batched_kernel<<<dim3(gx, S_t), 256, 0, s>>>(d_sys, nb, J0, j0);
   }
-  const unsigned cblk = static_cast<unsigned>(ceil_div(nmax, LASWP_COLS));
+  // a CTA forms a system's swap set once and moves up to four column blocks
+  const unsigned cblk = static_cast<unsigned>(ceil_div(ceil_div(nmax, LASWP_COLS), 4));
   lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_THREADS, 0, s>>>(d_sys, nb, J0);
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
   const size_t tsmem = trsm_smem_bytes(tnb);

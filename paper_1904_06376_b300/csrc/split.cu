@@ -38,15 +38,14 @@ __device__ __forceinline__ void split8_store(const float4 a, const float4 b, uin
 
 // Contiguous rows (ldx == ldp == cols): one flat range, no index division;
 // two groups of 8 elements a thread and iteration, all four 16-byte loads
-// issued before the splits.
+// issued before the splits.  Block bid of nblocks.
 template <int NP>
-__global__ void __launch_bounds__(256) split_flat_kernel(const float* __restrict__ x, int64_t n8,
-                                                         uint16_t* __restrict__ p0,
-                                                         uint16_t* __restrict__ p1,
-                                                         uint16_t* __restrict__ p2) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+__device__ __forceinline__ void split_flat_body(const float* __restrict__ x, int64_t n8,
+                                                uint16_t* __restrict__ p0, uint16_t* __restrict__ p1,
+                                                uint16_t* __restrict__ p2, int bid, int nblocks) {
+  const int64_t stride = static_cast<int64_t>(nblocks) * blockDim.x;
   const float4* src = reinterpret_cast<const float4*>(x);
-  int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int64_t v = bid * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   for (; v + stride < n8; v += 2 * stride) {
     const float4 a0 = __ldcs(src + 2 * v), b0 = __ldcs(src + 2 * v + 1);
     const float4 a1 = __ldcs(src + 2 * (v + stride)), b1 = __ldcs(src + 2 * (v + stride) + 1);
@@ -54,6 +53,13 @@ __global__ void __launch_bounds__(256) split_flat_kernel(const float* __restrict
     split8_store<NP>(a1, b1, p0, p1, p2, 8 * (v + stride));
   }
   if (v < n8) split8_store<NP>(__ldcs(src + 2 * v), __ldcs(src + 2 * v + 1), p0, p1, p2, 8 * v);
+}
+template <int NP>
+__global__ void __launch_bounds__(256) split_flat_kernel(const float* __restrict__ x, int64_t n8,
+                                                         uint16_t* __restrict__ p0,
+                                                         uint16_t* __restrict__ p1,
+                                                         uint16_t* __restrict__ p2) {
+  split_flat_body<NP>(x, n8, p0, p1, p2, static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
 }
 
 template <int NP>
@@ -104,16 +110,15 @@ __global__ void __launch_bounds__(256) split_scalar_kernel(const float* __restri
 // 64 x 64 tile, 256 threads (32 x 8).  Reads rows of x coalesced, writes rows
 // of the transposed pieces coalesced as pairs of bfloat16 (4 bytes a lane).
 constexpr int TT = 64;
-__global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ x,
-                                                              int64_t ldx, int64_t rows,
-                                                              int64_t cols, int np,
-                                                              uint16_t* __restrict__ p0,
-                                                              uint16_t* __restrict__ p1,
-                                                              uint16_t* __restrict__ p2,
-                                                              int64_t ldp, int pairs) {
-  __shared__ float tile[TT][TT + 1];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * TT;
-  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TT;
+// Tile (bx, by) of the transposed split; tile: the caller's shared memory.
+__device__ __forceinline__ void split_transpose_tile(float (*tile)[TT + 1], const float* __restrict__ x,
+                                                     int64_t ldx, int64_t rows, int64_t cols, int np,
+                                                     uint16_t* __restrict__ p0,
+                                                     uint16_t* __restrict__ p1,
+                                                     uint16_t* __restrict__ p2, int64_t ldp,
+                                                     int pairs, int64_t bx, int64_t by) {
+  const int64_t r0 = by * TT;
+  const int64_t c0 = bx * TT;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < TT; i += 8) {
@@ -184,6 +189,43 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
   }
 }
 
+__global__ void __launch_bounds__(256) split_transpose_kernel(const float* __restrict__ x,
+                                                              int64_t ldx, int64_t rows,
+                                                              int64_t cols, int np,
+                                                              uint16_t* __restrict__ p0,
+                                                              uint16_t* __restrict__ p1,
+                                                              uint16_t* __restrict__ p2,
+                                                              int64_t ldp, int pairs) {
+  __shared__ float tile[TT][TT + 1];
+  split_transpose_tile(tile, x, ldx, rows, cols, np, p0, p1, p2, ldp, pairs, blockIdx.x, blockIdx.y);
+}
+
+// Both operands of C = A B in one launch: CTAs [0, ga) split A as
+// split_flat_kernel (contiguous rows), the others take B's transposed tiles
+// (16-byte piece stores), so the two passes fill each other's tails instead
+// of running one after the other.  Same bytes and results as the two
+// kernels.
+__global__ void __launch_bounds__(256)
+    split_pair_kernel(const float* __restrict__ a, int64_t n8, int npa, uint16_t* __restrict__ a0,
+                      uint16_t* __restrict__ a1, uint16_t* __restrict__ a2, int ga,
+                      const float* __restrict__ b, int64_t ldb, int64_t rows, int64_t cols, int npb,
+                      uint16_t* __restrict__ b0, uint16_t* __restrict__ b1,
+                      uint16_t* __restrict__ b2, int64_t ldp, int64_t tiles_x) {
+  __shared__ float tile[TT][TT + 1];
+  const int bid = static_cast<int>(blockIdx.x);
+  if (bid < ga) {
+    if (npa == 1)
+      split_flat_body<1>(a, n8, a0, a1, a2, bid, ga);
+    else if (npa == 2)
+      split_flat_body<2>(a, n8, a0, a1, a2, bid, ga);
+    else
+      split_flat_body<3>(a, n8, a0, a1, a2, bid, ga);
+    return;
+  }
+  const int64_t t = bid - ga;
+  split_transpose_tile(tile, b, ldb, rows, cols, npb, b0, b1, b2, ldp, 2, t % tiles_x, t / tiles_x);
+}
+
 __global__ void scale_kernel(int64_t m, int64_t n, float beta, float* __restrict__ C, int64_t ldc) {
   const int64_t total = m * n;
   for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < total;
@@ -247,6 +289,32 @@ bfx_status launch_split_transpose(int64_t rows, int64_t cols, const float* x, in
   const int pairs = al16 ? 2 : (al4 ? 1 : 0);
   split_transpose_kernel<<<grid, 256, 0, s>>>(x, ldx, rows, cols, npieces, hi, mid, lo, ldp,
                                               pairs);
+  return last_launch_status();
+}
+
+// A (rows_a x cols_a, split as is) and B (rows_b x cols_b, split transposed)
+// in one launch when A's rows are contiguous (lda == ldpa == cols_a, 16-byte
+// aligned) and B's piece planes take 16-byte stores; otherwise the two
+// launches of launch_split and launch_split_transpose.
+bfx_status launch_split_pair(int64_t rows_a, int64_t cols_a, const float* a, int64_t lda, int npa,
+                             uint16_t* a0, uint16_t* a1, uint16_t* a2, int64_t ldpa,
+                             int64_t rows_b, int64_t cols_b, const float* b, int64_t ldb, int npb,
+                             uint16_t* b0, uint16_t* b1, uint16_t* b2, int64_t ldpb, cudaStream_t s) {
+  const bool flat = rows_a > 0 && cols_a > 0 && cols_a % 8 == 0 && lda == cols_a && ldpa == cols_a &&
+                    aligned(a, 16) && aligned(a0, 16) && (npa < 2 || aligned(a1, 16)) &&
+                    (npa < 3 || aligned(a2, 16));
+  const bool t16 = rows_b > 0 && cols_b > 0 && aligned(b0, 16) && (npb < 2 || aligned(b1, 16)) &&
+                   (npb < 3 || aligned(b2, 16)) && ldpb % 8 == 0;
+  const int64_t tx = ceil_div(cols_b, TT), ty = ceil_div(rows_b, TT);
+  const int64_t n8 = rows_a * cols_a / 8;
+  const int ga = grid_for(n8, 256);
+  if (!flat || !t16 || static_cast<int64_t>(ga) + tx * ty > INT32_MAX) {
+    const bfx_status st = launch_split(rows_a, cols_a, a, lda, npa, a0, a1, a2, ldpa, s);
+    if (st != BFX_OK) return st;
+    return launch_split_transpose(rows_b, cols_b, b, ldb, npb, b0, b1, b2, ldpb, s);
+  }
+  split_pair_kernel<<<static_cast<unsigned>(ga + tx * ty), 256, 0, s>>>(
+      a, n8, npa, a0, a1, a2, ga, b, ldb, rows_b, cols_b, npb, b0, b1, b2, ldpb, tx);
   return last_launch_status();
 }
 

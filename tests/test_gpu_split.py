@@ -67,3 +67,26 @@ def test_split_special_values(bfx, orc):
 def test_split_empty(bfx):
     x = torch.empty((0, 5), dtype=torch.float32, device="cuda")
     assert [p.shape for p in bfx.split(x, 3)] == [(0, 5)] * 3
+
+
+@pytest.mark.parametrize("ma,ka,kb,nb,npa,npb", [
+    (256, 512, 512, 384, 3, 3),   # one launch: A contiguous, B's planes 16-byte aligned
+    (1000, 64, 64, 777, 2, 3),    # one launch, ragged B tiles
+    (33, 40, 40, 129, 3, 2),      # one launch, small
+    (37, 53, 53, 70, 3, 3),       # A's width not a multiple of 8: two launches
+    (0, 16, 16, 20, 3, 3),        # empty A
+])
+def test_split_pair_equals_split_and_transpose(bfx, ma, ka, kb, nb, npa, npb):
+    """split_pair gives the pieces of split(A) and split_transpose(B) bit for
+    bit, in the combined launch and in the two-launch fallback (wide-range
+    values, so every piece is populated)."""
+    A = torch.from_numpy(bi.wide_range((ma, ka), ma + ka)).cuda()
+    B = torch.from_numpy(bi.wide_range((kb, nb), kb + nb)).cuda()
+    pa, pb = bfx.split_pair(A, B, npa, npb)
+    if ma:
+        ea = bfx.split(A, npa)
+        for g, e in zip(pa, ea):
+            assert torch.equal(g, e)
+    eb = bfx.split_transpose(B, npb)
+    for g, e in zip(pb, eb):
+        assert torch.equal(g, e)

@@ -759,12 +759,30 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
     for (int t = blockIdx.x; t < args.num_tiles; t += gridDim.x) {
       const TileInfo ti = get_tile<GROUPED>(t, args);
       const int mb = ti.mb, nb = ti.nb;
+      const int row = mb * BM + row_in_tile;
+      const bool row_ok = row < ti.M;
+      // With beta != 0 and a narrow tile, the tile's C row is loaded before
+      // the accumulator is awaited, so its latency overlaps the MMAs (the
+      // short-K trailing updates of the batched LU spent their time in these
+      // loads, one 16-column piece after another).
+      constexpr int PFC = (!D64 && BN <= 64) ? BN / 16 : 0;
+      float cpre[PFC > 0 ? PFC : 1][16];
+      const bool pre = PFC > 0 && args.beta != 0.0f && row_ok;
+      if constexpr (PFC > 0) {
+        if (pre) {
+          const float* src = ti.C + static_cast<int64_t>(row) * ti.ldc;
+#pragma unroll
+          for (int c = 0; c < PFC; ++c) {
+            const int col0 = nb * BN + c * 16;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) cpre[c][i] = col0 + i < ti.N ? src[col0 + i] : 0.0f;
+          }
+        }
+      }
       bool ok = mbar_wait_bounded(&acc_full[buf], aph, err, kErrWaitAccFull);
       ok = __all_sync(0xFFFFFFFFu, ok);
       if (!ok) break;
       tc_fence_after();
-      const int row = mb * BM + row_in_tile;
-      const bool row_ok = row < ti.M;
       const uint32_t tb = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                           static_cast<uint32_t>(buf * Cfg::NACC * BN);
       if constexpr (D64) {
@@ -800,7 +818,7 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
         continue;
       }
       float* crow = ti.C + static_cast<int64_t>(row_ok ? row : 0) * ti.ldc;
-#pragma unroll 1
+#pragma unroll(PFC > 0 ? PFC : 1)
       for (int c = 0; c < BN / 16; ++c) {
         __syncwarp();
         float v[16];
@@ -824,7 +842,12 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
           for (int i = 0; i < 16; i += 4) {
             float4 o;
             float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (args.beta != 0.0f) old = *reinterpret_cast<const float4*>(dst + i);
+            if constexpr (PFC > 0) {
+              if (pre) old = make_float4(cpre[c][i], cpre[c][i + 1], cpre[c][i + 2], cpre[c][i + 3]);
+              else if (args.beta != 0.0f) old = *reinterpret_cast<const float4*>(dst + i);
+            } else {
+              if (args.beta != 0.0f) old = *reinterpret_cast<const float4*>(dst + i);
+            }
             o.x = args.alpha * v[i + 0];
             o.y = args.alpha * v[i + 1];
             o.z = args.alpha * v[i + 2];
@@ -843,7 +866,13 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
           for (int i = 0; i < 16; ++i) {
             if (i < lim) {
               const float tv = args.alpha * v[i];
-              dst[i] = (args.beta == 0.0f) ? tv : fmaf(args.beta, dst[i], tv);
+              float cv = 0.0f;
+              if constexpr (PFC > 0) {
+                if (args.beta != 0.0f) cv = pre ? cpre[c][i] : dst[i];
+              } else {
+                if (args.beta != 0.0f) cv = dst[i];
+              }
+              dst[i] = (args.beta == 0.0f) ? tv : fmaf(args.beta, cv, tv);
             }
           }
         }

@@ -841,9 +841,10 @@ __global__ void lu_split_batched_kernel(const BatchLu* __restrict__ sys, int nb,
 // thread, the row's NB values in registers (one CTA of as many threads as
 // rows when they fit one CTA).  Per pivot column j:
 //  1. every thread offers its row's |a_rj| (rows >= j) as a key: the value's
-//     bits plus one (a NaN gets 0: never chosen over a number) with the row
-//     index; a warp keeps the largest key and, among equal keys, the lowest
-//     row (LAPACK's first row of the largest |a|) by two warp reductions;
+//     bits plus two (a NaN gets 1: never chosen over a number; no offer 0)
+//     with the row index; a warp keeps the largest key and, among equal keys,
+//     the lowest row (LAPACK's first row of the largest |a|) by one warp max
+//     and a ballot, as rows rise with lane, warp and CTA rank;
 //     each warp's winner posts its row to shared memory, and the thread
 //     holding row j posts row j;
 //  2. after a CTA barrier the pushing warps reduce the warps' offers the
@@ -973,20 +974,25 @@ __device__ __forceinline__ void panel_wait(uint64_t* bar, uint32_t parity, int* 
   }
 }
 
-// pivot offer of a row: larger key wins, ties to the lower row index
+// pivot offer of a row: larger key wins, ties to the lower row index.  A
+// number's key is its |a| bits plus 2, a NaN's 1 (below any number), and a
+// lane with nothing to offer passes 0.
 __device__ __forceinline__ uint32_t offer_key(float a) {
   const float m = fabsf(a);
-  return m == m ? __float_as_uint(m) + 1u : 0u;  // a NaN below any number
+  return m == m ? __float_as_uint(m) + 2u : 1u;
 }
 // warp winner of (key, idx) over all 32 lanes: the largest key, then the
-// smallest index; *lane_out = a lane that offered it
+// lowest lane holding it.  At every level the lanes hold rows (or groups of
+// rows) in increasing row order, so the lowest lane is the lowest row: one
+// max reduction and a ballot instead of a second reduction over the indices.
+// *lane_out = the winning lane.
 __device__ __forceinline__ void warp_offer(uint32_t key, uint32_t idx, uint32_t* kout,
                                            uint32_t* iout, int* lane_out) {
   const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, key);
-  const uint32_t i = __reduce_min_sync(0xFFFFFFFFu, key == m ? idx : 0xFFFFFFFFu);
+  const int l = __ffs(__ballot_sync(0xFFFFFFFFu, key == m)) - 1;
   *kout = m;
-  *iout = i;
-  *lane_out = __ffs(__ballot_sync(0xFFFFFFFFu, key == m && idx == i)) - 1;
+  *iout = __shfl_sync(0xFFFFFFFFu, idx, l);
+  *lane_out = l;
 }
 
 template <int NQ>

@@ -35,8 +35,10 @@
 
 namespace bfx {
 
+// perm (optional): receives P of P A = L U as a row list (perm[i] = the
+// original row at row i), built from the same swap sets as the row swaps
 bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, int32_t* ipiv,
-                     int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s);
+                     int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s, int32_t* perm);
 size_t lu_workspace_bytes(bfx_mode mode, int64_t n, int nb);
 
 namespace {
@@ -73,33 +75,6 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   // non-negative doubles order like their bit patterns (NaN sorts above Inf)
   atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
-}
-
-// perm[i] = source row of row i of P*v, from sequential swaps ipiv.
-// use_smem: both arrays (2 n ints) staged in shared memory.
-__global__ void ir_perm_kernel(const int32_t* __restrict__ ipiv, int n, int32_t* __restrict__ perm,
-                               bool use_smem) {
-  extern __shared__ int32_t sp[];
-  int32_t* p = use_smem ? sp : perm;
-  const int32_t* q = use_smem ? sp + n : ipiv;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    p[i] = i;
-    if (use_smem) sp[n + i] = ipiv[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < n; ++j) {
-      const int r = q[j];
-      if (r != j) {
-        const int32_t t = p[j];
-        p[j] = p[r];
-        p[r] = t;
-      }
-    }
-  }
-  __syncthreads();
-  if (use_smem)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sp[i];
 }
 
 // out[c] = max_i |M[i, c]| for c < ncols (out must start at 0).
@@ -204,32 +179,42 @@ __global__ void __launch_bounds__(256)
 constexpr unsigned long long kTrsvSentinel = 0xFFF4000000000001ull;
 
 // d[i, c] = r[perm[i], c]; when fill (fill2) != null, also fill[] (fill2[]) =
-// the triangular solve's sentinel (n x nrhs) and tickets[0..1] = 0.
+// the triangular solve's sentinel (n x nrhs), the same for fill3 (2 n x
+// nrhs), and tickets[0..1] = 0.
 __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
                                  const int32_t* __restrict__ perm, int64_t n, int nrhs,
                                  double* __restrict__ d, int64_t ldd, double* __restrict__ fill,
-                                 double* __restrict__ fill2, int* __restrict__ tickets,
-                                 const int32_t* __restrict__ gate) {
+                                 double* __restrict__ fill2, double* __restrict__ fill3,
+                                 int* __restrict__ tickets, const int32_t* __restrict__ gate) {
   pdl_begin();
   if (gate && *gate == 0) return;
   if (tickets && blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0;
+  const double sent = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * nrhs;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e / nrhs;
     const int c = static_cast<int>(e - i * nrhs);
     d[i * ldd + c] = r[static_cast<int64_t>(perm[i]) * ldr + c];
-    if (fill) fill[e] = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
-    if (fill2) fill2[e] = __longlong_as_double(static_cast<long long>(kTrsvSentinel));
+    if (fill) fill[e] = sent;
+    if (fill2) fill2[e] = sent;
+    if (fill3) {
+      fill3[e] = sent;
+      fill3[e + n * nrhs] = sent;
+    }
   }
 }
 
 // Inverses of the diagonal blocks of L (unit lower) and U (upper), FP64,
 // once per factorisation.  CTA b inverts block b: thread k solves
-// T x = e_k by column-oriented substitution in registers.
+// T x = e_k by column-oriented substitution in registers.  x stays zero
+// above row k (L) or below it (U), so a warp skips the steps whose pivot
+// column is zero in all its lanes' x; U's diagonal enters through its
+// reciprocals (one division a thread).
 template <bool LOWER>
 __device__ __forceinline__ void diag_inverse_body(const float* __restrict__ F, int64_t ldf, int n,
                                                   int blk, double* __restrict__ D) {
   __shared__ double T[TB][TB + 1];
+  __shared__ double rdiag[TB];
   const int b0 = blk * TB, bs = min(TB, n - b0), k = threadIdx.x;
   for (int e = k; e < TB * TB; e += TB) {
     const int i = e / TB, l = e % TB;
@@ -237,19 +222,24 @@ __device__ __forceinline__ void diag_inverse_body(const float* __restrict__ F, i
                                  : (i == l ? 1.0 : 0.0);
   }
   __syncthreads();
+  if (!LOWER) rdiag[k] = 1.0 / T[k][k];
+  __syncthreads();
+  const int w0 = k & ~31;  // the warp's first column
   double x[TB];
 #pragma unroll
   for (int i = 0; i < TB; ++i) x[i] = (i == k) ? 1.0 : 0.0;
   if (LOWER) {
 #pragma unroll
     for (int l = 0; l < TB - 1; ++l) {
+      if (l < w0) continue;  // x[l] == 0 in every lane of the warp
 #pragma unroll
       for (int i = l + 1; i < TB; ++i) x[i] = fma(-T[i][l], x[l], x[i]);
     }
   } else {
 #pragma unroll
     for (int l = TB - 1; l >= 0; --l) {
-      x[l] = x[l] / T[l][l];
+      if (l > w0 + 31) continue;
+      x[l] *= rdiag[l];
 #pragma unroll
       for (int i = 0; i < l; ++i) x[i] = fma(-T[i][l], x[l], x[i]);
     }
@@ -258,69 +248,94 @@ __device__ __forceinline__ void diag_inverse_body(const float* __restrict__ F, i
   for (int i = 0; i < TB; ++i) D[i * TB + k] = x[i];  // column k of the inverse
 }
 
-template <bool LOWER>
+// Both factors' diagonal-block inverses in one launch: CTAs [0, nblk) for L,
+// [nblk, 2 nblk) for U.
 __global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __restrict__ F,
                                                              int64_t ldf, int n,
-                                                             double* __restrict__ Dinv) {
-  diag_inverse_body<LOWER>(F, ldf, n, blockIdx.x,
-                           Dinv + static_cast<int64_t>(blockIdx.x) * TB * TB);
+                                                             double* __restrict__ Linv,
+                                                             double* __restrict__ Uinv) {
+  const int nblk = (n + TB - 1) / TB, bx = static_cast<int>(blockIdx.x);
+  if (bx < nblk)
+    diag_inverse_body<true>(F, ldf, n, bx, Linv + static_cast<int64_t>(bx) * TB * TB);
+  else
+    diag_inverse_body<false>(F, ldf, n, bx - nblk, Uinv + static_cast<int64_t>(bx - nblk) * TB * TB);
 }
 
-// G_b = Dinv_b F[b, p] for every row block b with a predecessor p in solve
-// order (p = b - 1 forward, b + 1 backward), FP64, once per factorisation:
-// the triangular solve then needs only one 64 x 64 product between the
-// arrival of y_p and the publication of y_b (y_b = z_b - G_b y_p, z_b the
-// inverse applied to everything else).  CTA b, a thread per 16 outputs.
-template <bool LOWER>
+// Chain matrices, FP64, once per factorisation: G_b = Dinv_b F[b, p] and
+// G2_b = Dinv_b F[b, q] for every row block b with a predecessor p (and q)
+// one (two) steps back in solve order (p = b - 1, q = b - 2 forward; b + 1,
+// b + 2 backward), stored at block b (G) and nblk + b (G2).  The triangular
+// solve then needs only the products G2_b y_q and G_b y_p between those
+// blocks' arrivals and the publication of y_b.  One launch for both factors:
+// CTA (b', h, d) with b' < nblk - 1 for L, else U, h the half of the rows it
+// computes and d + 1 the distance; a warp's 32 outputs share a row i, so the
+// product runs only over Dinv_b's nonzero columns (l <= i for L, l >= i for U).
+constexpr int CHAIN_HALF = TB / 2;
 __global__ void __launch_bounds__(256)
     ir_chain_kernel(const float* __restrict__ F, int64_t ldf, int n,
-                    const double* __restrict__ Dinv, double* __restrict__ G) {
-  __shared__ double Ds[TB][TB];  // rows read by broadcast, Fs rows by consecutive lanes:
-  __shared__ float Fs[TB][TB];   // no padding needed (48 KB in all)
+                    const double* __restrict__ Linv, const double* __restrict__ Uinv,
+                    double* __restrict__ Lg, double* __restrict__ Ug) {
+  __shared__ double Ds[CHAIN_HALF][TB];  // rows read by broadcast, Fs rows by consecutive lanes:
+  __shared__ float Fs[TB][TB];           // no padding needed (32 KB in all)
   const int nblk = (n + TB - 1) / TB;
-  const int b = LOWER ? blockIdx.x + 1 : blockIdx.x;  // blocks with a predecessor
-  const int p = LOWER ? b - 1 : b + 1;
+  const bool lower = static_cast<int>(blockIdx.x) < nblk - 1;
+  const int bi = lower ? blockIdx.x : blockIdx.x - (nblk - 1);
+  const int dist = 1 + static_cast<int>(blockIdx.z);
+  const int b = lower ? bi + 1 : bi;  // blocks with a predecessor
+  const int p = lower ? b - dist : b + dist;
   if (p < 0 || p >= nblk) return;
+  const int h0 = blockIdx.y * CHAIN_HALF;  // first row of G_b here
   const int b0 = b * TB, bs = min(TB, n - b0), p0 = p * TB, ps = min(TB, n - p0);
-  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
+  const double* D = (lower ? Linv : Uinv) + static_cast<int64_t>(b) * TB * TB;
+  for (int e = threadIdx.x; e < CHAIN_HALF * TB; e += 256)
+    Ds[e / TB][e % TB] = D[h0 * TB + e];
   for (int e = threadIdx.x; e < TB * TB; e += 256) {
     const int i = e / TB, l = e % TB;
-    Ds[i][l] = D[e];
     Fs[i][l] = (i < bs && l < ps) ? F[static_cast<int64_t>(b0 + i) * ldf + p0 + l] : 0.0f;
   }
   __syncthreads();
-  double* g = G + static_cast<int64_t>(b) * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += 256) {
-    const int i = e / TB, j = e % TB;
-    double s0 = 0.0, s1 = 0.0;
-    for (int l = 0; l < TB; l += 2) {
-      s0 = fma(Ds[i][l], static_cast<double>(Fs[l][j]), s0);
-      s1 = fma(Ds[i][l + 1], static_cast<double>(Fs[l + 1][j]), s1);
-    }
-    g[e] = s0 + s1;
+  double* g = (lower ? Lg : Ug) + (static_cast<int64_t>(dist - 1) * nblk + b) * TB * TB;
+  for (int e = threadIdx.x; e < CHAIN_HALF * TB; e += 256) {
+    const int ii = e / TB, i = h0 + ii, j = e % TB;
+    const int la = lower ? 0 : i, lb = lower ? i + 1 : TB;  // Dinv_b's nonzero columns of row i
+    double s0 = 0.0;
+    for (int l = la; l < lb; ++l) s0 = fma(Ds[ii][l], widen(Fs[l][j]), s0);
+    g[static_cast<int64_t>(i) * TB + j] = s0;
   }
 }
 
 // Triangular solve L y = v (unit lower, forward) or U y = v (upper, backward)
 // with the FP32 factors in FP64 arithmetic, in one launch without a grid-wide
-// barrier.  Row blocks of 64; right-hand sides in groups of up to 4 columns.
-// A CTA takes a (row block, column group) from an atomic ticket in solve
-// order, so every block it waits on belongs to a CTA that started earlier and
-// is running: the waits always end (and are bounded in time regardless).
-// CTA for block b, group g:
-//   acc = v_b;  for each earlier block k in solve order: wait until y_k is
-//   published, acc -= F[b, k] y_k;   y_b = Dinv_b acc (the block's inverse);
-//   store y_b, fence, publish.
-// The tile of F is fetched before the wait, so it overlaps the wait; the sums
-// run in a fixed order (deterministic).  A block's result is published by
-// storing it into y, which holds a sentinel (a signalling-NaN pattern no
-// arithmetic produces) until then: consumers poll the values themselves, so
-// there is no flag and no fence between the product and the next block.  y
-// must be all sentinel at launch; each launch resets the v rows it consumed
-// to the sentinel, so the forward launch prepares the backward one's output.
+// barrier.  Row blocks of 64, each computed by TRSV_SLICES CTAs of 32 rows;
+// right-hand sides in groups of up to 4 columns.  A CTA takes a (row block,
+// column group, slice) from an atomic ticket in solve order, so every block
+// it waits on belongs to CTAs that started earlier and are running: the
+// waits always end (and are bounded in time regardless).
+// CTA for block b, group g, rows S of the block; p and q the blocks one and
+// two steps back in solve order:
+//   acc_S = v_b[S] - sum over the earlier blocks k but p and q of
+//           F[b, k][S, :] y_k   (each y_k polled as it is published);
+//   the other slice's acc rows through an exchange buffer (the inverse of
+//   the triangular diagonal block needs them on one side only: the slice
+//   whose rows come first in solve order publishes, the other reads);
+//   z = (Dinv_b acc)[S] - (G2_b y_q)[S];   y_b[S] = z - (G_b y_p)[S];  publish.
+// One SM's FP64 rate bounds the products (a 32 x 64 tile takes about 1.3 us
+// with the pipeline's fill and drain), so the slices halve each step's tile,
+// and the chain matrices G_b = Dinv_b F[b, p], G2_b = Dinv_b F[b, q] leave
+// only G2_b y_q and G_b y_p between the arrivals of y_q, y_p and the
+// publication of y_b.  The tile of F is fetched before the wait, so it
+// overlaps the wait; the sums run in a fixed order (deterministic).  A
+// block's result is published by storing it into y, which holds a sentinel (a
+// signalling-NaN pattern no arithmetic produces) until then: consumers poll
+// the values themselves, so there is no flag and no fence between the
+// product and the next block; the exchange works the same way.  y and the
+// exchange buffer xch (n x R) must be all sentinel at launch (the row gather
+// fills them); v is only read.  out (optional) gets a plain copy of y.
 // ticket: zero at launch.
 constexpr int TRSV_THREADS = 256;
 constexpr int TRSV_CG = 4;  // right-hand sides a CTA
+constexpr int TRSV_SLICES = 2;               // CTAs a row block
+constexpr int TRSV_RS = TB / TRSV_SLICES;    // rows a CTA publishes
 
 __device__ __forceinline__ bool is_trsv_sentinel(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x)) == kTrsvSentinel;
@@ -359,14 +374,16 @@ __device__ __forceinline__ double poll_published(const double* src, volatile int
   return val;
 }
 
-// out[i][c] (+)= sign * sum_l T[i][l] x[l][c], i < TB, c < cg; Q threads a
-// product (Q = 4, 2, 1 for cg = 1, 2, >2), their partial sums added by shuffle.
-template <typename T, int LDT>
+// out[i][c] (+)= sign * sum_l T[i][l] x[l][c], i < ROWS, c < cg; Q threads a
+// product (the largest of 8, 4, 2, 1 with ROWS cg Q <= 256), their partial
+// sums added by shuffle.
+template <typename T, int LDT, int ROWS>
 __device__ __forceinline__ void trsv_tile_product(const T* Tm, const double (*x)[TRSV_CG + 1],
                                                   double (*out)[TRSV_CG + 1], int cg, bool sub) {
   const int t = threadIdx.x;
-  const int Q = cg == 1 ? 4 : (cg == 2 ? 2 : 1);
-  const int items = TB * cg * Q;  // <= 256
+  const int rc = ROWS * cg;
+  const int Q = 8 * rc <= TRSV_THREADS ? 8 : (4 * rc <= TRSV_THREADS ? 4 : (2 * rc <= TRSV_THREADS ? 2 : 1));
+  const int items = rc * Q;  // a multiple of 32: whole warps take part or leave
   if (t >= items) return;
   const int o = t / Q, q = t - o * Q;
   const int i = o / cg, c = o - i * cg;
@@ -379,9 +396,9 @@ __device__ __forceinline__ void trsv_tile_product(const T* Tm, const double (*x)
     s1 = fma(widen(row[l + 1]), x[l0 + l + 1][c], s1);
   }
   double sum = s0 + s1;
-  // items == 256 whenever Q > 1, so every lane of the warp takes part
   if (Q >= 2) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
   if (Q >= 4) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 2);
+  if (Q >= 8) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 4);
   if (q == 0) out[i][c] = sub ? out[i][c] - sum : sum;
 }
 
@@ -398,17 +415,19 @@ template <bool LOWER>
 __global__ void __launch_bounds__(TRSV_THREADS)
     ir_trsv_kernel(const float* __restrict__ F, int64_t ldf, int n,
                    const double* __restrict__ Dinv, const double* __restrict__ Gm,
-                   double* __restrict__ v, double* __restrict__ y, int R,
-                   int* __restrict__ ticket, int* __restrict__ err,
+                   const double* __restrict__ v, double* __restrict__ y, double* __restrict__ out,
+                   double* __restrict__ xch, int R, int* __restrict__ ticket, int* __restrict__ err,
                    const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;  // every CTA leaves: no block is waited on
+  constexpr int RS = TRSV_RS, LD = TB + 1;
   extern __shared__ __align__(16) uint8_t trsv_smem[];
-  double* Ds = reinterpret_cast<double*>(trsv_smem);                       // [TB][TB + 1]
-  double* Gs = Ds + TB * (TB + 1);                                          // [TB][TB + 1]
-  float* Fs = reinterpret_cast<float*>(Gs + TB * (TB + 1));                // 2 x [TB][TB + 1]
-  auto acc = reinterpret_cast<double (*)[TRSV_CG + 1]>(Fs + 2 * TB * (TB + 1));  // [TB][CG + 1]
-  auto xs = acc + TB;                                                       // [TB][CG + 1]
-  auto zs = xs + TB;                                                        // [TB][CG + 1]
+  double* Ds = reinterpret_cast<double*>(trsv_smem);              // [RS][LD]: rows S of Dinv_b
+  double* Gs = Ds + RS * LD;                                       // [RS][LD]: rows S of G_b
+  double* G2s = Gs + RS * LD;                                      // [RS][LD]: rows S of G2_b
+  float* Fs = reinterpret_cast<float*>(G2s + RS * LD);            // 2 x [RS][LD]
+  auto acc = reinterpret_cast<double (*)[TRSV_CG + 1]>(Fs + 2 * RS * LD);  // [TB][CG + 1]
+  auto xs = acc + TB;                                              // [TB][CG + 1]
+  auto zs = xs + TB;                                               // [RS][CG + 1]
   __shared__ int s_ticket, s_fail;
   const int t = threadIdx.x;
   const int nblk = (n + TB - 1) / TB;
@@ -418,44 +437,48 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     s_fail = 0;
   }
   __syncthreads();
-  const int step = s_ticket / G, grp = s_ticket - step * G;
+  // the slice whose rows come first in solve order takes the earlier ticket
+  const int sk = s_ticket % TRSV_SLICES, unit = s_ticket / TRSV_SLICES;
+  const int slice = LOWER ? sk : TRSV_SLICES - 1 - sk;
+  const int step = unit / G, grp = unit - step * G;
   const int b = LOWER ? step : nblk - 1 - step;
   const int b0 = b * TB, bs = min(TB, n - b0);
+  const int r0 = slice * RS;  // the slice's first row in the block
+  const bool first = sk == 0;  // its acc rows feed the other slice's rows of Dinv_b acc
   const int c0 = grp * TRSV_CG, cg = min(TRSV_CG, R - c0);
-  // F[b, k] -> Fs buffer (s & 1), asynchronously; rows >= bs / columns >= ks zero
+  // rows S of F[b, k_s] -> Fs buffer (s & 1), asynchronously; rows >= bs /
+  // columns >= ks zero
   auto prefetch = [&](int s) {
     const int k = LOWER ? s : nblk - 1 - s;
     const int k0 = k * TB, ks = min(TB, n - k0);
-    float* dst = Fs + (s & 1) * TB * (TB + 1);
-    for (int e = t; e < TB * TB; e += TRSV_THREADS) {
+    float* dst = Fs + (s & 1) * RS * LD;
+    for (int e = t; e < RS * TB; e += TRSV_THREADS) {
       const int i = e / TB, l = e % TB;
-      const bool ok = i < bs && l < ks;
-      cp_async4(dst + i * (TB + 1) + l, ok ? F + static_cast<int64_t>(b0 + i) * ldf + k0 + l : F, ok);
+      const bool ok = r0 + i < bs && l < ks;
+      cp_async4(dst + i * LD + l, ok ? F + static_cast<int64_t>(b0 + r0 + i) * ldf + k0 + l : F, ok);
     }
   };
-  // tiles of all predecessors but the last (that one goes through G_b)
-  const int ntile = step > 0 ? step - 1 : 0;
+  // tiles of all predecessors but the last two (those go through G2_b, G_b)
+  const int ntile = step > 2 ? step - 2 : 0;
   if (ntile > 0) prefetch(0);
   cp_async_commit();
-  // the block's inverse and chain matrix (independent of the other blocks), acc = v_b
-  const double* D = Dinv + static_cast<int64_t>(b) * TB * TB;
-  const double* Gb = Gm + static_cast<int64_t>(b) * TB * TB;
-  for (int e = t; e < TB * TB; e += TRSV_THREADS) {
-    Ds[(e / TB) * (TB + 1) + e % TB] = D[e];
-    if (step > 0) Gs[(e / TB) * (TB + 1) + e % TB] = Gb[e];
+  // the slice's rows of the block's inverse and chain matrices
+  const double* D = Dinv + (static_cast<int64_t>(b) * TB + r0) * TB;
+  const double* Gb = Gm + (static_cast<int64_t>(b) * TB + r0) * TB;
+  const double* G2b = Gm + (static_cast<int64_t>(nblk + b) * TB + r0) * TB;
+  for (int e = t; e < RS * TB; e += TRSV_THREADS) {
+    const int i = e / TB, l = e % TB;
+    Ds[i * LD + l] = D[e];
+    if (step > 0) Gs[i * LD + l] = Gb[e];
+    if (step > 1) G2s[i * LD + l] = G2b[e];
   }
-  // acc = v_b; the v rows read are then set to the sentinel: this launch is
-  // their last reader, and the next triangle writes its result there
+  // acc = v_b on rows S, 0 elsewhere (the other rows come from the exchange)
   for (int e = t; e < TB * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
-    double a = 0.0;
-    if (i < bs) {
-      double* vp = v + static_cast<int64_t>(b0 + i) * R + c0 + c;
-      a = *vp;
-      *vp = __longlong_as_double(static_cast<long long>(kTrsvSentinel));  // next launch's output
-    }
-    acc[i][c] = a;
+    const bool own = i >= r0 && i < r0 + RS && i < bs;
+    acc[i][c] = own ? v[static_cast<int64_t>(b0 + i) * R + c0 + c] : 0.0;
   }
+  __syncthreads();  // acc rows are read and written by other threads below
   // fetch y_k into xs, each thread polling one value until it is not the
   // sentinel (an 8-byte aligned store is seen whole or not at all); with a
   // warp polling two values a lane, the second poll cost a round trip more
@@ -463,13 +486,11 @@ __global__ void __launch_bounds__(TRSV_THREADS)
   volatile int* fail = &s_fail;
   auto fetch = [&](int k) {
     const int k0 = k * TB, ks = min(TB, n - k0);
-    {  // one value a thread (TB * cg <= TRSV_THREADS): every value is polled at once
-      for (int e = t; e < TB * cg; e += TRSV_THREADS) {
-        const int i = e / cg, c = e - i * cg;
-        double val = 0.0;
-        if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
-        xs[i][c] = val;
-      }
+    for (int e = t; e < TB * cg; e += TRSV_THREADS) {  // one value a thread: all polled at once
+      const int i = e / cg, c = e - i * cg;
+      double val = 0.0;
+      if (i < ks) val = poll_published(y + static_cast<int64_t>(k0 + i) * R + c0 + c, fail, err);
+      xs[i][c] = val;
     }
   };
   for (int s = 0; s < ntile; ++s) {
@@ -478,29 +499,48 @@ __global__ void __launch_bounds__(TRSV_THREADS)
     fetch(LOWER ? s : nblk - 1 - s);
     cp_async_wait1();  // this thread's copies of tile s have landed
     __syncthreads();
-    trsv_tile_product<float, TB + 1>(Fs + (s & 1) * TB * (TB + 1), xs, acc, cg, true);
+    trsv_tile_product<float, LD, RS>(Fs + (s & 1) * RS * LD, xs, acc + r0, cg, true);
     __syncthreads();
   }
-  // z_b = Dinv_b acc (rows past a partial block come out 0: acc and the
-  // inverse's padding are zero / identity there)
+  // the exchange of acc rows between the slices
+  if (first) {
+    for (int e = t; e < RS * cg; e += TRSV_THREADS) {
+      const int i = e / cg, c = e - i * cg;
+      if (r0 + i < bs)
+        st_relaxed_gpu(xch + static_cast<int64_t>(b0 + r0 + i) * R + c0 + c, acc[r0 + i][c]);
+    }
+  } else {
+    const int o0 = LOWER ? r0 - RS : r0 + RS;  // the other slice's rows
+    for (int e = t; e < RS * cg; e += TRSV_THREADS) {
+      const int i = e / cg, c = e - i * cg;
+      if (o0 + i < bs)
+        acc[o0 + i][c] = poll_published(xch + static_cast<int64_t>(b0 + o0 + i) * R + c0 + c, fail, err);
+    }
+  }
+  // z = rows S of Dinv_b acc (rows past a partial block come out 0: acc and
+  // the inverse's padding are zero / identity there)
   __syncthreads();
-  trsv_tile_product<double, TB + 1>(Ds, acc, step > 0 ? zs : xs, cg, false);
+  trsv_tile_product<double, LD, RS>(Ds, acc, zs, cg, false);
   __syncthreads();
-  if (step > 0) {  // y_b = z_b - G_b y_p, p the last predecessor
+  if (step > 1) {  // z -= G2_b y_q
+    fetch(LOWER ? b - 2 : b + 2);
+    __syncthreads();
+    trsv_tile_product<double, LD, RS>(G2s, xs, zs, cg, true);
+    __syncthreads();
+  }
+  if (step > 0) {  // y_b = z - G_b y_p
     fetch(LOWER ? b - 1 : b + 1);
     __syncthreads();
-    trsv_tile_product<double, TB + 1>(Gs, xs, zs, cg, true);
-    __syncthreads();
-    for (int e = t; e < TB * cg; e += TRSV_THREADS) {
-      const int i = e / cg, c = e - i * cg;
-      xs[i][c] = zs[i][c];
-    }
+    trsv_tile_product<double, LD, RS>(Gs, xs, zs, cg, true);
     __syncthreads();
   }
   // publish: the values themselves are the signal (no flag, no fence)
-  for (int e = t; e < bs * cg; e += TRSV_THREADS) {
+  for (int e = t; e < RS * cg; e += TRSV_THREADS) {
     const int i = e / cg, c = e - i * cg;
-    st_relaxed_gpu(y + static_cast<int64_t>(b0 + i) * R + c0 + c, xs[i][c]);
+    if (r0 + i >= bs) continue;
+    const int64_t o = static_cast<int64_t>(b0 + r0 + i) * R + c0 + c;
+    st_relaxed_gpu(y + o, zs[i][c]);
+    if (out) out[o] = zs[i][c];
   }
 }
 
@@ -845,8 +885,14 @@ __global__ void __launch_bounds__(XMV_THREADS)
   }
 }
 
-constexpr size_t kTrsvSmem = 2 * sizeof(double) * TB * (TB + 1) + 2 * sizeof(float) * TB * (TB + 1) +
-                             3 * sizeof(double) * TB * (TRSV_CG + 1);
+constexpr size_t kTrsvSmemUsed = 3 * sizeof(double) * TRSV_RS * (TB + 1) +
+                                 2 * sizeof(float) * TRSV_RS * (TB + 1) +
+                                 sizeof(double) * (2 * TB + TRSV_RS) * (TRSV_CG + 1);
+// launched with more than half an SM's shared memory, so no two CTAs of a
+// triangular solve share an SM: every CTA runs a 64 x 64 FP64 tile product
+// for each block that arrives, and two on one SM's FP64 pipe stretch every
+// step of the chain
+constexpr size_t kTrsvSmem = kTrsvSmemUsed > 120 * 1024 ? kTrsvSmemUsed : 120 * 1024;
 
 // x += d on active columns; dn[c] = max|d|, xn[c] = max|x| (must start at 0).
 __global__ void ir_update_kernel(double* __restrict__ x, int64_t ldx, const double* __restrict__ d,
@@ -1530,14 +1576,15 @@ struct IrWs {
   double* norms;  // [0] anorm, then per column: bn, dn, xn, rn
   double* Linv;   // inverses of the 64 x 64 diagonal blocks of L, then of U
   double* Uinv;
-  double* Lg;     // chain matrices G_b = Linv_b L[b, b-1] and Uinv_b U[b, b+1]
-  double* Ug;
+  double* Lg;     // chain matrices Linv_b L[b, b-1] (block b), Linv_b L[b, b-2] (nblk + b)
+  double* Ug;     // the same for U with U[b, b+1], U[b, b+2]
+  double* xch;    // triangular solves' exchange of row-slice sums (2 n x nrhs)
   double* y1;     // forward-solve result (sentinel-filled between solves)
   double* XL;     // L^-1 and U^-1 in FP64 (GMRES only), 64 x 64 blocks in solve order
   double* XU;
   double* Hl;     // inverse-scaled blocks Linv_b L[b, k] (GMRES only, in place of XL)
   double* Hu;     // the same for U (in place of XU)
-  double* y2;     // backward-solve result of the row-sliced solve (GMRES only)
+  double* y2;     // backward-solve output of the triangular solves (published values)
   int32_t* tsync; // triangular-solve tickets, one per triangle
   int32_t* live;  // asynchronous solve: columns still refining (0: later steps skip)
   IraState* ira;  // asynchronous solve: per-column stop state
@@ -1579,9 +1626,11 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
   const int64_t nblk = (n + TB - 1) / TB;
   w.Linv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
   w.Uinv = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
-  w.Lg = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
-  w.Ug = reinterpret_cast<double*>(take(sizeof(double) * nblk * TB * TB));
+  w.Lg = reinterpret_cast<double*>(take(sizeof(double) * 2 * nblk * TB * TB));
+  w.Ug = reinterpret_cast<double*>(take(sizeof(double) * 2 * nblk * TB * TB));
   w.y1 = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
+  w.y2 = reinterpret_cast<double*>(take(sizeof(double) * n * nrhs));
+  w.xch = reinterpret_cast<double*>(take(sizeof(double) * 2 * n * nrhs));
   w.tsync = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2));
   w.live = reinterpret_cast<int32_t*>(take(sizeof(int32_t)));
   w.ira = reinterpret_cast<IraState*>(take(sizeof(IraState) * nrhs));
@@ -1598,7 +1647,6 @@ IrWs carve(void* base, bfx_mode mode, int64_t n, int64_t nrhs, int nb, int gm_m)
     w.XU = reinterpret_cast<double*>(take(sizeof(double) * xblocks * TB * TB));
     w.Hl = w.XL;  // a GMRES phase uses one preconditioner form
     w.Hu = w.XU;
-    w.y2 = reinterpret_cast<double*>(take(sizeof(double) * n * R));
     int64_t rows = std::max<int64_t>(1, GM_ELEMS / R);
     int64_t nch = ceil_div(n, rows);
     if (nch > GM_MAXCH) {
@@ -1668,7 +1716,8 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s,
     launch_pdl(ir_gather_kernel, dim3(static_cast<unsigned>(grid_elems(n * nrhs))), 256, 0, s,
                static_cast<const double*>(w.r), static_cast<int64_t>(nrhs),
                static_cast<const int32_t*>(w.perm), n, nrhs, w.d, static_cast<int64_t>(nrhs),
-               static_cast<double*>(nullptr), static_cast<double*>(nullptr), static_cast<int*>(nullptr),
+               static_cast<double*>(nullptr), static_cast<double*>(nullptr),
+               static_cast<double*>(nullptr), static_cast<int*>(nullptr),
                gate);
     inverse_mv<true>(w.XL, n, nrhs, w.d, w.y1, s);
     inverse_mv<false>(w.XU, n, nrhs, w.y1, w.d, s);
@@ -1678,7 +1727,7 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s,
     const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
     const unsigned hgrid = static_cast<unsigned>(nblk * G * TRSV_S);
     ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                          w.y1, w.y2, w.tsync, gate);
+                                                          w.y1, w.y2, nullptr, w.tsync, gate);
     ir_trsv_h_kernel<true><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hl, w.Linv, N, w.d, w.y1, nullptr,
                                                           nrhs, w.tsync, err);
     ir_trsv_h_kernel<false><<<hgrid, TRSV_THREADS, 0, s>>>(w.Hu, w.Uinv, N, w.y1, w.y2, w.d,
@@ -1686,13 +1735,15 @@ bfx_status lu_solve64(const IrWs& w, int64_t n, int nrhs, cudaStream_t s,
     return last_launch_status();
   }
   const int G = static_cast<int>(ceil_div(nrhs, TRSV_CG));
-  const unsigned grid = static_cast<unsigned>(nblk * G);
+  const unsigned grid = static_cast<unsigned>(nblk * G * TRSV_SLICES);
+  // d = P r; both triangles' outputs set to the sentinel; L y1 = d; U y2 = y1
+  // with the result also copied into d
   ir_gather_kernel<<<grid_elems(n * nrhs), 256, 0, s>>>(w.r, nrhs, w.perm, n, nrhs, w.d, nrhs,
-                                                        w.y1, nullptr, w.tsync, gate);
-  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Linv, w.Lg, w.d, w.y1,
-                                                             nrhs, w.tsync, err, gate);
-  ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(w.LU, n, N, w.Uinv, w.Ug, w.y1, w.d,
-                                                              nrhs, w.tsync + 1, err, gate);
+                                                        w.y1, w.y2, w.xch, w.tsync, gate);
+  ir_trsv_kernel<true><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(
+      w.LU, n, N, w.Linv, w.Lg, w.d, w.y1, nullptr, w.xch, nrhs, w.tsync, err, gate);
+  ir_trsv_kernel<false><<<grid, TRSV_THREADS, kTrsvSmem, s>>>(
+      w.LU, n, N, w.Uinv, w.Ug, w.y1, w.y2, w.d, w.xch + n * nrhs, nrhs, w.tsync + 1, err, gate);
   return last_launch_status();
 }
 
@@ -2403,7 +2454,7 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n,
                             n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return BFX_ECUDA;
-      st = lu_factor(cur, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s);
+      st = lu_factor(cur, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s, w.perm);
       if (st != BFX_OK) return st;
       int32_t info = 0;
       if (cudaMemcpyAsync(&info, w.info, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
@@ -2413,15 +2464,11 @@ BFX_API bfx_status bfx_solve_ir(bfx_mode mode, int64_t n, int64_t nrhs, const fl
       h_result->info = info;
       if (info != 0) return BFX_SINGULAR;
       const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
-      ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
-      ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
-      if (nblk > 1) {
-        ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
-        ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
-      }
+      ir_diag_inverse_kernel<<<2 * nblk, TB, 0, s>>>(w.LU, n, N, w.Linv, w.Uinv);
+      if (nblk > 1)
+        ir_chain_kernel<<<dim3(2 * (nblk - 1), TB / CHAIN_HALF, 2), 256, 0, s>>>(w.LU, n, N, w.Linv,
+                                                                            w.Uinv, w.Lg, w.Ug);
       x_ready = false;
-      const bool sm = n <= 6144;  // both int arrays fit the default 48 KB of shared memory
-      ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
     }
     if (cudaMemcpyAsync(w.active, act.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
@@ -2587,18 +2634,15 @@ BFX_API bfx_status bfx_solve_ir_async(bfx_mode mode, int64_t n, int64_t nrhs, co
   if (cudaMemcpy2DAsync(w.LU, sizeof(float) * n, d_A, sizeof(float) * lda, sizeof(float) * n, n,
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return BFX_ECUDA;
-  if ((st = lu_factor(mode, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s)) != BFX_OK)
+  if ((st = lu_factor(mode, n, p.nb, w.LU, n, w.ipiv, w.info, w.luws, w.luws_bytes, s, w.perm)) !=
+      BFX_OK)
     return st;
   ira_start_kernel<<<cgrid, 256, 0, s>>>(w.info, R, w.active, w.live, w.ira);
   const unsigned nblk = static_cast<unsigned>(ceil_div(n, TB));
-  ir_diag_inverse_kernel<true><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Linv);
-  ir_diag_inverse_kernel<false><<<nblk, TB, 0, s>>>(w.LU, n, N, w.Uinv);
-  if (nblk > 1) {
-    ir_chain_kernel<true><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Linv, w.Lg);
-    ir_chain_kernel<false><<<nblk - 1, 256, 0, s>>>(w.LU, n, N, w.Uinv, w.Ug);
-  }
-  const bool sm = n <= 6144;
-  ir_perm_kernel<<<1, 1024, sm ? 2 * sizeof(int32_t) * n : 0, s>>>(w.ipiv, N, w.perm, sm);
+  ir_diag_inverse_kernel<<<2 * nblk, TB, 0, s>>>(w.LU, n, N, w.Linv, w.Uinv);
+  if (nblk > 1)
+    ir_chain_kernel<<<dim3(2 * (nblk - 1), TB / CHAIN_HALF, 2), 256, 0, s>>>(w.LU, n, N, w.Linv, w.Uinv,
+                                                                        w.Lg, w.Ug);
   // ---- x0 = LU^-1 P b
   if (cudaMemcpy2DAsync(w.r, sizeof(double) * R, d_b, sizeof(double) * ldb, sizeof(double) * R, n,
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)

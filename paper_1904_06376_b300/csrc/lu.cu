@@ -589,8 +589,8 @@ __device__ __forceinline__ void swapset_warp(const int* __restrict__ piv, int j0
 // (blockDim = LASWP_THREADS).
 __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, int j0, int jb,
                                            const int32_t* __restrict__ ipiv, int c0, int n0,
-                                           int c1, int n1, int cb0, int cstep) {
-  __shared__ SwapSet ss;
+                                           int c1, int n1, int cb0, int cstep, SwapSet* ssp) {
+  SwapSet& ss = *ssp;
   __shared__ __align__(16) int piv[128];
   __shared__ int sp[128];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -618,12 +618,28 @@ __device__ __forceinline__ void laswp_body(float* __restrict__ A, int64_t lda, i
   }
 }
 
-// Columns [c0, c0 + n0) ++ [c1, c1 + n1) of one matrix.
+// Columns [c0, c0 + n0) ++ [c1, c1 + n1) of one matrix.  perm (optional,
+// n rows): the row permutation so far, perm[i] = the original row now at
+// row i; CTA 0 applies the block's swaps to it as to one more column (for
+// j0 == 0 it starts from the identity).  The launches for consecutive
+// blocks run in order, so perm ends as P of P A = L U.
 __global__ void __launch_bounds__(LASWP_THREADS)
     lu_laswp_kernel(float* __restrict__ A, int64_t lda, int j0, int jb,
-                    const int32_t* __restrict__ ipiv, int c0, int n0, int c1, int n1) {
+                    const int32_t* __restrict__ ipiv, int c0, int n0, int c1, int n1,
+                    int32_t* __restrict__ perm, int n) {
+  __shared__ SwapSet ss;
   laswp_body(A, lda, j0, jb, ipiv, c0, n0, c1, n1, static_cast<int>(blockIdx.x),
-             static_cast<int>(gridDim.x));
+             static_cast<int>(gridDim.x), &ss);
+  if (!perm || blockIdx.x != 0) return;
+  static_assert(LASWP_THREADS >= LASWP_SLOTS, "one slot a thread");
+  const int k = threadIdx.x;
+  if (j0 == 0)
+    for (int i = k; i < n; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  const bool on = k < ss.nslots;
+  const int32_t moved = on ? perm[ss.cont[k]] : 0;
+  __syncthreads();
+  if (on) perm[ss.rowid[k]] = moved;
 }
 
 // U12 = L11^-1 A12: forward substitution with the unit lower triangle L11,
@@ -781,8 +797,9 @@ __global__ void __launch_bounds__(LASWP_THREADS)
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
   if (JB <= 0 || static_cast<int>(blockIdx.x) * LASWP_COLS >= b.n - JB) return;
+  __shared__ SwapSet ss;
   laswp_body(b.A, b.n, J0, JB, b.ipiv, 0, J0, J0 + JB, b.n - J0 - JB, static_cast<int>(blockIdx.x),
-             static_cast<int>(gridDim.x));
+             static_cast<int>(gridDim.x), &ss);
 }
 
 template <int NB>
@@ -1271,7 +1288,7 @@ LuWs lu_ws(int np, int64_t n, int nb) {
 }  // namespace
 
 bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, int32_t* ipiv,
-                     int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s) {
+                     int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s, int32_t* perm) {
   if (nb <= 0) nb = 64;
   if (nb > 128) return BFX_EINVAL;
   if (cudaMemsetAsync(info, 0, sizeof(int32_t), s) != cudaSuccess) return BFX_ECUDA;
@@ -1411,13 +1428,13 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     // of the columns left of the block, the row swaps and solve of the
     // columns right of the next one, and their update
     const int c_far = j0 + jb + nc, n_far = N - c_far;
-    if (j0 + n_far > 0) {
+    if (j0 + n_far > 0 || perm) {
       if (cudaEventRecord(ev_fork, s) != cudaSuccess ||
           cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
         return BFX_ECUDA;
-      if (j0 > 0)
-        lu_laswp_kernel<<<static_cast<unsigned>(ceil_div(j0, LASWP_COLS)), LASWP_THREADS, 0, aux>>>(
-            A, lda, j0, jb, ipiv, 0, j0, 0, 0);
+      if (j0 > 0 || perm)  // (perm: the block's swaps also go into the permutation)
+        lu_laswp_kernel<<<static_cast<unsigned>(std::max<int64_t>(1, ceil_div(j0, LASWP_COLS))),
+                          LASWP_THREADS, 0, aux>>>(A, lda, j0, jb, ipiv, 0, j0, 0, 0, perm, N);
       if (n_far > 0) {
         solve<<<static_cast<unsigned>(ceil_div(n_far, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
             A, lda, j0, jb, c_far, N, ipiv, np, Up, w.bp, w.kp);
@@ -1537,7 +1554,7 @@ BFX_API bfx_status bfx_lu_bf16xN(bfx_mode mode, int64_t n, int nb, float* d_A, i
   if (n >= INT32_MAX) return BFX_EUNSUPPORTED;
   if (mode != BFX_FP32 && !is_sm103()) return BFX_EUNSUPPORTED;
   return lu_factor(mode, n, nb, d_A, lda, d_ipiv, d_info, d_ws, ws_bytes,
-                   static_cast<cudaStream_t>(stream));
+                   static_cast<cudaStream_t>(stream), nullptr);
 }
 
 }  // extern "C"

@@ -1304,7 +1304,7 @@ __global__ void __launch_bounds__(GM_THREADS)
 }
 
 // ------------------------------------------------------------- batched forms
-constexpr int BIR_THREADS = 256;
+constexpr int BIR_THREADS = 512;
 constexpr int BGM_GIV_E = 4;  // Krylov length of the batched GMRES at most 4 x BIR_THREADS
 
 __device__ __forceinline__ double block_max(double v, double* red) {
@@ -2076,9 +2076,17 @@ __global__ void __launch_bounds__(BIR_THREADS)
           for (int64_t e = t; e < vs; e += BIR_THREADS) {
             const int c = static_cast<int>(e % R);
             if (!s_arn[c]) continue;
-            double u = q.d[e];
-            for (int i = 0; i <= j; ++i) u = fma(-sl.hc[static_cast<int64_t>(i) * R + c], sl.V[i * vs + e], u);
-            q.d[e] = u;
+            // four partial sums over i mod 4 (independent chains), then w -= their sum
+            double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+            int i = 0;
+            for (; i + 3 <= j; i += 4) {
+              u0 = fma(sl.hc[static_cast<int64_t>(i) * R + c], sl.V[i * vs + e], u0);
+              u1 = fma(sl.hc[static_cast<int64_t>(i + 1) * R + c], sl.V[(i + 1) * vs + e], u1);
+              u2 = fma(sl.hc[static_cast<int64_t>(i + 2) * R + c], sl.V[(i + 2) * vs + e], u2);
+              u3 = fma(sl.hc[static_cast<int64_t>(i + 3) * R + c], sl.V[(i + 3) * vs + e], u3);
+            }
+            for (; i <= j; ++i) u0 = fma(sl.hc[static_cast<int64_t>(i) * R + c], sl.V[i * vs + e], u0);
+            q.d[e] -= (u0 + u1) + (u2 + u3);
           }
           __syncthreads();
         }

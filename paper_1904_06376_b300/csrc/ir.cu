@@ -1391,8 +1391,9 @@ __global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restri
 }
 
 // d <- U^-1 L^-1 P r for one system in one CTA: blocks in sequence, each
-// block's inverse applied (a thread per row and column), then the rows still
-// to solve updated.
+// block's inverse applied (Q threads an output, their partial sums added by
+// shuffle), then the rows still to solve updated (a thread a row and column,
+// four independent partial sums).
 __device__ void bir_solve_body(const BatchIr& q) {
   __shared__ double y[TB][MAXR + 1];
   const int n = q.n, R = q.nrhs, t = threadIdx.x;
@@ -1402,20 +1403,31 @@ __device__ void bir_solve_body(const BatchIr& q) {
   }
   __syncthreads();
   const int nblk = (n + TB - 1) / TB;
+  // the largest power of two Q <= 8 with TB R Q <= BIR_THREADS: TB R Q is a
+  // multiple of 64, so whole warps take part in the shuffles or leave
+  int Q = 8;
+  while (Q > 1 && TB * R * Q > BIR_THREADS) Q >>= 1;
+  const int len = TB / Q;
   for (int pass = 0; pass < 2; ++pass) {
     const bool lower = pass == 0;
     for (int bb = 0; bb < nblk; ++bb) {
       const int blk = lower ? bb : nblk - 1 - bb;
       const int b0 = blk * TB, bs = min(TB, n - b0);
       const double* D = (lower ? q.Linv : q.Uinv) + static_cast<int64_t>(blk) * TB * TB;
-      for (int e = t; e < bs * R; e += BIR_THREADS) {
-        const int i = e / R, c = e % R;
+      for (int e = t; e < TB * R * Q; e += BIR_THREADS) {  // one pass when TB R <= BIR_THREADS
+        const int o = e / Q, qq = e - o * Q;
+        const int i = o / R, c = o - i * R;
+        const int l0 = qq * len, l1 = min(l0 + len, bs);
         double s0 = 0.0, s1 = 0.0;
-        for (int l = 0; l < bs; l += 2) {
+        int l = l0;
+        for (; l + 1 < l1; l += 2) {
           s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
-          if (l + 1 < bs) s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
+          s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
         }
-        y[i][c] = s0 + s1;
+        if (l < l1) s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+        double sum = s0 + s1;
+        for (int o2 = 1; o2 < Q; o2 <<= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o2);
+        if (qq == 0 && i < bs) y[i][c] = sum;
       }
       __syncthreads();
       for (int e = t; e < bs * R; e += BIR_THREADS) {
@@ -1426,12 +1438,16 @@ __device__ void bir_solve_body(const BatchIr& q) {
       for (int e = t; e < (re - rs) * R; e += BIR_THREADS) {
         const int i = rs + e / R, c = e % R;
         const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
-        double s0 = 0.0, s1 = 0.0;
-        for (int l = 0; l < bs; l += 2) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int l = 0;
+        for (; l + 3 < bs; l += 4) {
           s0 = fma(widen(fr[l]), y[l][c], s0);
-          if (l + 1 < bs) s1 = fma(widen(fr[l + 1]), y[l + 1][c], s1);
+          s1 = fma(widen(fr[l + 1]), y[l + 1][c], s1);
+          s2 = fma(widen(fr[l + 2]), y[l + 2][c], s2);
+          s3 = fma(widen(fr[l + 3]), y[l + 3][c], s3);
         }
-        q.d[static_cast<int64_t>(i) * R + c] -= s0 + s1;
+        for (; l < bs; ++l) s0 = fma(widen(fr[l]), y[l][c], s0);
+        q.d[static_cast<int64_t>(i) * R + c] -= (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
     }

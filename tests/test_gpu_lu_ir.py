@@ -116,6 +116,32 @@ def test_solve_ir_vs_oracle(bfx, orc, mode, kappa):
         assert np.max(np.abs(x - xo)) <= 8 * kappa * 2.0 ** -53 * np.max(np.abs(xo))
 
 
+@pytest.mark.parametrize("mode", [0, 3])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (37, 2), (64, 1), (65, 5), (128, 3), (300, 1),
+                                    (300, 9), (1000, 4), (1111, 1)])
+def test_correction_solve_vs_oracle_with_same_factors(bfx, orc, mode, n, nrhs):
+    """The solve of Sec. III's correction equation in isolation: x0 =
+    U^-1 L^-1 P b with the device's FP32 factors (the refinement's first
+    solution, no correction) against the oracle's FP64 dgetrs with the same
+    factors and pivots, element by element.  Covers one block and partial
+    last blocks, column groups of 4 with a ragged last group, and the row
+    permutation the LU builds on the side."""
+    P = bi.svd_system(n, 1e2, 40 + n, nrhs=nrhs)
+    A = torch.from_numpy(P.A32).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    LU, ipiv, info = _lu_gpu(bfx, mode, P.A32, 64)
+    assert info == 0
+    x0, res, code = bfx.solve_ir(mode, A, b, max_iter=0, escalate=False, gmres=0)
+    x0 = x0.cpu().numpy()
+    xo = orc.dgetrs(LU.astype(np.float64), ipiv, P.b)
+    # two FP64 evaluations of the same triangular solves in different sum
+    # orders: relative to max |x| per column, far below the factors' own
+    # error (~1e-6 here) and above the order effects (~n kappa 2^-53)
+    scale = np.max(np.abs(xo), axis=0)
+    assert np.all(np.max(np.abs(x0 - xo), axis=0) <= 1e-11 * scale), (
+        np.max(np.abs(x0 - xo), axis=0) / scale)
+
+
 def test_solve_ir_escalates_x3_at_high_condition(bfx, orc):
     """cond 1e6 is beyond x3-factor refinement; escalation to x6 converges."""
     P = bi.svd_system(256, 1e6, 3)

@@ -11,8 +11,8 @@
  * caller-provided workspace whose size a *_workspace_size query returns.  Two
  * host-thread resources are created once and kept until the thread ends:
  * the LU's auxiliary stream and two events (on the thread's first LU call on
- * a device) and, for the GMRES phase of bfx_solve_ir, a small pinned host
- * ring with its events.  The batch, autotune and server calls allocate as
+ * a device) and, for the GMRES phase of bfx_solve_ir, a small pinned,
+ * device-mapped host ring of flags with its events.  The batch, autotune and server calls allocate as
  * each says.  Matrices are row-major with a leading dimension (elements
  * between the starts of consecutive rows).  bfloat16 values travel as their
  * 16-bit patterns in uint16_t.

@@ -98,9 +98,10 @@ BFX_API int bfx_num_sms(void);
 /* Read and clear the device error word of the current device.  Kernels whose
  * waits are bounded (tensor-core GEMM pipeline barriers, the refinement's
  * triangular solves waiting on earlier row blocks, the LU panel's pivot
- * exchange between the CTAs of a cluster) set it instead of hanging: 0 = no
+ * exchange between the CTAs of a cluster, the batched GMRES-IR's exchanges
+ * between the two CTAs of a hard system) set it instead of hanging: 0 = no
  * error, otherwise a code naming the wait that expired (1-5 GEMM pipeline,
- * 6 triangular solve, 7 LU panel).
+ * 6 triangular solve, 7 LU panel, 8 batched GMRES-IR).
  * Synchronises `stream`.  h_code: host int (output). */
 BFX_API bfx_status bfx_device_error(int* h_code, bfx_stream stream);
 

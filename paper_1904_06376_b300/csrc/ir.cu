@@ -1394,10 +1394,31 @@ __global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restri
     diag_inverse_body<false>(q.LU, q.n, q.n, blk, q.Uinv + static_cast<int64_t>(blk) * TB * TB);
 }
 
+// d[i] -= F[i, b0 .. b0+bs) y for rows rs <= i < re (F the system's FP32
+// factors): a warp a row, lanes over the block's columns (coalesced reads of
+// the factor row), the products summed by shuffle.
+__device__ __forceinline__ void block_row_update(const BatchIr& q, const double (*y)[MAXR + 1],
+                                                 int b0, int bs, int rs, int re) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = q.n, R = q.nrhs;
+  const bool in0 = lane < bs, in1 = lane + 32 < bs;
+  for (int i = rs + wid; i < re; i += nw) {
+    const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
+    const double f0 = in0 ? widen(fr[lane]) : 0.0, f1 = in1 ? widen(fr[lane + 32]) : 0.0;
+    for (int c = 0; c < R; ++c) {
+      double sum = fma(f1, in1 ? y[lane + 32][c] : 0.0, f0 * (in0 ? y[lane][c] : 0.0));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+      if (lane == 0) q.d[static_cast<int64_t>(i) * R + c] -= sum;
+    }
+  }
+}
+
 // d <- U^-1 L^-1 P r for one system in one CTA: blocks in sequence, each
 // block's inverse applied (Q threads an output, their partial sums added by
 // shuffle), then the rows still to solve updated (a thread a row and column,
-// four independent partial sums).
+// four independent partial sums: with many systems resident an SM this
+// beats the coalesced warp-a-row form of block_row_update).
 __device__ void bir_solve_body(const BatchIr& q) {
   __shared__ double y[TB][MAXR + 1];
   const int n = q.n, R = q.nrhs, t = threadIdx.x, NT = blockDim.x;
@@ -1986,6 +2007,208 @@ __device__ __forceinline__ BgmSlot bgm_carve(double* base, int mm, int n, int R)
   return sl;
 }
 
+// ---- groups of CTAs on one hard system (batched GMRES-IR)
+// BGM_GROUP CTAs share a system: CTA rank r owns whole 64-row blocks
+// [r nbr, (r+1) nbr) (nbr = ceil(nblk / BGM_GROUP)), computes matrix-vector
+// products, dot products and updates on those rows only, and the group
+// combines its partial sums through a mailbox in global memory: each CTA
+// writes its values, then publishes an exchange number with a release
+// store; its partners wait (bounded) for that number with acquire loads and
+// read the values from L2.  Every CTA of a group runs the same control flow
+// on the same combined values (sums taken in rank order), so their decisions
+// agree.  Mailbox slots alternate by exchange parity: a CTA writes slot
+// e & 1 again only at exchange e + 2, which it reaches after its partners
+// have finished reading exchange e.
+constexpr int BGM_GROUP = 2;
+constexpr int kErrWaitGroup = 8;  // device error word: a group exchange expired
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+struct BgmBox {
+  double* data;               // [BGM_GROUP][2][xmax]: exchanged values
+  unsigned long long* seq;    // [BGM_GROUP]: the last exchange each rank published
+  double* ybox;               // [2][nbmax][TB * MAXR]: block results of the triangular solves
+  unsigned long long* yseq;   // [2][nbmax]: the solve each block result belongs to
+  int xmax, nbmax;
+};
+__host__ __device__ inline int64_t bgm_box_doubles(int xmax, int nbmax) {
+  return static_cast<int64_t>(BGM_GROUP) * 2 * xmax + BGM_GROUP +
+         static_cast<int64_t>(2) * nbmax * TB * MAXR + 2 * static_cast<int64_t>(nbmax);
+}
+__device__ __forceinline__ BgmBox bgm_box(double* base, int xmax, int nbmax) {
+  BgmBox b;
+  b.data = base;
+  b.seq = reinterpret_cast<unsigned long long*>(base + static_cast<int64_t>(BGM_GROUP) * 2 * xmax);
+  b.ybox = base + static_cast<int64_t>(BGM_GROUP) * 2 * xmax + BGM_GROUP;
+  b.yseq = reinterpret_cast<unsigned long long*>(b.ybox + static_cast<int64_t>(2) * nbmax * TB * MAXR);
+  b.xmax = xmax;
+  b.nbmax = nbmax;
+  return b;
+}
+// thread 0: wait until *p >= want (4 s of %globaltimer at most)
+__device__ __forceinline__ bool group_wait(const unsigned long long* p, unsigned long long want,
+                                           int* err) {
+  if (ld_acquire_u64(p) >= want) return true;
+  const uint64_t t0 = global_ns();
+  while (ld_acquire_u64(p) < want) {
+    if (global_ns() - t0 > 4000000000ull) {
+      atomicExch(err, kErrWaitGroup);
+      return false;
+    }
+  }
+  return true;
+}
+// res[i] = sum (OP 0) or max of non-negative values (OP 1) over the group's
+// vals[i], i < cnt <= xmax, in rank order; res may alias vals.  All threads
+// call it; false: a wait expired (*fail set, the group leaves).
+template <int OP>
+__device__ bool group_reduce(const BgmBox& bx, int rank, unsigned long long& ex, const double* vals,
+                             double* res, int cnt, int* err, volatile int* fail) {
+  const int t = threadIdx.x, NT = blockDim.x;
+  if (BGM_GROUP == 1) {
+    if (res != vals)
+      for (int i = t; i < cnt; i += NT) res[i] = vals[i];
+    __syncthreads();
+    return true;
+  }
+  const unsigned long long e = ++ex;
+  double* mine = bx.data + (static_cast<int64_t>(rank) * 2 + (e & 1)) * bx.xmax;
+  for (int i = t; i < cnt; i += NT) mine[i] = vals[i];
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    st_release_u64(&bx.seq[rank], e);
+    for (int r = 0; r < BGM_GROUP && !*fail; ++r)
+      if (r != rank && !group_wait(&bx.seq[r], e, err)) *fail = 1;
+  }
+  __syncthreads();
+  if (*fail) return false;
+  for (int i = t; i < cnt; i += NT) {
+    double a = 0.0;
+    for (int r = 0; r < BGM_GROUP; ++r) {
+      const double v =
+          r == rank ? vals[i] : __ldcg(bx.data + (static_cast<int64_t>(r) * 2 + (e & 1)) * bx.xmax + i);
+      if (r == 0 || OP == 0) {
+        a = r == 0 ? v : a + v;
+      } else {  // non-negative doubles order like their bits (NaN above Inf)
+        a = __longlong_as_double(max(static_cast<unsigned long long>(__double_as_longlong(a)),
+                                     static_cast<unsigned long long>(__double_as_longlong(v))));
+      }
+    }
+    res[i] = a;
+  }
+  __syncthreads();
+  return true;
+}
+// the group waits until every rank has reached this point (its earlier
+// global writes visible to the others)
+__device__ __forceinline__ bool group_sync(const BgmBox& bx, int rank, unsigned long long& ex,
+                                           int* err, volatile int* fail) {
+  return group_reduce<0>(bx, rank, ex, nullptr, nullptr, 0, err, fail);
+}
+
+// out = b - A x (b null: out = A x) on rows [lo, hi) of one system (warp a
+// row, four independent partial sums a lane); x is read from L2 (its rows
+// come from the whole group).  Returns the CTA's max |out|.
+__device__ __forceinline__ double bgm_matvec_rows(const float* __restrict__ A, int n, int R,
+                                                  const double* x, const double* __restrict__ b,
+                                                  double* out, int lo, int hi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double rm = 0.0;
+  for (int i = lo + wid; i < hi; i += nw) {
+    const float* a = A + static_cast<int64_t>(i) * n;
+    for (int c = 0; c < R; ++c) {
+      double sum = 0.0;
+      for (int l = lane; l < n; l += 32) sum = fma(widen(a[l]), __ldcg(x + static_cast<int64_t>(l) * R + c), sum);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+      const double v = b ? b[static_cast<int64_t>(i) * R + c] - sum : sum;
+      if (lane == 0) out[static_cast<int64_t>(i) * R + c] = v;
+      rm = fmax(rm, fabs(v));
+    }
+  }
+  return rm;
+}
+
+// d <- U^-1 L^-1 P r on rows [lo, hi) of one system, shared by the group:
+// the owner of each 64-row block applies its inverse and hands the block's
+// result to the others through the mailbox (tagged with the solve number
+// sv); every rank updates its own rows below (L) or above (U) the block.
+// r is read from L2 (its rows come from the whole group).
+__device__ bool bgm_solve(const BatchIr& q, const BgmBox& bx, int rank, int nbr, int lo, int hi,
+                          unsigned long long& sv, int* err, volatile int* fail) {
+  __shared__ double y[TB][MAXR + 1];
+  const int n = q.n, R = q.nrhs, t = threadIdx.x, NT = blockDim.x;
+  for (int e = t; e < (hi - lo) * R; e += NT) {
+    const int i = lo + e / R, c = e % R;
+    q.d[static_cast<int64_t>(i) * R + c] = __ldcg(q.r + static_cast<int64_t>(q.perm[i]) * R + c);
+  }
+  __syncthreads();
+  const unsigned long long tok = ++sv;
+  const int nblk = (n + TB - 1) / TB;
+  int Q = 8;  // as in bir_solve_body
+  while (Q > 1 && TB * R * Q > NT) Q >>= 1;
+  const int len = TB / Q;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lower = pass == 0;
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int blk = lower ? bb : nblk - 1 - bb;
+      const int b0 = blk * TB, bs = min(TB, n - b0);
+      const int owner = min(BGM_GROUP - 1, blk / nbr);
+      if (owner == rank) {
+        const double* D = (lower ? q.Linv : q.Uinv) + static_cast<int64_t>(blk) * TB * TB;
+        for (int e = t; e < TB * R * Q; e += NT) {
+          const int o = e / Q, qq = e - o * Q;
+          const int i = o / R, c = o - i * R;
+          const int l0 = qq * len, l1 = min(l0 + len, bs);
+          double s0 = 0.0, s1 = 0.0;
+          int l = l0;
+          for (; l + 1 < l1; l += 2) {
+            s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+            s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
+          }
+          if (l < l1) s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+          double sum = s0 + s1;
+          for (int o2 = 1; o2 < Q; o2 <<= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o2);
+          if (qq == 0 && i < bs) y[i][c] = sum;
+        }
+        __syncthreads();
+        double* box = bx.ybox + (static_cast<int64_t>(pass) * bx.nbmax + blk) * TB * MAXR;
+        for (int e = t; e < bs * R; e += NT) {
+          const int i = e / R, c = e % R;
+          q.d[static_cast<int64_t>(b0 + i) * R + c] = y[i][c];
+          if (BGM_GROUP > 1) box[e] = y[i][c];
+        }
+        if (BGM_GROUP > 1) {
+          __syncthreads();
+          if (t == 0) {
+            __threadfence();
+            st_release_u64(bx.yseq + pass * bx.nbmax + blk, tok);
+          }
+        }
+      } else {
+        if (t == 0 && !*fail && !group_wait(bx.yseq + pass * bx.nbmax + blk, tok, err)) *fail = 1;
+        __syncthreads();
+        if (*fail) return false;
+        const double* box = bx.ybox + (static_cast<int64_t>(pass) * bx.nbmax + blk) * TB * MAXR;
+        for (int e = t; e < bs * R; e += NT) y[e / R][e % R] = __ldcg(box + e);
+        __syncthreads();
+      }
+      const int rs = max(lower ? b0 + bs : 0, lo), re = min(lower ? n : b0, hi);
+      block_row_update(q, y, b0, bs, rs, re);
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
 // per-column sum of squares of v (n x R) -> out[c] (warp c, c + 8, ...)
 __device__ __forceinline__ void bgm_colnorm(const double* v, int n, int R, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -2003,27 +2226,49 @@ __device__ __forceinline__ void bgm_colnorm(const double* v, int n, int R, doubl
 
 __global__ void __launch_bounds__(BGM_THREADS)
     bgm_kernel(const BatchIr* __restrict__ sys, int S, int* __restrict__ queue,
-               double* __restrict__ slots, int64_t slot_doubles, int m, BatchIrParams p,
-               int max_outer, double tau) {
-  __shared__ double red[BGM_THREADS / 32];
+               double* __restrict__ slots, int64_t slot_doubles, double* __restrict__ boxes,
+               int xmax, int nbmax, int m, BatchIrParams p, int max_outer, double tau,
+               int* __restrict__ err) {
   __shared__ double s_beta[MAXR], s_tmp[MAXR], s_dprev[MAXR], s_dn[MAXR], s_xn[MAXR];
   __shared__ int s_act[MAXR], s_arn[MAXR], s_k[MAXR], s_conv[MAXR], s_stall[MAXR];
-  __shared__ int s_sys, s_any, s_steps;
+  __shared__ int s_sys, s_any, s_steps, s_fail;
   __shared__ double s_gA[BGM_THREADS / 32], s_gB[BGM_THREADS / 32], s_gp;  // Givens scan
+  __shared__ double s_x[2];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   constexpr int NW = BGM_THREADS / 32;
-  double* base = slots + static_cast<int64_t>(blockIdx.x) * slot_doubles;
+  const int rank = static_cast<int>(blockIdx.x) % BGM_GROUP, grp = blockIdx.x / BGM_GROUP;
+  // the group's shared Krylov basis, this rank's Hessenberg data, the mailbox
+  double* base = slots + static_cast<int64_t>(grp) * slot_doubles;
+  const BgmBox bx = bgm_box(boxes + static_cast<int64_t>(grp) * bgm_box_doubles(xmax, nbmax), xmax, nbmax);
+  unsigned long long ex = 0, sv = 0;
+  volatile int* fail = &s_fail;
+  if (t == 0) s_fail = 0;
+  __syncthreads();
   for (;;) {
-    if (t == 0) s_sys = atomicAdd(queue, 1);
+    // rank 0 takes the next system from the queue and hands it to the group
+    if (t == 0) s_x[0] = rank == 0 ? static_cast<double>(atomicAdd(queue, 1)) : 0.0;
     __syncthreads();
-    const int k = s_sys;
-    __syncthreads();
+    if (!group_reduce<0>(bx, rank, ex, s_x, s_x, 1, err, fail)) return;
+    const int k = static_cast<int>(s_x[0]);
     if (k >= S) break;
     const BatchIr q = sys[k];
     if (*q.info != 0 || q.st->conv) continue;
     const int n = q.n, R = q.nrhs, mm = min(m, n);
-    const BgmSlot sl = bgm_carve(base, mm, n, R);
+    const int nblk = (n + TB - 1) / TB, nbr = (nblk + BGM_GROUP - 1) / BGM_GROUP;
+    const int lo = min(n, rank * nbr * TB), hi = min(n, (rank + 1) * nbr * TB);
+    BgmSlot sl = bgm_carve(base, mm, n, R);
+    {  // this rank's own copy of the small arrays (after the shared basis)
+      const int64_t small = static_cast<int64_t>(R) * mm * (mm + 1) + (mm + 1) * R + R * (mm + 1) + 3 * R * mm;
+      const int64_t shift = static_cast<int64_t>(rank) * small;
+      sl.H += shift;
+      sl.hc += shift;
+      sl.g += shift;
+      sl.cs += shift;
+      sl.sn += shift;
+      sl.y += shift;
+    }
     const int64_t vs = static_cast<int64_t>(n) * R;  // one basis vector
+    const int64_t e_lo = static_cast<int64_t>(lo) * R, e_hi = static_cast<int64_t>(hi) * R;
     if (t < R) {
       s_act[t] = 1;
       s_conv[t] = 0;
@@ -2041,11 +2286,13 @@ __global__ void __launch_bounds__(BGM_THREADS)
       __syncthreads();
       if (!s_any) break;
       // ---- r = b - A x, w = M^-1 r, beta = |w|_2, V_0 = w / beta, g = beta e_1
-      bir_matvec(q.A, n, R, q.x, q.b, q.r, red, false);
+      bgm_matvec_rows(q.A, n, R, q.x, q.b, q.r, lo, hi);
       __syncthreads();
-      bir_solve_body(q);
-      bgm_colnorm(q.d, n, R, s_tmp);
+      if (!group_sync(bx, rank, ex, err, fail)) return;
+      if (!bgm_solve(q, bx, rank, nbr, lo, hi, sv, err, fail)) return;
+      bgm_colnorm(q.d + e_lo, hi - lo, R, s_tmp);
       __syncthreads();
+      if (!group_reduce<0>(bx, rank, ex, s_tmp, s_tmp, R, err, fail)) return;
       if (t < R) {
         const double b = sqrt(s_tmp[t]);
         s_beta[t] = b;
@@ -2056,11 +2303,12 @@ __global__ void __launch_bounds__(BGM_THREADS)
         gc[0] = b;
       }
       __syncthreads();
-      for (int64_t e = t; e < vs; e += BGM_THREADS) {
+      for (int64_t e = e_lo + t; e < e_hi; e += BGM_THREADS) {
         const int c = static_cast<int>(e % R);
         if (s_arn[c]) sl.V[e] = q.d[e] / s_beta[c];
       }
       __syncthreads();
+      if (!group_sync(bx, rank, ex, err, fail)) return;
       // ---- Arnoldi
       for (int j = 0; j < mm; ++j) {
         if (t == 0) {
@@ -2071,29 +2319,33 @@ __global__ void __launch_bounds__(BGM_THREADS)
         __syncthreads();
         if (!s_any) break;
         // w = M^-1 A v_j
-        bir_matvec(q.A, n, R, sl.V + j * vs, nullptr, q.r, red, false);
+        bgm_matvec_rows(q.A, n, R, sl.V + j * vs, nullptr, q.r, lo, hi);
         __syncthreads();
-        bir_solve_body(q);
+        if (!group_sync(bx, rank, ex, err, fail)) return;
+        if (!bgm_solve(q, bx, rank, nbr, lo, hi, sv, err, fail)) return;
         for (int pass = 0; pass < 2; ++pass) {
-          // hc[i][c] = <V_i, w> (warp i mod NW), then H(:, j) += hc
+          // hc[i][c] = <V_i, w> on this rank's rows (warp i mod NW), summed
+          // over the group, then H(:, j) += hc
           for (int i = wid; i <= j; i += NW) {
             const double* vi = sl.V + i * vs;
             for (int c = 0; c < R; ++c) {
               double sum = 0.0;
               if (s_arn[c])
-                for (int r = lane; r < n; r += 32)
+                for (int r = lo + lane; r < hi; r += 32)
                   sum = fma(vi[static_cast<int64_t>(r) * R + c], q.d[static_cast<int64_t>(r) * R + c], sum);
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-              if (lane == 0) {
-                sl.hc[static_cast<int64_t>(i) * R + c] = sum;
-                double* hp = sl.H + (static_cast<int64_t>(c) * mm + j) * (mm + 1) + i;
-                *hp = pass ? *hp + sum : sum;
-              }
+              if (lane == 0) sl.hc[static_cast<int64_t>(i) * R + c] = sum;
             }
           }
           __syncthreads();
-          for (int64_t e = t; e < vs; e += BGM_THREADS) {
+          if (!group_reduce<0>(bx, rank, ex, sl.hc, sl.hc, (j + 1) * R, err, fail)) return;
+          for (int e = t; e < (j + 1) * R; e += BGM_THREADS) {
+            const int i = e / R, c = e % R;
+            double* hp = sl.H + (static_cast<int64_t>(c) * mm + j) * (mm + 1) + i;
+            *hp = pass ? *hp + sl.hc[e] : sl.hc[e];
+          }
+          for (int64_t e = e_lo + t; e < e_hi; e += BGM_THREADS) {
             const int c = static_cast<int>(e % R);
             if (!s_arn[c]) continue;
             // four partial sums over i mod 4 (independent chains), then w -= their sum
@@ -2111,11 +2363,12 @@ __global__ void __launch_bounds__(BGM_THREADS)
           __syncthreads();
         }
         // h_{j+1,j} = |w|_2, V_{j+1} = w / h, Givens (thread c)
-        bgm_colnorm(q.d, n, R, s_tmp);
+        bgm_colnorm(q.d + e_lo, hi - lo, R, s_tmp);
         __syncthreads();
+        if (!group_reduce<0>(bx, rank, ex, s_tmp, s_tmp, R, err, fail)) return;
         if (t < R) s_tmp[t] = sqrt(s_tmp[t]);
         __syncthreads();
-        for (int64_t e = t; e < vs; e += BGM_THREADS) {
+        for (int64_t e = e_lo + t; e < e_hi; e += BGM_THREADS) {
           const int c = static_cast<int>(e % R);
           if (s_arn[c] && s_tmp[c] > 0.0) sl.V[(j + 1) * vs + e] = q.d[e] / s_tmp[c];
         }
@@ -2143,6 +2396,7 @@ __global__ void __launch_bounds__(BGM_THREADS)
           if (res <= tau * s_beta[c] || !(hj > 0.0) || j + 1 >= mm || !(res == res)) s_arn[c] = 0;
         }
         __syncthreads();
+        if (!group_sync(bx, rank, ex, err, fail)) return;  // V_{j+1} whole before the next product
       }
       // ---- y = R_k^-1 g_k (warp per column, lanes split each row's sum)
       for (int c = wid; c < R; c += NW) {
@@ -2168,7 +2422,7 @@ __global__ void __launch_bounds__(BGM_THREADS)
         s_xn[t] = 0.0;
       }
       __syncthreads();
-      for (int64_t e = t; e < vs; e += BGM_THREADS) {
+      for (int64_t e = e_lo + t; e < e_hi; e += BGM_THREADS) {
         const int c = static_cast<int>(e % R);
         if (!s_act[c]) continue;
         const double* yc = sl.y + static_cast<int64_t>(c) * mm;
@@ -2180,6 +2434,8 @@ __global__ void __launch_bounds__(BGM_THREADS)
         atomic_max_nonneg(&s_xn[c], fabs(xv));
       }
       __syncthreads();
+      if (!group_reduce<1>(bx, rank, ex, s_dn, s_dn, R, err, fail)) return;
+      if (!group_reduce<1>(bx, rank, ex, s_xn, s_xn, R, err, fail)) return;
       if (t < R && s_act[t]) {
         const double dn = s_dn[t], xn = s_xn[t];
         if (!(dn == dn) || !(xn == xn)) {
@@ -2198,11 +2454,19 @@ __global__ void __launch_bounds__(BGM_THREADS)
       __syncthreads();
     }
     // ---- backward error as bir_finish_kernel; converged if every column is
-    const double rn = bir_matvec(q.A, n, R, q.x, q.b, q.r, red, true);
-    double xm = 0.0;
-    for (int64_t e = t; e < vs; e += BGM_THREADS) xm = fmax(xm, fabs(q.x[e]));
-    const double xn = block_max(xm, red);
-    if (t == 0) {
+    if (t < 2) s_x[t] = 0.0;
+    __syncthreads();
+    {
+      const double rm = bgm_matvec_rows(q.A, n, R, q.x, q.b, q.r, lo, hi);
+      double xm = 0.0;
+      for (int64_t e = e_lo + t; e < e_hi; e += BGM_THREADS) xm = fmax(xm, fabs(q.x[e]));
+      atomic_max_nonneg(&s_x[0], rm);
+      atomic_max_nonneg(&s_x[1], xm);
+    }
+    __syncthreads();
+    if (!group_reduce<1>(bx, rank, ex, s_x, s_x, 2, err, fail)) return;
+    const double rn = s_x[0], xn = s_x[1];
+    if (t == 0 && rank == 0) {
       BatchIrState* st = q.st;
       const double den = st->anorm * xn + st->bnorm;
       double be = den > 0.0 ? rn / den : 0.0;
@@ -2342,20 +2606,38 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
+// mailbox sizes of a group: any nrhs <= MAXR, any n <= BIR_MAXN
+int bgm_xmax(int m) { return std::max(2, (m + 1) * MAXR); }
+constexpr int kBgmNbMax = (BIR_MAXN + TB - 1) / TB;
+
+// nslots slots of slot_doubles each (batched_gmres_slot_doubles): the groups'
+// mailboxes first (cleared here, so every launch starts its exchange
+// numbers from zero), then each group's Krylov basis and its ranks' small
+// arrays.  One group of BGM_GROUP CTAs a slot, at most one CTA an SM.
 bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_slots,
                             int64_t slot_doubles, int nslots, int m, BatchIrParams p,
                             int max_outer, double tau, cudaStream_t s) {
   if (S <= 0 || nslots <= 0) return BFX_OK;
   if (m > BGM_GIV_E * BGM_THREADS) return BFX_EINVAL;  // the Givens scan's rows per thread
-  if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return BFX_ECUDA;
-  bgm_kernel<<<nslots, BGM_THREADS, 0, s>>>(d_ir, S, d_queue, d_slots, slot_doubles, m, p,
-                                            max_outer, tau);
+  int* err = device_error_word();
+  if (!err) return BFX_ECUDA;
+  const int sms = current_num_sms() > 0 ? current_num_sms() : 148;
+  const int groups = std::max(1, std::min(nslots, sms / BGM_GROUP));
+  const int xmax = bgm_xmax(m);
+  const int64_t box = bgm_box_doubles(xmax, kBgmNbMax);
+  if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(d_slots, 0, sizeof(double) * box * nslots, s) != cudaSuccess)
+    return BFX_ECUDA;
+  bgm_kernel<<<groups * BGM_GROUP, BGM_THREADS, 0, s>>>(
+      d_ir, S, d_queue, d_slots + box * nslots, slot_doubles - box, d_slots, xmax, kBgmNbMax, m, p,
+      max_outer, tau, err);
   return last_launch_status();
 }
 
 int64_t batched_gmres_slot_doubles(int m, int nmax, int R) {
   const int64_t mm = std::min(m, nmax);
-  return (mm + 1) * nmax * R + R * mm * (mm + 1) + (mm + 1) * R + R * (mm + 1) + 3 * R * mm;
+  const int64_t small = R * mm * (mm + 1) + (mm + 1) * R + R * (mm + 1) + 3 * R * mm;
+  return (mm + 1) * nmax * R + BGM_GROUP * small + bgm_box_doubles(bgm_xmax(m), kBgmNbMax);
 }
 
 bfx_status ir_batched_prepare(const BatchIr* d_ir, int S, int nmax, cudaStream_t s) {

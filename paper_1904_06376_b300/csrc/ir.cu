@@ -210,11 +210,12 @@ __global__ void ir_gather_kernel(const double* __restrict__ r, int64_t ldr,
 // above row k (L) or below it (U), so a warp skips the steps whose pivot
 // column is zero in all its lanes' x; U's diagonal enters through its
 // reciprocals (one division a thread).
+// T, rdiag: the caller's shared memory ([TB][TB + 1] and [TB] doubles), one
+// pair a kernel whichever triangle its CTA inverts
 template <bool LOWER>
 __device__ __forceinline__ void diag_inverse_body(const float* __restrict__ F, int64_t ldf, int n,
-                                                  int blk, double* __restrict__ D) {
-  __shared__ double T[TB][TB + 1];
-  __shared__ double rdiag[TB];
+                                                  int blk, double* __restrict__ D,
+                                                  double (*T)[TB + 1], double* rdiag) {
   const int b0 = blk * TB, bs = min(TB, n - b0), k = threadIdx.x;
   for (int e = k; e < TB * TB; e += TB) {
     const int i = e / TB, l = e % TB;
@@ -254,11 +255,14 @@ __global__ void __launch_bounds__(TB) ir_diag_inverse_kernel(const float* __rest
                                                              int64_t ldf, int n,
                                                              double* __restrict__ Linv,
                                                              double* __restrict__ Uinv) {
+  __shared__ double T[TB][TB + 1];
+  __shared__ double rdiag[TB];
   const int nblk = (n + TB - 1) / TB, bx = static_cast<int>(blockIdx.x);
   if (bx < nblk)
-    diag_inverse_body<true>(F, ldf, n, bx, Linv + static_cast<int64_t>(bx) * TB * TB);
+    diag_inverse_body<true>(F, ldf, n, bx, Linv + static_cast<int64_t>(bx) * TB * TB, T, rdiag);
   else
-    diag_inverse_body<false>(F, ldf, n, bx - nblk, Uinv + static_cast<int64_t>(bx - nblk) * TB * TB);
+    diag_inverse_body<false>(F, ldf, n, bx - nblk, Uinv + static_cast<int64_t>(bx - nblk) * TB * TB,
+                             T, rdiag);
 }
 
 // Chain matrices, FP64, once per factorisation: G_b = Dinv_b F[b, p] and
@@ -1362,7 +1366,12 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_prepare_kernel(const BatchIr*
 // pivots; inverses of the diagonal blocks (grid: blocks x systems).
 constexpr int BIR_MAXN = 1024;
 __global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restrict__ sys) {
-  __shared__ int32_t sp[2 * BIR_MAXN];
+  // one shared buffer: the permutation's staging first (CTA 0), then the
+  // inverse's triangle (every CTA holds one block: 34 KB, six CTAs an SM)
+  __shared__ double T[TB][TB + 1];
+  __shared__ double rdiag[TB];
+  static_assert(2 * BIR_MAXN * sizeof(int32_t) <= sizeof(T), "the staging fits the triangle");
+  int32_t* sp = reinterpret_cast<int32_t*>(&T[0][0]);
   const BatchIr q = sys[blockIdx.y];
   const int nblk = (q.n + TB - 1) / TB;
   if (blockIdx.x == 0) {  // the permutation, staged in shared memory
@@ -1384,14 +1393,17 @@ __global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restri
     }
     __syncthreads();
     for (int i = threadIdx.x; i < q.n; i += TB) q.perm[i] = sp[i];
+    __syncthreads();  // the staging is read before the triangle overwrites it
   }
   if (static_cast<int>(blockIdx.x) >= 2 * nblk) return;
   const bool lower = static_cast<int>(blockIdx.x) < nblk;
   const int blk = lower ? blockIdx.x : blockIdx.x - nblk;
   if (lower)
-    diag_inverse_body<true>(q.LU, q.n, q.n, blk, q.Linv + static_cast<int64_t>(blk) * TB * TB);
+    diag_inverse_body<true>(q.LU, q.n, q.n, blk, q.Linv + static_cast<int64_t>(blk) * TB * TB, T,
+                            rdiag);
   else
-    diag_inverse_body<false>(q.LU, q.n, q.n, blk, q.Uinv + static_cast<int64_t>(blk) * TB * TB);
+    diag_inverse_body<false>(q.LU, q.n, q.n, blk, q.Uinv + static_cast<int64_t>(blk) * TB * TB, T,
+                             rdiag);
 }
 
 // d[i] -= F[i, b0 .. b0+bs) y for rows rs <= i < re (F the system's FP32

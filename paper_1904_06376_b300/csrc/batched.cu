@@ -13,6 +13,9 @@
 #include "bfx_internal.cuh"
 
 namespace bfx {
+// refinement step in the latency form (ir.cu)
+bfx_status ir_batched_step_latency(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s);
+
 namespace {
 
 constexpr int kBatchNb = 64;      // default block-column width of the batched LU
@@ -20,6 +23,9 @@ constexpr int kBatchBn = 256;     // default tile width of the grouped trailing 
 constexpr int kBatchMaxN = 1024;  // largest system of a batch
 constexpr int kSolveTB = 64;      // diagonal-block size of the refinement solves
 constexpr int kGmresM = 256;      // Krylov length of the batched GMRES-IR (capped at n)
+// refinement steps from this one on use the latency form (most systems have
+// stopped by then: a step lasts as long as its slowest system's)
+constexpr int kLatencyStep = 5;
 constexpr int kGmresOuter = 20;   // its refinement steps at most
 constexpr double kGmresTau = 1e-10;
 constexpr size_t kGmresSlotBudget = size_t(1) << 30;  // Krylov memory of all slots, at most
@@ -94,7 +100,9 @@ bfx_status enqueue(bfx_batch_plan* P, cudaStream_t s) {
   if ((st = ir_batched_post_lu(ir_tab, P->S, P->nmax, s)) != BFX_OK) return st;
   if ((st = ir_batched_first_solve(ir_tab, P->S, s)) != BFX_OK) return st;
   for (int it = 0; it < P->max_iter; ++it)
-    if ((st = ir_batched_step(ir_tab, P->S, P->p, s)) != BFX_OK) return st;
+    if ((st = (it < kLatencyStep ? ir_batched_step : ir_batched_step_latency)(ir_tab, P->S, P->p, s)) !=
+        BFX_OK)
+      return st;
   if ((st = ir_batched_finish(ir_tab, P->S, P->p, s)) != BFX_OK) return st;
   if (!P->gmres) return BFX_OK;
   return ir_batched_gmres(ir_tab, P->S, reinterpret_cast<int*>(ws + P->o_gm_queue),

@@ -1431,6 +1431,7 @@ __device__ __forceinline__ void block_row_update(const BatchIr& q, const double 
 // shuffle), then the rows still to solve updated (a thread a row and column,
 // four independent partial sums: with many systems resident an SM this
 // beats the coalesced warp-a-row form of block_row_update).
+template <bool WARPROW = false>
 __device__ void bir_solve_body(const BatchIr& q) {
   __shared__ double y[TB][MAXR + 1];
   const int n = q.n, R = q.nrhs, t = threadIdx.x, NT = blockDim.x;
@@ -1472,7 +1473,10 @@ __device__ void bir_solve_body(const BatchIr& q) {
         q.d[static_cast<int64_t>(b0 + i) * R + c] = y[i][c];
       }
       const int rs = lower ? b0 + bs : 0, re = lower ? n : b0;
-      for (int e = t; e < (re - rs) * R; e += NT) {
+      if (WARPROW) {
+        block_row_update(q, y, b0, bs, rs, re);
+      } else {
+        for (int e = t; e < (re - rs) * R; e += NT) {
         const int i = rs + e / R, c = e % R;
         const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -1485,6 +1489,7 @@ __device__ void bir_solve_body(const BatchIr& q) {
         }
         for (; l < bs; ++l) s0 = fma(widen(fr[l]), y[l][c], s0);
         q.d[static_cast<int64_t>(i) * R + c] -= (s0 + s1) + (s2 + s3);
+        }
       }
       __syncthreads();
     }
@@ -1537,14 +1542,20 @@ __device__ double bir_residual_body(const BatchIr& q, double* red, bool want_max
 
 // One refinement step of every active system: r = b - A x, d = LU^-1 P r,
 // x += d, and the stop decision (converged / stalled) on the device.
-__global__ void __launch_bounds__(BIR_THREADS) bir_step_kernel(const BatchIr* __restrict__ sys,
-                                                              BatchIrParams p) {
-  __shared__ double red[BIR_THREADS / 32];
+// LAT: the form for the later steps, when few systems are still active
+// and a step's time is the latency of the slowest: BIR_LAT_THREADS threads
+// and the coalesced warp-a-row block updates (with many systems resident an
+// SM, the default form's thread-a-row updates and three CTAs an SM win).
+constexpr int BIR_LAT_THREADS = 1024;
+template <bool LAT>
+__global__ void __launch_bounds__(LAT ? BIR_LAT_THREADS : BIR_THREADS)
+    bir_step_kernel(const BatchIr* __restrict__ sys, BatchIrParams p) {
+  __shared__ double red[BIR_LAT_THREADS / 32];
   const BatchIr q = sys[blockIdx.x];
   if (!q.st->active) return;
   bir_residual_body(q, red, false);
   __syncthreads();
-  bir_solve_body(q);
+  bir_solve_body<LAT>(q);
   double dm = 0.0, xm = 0.0;
   for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) {
     const double xv = q.x[e] + q.d[e];
@@ -2671,7 +2682,13 @@ bfx_status ir_batched_first_solve(const BatchIr* d_ir, int S, cudaStream_t s) {
 }
 bfx_status ir_batched_step(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s) {
   if (S <= 0) return BFX_OK;
-  bir_step_kernel<<<S, BIR_THREADS, 0, s>>>(d_ir, p);
+  bir_step_kernel<false><<<S, BIR_THREADS, 0, s>>>(d_ir, p);
+  return last_launch_status();
+}
+// the same step in the latency form (later steps of a batch)
+bfx_status ir_batched_step_latency(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s) {
+  if (S <= 0) return BFX_OK;
+  bir_step_kernel<true><<<S, BIR_LAT_THREADS, 0, s>>>(d_ir, p);
   return last_launch_status();
 }
 bfx_status ir_batched_finish(const BatchIr* d_ir, int S, BatchIrParams p, cudaStream_t s) {

@@ -1407,21 +1407,35 @@ __global__ void __launch_bounds__(TB) bir_post_lu_kernel(const BatchIr* __restri
 }
 
 // d[i] -= F[i, b0 .. b0+bs) y for rows rs <= i < re (F the system's FP32
-// factors): a warp a row, lanes over the block's columns (coalesced reads of
-// the factor row), the products summed by shuffle.
+// factors): eight lanes a row, four rows a warp at a time, each lane eight
+// consecutive columns (the eight lanes read the row's 256 bytes together),
+// the eight partial sums added by three shuffles.  A warp a row would add
+// five shuffle levels of FP64 adds to the row's two FMAs a lane, a thread a
+// row would read the factor column-wise.
 __device__ __forceinline__ void block_row_update(const BatchIr& q, const double (*y)[MAXR + 1],
                                                  int b0, int bs, int rs, int re) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = q.n, R = q.nrhs;
-  const bool in0 = lane < bs, in1 = lane + 32 < bs;
-  for (int i = rs + wid; i < re; i += nw) {
-    const float* fr = q.LU + static_cast<int64_t>(i) * n + b0;
-    const double f0 = in0 ? widen(fr[lane]) : 0.0, f1 = in1 ? widen(fr[lane + 32]) : 0.0;
-    for (int c = 0; c < R; ++c) {
-      double sum = fma(f1, in1 ? y[lane + 32][c] : 0.0, f0 * (in0 ? y[lane][c] : 0.0));
+  const int g = lane >> 3, c0 = (lane & 7) * 8;  // row slot in the warp, first column
+  for (int c = 0; c < R; ++c) {
+    double yv[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-      if (lane == 0) q.d[static_cast<int64_t>(i) * R + c] -= sum;
+    for (int k = 0; k < 8; ++k) yv[k] = c0 + k < bs ? y[c0 + k][c] : 0.0;
+    for (int i0 = rs + wid * 4; i0 < re; i0 += nw * 4) {
+      const int i = i0 + g;
+      const bool ok = i < re;
+      const float* fr = q.LU + static_cast<int64_t>(ok ? i : i0) * n + b0 + c0;
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        if (ok && c0 + k < bs) s0 = fma(widen(fr[k]), yv[k], s0);
+        if (ok && c0 + k + 1 < bs) s1 = fma(widen(fr[k + 1]), yv[k + 1], s1);
+      }
+      double sum = s0 + s1;
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 4);
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 2);
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+      if (ok && (lane & 7) == 0) q.d[static_cast<int64_t>(i) * R + c] -= sum;
     }
   }
 }
@@ -2160,14 +2174,62 @@ __device__ __forceinline__ double bgm_matvec_rows(const float* __restrict__ A, i
   return rm;
 }
 
+// y = D_blk d[block blk] (the block's inverse, Q threads an output) into ys,
+// written back into d; published in the mailbox for the other ranks when
+// the group has more than one CTA.  All threads call it.
+__device__ __forceinline__ void bgm_block_inverse(const BatchIr& q, const BgmBox& bx, int pass,
+                                                  int blk, unsigned long long tok,
+                                                  double (*ys)[MAXR + 1]) {
+  const int n = q.n, R = q.nrhs, t = threadIdx.x, NT = blockDim.x;
+  const int b0 = blk * TB, bs = min(TB, n - b0);
+  int Q = 8;  // as in bir_solve_body
+  while (Q > 1 && TB * R * Q > NT) Q >>= 1;
+  const int len = TB / Q;
+  const double* D = (pass == 0 ? q.Linv : q.Uinv) + static_cast<int64_t>(blk) * TB * TB;
+  for (int e = t; e < TB * R * Q; e += NT) {
+    const int o = e / Q, qq = e - o * Q;
+    const int i = o / R, c = o - i * R;
+    const int l0 = qq * len, l1 = min(l0 + len, bs);
+    double s0 = 0.0, s1 = 0.0;
+    int l = l0;
+    for (; l + 1 < l1; l += 2) {
+      s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+      s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
+    }
+    if (l < l1) s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
+    double sum = s0 + s1;
+    for (int o2 = 1; o2 < Q; o2 <<= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o2);
+    if (qq == 0 && i < bs) ys[i][c] = sum;
+  }
+  __syncthreads();
+  double* box = bx.ybox + (static_cast<int64_t>(pass) * bx.nbmax + blk) * TB * MAXR;
+  for (int e = t; e < bs * R; e += NT) {
+    const int i = e / R, c = e % R;
+    q.d[static_cast<int64_t>(b0 + i) * R + c] = ys[i][c];
+    if (BGM_GROUP > 1) box[e] = ys[i][c];
+  }
+  if (BGM_GROUP > 1) {
+    __syncthreads();
+    if (t == 0) {
+      __threadfence();
+      st_release_u64(bx.yseq + pass * bx.nbmax + blk, tok);
+    }
+  }
+  __syncthreads();
+}
+
 // d <- U^-1 L^-1 P r on rows [lo, hi) of one system, shared by the group:
 // the owner of each 64-row block applies its inverse and hands the block's
 // result to the others through the mailbox (tagged with the solve number
 // sv); every rank updates its own rows below (L) or above (U) the block.
-// r is read from L2 (its rows come from the whole group).
+// One block of look-ahead: a rank that owns the next block in solve order
+// first updates that block's rows, applies its inverse and publishes it,
+// and only then updates its other rows, so the chain from one block's
+// result to the next block's result holds one 64-row update, not all of
+// them.  r is read from L2 (its rows come from the whole group).
 __device__ bool bgm_solve(const BatchIr& q, const BgmBox& bx, int rank, int nbr, int lo, int hi,
                           unsigned long long& sv, int* err, volatile int* fail) {
-  __shared__ double y[TB][MAXR + 1];
+  __shared__ double ybuf[2][TB][MAXR + 1];
   const int n = q.n, R = q.nrhs, t = threadIdx.x, NT = blockDim.x;
   for (int e = t; e < (hi - lo) * R; e += NT) {
     const int i = lo + e / R, c = e % R;
@@ -2176,57 +2238,40 @@ __device__ bool bgm_solve(const BatchIr& q, const BgmBox& bx, int rank, int nbr,
   __syncthreads();
   const unsigned long long tok = ++sv;
   const int nblk = (n + TB - 1) / TB;
-  int Q = 8;  // as in bir_solve_body
-  while (Q > 1 && TB * R * Q > NT) Q >>= 1;
-  const int len = TB / Q;
+  auto owner_of = [&](int blk) { return min(BGM_GROUP - 1, blk / nbr); };
   for (int pass = 0; pass < 2; ++pass) {
     const bool lower = pass == 0;
+    int cur = 0;  // ybuf[cur] holds the current block's result once known here
+    const int first = lower ? 0 : nblk - 1;
+    if (owner_of(first) == rank) bgm_block_inverse(q, bx, pass, first, tok, ybuf[cur]);
     for (int bb = 0; bb < nblk; ++bb) {
       const int blk = lower ? bb : nblk - 1 - bb;
       const int b0 = blk * TB, bs = min(TB, n - b0);
-      const int owner = min(BGM_GROUP - 1, blk / nbr);
-      if (owner == rank) {
-        const double* D = (lower ? q.Linv : q.Uinv) + static_cast<int64_t>(blk) * TB * TB;
-        for (int e = t; e < TB * R * Q; e += NT) {
-          const int o = e / Q, qq = e - o * Q;
-          const int i = o / R, c = o - i * R;
-          const int l0 = qq * len, l1 = min(l0 + len, bs);
-          double s0 = 0.0, s1 = 0.0;
-          int l = l0;
-          for (; l + 1 < l1; l += 2) {
-            s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
-            s1 = fma(D[i * TB + l + 1], q.d[static_cast<int64_t>(b0 + l + 1) * R + c], s1);
-          }
-          if (l < l1) s0 = fma(D[i * TB + l], q.d[static_cast<int64_t>(b0 + l) * R + c], s0);
-          double sum = s0 + s1;
-          for (int o2 = 1; o2 < Q; o2 <<= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o2);
-          if (qq == 0 && i < bs) y[i][c] = sum;
-        }
-        __syncthreads();
-        double* box = bx.ybox + (static_cast<int64_t>(pass) * bx.nbmax + blk) * TB * MAXR;
-        for (int e = t; e < bs * R; e += NT) {
-          const int i = e / R, c = e % R;
-          q.d[static_cast<int64_t>(b0 + i) * R + c] = y[i][c];
-          if (BGM_GROUP > 1) box[e] = y[i][c];
-        }
-        if (BGM_GROUP > 1) {
-          __syncthreads();
-          if (t == 0) {
-            __threadfence();
-            st_release_u64(bx.yseq + pass * bx.nbmax + blk, tok);
-          }
-        }
-      } else {
+      if (owner_of(blk) != rank) {  // the block's result from its owner
         if (t == 0 && !*fail && !group_wait(bx.yseq + pass * bx.nbmax + blk, tok, err)) *fail = 1;
         __syncthreads();
         if (*fail) return false;
         const double* box = bx.ybox + (static_cast<int64_t>(pass) * bx.nbmax + blk) * TB * MAXR;
-        for (int e = t; e < bs * R; e += NT) y[e / R][e % R] = __ldcg(box + e);
+        for (int e = t; e < bs * R; e += NT) ybuf[cur][e / R][e % R] = __ldcg(box + e);
         __syncthreads();
       }
-      const int rs = max(lower ? b0 + bs : 0, lo), re = min(lower ? n : b0, hi);
+      const double (*y)[MAXR + 1] = ybuf[cur];
+      // rows this rank still updates with this block: below (L) or above (U)
+      int rs = max(lower ? b0 + bs : 0, lo), re = min(lower ? n : b0, hi);
+      const int nxt = lower ? blk + 1 : blk - 1;
+      if (nxt >= 0 && nxt < nblk && owner_of(nxt) == rank) {  // look-ahead
+        const int n0 = nxt * TB, ns = min(TB, n - n0);
+        block_row_update(q, y, b0, bs, n0, n0 + ns);
+        __syncthreads();
+        bgm_block_inverse(q, bx, pass, nxt, tok, ybuf[cur ^ 1]);
+        if (lower)
+          rs = max(rs, n0 + ns);
+        else
+          re = min(re, n0);
+      }
       block_row_update(q, y, b0, bs, rs, re);
       __syncthreads();
+      cur ^= 1;
     }
   }
   return true;

@@ -1532,18 +1532,34 @@ __global__ void __launch_bounds__(BIR_THREADS) bir_first_solve_kernel(const Batc
 __device__ double bir_matvec(const float* __restrict__ A, int n, int R, const double* x,
                              const double* __restrict__ b, double* out, double* red,
                              bool want_max) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // eight lanes a row, four rows a warp at a time: each lane takes every
+  // eighth column (two independent partial sums), three shuffle levels add
+  // the eight lanes' sums (a warp a row spent five levels of FP64 adds on
+  // each row's sixteen FMAs a lane at n = 512)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane >> 3, sub = lane & 7;
   double rm = 0.0;
-  for (int i = wid; i < n; i += static_cast<int>(blockDim.x >> 5)) {
-    const float* a = A + static_cast<int64_t>(i) * n;
+  for (int i0 = wid * 4; i0 < n; i0 += nw * 4) {
+    const int i = i0 + g;
+    const bool ok = i < n;
+    const float* a = A + static_cast<int64_t>(ok ? i : i0) * n;
     for (int c = 0; c < R; ++c) {
-      double sum = 0.0;
-      for (int l = lane; l < n; l += 32) sum = fma(widen(a[l]), x[static_cast<int64_t>(l) * R + c], sum);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-      const double v = b ? b[static_cast<int64_t>(i) * R + c] - sum : sum;
-      if (lane == 0) out[static_cast<int64_t>(i) * R + c] = v;
-      rm = fmax(rm, fabs(v));
+      double s0 = 0.0, s1 = 0.0;
+      int l = sub;
+      for (; l + 8 < n; l += 16) {
+        s0 = fma(widen(a[l]), x[static_cast<int64_t>(l) * R + c], s0);
+        s1 = fma(widen(a[l + 8]), x[static_cast<int64_t>(l + 8) * R + c], s1);
+      }
+      if (l < n) s0 = fma(widen(a[l]), x[static_cast<int64_t>(l) * R + c], s0);
+      double sum = s0 + s1;
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 4);
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 2);
+      sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+      if (ok && sub == 0) {
+        const double v = b ? b[static_cast<int64_t>(i) * R + c] - sum : sum;
+        out[static_cast<int64_t>(i) * R + c] = v;
+        rm = fmax(rm, fabs(v));
+      }
     }
   }
   return want_max ? block_max(rm, red) : 0.0;

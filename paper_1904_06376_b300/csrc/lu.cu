@@ -1030,7 +1030,7 @@ __device__ __forceinline__ void get_row(float* v, const float* src) {
 
 // One pivot column of the cluster panel; K = the column's register (the
 // current rotation puts column g*8 + K there), JB the block-column width.
-template <int NB, int K>
+template <int NB, int K, bool LOCAL>
 __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int n, int J0, int r,
                                              bool has, int t, int lane, int wid, int nw, int cr,
                                              int cs, PanelShared<NB>& sh, int* err,
@@ -1038,7 +1038,7 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
   constexpr int NQ = NB / 4;
   const int j = J0 + jj, bf = jj & 1;
   const int g8 = jj - K;  // columns rotated away so far
-  const bool local = cs == 1;
+  constexpr bool local = LOCAL;  // one CTA (cs == 1): no cluster exchange
   ClusterSlot<NB>& sl = sh.slot[bf];
   // ---- 1. offers: every warp's winner posts its row, the holder of row j posts row j
   const bool offers = has && r >= j;
@@ -1050,11 +1050,25 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
     sh.wkey[bf][wid] = wk;
     sh.widx[bf][wid] = wi;
   }
-  if (lane == wl && offers) put_row<NQ>(sh.wrow[bf][wid], v);
-  if (cr == 0 && t == jj) put_row<NQ>(sh.rowj[bf], v);  // row j: CTA 0, thread jj
-  __syncthreads();
+  if (local) {
+    // one CTA: only the CTA's winner stores its row, straight into the
+    // slot, once every warp has found it; the holder of row j stores row j
+    // there too
+    if (cr == 0 && t == jj) put_row<NQ>(sl.rowj, v);
+    __syncthreads();
+    uint32_t ck, ci;
+    int cw;
+    warp_offer(lane < nw ? sh.wkey[bf][lane] : 0u, lane < nw ? sh.widx[bf][lane] : 0xFFFFFFFFu,
+               &ck, &ci, &cw);
+    if (offers && static_cast<uint32_t>(r) == ci) put_row<NQ>(sl.row[0], v);
+    if (t == 0) sl.ki[0] = make_uint2(ck, ci);
+  } else {
+    if (lane == wl && offers) put_row<NQ>(sh.wrow[bf][wid], v);
+    if (cr == 0 && t == jj) put_row<NQ>(sh.rowj[bf], v);  // row j: CTA 0, thread jj
+    __syncthreads();
+  }
   // ---- 2. pushes: the pushing warps reduce the warps' offers themselves
-  const int npush = cs * NQ;
+  const int npush = local ? 0 : cs * NQ;
   if (!local && t == 0) mbar_arrive_expect_tx(&sh.bar[bf], slot_bytes<NB>(cs, cr));
   if (wid * 32 < npush) {  // whole warps: the reductions need every lane
     uint32_t ck, ci;
@@ -1130,7 +1144,7 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
   }
 }
 
-template <int NB>
+template <int NB, bool LOCAL>
 __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
                                            int32_t* __restrict__ ipiv, int32_t* __restrict__ info,
                                            int* __restrict__ err) {
@@ -1172,7 +1186,7 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
   for (int g = 0; g < NB; g += 8) {
 #define BFX_PANEL_COL(K)                                                                      \
   if (g + K < JB)                                                                             \
-    panel_column<NB, K>(v, g + K, JB, n, J0, r, has, t, lane, wid, nw, cr, cs, sh, err,       \
+    panel_column<NB, K, LOCAL>(v, g + K, JB, n, J0, r, has, t, lane, wid, nw, cr, cs, sh, err,\
                         &expired);
     BFX_PANEL_COL(0)
     BFX_PANEL_COL(1)
@@ -1208,24 +1222,25 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
   cl_sync();  // every CTA has received all it waits for before any leaves
 }
 
-template <int NB>
+// LOCAL: launched as one CTA (a cluster of one)
+template <int NB, bool LOCAL>
 __global__ void __launch_bounds__(CLP_THREADS, 1)
     lu_panel_cluster_kernel(float* __restrict__ A, int64_t lda, int n, int J0, int JB,
                             int32_t* __restrict__ ipiv, int32_t* __restrict__ info,
                             int* __restrict__ err) {
-  panel_body<NB>(A, lda, n, J0, JB, ipiv, info, err);
+  panel_body<NB, LOCAL>(A, lda, n, J0, JB, ipiv, info, err);
 }
 
 // Batched form: cluster c (of the grid's clusters) factors block column J0
 // of system sys[c]; a system whose n <= J0 has no work (the whole cluster
 // leaves together).
-template <int NB>
+template <int NB, bool LOCAL>
 __global__ void __launch_bounds__(CLP_THREADS, 1)
     lu_panel_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0, int* __restrict__ err) {
   const BatchLu b = sys[blockIdx.x / cl_size()];
   const int JB = min(nb, b.n - J0);
   if (JB <= 0) return;
-  panel_body<NB>(b.A, b.n, b.n, J0, JB, b.ipiv, b.info, err);
+  panel_body<NB, LOCAL>(b.A, b.n, b.n, J0, JB, b.ipiv, b.info, err);
 }
 
 // Launch the cluster panel for the block column [J0, J0+JB) if it fits
@@ -1255,11 +1270,9 @@ bool launch_panel_cluster(float* A, int64_t lda, int n, int J0, int JB, int32_t*
     *st = BFX_ECUDA;
     return false;
   }
-  const cudaError_t e =
-      JB <= 32 ? cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<32>, A, lda, n, J0, JB, ipiv, info,
-                                    err)
-               : cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<64>, A, lda, n, J0, JB, ipiv, info,
-                                    err);
+  auto kern = JB <= 32 ? (cs == 1 ? lu_panel_cluster_kernel<32, true> : lu_panel_cluster_kernel<32, false>)
+                       : (cs == 1 ? lu_panel_cluster_kernel<64, true> : lu_panel_cluster_kernel<64, false>);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, n, J0, JB, ipiv, info, err);
   if (e != cudaSuccess) {  // e.g. a cluster size the device does not offer: use the tiles
     cudaGetLastError();
     return false;
@@ -1484,11 +1497,9 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
       cfg.stream = s;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      const cudaError_t e = nb <= 32
-                                ? cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<32>, d_sys, nb, J0,
-                                                     device_error_word())
-                                : cudaLaunchKernelEx(&cfg, lu_panel_batched_kernel<64>, d_sys, nb, J0,
-                                                     device_error_word());
+      auto kern = nb <= 32 ? (cs == 1 ? lu_panel_batched_kernel<32, true> : lu_panel_batched_kernel<32, false>)
+                           : (cs == 1 ? lu_panel_batched_kernel<64, true> : lu_panel_batched_kernel<64, false>);
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, d_sys, nb, J0, device_error_word());
       if (e == cudaSuccess)
         paneled = true;
       else

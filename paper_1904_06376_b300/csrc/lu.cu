@@ -1063,8 +1063,14 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
     if (offers && static_cast<uint32_t>(r) == ci) put_row<NQ>(sl.row[0], v);
     if (t == 0) sl.ki[0] = make_uint2(ck, ci);
   } else {
-    if (lane == wl && offers) put_row<NQ>(sh.wrow[bf][wid], v);
+    // only the CTA's winner stores its row, once every warp has found it
     if (cr == 0 && t == jj) put_row<NQ>(sh.rowj[bf], v);  // row j: CTA 0, thread jj
+    __syncthreads();
+    uint32_t ck, ci;
+    int cw;
+    warp_offer(lane < nw ? sh.wkey[bf][lane] : 0u, lane < nw ? sh.widx[bf][lane] : 0xFFFFFFFFu,
+               &ck, &ci, &cw);
+    if (offers && static_cast<uint32_t>(r) == ci) put_row<NQ>(sh.wrow[bf][0], v);
     __syncthreads();
   }
   // ---- 2. pushes: the pushing warps reduce the warps' offers themselves
@@ -1078,7 +1084,7 @@ __device__ __forceinline__ void panel_column(float (&v)[NB], int jj, int JB, int
     cw = min(cw, nw - 1);  // every CTA offers a row (its rows are >= j)
     if (t < npush) {
       const int dst = t / NQ, q = t % NQ;
-      const float4 x = *reinterpret_cast<const float4*>(&sh.wrow[bf][cw][4 * q]);
+      const float4 x = *reinterpret_cast<const float4*>(&sh.wrow[bf][0][4 * q]);
       float4* to = reinterpret_cast<float4*>(&sl.row[cr][4 * q]);
       if (dst == cr) {  // this CTA's own slot: plain stores, then an arrival
         *to = x;

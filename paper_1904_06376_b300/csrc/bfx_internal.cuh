@@ -140,10 +140,11 @@ bfx_status ir_batched_gmres(const BatchIr* d_ir, int S, int* d_queue, double* d_
                             int max_outer, double tau, cudaStream_t s);
 int64_t batched_gmres_slot_doubles(int m, int nmax, int R);
 // tcgen05 GEMM on pieces (gemm_tc.cu)
+// pdl: launch as a programmatic dependent of the previous kernel on s
 bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,
                                 const uint16_t* Btp, int64_t ldb_p, int64_t b_plane, float beta,
-                                float* C, int64_t ldc, cudaStream_t s);
+                                float* C, int64_t ldc, cudaStream_t s, bool pdl = false);
 // FP64 collection of the mode's partial products (Sec. IV-A "d"); same piece
 // layout as launch_gemm_presplit, C is FP64.
 bfx_status launch_gemm_f64(bfx_mode mode, int64_t m, int64_t n, int64_t k, const uint16_t* Ap,

@@ -405,6 +405,9 @@ __global__ void __launch_bounds__(TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>
   using Cfg = TcConfig<MODE, BN, BK, STAGES, FUSED, D64, CH>;
   static_assert(!(D64 && GROUPED), "FP64 collection: single problem");
   constexpr uint32_t IDESC = idesc_bf16_f32<BM, BN>();
+  // launched as a programmatic dependent of the previous kernel (the LU's
+  // next-column update): wait for it to complete; a no-op otherwise
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_addr(smem_raw);
@@ -936,7 +939,7 @@ bool make_piece_map(CUtensorMap* map, const uint16_t* base, int64_t inner, int64
 template <int MODE, int BN, int BK, int STAGES, bool D64 = false, int CH = 0>
 bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* Ap, int64_t lda_p,
                   int64_t a_plane, const uint16_t* Btp, int64_t ldb_p, int64_t b_plane,
-                  float beta, void* C, int64_t ldc, cudaStream_t s) {
+                  float beta, void* C, int64_t ldc, cudaStream_t s, bool pdl = false) {
   using Cfg = TcConfig<MODE, BN, BK, STAGES, false, D64, CH>;
   // with a single piece only plane 0 is read; any legal plane stride will do
   if (Cfg::NPA == 1) a_plane = round_up(lda_p * m, 8);
@@ -970,6 +973,20 @@ bfx_status run_tc(int64_t m, int64_t n, int64_t k, float alpha, const uint16_t* 
     return BFX_ECUDA;
   const int sms = current_num_sms();
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+  if (pdl) {  // may start while the previous kernel on s finishes (the kernel waits for it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(Cfg::THREADS);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, ma, mb, a) != cudaSuccess) return BFX_ECUDA;
+    return BFX_OK;
+  }
   kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(ma, mb, a);
   return last_launch_status();
 }
@@ -1140,7 +1157,7 @@ bfx_status launch_gemm_fused(bfx_mode mode, int64_t m, int64_t n, int64_t k, flo
 bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, float alpha,
                                 const uint16_t* Ap, int64_t lda_p, int64_t a_plane,
                                 const uint16_t* Btp, int64_t ldb_p, int64_t b_plane, float beta,
-                                float* C, int64_t ldc, cudaStream_t s) {
+                                float* C, int64_t ldc, cudaStream_t s, bool pdl) {
   if (m == 0 || n == 0) return BFX_OK;
   if (k == 0) return launch_scale(m, n, beta, C, ldc, s);
   if (k > kChunkMinK) {
@@ -1150,13 +1167,13 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
     switch (mode) {
       case BFX_X6:
         return run_tc<6, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
-                                                          ldb_p, b_plane, beta, C, ldc, s);
+                                                          ldb_p, b_plane, beta, C, ldc, s, pdl);
       case BFX_X8:
         return run_tc<8, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
-                                                          ldb_p, b_plane, beta, C, ldc, s);
+                                                          ldb_p, b_plane, beta, C, ldc, s, pdl);
       case BFX_X9:
         return run_tc<9, 256, 32, 3, false, kChunkK / 32>(m, n, k, alpha, Ap, lda_p, a_plane, Btp,
-                                                          ldb_p, b_plane, beta, C, ldc, s);
+                                                          ldb_p, b_plane, beta, C, ldc, s, pdl);
       default:
         break;
     }
@@ -1164,22 +1181,22 @@ bfx_status launch_gemm_presplit(bfx_mode mode, int64_t m, int64_t n, int64_t k, 
   switch (mode) {
     case BFX_X1:
       return run_tc<1, 256, 64, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     case BFX_X3:
       return run_tc<3, 256, 32, 4>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     case BFX_X5:
       return run_tc<5, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     case BFX_X6:
       return run_tc<6, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     case BFX_X8:
       return run_tc<8, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     case BFX_X9:
       return run_tc<9, 256, 32, 3>(m, n, k, alpha, Ap, lda_p, a_plane, Btp, ldb_p, b_plane, beta,
-                                   C, ldc, s);
+                                   C, ldc, s, pdl);
     default:
       return BFX_EINVAL;
   }

@@ -1163,6 +1163,9 @@ __device__ __forceinline__ void panel_body(float* __restrict__ A, int64_t lda, i
   static_assert(2 * CLP_MAX_CL * NQ <= CLP_THREADS, "pushes of the offered row and of row j");
   static_assert(NB % 8 == 0, "columns go in groups of 8");
   __shared__ __align__(16) PanelShared<NB> sh;
+  // launched as a programmatic dependent of the previous block column's
+  // update: wait for it before reading the block column (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   const int cr = static_cast<int>(cl_rank()), cs = static_cast<int>(cl_size());
   const int r = J0 + cr * CLP_THREADS + t;  // this thread's row
@@ -1264,17 +1267,19 @@ bool launch_panel_cluster(float* A, int64_t lda, int n, int J0, int JB, int32_t*
   if (JB > 64 || cs > kPanelMaxCluster) return false;
   const int threads = cs == 1 ? static_cast<int>(round_up(rows, 32)) : CLP_THREADS;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = static_cast<unsigned>(cs);
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // the kernel waits itself
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.gridDim = dim3(static_cast<unsigned>(cs), 1, 1);
   cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   int* err = device_error_word();
   if (!err) {
     *st = BFX_ECUDA;
@@ -1309,6 +1314,10 @@ LuWs lu_ws(int np, int64_t n, int nb) {
 }
 
 }  // namespace
+
+// split.cu: launch_split as a programmatic dependent of the previous kernel
+bfx_status launch_split_pdl(int64_t rows, int64_t cols, const float* x, int64_t ldx, int npieces,
+                            uint16_t* hi, uint16_t* mid, uint16_t* lo, int64_t ldp, cudaStream_t s);
 
 bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, int32_t* ipiv,
                      int32_t* info, void* ws, size_t ws_bytes, cudaStream_t s, int32_t* perm) {
@@ -1388,7 +1397,8 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
   // C[:, c0 .. c0+nc) -= L21 U12[:, c0 .. c0+nc) for block column j0 on stream st
   // (pieces: L21's in Lp, split after the panel; U12^T's written by the
   // block solve)
-  auto update = [&](int j0, int jb, int c0, int nc, const uint16_t* Lp, cudaStream_t st) -> bfx_status {
+  auto update = [&](int j0, int jb, int c0, int nc, const uint16_t* Lp, cudaStream_t st,
+                    bool pdl) -> bfx_status {
     const int nr = N - j0 - jb;
     float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
     float* U12 = A + static_cast<int64_t>(j0) * lda + j0 + jb + c0;
@@ -1396,7 +1406,7 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     if (np == 0) return launch_sgemm_simt(nr, nc, jb, -1.0f, L21, lda, U12, lda, 1.0f, A22, lda, st);
     const uint16_t* Uc = Up + static_cast<int64_t>(c0) * w.kp;  // rows c0.. of the U12^T planes
     return launch_gemm_presplit(mode, nr, nc, jb, -1.0f, Lp, w.kp, w.ap, Uc, w.kp, w.bp, 1.0f, A22,
-                                lda, st);
+                                lda, st, pdl);
   };
   for (int j0 = 0, blk = 0; j0 < N; j0 += nb, ++blk) {
     const int jb = (N - j0 < nb) ? N - j0 : nb;
@@ -1432,8 +1442,8 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     // still read the other), before waiting for that update
     if (np > 0 && nr > 0) {
       const float* L21 = A + static_cast<int64_t>(j0 + jb) * lda + j0;
-      const bfx_status e = launch_split(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
-                                        np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, s);
+      const bfx_status e = launch_split_pdl(nr, jb, L21, lda, np, Lp, np > 1 ? Lp + w.ap : nullptr,
+                                            np > 2 ? Lp + 2 * w.ap : nullptr, w.kp, s);
       if (e != BFX_OK) return e;
     }
     // the row swaps move rows of columns the previous rest update writes
@@ -1444,7 +1454,7 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     if (nc > 0) {
       solve<<<static_cast<unsigned>(ceil_div(nc, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, s>>>(
           A, lda, j0, jb, j0 + jb, j0 + jb + nc, ipiv, np, Up, w.bp, w.kp);
-      const bfx_status st = update(j0, jb, 0, nc, Lp, s);
+      const bfx_status st = update(j0, jb, 0, nc, Lp, s, true);
       if (st != BFX_OK) return st;
     }
     // the rest on the auxiliary stream, after the L21 pieces: the row swaps
@@ -1452,6 +1462,9 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
     // columns right of the next one, and their update
     const int c_far = j0 + jb + nc, n_far = N - c_far;
     if (j0 + n_far > 0 || perm) {
+      // (forked after the next column's update: started earlier, the rest
+      // competed with that critical work for the SMs: n = 4096 LU 8.10 ->
+      // 8.48 ms)
       if (cudaEventRecord(ev_fork, s) != cudaSuccess ||
           cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
         return BFX_ECUDA;
@@ -1461,7 +1474,7 @@ bfx_status lu_factor(bfx_mode mode, int64_t n, int nb, float* A, int64_t lda, in
       if (n_far > 0) {
         solve<<<static_cast<unsigned>(ceil_div(n_far, TRSM_COLS)), TRSM_COLS * 32, trsm_smem, aux>>>(
             A, lda, j0, jb, c_far, N, ipiv, np, Up, w.bp, w.kp);
-        const bfx_status st = update(j0, jb, nc, n_far, Lp, aux);
+        const bfx_status st = update(j0, jb, nc, n_far, Lp, aux, false);
         if (st != BFX_OK) return st;
       }
       if (cudaEventRecord(ev_rest, aux) != cudaSuccess) return BFX_ECUDA;

@@ -68,6 +68,9 @@ __global__ void __launch_bounds__(256) split_vec8_kernel(const float* __restrict
                                                          uint16_t* __restrict__ p0,
                                                          uint16_t* __restrict__ p1,
                                                          uint16_t* __restrict__ p2, int64_t ldp) {
+  // launched as a programmatic dependent (the LU's L21 pieces after the
+  // panel): wait for the previous kernel; a no-op otherwise
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t total = rows * cols8;
   for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < total;
        v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -272,6 +275,31 @@ bfx_status launch_split(int64_t rows, int64_t cols, const float* x, int64_t ldx,
   }
   return last_launch_status();
 }
+
+// launch_split as a programmatic dependent of the previous kernel on s when
+// the 8-wide form applies (the LU's L21 pieces), else launch_split
+bfx_status launch_split_pdl(int64_t rows, int64_t cols, const float* x, int64_t ldx, int npieces,
+                            uint16_t* hi, uint16_t* mid, uint16_t* lo, int64_t ldp, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return BFX_OK;
+  const bool vec = (cols % 8 == 0) && (ldx % 4 == 0) && (ldp % 8 == 0) && aligned(x, 16) &&
+                   aligned(hi, 16) && (npieces < 2 || aligned(mid, 16)) &&
+                   (npieces < 3 || aligned(lo, 16)) && !(ldx == cols && ldp == cols);
+  if (!vec) return launch_split(rows, cols, x, ldx, npieces, hi, mid, lo, ldp, s);
+  const int64_t cols8 = cols / 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid_for(rows * cols8, 256)));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  auto kern = npieces == 1 ? split_vec8_kernel<1> : (npieces == 2 ? split_vec8_kernel<2> : split_vec8_kernel<3>);
+  return cudaLaunchKernelEx(&cfg, kern, x, ldx, rows, cols8, hi, mid, lo, ldp) == cudaSuccess ? BFX_OK
+                                                                                              : BFX_ECUDA;
+}
+
 
 bfx_status launch_split_transpose(int64_t rows, int64_t cols, const float* x, int64_t ldx,
                                   int npieces, uint16_t* hi, uint16_t* mid, uint16_t* lo,

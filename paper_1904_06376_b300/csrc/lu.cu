@@ -697,18 +697,62 @@ __device__ __forceinline__ void solve_col(float* __restrict__ col, int64_t lda, 
   }
 }
 
+// Batched block solve: TRSM_WCOLS adjacent columns a warp, solved together
+// (independent FMA chains, each L11 element read once for all of them; per
+// element the FMA sequence of solve_col), so that a CTA stages L11 once for
+// TRSM_COLS * TRSM_WCOLS columns.  Columns c_begin + (cb * TRSM_COLS + warp)
+// * TRSM_WCOLS + j below c_end of the block row j0.
+constexpr int TRSM_WCOLS = 4;
 template <int NB>
-// Columns c_begin + cb * TRSM_COLS + (warp) below c_end of the block row j0.
-__device__ __forceinline__ void trsm_body(float* __restrict__ A, int64_t lda, int c_end, int j0,
-                                          int jb, int c_begin, int cb) {
+__device__ __forceinline__ void trsm_wide_body(float* __restrict__ A, int64_t lda, int c_end,
+                                               int j0, int jb, int c_begin, int cb) {
   extern __shared__ float L11[];
+  constexpr int RPL = NB / 32;  // rows a lane
+  constexpr int LS = trsm_lds(NB);
   load_l11<NB>(A, lda, j0, jb, L11);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t c = c_begin + cb * static_cast<int64_t>(TRSM_COLS) + w;
-  if (c >= c_end) return;
-  float x[NB / 32];
-  solve_col<NB>(A + static_cast<int64_t>(j0) * lda + c, lda, jb, L11, lane, x);
+  const int64_t c0 = c_begin + (static_cast<int64_t>(cb) * TRSM_COLS + w) * TRSM_WCOLS;
+  if (c0 >= c_end) return;
+  float* col = A + static_cast<int64_t>(j0) * lda + c0;
+  float x[TRSM_WCOLS][RPL];
+#pragma unroll
+  for (int j = 0; j < TRSM_WCOLS; ++j) {
+    const bool on = c0 + j < c_end;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int i = lane + 32 * q;
+      x[j][q] = (on && i < jb) ? col[static_cast<int64_t>(i) * lda + j] : 0.0f;
+    }
+  }
+#pragma unroll
+  for (int q0 = 0; q0 < RPL; ++q0) {
+    for (int ll = 0; ll < 32; ++ll) {
+      const int l = 32 * q0 + ll;
+      if (l >= jb - 1) break;
+      float xl[TRSM_WCOLS];
+#pragma unroll
+      for (int j = 0; j < TRSM_WCOLS; ++j) xl[j] = __shfl_sync(0xFFFFFFFFu, x[j][q0], ll);
+#pragma unroll
+      for (int q = q0; q < RPL; ++q) {
+        const int i = lane + 32 * q;
+        if (i > l && i < jb) {
+          const float lil = L11[i * LS + l];
+#pragma unroll
+          for (int j = 0; j < TRSM_WCOLS; ++j) x[j][q] = fmaf(-lil, xl[j], x[j][q]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < TRSM_WCOLS; ++j) {
+    if (c0 + j >= c_end) break;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int i = lane + 32 * q;
+      if (i >= 1 && i < jb) col[static_cast<int64_t>(i) * lda + j] = x[j][q];
+    }
+  }
 }
 
 // Single system: columns [c_begin, c_end) of block row j0 (one warp a
@@ -807,8 +851,8 @@ __global__ void __launch_bounds__(TRSM_COLS * 32)
     lu_trsm_batched_kernel(const BatchLu* __restrict__ sys, int nb, int J0) {
   const BatchLu b = sys[blockIdx.y];
   const int JB = min(nb, b.n - J0);
-  if (JB <= 0 || J0 + JB + static_cast<int>(blockIdx.x) * TRSM_COLS >= b.n) return;
-  trsm_body<NB>(b.A, b.n, b.n, J0, JB, J0 + JB, blockIdx.x);
+  if (JB <= 0 || J0 + JB + static_cast<int>(blockIdx.x) * TRSM_COLS * TRSM_WCOLS >= b.n) return;
+  trsm_wide_body<NB>(b.A, b.n, b.n, J0, JB, J0 + JB, blockIdx.x);
 }
 
 // Pieces of L21 (rows below the block, block columns) and of U12^T for the
@@ -1573,7 +1617,7 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
   lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_THREADS, 0, s>>>(d_sys, nb, J0);
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
   const size_t tsmem = trsm_smem_bytes(tnb);
-  const unsigned tblk = static_cast<unsigned>(ceil_div(nmax, TRSM_COLS));
+  const unsigned tblk = static_cast<unsigned>(ceil_div(nmax - J0, TRSM_COLS * TRSM_WCOLS));
   if (tnb == 32)
     lu_trsm_batched_kernel<32><<<dim3(tblk, S_act), TRSM_COLS * 32, tsmem, s>>>(d_sys, nb, J0);
   else if (tnb == 64)

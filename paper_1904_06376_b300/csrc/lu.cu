@@ -1612,8 +1612,11 @@ bfx_status lu_batched_block(bfx_mode mode, const BatchLu* d_sys, const int* h_n_
     const unsigned gx = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), 32)));
     lu_tile_update_batched_kernel<<<dim3(gx, S_t), 256, 0, s>>>(d_sys, nb, J0, j0);
   }
-  // a CTA forms a system's swap set once and moves up to four column blocks
-  const unsigned cblk = static_cast<unsigned>(ceil_div(ceil_div(nmax, LASWP_COLS), 4));
+  // a CTA forms a system's swap set once and moves up to sixteen column
+  // blocks (one CTA a system up to n = 512: the serial swap-set build,
+  // repeated by every CTA of a system, cost more than the CTAs' parallelism
+  // gained; four blocks a CTA: +0.3 ms a batch of 2000 systems)
+  const unsigned cblk = static_cast<unsigned>(ceil_div(ceil_div(nmax, LASWP_COLS), 16));
   lu_laswp_batched_kernel<<<dim3(cblk, S_act), LASWP_THREADS, 0, s>>>(d_sys, nb, J0);
   const int tnb = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
   const size_t tsmem = trsm_smem_bytes(tnb);

@@ -1587,7 +1587,7 @@ __global__ void __launch_bounds__(LAT ? BIR_LAT_THREADS : BIR_THREADS)
   __syncthreads();
   bir_solve_body<LAT>(q);
   double dm = 0.0, xm = 0.0;
-  for (int e = threadIdx.x; e < q.n * q.nrhs; e += BIR_THREADS) {
+  for (int e = threadIdx.x; e < q.n * q.nrhs; e += static_cast<int>(blockDim.x)) {
     const double xv = q.x[e] + q.d[e];
     q.x[e] = xv;
     dm = fmax(dm, fabs(q.d[e]));

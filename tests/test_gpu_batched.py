@@ -161,3 +161,34 @@ def test_batched_gmres_multiple_rhs(bfx, orc):
         fe = np.max(np.abs(xb - p.x_true)) / np.max(np.abs(p.x_true))
         fe64 = np.max(np.abs(xd - p.x_true)) / np.max(np.abs(p.x_true))
         assert fe <= 10 * fe64 + 1e-15
+
+
+def test_batched_late_steps_large_systems(bfx, orc):
+    """Systems of more than 512 unknowns that need more than five refinement
+    steps run the later steps in the 1024-thread latency form, where every
+    element of x must receive its correction exactly once: results agree
+    with the single-system path and repeat bit for bit."""
+    ns = [600, 1000, 130, 777]
+    probs = _make(ns, [1e4, 1e4, 1e2, 3e4], 1300)
+    B = bfx.Batch(3, ns, max_iter=30, gmres=0)
+    A, b = B.pack([p.A32 for p in probs], [p.b for p in probs])
+    x1, st1 = B.solve(A, b)
+    torch.cuda.synchronize()
+    x1 = x1.clone()
+    conv, iters, info, berr = B.decode_status(st1)
+    assert conv.all() and (info == 0).all(), (conv, iters, berr)
+    big = np.array([n > 512 for n in ns])
+    assert (iters[big] > 5).all(), iters  # the latency form ran on them
+    x2, st2 = B.solve(A, b)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    for p, xb in zip(probs, B.unpack(x1)):
+        xd, _ = orc.dgesv(p.A32, p.b)
+        fe = np.max(np.abs(xb - p.x_true)) / np.max(np.abs(p.x_true))
+        fe64 = np.max(np.abs(xd - p.x_true)) / np.max(np.abs(p.x_true))
+        assert fe <= 10 * fe64 + 1e-15, (p.n, fe, fe64)
+        xs1, res, code = bfx.solve_ir(3, torch.from_numpy(p.A32).cuda(),
+                                      torch.from_numpy(p.b).cuda(), escalate=False)
+        assert code == 0
+        scale = np.max(np.abs(xs1.cpu().numpy()))
+        assert np.max(np.abs(xb - xs1.cpu().numpy())) <= 100 * p.kappa_nominal * 2.0 ** -53 * scale * p.n

@@ -24,7 +24,9 @@ constexpr int kBatchMaxN = 1024;  // largest system of a batch
 constexpr int kSolveTB = 64;      // diagonal-block size of the refinement solves
 constexpr int kGmresM = 256;      // Krylov length of the batched GMRES-IR (capped at n)
 // refinement steps from this one on use the latency form (most systems have
-// stopped by then: a step lasts as long as its slowest system's)
+// stopped by then: a step lasts as long as its slowest system's); on a batch
+// of 2000 systems up to n = 512, switching at steps 4, 5 or 6 measured the
+// same within 0.1 ms, at step 3 0.9 ms slower
 constexpr int kLatencyStep = 5;
 constexpr int kGmresOuter = 20;   // its refinement steps at most
 constexpr double kGmresTau = 1e-10;
